@@ -1,0 +1,490 @@
+/*
+ * CPU oracle (test infrastructure only; see oracle.h).  Plain C,
+ * single-threaded, integer arithmetic for every plane, FP64 for features.
+ * Each function states the passage of the paper it follows and the reading
+ * taken where the paper is silent.
+ */
+#include "oracle.h"
+
+#include <limits.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------ */
+/* Colour deconvolution (Sec. V-A, feature-stage transforms)          */
+/* ------------------------------------------------------------------ */
+
+static void normalize3(double v[3]) {
+    double n = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    v[0] /= n; v[1] /= n; v[2] /= n;
+}
+
+void oracle_deconv_tables(int32_t od_lut[256], int32_t wq[3], double w_out[3]) {
+    /* Stain optical-density vectors (Ruifrok & Johnston 2001): hematoxylin,
+       eosin, and the residual as their normalised cross product. */
+    double Hs[3] = {0.650, 0.704, 0.286}, Es[3] = {0.072, 0.990, 0.105}, Rs[3];
+    normalize3(Hs);
+    normalize3(Es);
+    Rs[0] = Hs[1] * Es[2] - Hs[2] * Es[1];
+    Rs[1] = Hs[2] * Es[0] - Hs[0] * Es[2];
+    Rs[2] = Hs[0] * Es[1] - Hs[1] * Es[0];
+    normalize3(Rs);
+    /* M has rows H, E, R; concentrations c = od * M^-1 (od as a row vector),
+       so the hematoxylin weight of channel k is (M^-1)[k][0]. */
+    double M[3][3] = {{Hs[0], Hs[1], Hs[2]}, {Es[0], Es[1], Es[2]}, {Rs[0], Rs[1], Rs[2]}};
+    double det = M[0][0] * (M[1][1] * M[2][2] - M[1][2] * M[2][1]) -
+                 M[0][1] * (M[1][0] * M[2][2] - M[1][2] * M[2][0]) +
+                 M[0][2] * (M[1][0] * M[2][1] - M[1][1] * M[2][0]);
+    /* first column of the inverse = first column of the adjugate / det */
+    double w[3];
+    w[0] = (M[1][1] * M[2][2] - M[1][2] * M[2][1]) / det;
+    w[1] = -(M[1][0] * M[2][2] - M[1][2] * M[2][0]) / det;
+    w[2] = (M[1][0] * M[2][1] - M[1][1] * M[2][0]) / det;
+    for (int v = 0; v < 256; v++) od_lut[v] = (int32_t)floor(-log((v + 1) / 256.0) * 256.0 + 0.5);
+    for (int k = 0; k < 3; k++) {
+        wq[k] = (int32_t)llround(100.0 * w[k] * 2048.0);
+        if (w_out) w_out[k] = w[k];
+    }
+}
+
+void oracle_deconv(const uint8_t* rgb, int W, int H, size_t pitch, uint8_t* hem8) {
+    int32_t lut[256], wq[3];
+    oracle_deconv_tables(lut, wq, NULL);
+    for (int y = 0; y < H; y++)
+        for (int x = 0; x < W; x++) {
+            const uint8_t* p = rgb + (size_t)y * pitch + (size_t)x * 3;
+            int32_t acc = wq[0] * lut[p[0]] + wq[1] * lut[p[1]] + wq[2] * lut[p[2]];
+            int32_t v = acc < 0 ? 0 : (acc + (1 << 18)) >> 19;
+            hem8[(size_t)y * W + x] = (uint8_t)(v > 255 ? 255 : v);
+        }
+}
+
+/* ------------------------------------------------------------------ */
+/* Morphological reconstruction (Table I, ReconToNuclei)              */
+/* ------------------------------------------------------------------ */
+
+typedef struct { int32_t* a; size_t head, tail, cap; } fifo;
+static int fifo_push(fifo* f, int32_t v) {
+    if (f->tail == f->cap) {
+        if (f->head > 0) { /* compact */
+            memmove(f->a, f->a + f->head, (f->tail - f->head) * sizeof(int32_t));
+            f->tail -= f->head;
+            f->head = 0;
+        }
+        if (f->tail == f->cap) {
+            size_t nc = f->cap ? 2 * f->cap : 1024;
+            int32_t* na = (int32_t*)realloc(f->a, nc * sizeof(int32_t));
+            if (!na) return -1;
+            f->a = na;
+            f->cap = nc;
+        }
+    }
+    f->a[f->tail++] = v;
+    return 0;
+}
+
+static const int DY8[8] = {-1, -1, -1, 0, 0, 1, 1, 1};
+static const int DX8[8] = {-1, 0, 1, -1, 1, -1, 0, 1};
+
+int oracle_recon(const uint8_t* marker, const uint8_t* mask, int W, int H, uint8_t* J,
+                 oracle_recon_stats* st) {
+    size_t N = (size_t)W * H;
+    for (size_t i = 0; i < N; i++) {
+        if (marker[i] > mask[i]) return -1;
+        J[i] = marker[i];
+    }
+    const uint8_t* I = mask;
+    /* raster sweep: causal half-neighbourhood (up-left, up, up-right, left) */
+    for (int y = 0; y < H; y++)
+        for (int x = 0; x < W; x++) {
+            size_t p = (size_t)y * W + x;
+            int m = J[p];
+            for (int k = 0; k < 4; k++) {
+                int yy = y + DY8[k], xx = x + DX8[k];
+                if (yy < 0 || xx < 0 || xx >= W) continue;
+                int v = J[(size_t)yy * W + xx];
+                if (v > m) m = v;
+            }
+            J[p] = (uint8_t)(m < I[p] ? m : I[p]);
+        }
+    /* anti-raster sweep: anti-causal half (right, down-left, down, down-right);
+       pixels that can still raise an anti-causal neighbour seed the queue */
+    fifo f = {NULL, 0, 0, 0};
+    uint32_t* depth = NULL;
+    if (st) {
+        depth = (uint32_t*)calloc(N, sizeof(uint32_t));
+        st->fifo_pushes = 0;
+        st->max_depth = 0;
+    }
+    for (int y = H - 1; y >= 0; y--)
+        for (int x = W - 1; x >= 0; x--) {
+            size_t p = (size_t)y * W + x;
+            int m = J[p];
+            for (int k = 4; k < 8; k++) {
+                int yy = y + DY8[k], xx = x + DX8[k];
+                if (yy >= H || xx < 0 || xx >= W) continue;
+                int v = J[(size_t)yy * W + xx];
+                if (v > m) m = v;
+            }
+            J[p] = (uint8_t)(m < I[p] ? m : I[p]);
+            for (int k = 4; k < 8; k++) {
+                int yy = y + DY8[k], xx = x + DX8[k];
+                if (yy >= H || xx < 0 || xx >= W) continue;
+                size_t q = (size_t)yy * W + xx;
+                if (J[q] < J[p] && J[q] < I[q]) {
+                    fifo_push(&f, (int32_t)p);
+                    break;
+                }
+            }
+        }
+    /* breadth-first propagation until no pixel can be raised */
+    while (f.head < f.tail) {
+        int32_t p = f.a[f.head++];
+        int y = p / W, x = p % W;
+        for (int k = 0; k < 8; k++) {
+            int yy = y + DY8[k], xx = x + DX8[k];
+            if (yy < 0 || yy >= H || xx < 0 || xx >= W) continue;
+            size_t q = (size_t)yy * W + xx;
+            if (J[q] < J[p] && I[q] != J[q]) {
+                J[q] = (uint8_t)(J[p] < I[q] ? J[p] : I[q]);
+                fifo_push(&f, (int32_t)q);
+                if (st) {
+                    st->fifo_pushes++;
+                    depth[q] = depth[p] + 1;
+                    if ((int)depth[q] > st->max_depth) st->max_depth = (int)depth[q];
+                }
+            }
+        }
+    }
+    free(f.a);
+    free(depth);
+    return 0;
+}
+
+int oracle_recon_plain(const uint8_t* marker, const uint8_t* mask, int W, int H, uint8_t* R) {
+    size_t N = (size_t)W * H;
+    uint8_t* nx = (uint8_t*)malloc(N ? N : 1);
+    for (size_t i = 0; i < N; i++) R[i] = marker[i];
+    int iters = 0;
+    for (;;) {
+        int changed = 0;
+        for (int y = 0; y < H; y++)
+            for (int x = 0; x < W; x++) {
+                int m = 0;
+                for (int dy = -1; dy <= 1; dy++)
+                    for (int dx = -1; dx <= 1; dx++) {
+                        int yy = y + dy, xx = x + dx;
+                        if (yy < 0 || yy >= H || xx < 0 || xx >= W) continue;
+                        int v = R[(size_t)yy * W + xx];
+                        if (v > m) m = v;
+                    }
+                size_t p = (size_t)y * W + x;
+                int v = m < mask[p] ? m : mask[p];
+                nx[p] = (uint8_t)v;
+                if (v != R[p]) changed = 1;
+            }
+        memcpy(R, nx, N);
+        if (!changed) break;
+        iters++;
+    }
+    free(nx);
+    return iters;
+}
+
+void oracle_hdome(const uint8_t* hem8, int W, int H, int h, int thr, uint8_t* R, uint8_t* fg,
+                  oracle_recon_stats* st) {
+    size_t N = (size_t)W * H;
+    uint8_t* mk = (uint8_t*)malloc(N ? N : 1);
+    uint8_t* r = R ? R : (uint8_t*)malloc(N ? N : 1);
+    for (size_t i = 0; i < N; i++) mk[i] = (uint8_t)(hem8[i] > h ? hem8[i] - h : 0);
+    oracle_recon(mk, hem8, W, H, r, st);
+    if (fg)
+        for (size_t i = 0; i < N; i++) fg[i] = (uint8_t)((int)hem8[i] - (int)r[i] >= thr);
+    free(mk);
+    if (!R) free(r);
+}
+
+/* ------------------------------------------------------------------ */
+/* Fill holes (Table I, FillHoles)                                     */
+/* ------------------------------------------------------------------ */
+
+void oracle_fill_holes(const uint8_t* fg, int W, int H, uint8_t* filled) {
+    size_t N = (size_t)W * H;
+    uint8_t* reach = (uint8_t*)calloc(N ? N : 1, 1);
+    int32_t* q = (int32_t*)malloc((N ? N : 1) * sizeof(int32_t));
+    size_t qh = 0, qt = 0;
+    /* seeds: background pixels on the image border */
+    for (int y = 0; y < H; y++)
+        for (int x = 0; x < W; x++) {
+            if (y != 0 && y != H - 1 && x != 0 && x != W - 1) continue;
+            size_t p = (size_t)y * W + x;
+            if (!fg[p] && !reach[p]) { reach[p] = 1; q[qt++] = (int32_t)p; }
+        }
+    static const int dy4[4] = {-1, 1, 0, 0}, dx4[4] = {0, 0, -1, 1};
+    while (qh < qt) {
+        int32_t p = q[qh++];
+        int y = p / W, x = p % W;
+        for (int k = 0; k < 4; k++) {
+            int yy = y + dy4[k], xx = x + dx4[k];
+            if (yy < 0 || yy >= H || xx < 0 || xx >= W) continue;
+            size_t n = (size_t)yy * W + xx;
+            if (!fg[n] && !reach[n]) { reach[n] = 1; q[qt++] = (int32_t)n; }
+        }
+    }
+    for (size_t i = 0; i < N; i++) filled[i] = (uint8_t)(!reach[i]);
+    free(reach);
+    free(q);
+}
+
+/* ------------------------------------------------------------------ */
+/* Labelling + area filter (Table I, BWLabel and AreaThreshold)        */
+/* ------------------------------------------------------------------ */
+
+int oracle_label(const uint8_t* filled, int W, int H, int amin, int amax, int32_t* labels) {
+    size_t N = (size_t)W * H;
+    int32_t* q = (int32_t*)malloc((N ? N : 1) * sizeof(int32_t));
+    for (size_t i = 0; i < N; i++) labels[i] = 0;
+    int K = 0;
+    /* raster order: the first unvisited foreground pixel starts a component,
+       so components are discovered in order of their first pixel */
+    uint8_t* seen = (uint8_t*)calloc(N ? N : 1, 1);
+    for (size_t s = 0; s < N; s++) {
+        if (!filled[s] || seen[s]) continue;
+        size_t qh = 0, qt = 0;
+        seen[s] = 1;
+        q[qt++] = (int32_t)s;
+        while (qh < qt) {
+            int32_t p = q[qh++];
+            int y = p / W, x = p % W;
+            for (int k = 0; k < 8; k++) {
+                int yy = y + DY8[k], xx = x + DX8[k];
+                if (yy < 0 || yy >= H || xx < 0 || xx >= W) continue;
+                size_t n = (size_t)yy * W + xx;
+                if (filled[n] && !seen[n]) { seen[n] = 1; q[qt++] = (int32_t)n; }
+            }
+        }
+        int area = (int)qt;
+        if (area >= amin && area <= amax) {
+            K++;
+            for (size_t i = 0; i < qt; i++) labels[q[i]] = K;
+        }
+    }
+    free(q);
+    free(seen);
+    return K;
+}
+
+/* ------------------------------------------------------------------ */
+/* Exact squared EDT (Table I, Pre-Watershed distance transform)       */
+/* ------------------------------------------------------------------ */
+
+static inline int64_t floordiv64(int64_t a, int64_t b) { /* b > 0 */
+    int64_t q = a / b;
+    if ((a % b != 0) && (a < 0)) q--;
+    return q;
+}
+
+void oracle_edt(const int32_t* labels, int W, int H, int32_t* edt) {
+    size_t N = (size_t)W * H;
+    const int64_t INF = (int64_t)W + H; /* larger than any in-image distance */
+    int64_t* g = (int64_t*)malloc((N ? N : 1) * sizeof(int64_t));
+    int any_bg = 0;
+    /* phase 1: per column, distance to the nearest background pixel */
+    for (int x = 0; x < W; x++) {
+        g[x] = labels[x] == 0 ? 0 : INF;
+        for (int y = 1; y < H; y++) {
+            size_t p = (size_t)y * W + x;
+            g[p] = labels[p] == 0 ? 0 : (g[p - W] >= INF ? INF : g[p - W] + 1);
+        }
+        for (int y = H - 2; y >= 0; y--) {
+            size_t p = (size_t)y * W + x;
+            if (g[p + W] < g[p]) g[p] = g[p + W] + 1;
+        }
+    }
+    for (size_t i = 0; i < N; i++)
+        if (labels[i] == 0) { any_bg = 1; break; }
+    /* phase 2: per row, lower envelope of parabolas f_i(u) = (u-i)^2 + g_i^2 */
+    int* s = (int*)malloc((W ? W : 1) * sizeof(int));
+    int* t = (int*)malloc((W ? W : 1) * sizeof(int));
+    for (int y = 0; y < H; y++) {
+        const int64_t* gr = g + (size_t)y * W;
+#define F(u, i) ((int64_t)((u) - (i)) * ((u) - (i)) + gr[i] * gr[i])
+        int qn = 0;
+        s[0] = 0;
+        t[0] = 0;
+        for (int u = 1; u < W; u++) {
+            while (qn >= 0 && F(t[qn], s[qn]) > F(t[qn], u)) qn--;
+            if (qn < 0) {
+                qn = 0;
+                s[0] = u;
+            } else {
+                int i = s[qn];
+                int64_t num = (int64_t)u * u - (int64_t)i * i + gr[u] * gr[u] - gr[i] * gr[i];
+                int64_t w = 1 + floordiv64(num, 2 * (int64_t)(u - i));
+                if (w < W) {
+                    qn++;
+                    s[qn] = u;
+                    t[qn] = (int)w;
+                }
+            }
+        }
+        for (int u = W - 1; u >= 0; u--) {
+            int64_t d = F(u, s[qn]);
+            edt[(size_t)y * W + u] = any_bg ? (int32_t)d : INT32_MAX;
+            if (u == t[qn]) qn--;
+        }
+#undef F
+    }
+    free(s);
+    free(t);
+    free(g);
+}
+
+/* ------------------------------------------------------------------ */
+/* Per-object features (Sec. II feature families; Sec. V-A transforms) */
+/* ------------------------------------------------------------------ */
+
+static const int GLCM_DX[4] = {1, 0, 1, 1};
+static const int GLCM_DY[4] = {0, 1, 1, -1};
+
+static inline int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+/* Sobel on hem8 with replicate (clamp-to-edge) border; returns gx^2+gy^2 */
+static int sobel_m2(const uint8_t* I, int W, int H, int y, int x) {
+#define P(yy, xx) ((int)I[(size_t)clampi(yy, 0, H - 1) * W + clampi(xx, 0, W - 1)])
+    int gx = (P(y - 1, x + 1) + 2 * P(y, x + 1) + P(y + 1, x + 1)) -
+             (P(y - 1, x - 1) + 2 * P(y, x - 1) + P(y + 1, x - 1));
+    int gy = (P(y + 1, x - 1) + 2 * P(y + 1, x) + P(y + 1, x + 1)) -
+             (P(y - 1, x - 1) + 2 * P(y - 1, x) + P(y - 1, x + 1));
+#undef P
+    return gx * gx + gy * gy;
+}
+
+void oracle_features(const uint8_t* hem8, const int32_t* labels, int W, int H, int K,
+                     double* feats) {
+    if (K <= 0) return;
+    long long* n = (long long*)calloc(K + 1, sizeof(long long));
+    long long* per = (long long*)calloc(K + 1, sizeof(long long));
+    long long* S = (long long*)calloc(K + 1, sizeof(long long));
+    long long* Qs = (long long*)calloc(K + 1, sizeof(long long));
+    int* mn = (int*)malloc((K + 1) * sizeof(int));
+    int* mx = (int*)malloc((K + 1) * sizeof(int));
+    double* gs = (double*)calloc(K + 1, sizeof(double));
+    double* gss = (double*)calloc(K + 1, sizeof(double));
+    int* gmn = (int*)malloc((K + 1) * sizeof(int));
+    int* gmx = (int*)malloc((K + 1) * sizeof(int));
+    long long* C = (long long*)calloc((size_t)(K + 1) * 4 * 64, sizeof(long long));
+    for (int k = 0; k <= K; k++) { mn[k] = INT_MAX; mx[k] = -1; gmn[k] = INT_MAX; gmx[k] = -1; }
+
+    for (int y = 0; y < H; y++)
+        for (int x = 0; x < W; x++) {
+            size_t p = (size_t)y * W + x;
+            int l = labels[p];
+            if (l <= 0 || l > K) continue;
+            int v = hem8[p];
+            n[l]++;
+            S[l] += v;
+            Qs[l] += (long long)v * v;
+            if (v < mn[l]) mn[l] = v;
+            if (v > mx[l]) mx[l] = v;
+            /* crack length: 4-neighbours outside the object or the image */
+            static const int dy4[4] = {-1, 1, 0, 0}, dx4[4] = {0, 0, -1, 1};
+            for (int k = 0; k < 4; k++) {
+                int yy = y + dy4[k], xx = x + dx4[k];
+                if (yy < 0 || yy >= H || xx < 0 || xx >= W || labels[(size_t)yy * W + xx] != l)
+                    per[l]++;
+            }
+            int m2 = sobel_m2(hem8, W, H, y, x);
+            gs[l] += sqrt((double)m2);
+            if (m2 < gmn[l]) gmn[l] = m2;
+            if (m2 > gmx[l]) gmx[l] = m2;
+            /* co-occurrence: both ends inside the same object; 8 levels */
+            for (int o = 0; o < 4; o++) {
+                int yy = y + GLCM_DY[o], xx = x + GLCM_DX[o];
+                if (yy < 0 || yy >= H || xx < 0 || xx >= W) continue;
+                size_t q = (size_t)yy * W + xx;
+                if (labels[q] != l) continue;
+                C[((size_t)l * 4 + o) * 64 + (v >> 5) * 8 + (hem8[q] >> 5)]++;
+            }
+        }
+    /* second pass: squared deviations of the gradient magnitude from its mean */
+    for (int y = 0; y < H; y++)
+        for (int x = 0; x < W; x++) {
+            size_t p = (size_t)y * W + x;
+            int l = labels[p];
+            if (l <= 0 || l > K) continue;
+            double d = sqrt((double)sobel_m2(hem8, W, H, y, x)) - gs[l] / (double)n[l];
+            gss[l] += d * d;
+        }
+
+    for (int l = 1; l <= K; l++) {
+        double* f = feats + (size_t)(l - 1) * ORACLE_NFEAT;
+        if (n[l] == 0) {
+            for (int k = 0; k < ORACLE_NFEAT; k++) f[k] = 0.0;
+            continue;
+        }
+        double N = (double)n[l];
+        f[0] = N;
+        f[1] = (double)per[l];
+        f[2] = (double)S[l] / N;
+        __int128 var_num = (__int128)n[l] * Qs[l] - (__int128)S[l] * S[l]; /* N*Q - S^2 >= 0 */
+        f[3] = sqrt((double)var_num) / N;
+        f[4] = mn[l];
+        f[5] = mx[l];
+        f[6] = gs[l] / N;
+        f[7] = sqrt(gss[l] / N);
+        f[8] = sqrt((double)gmn[l]);
+        f[9] = sqrt((double)gmx[l]);
+        double acc[5] = {0, 0, 0, 0, 0};
+        int used = 0;
+        for (int o = 0; o < 4; o++) {
+            const long long* c = C + ((size_t)l * 4 + o) * 64;
+            long long T = 0, si = 0, sj = 0, sii = 0, sjj = 0, sij = 0;
+            for (int i = 0; i < 8; i++)
+                for (int j = 0; j < 8; j++) {
+                    long long v = c[i * 8 + j];
+                    T += v; si += i * v; sj += j * v;
+                    sii += (long long)i * i * v; sjj += (long long)j * j * v; sij += (long long)i * j * v;
+                }
+            if (T == 0) continue;
+            used++;
+            double con = 0, ene = 0, hom = 0, ent = 0;
+            for (int i = 0; i < 8; i++)
+                for (int j = 0; j < 8; j++) {
+                    long long v = c[i * 8 + j];
+                    if (!v) continue;
+                    double P = (double)v / (double)T;
+                    con += (double)((i - j) * (i - j)) * P;
+                    ene += P * P;
+                    hom += P / (1.0 + (double)((i - j) * (i - j)));
+                    ent -= P * log(P);
+                }
+            /* correlation from exact integer moments: T^2 * cov and T^2 * var
+               are integers, so a constant marginal gives exactly 0 */
+            long long vi = T * sii - si * si, vj = T * sjj - sj * sj, cv = T * sij - si * sj;
+            double cor = (vi == 0 || vj == 0) ? 0.0 : (double)cv / sqrt((double)vi * (double)vj);
+            acc[0] += con; acc[1] += ene; acc[2] += hom; acc[3] += ent; acc[4] += cor;
+        }
+        for (int k = 0; k < 5; k++) f[10 + k] = used ? acc[k] / used : 0.0;
+    }
+    free(n); free(per); free(S); free(Qs); free(mn); free(mx);
+    free(gs); free(gss); free(gmn); free(gmx); free(C);
+}
+
+int oracle_seg(const uint8_t* rgb, int W, int H, size_t pitch, int h, int thr, int amin, int amax,
+               uint8_t* hem8, uint8_t* R, uint8_t* fg, uint8_t* filled, int32_t* labels,
+               int32_t* edt) {
+    if (W <= 0 || H <= 0 || pitch < (size_t)W * 3 || !hem8 || !labels) return -1;
+    size_t N = (size_t)W * H;
+    uint8_t* f = fg ? fg : (uint8_t*)malloc(N);
+    uint8_t* fl = filled ? filled : (uint8_t*)malloc(N);
+    oracle_deconv(rgb, W, H, pitch, hem8);
+    oracle_hdome(hem8, W, H, h, thr, R, f, NULL);
+    oracle_fill_holes(f, W, H, fl);
+    int K = oracle_label(fl, W, H, amin, amax, labels);
+    if (edt) oracle_edt(labels, W, H, edt);
+    if (!fg) free(f);
+    if (!filled) free(fl);
+    return K;
+}

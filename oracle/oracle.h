@@ -1,0 +1,94 @@
+/*
+ * CPU oracle for the per-tile nucleus pipeline: plain, slow, single-threaded,
+ * FP64 for every floating-point feature.  TEST INFRASTRUCTURE ONLY: it is
+ * called by the tests, by the smoke check and by the benchmark's CPU-baseline
+ * leg, never by the library.  It shares no code, header or table with the
+ * CUDA path; both sides rebuild the colour-deconvolution constants from the
+ * same formulas.
+ *
+ * Paper: Teodoro et al., "High-throughput Execution of Hierarchical Analysis
+ * Pipelines on Hybrid Cluster Platforms".  The pipeline is the segmentation
+ * and feature stages of Sec. II / Fig. 1; the operations are those of
+ * Table I (ReconToNuclei, FillHoles, BWLabel + AreaThreshold, the distance
+ * transform of Pre-Watershed) and the feature-stage transforms of Sec. V-A
+ * (colour deconvolution, gradient) with the feature families of Sec. II.
+ * The paper gives no formulas; the readings taken for every silent point are
+ * stated at each function.
+ */
+#ifndef ORACLE_H
+#define ORACLE_H
+#include <stddef.h>
+#include <stdint.h>
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ORACLE_NFEAT 15
+
+/* Fixed-point colour deconvolution constants (Sec. V-A "Color
+ * deconvolution"; stain vectors of Ruifrok & Johnston 2001):
+ * od_lut[v] = floor(-ln((v+1)/256)*256 + 0.5), wq[c] = round(100*w_c*2^11)
+ * with w the hematoxylin column of the inverse stain matrix. */
+void oracle_deconv_tables(int32_t od_lut[256], int32_t wq[3], double w[3]);
+
+/* hem8 = clamp((sum_c wq[c]*od_lut[rgb_c] + 2^18) >> 19, 0, 255), 0 when the
+ * sum is negative.  rgb: H rows of 3*W bytes at `pitch`; hem8: H*W. */
+void oracle_deconv(const uint8_t* rgb, int W, int H, size_t pitch, uint8_t* hem8);
+
+typedef struct {
+    long long fifo_pushes;   /* pixels queued by the propagation phase */
+    int max_depth;           /* longest chain of queue hops from a seed */
+} oracle_recon_stats;
+
+/* Grayscale reconstruction by dilation, 8-connected (Table I
+ * "ReconToNuclei": Vincent's MR).  R = lim R_k, R_0 = marker,
+ * R_{k+1} = min(dilate8(R_k), mask); neighbours outside the image are
+ * ignored.  Algorithm: Vincent 1993 hybrid (raster sweep, anti-raster sweep,
+ * FIFO propagation).  Requires marker <= mask; returns -1 otherwise. */
+int oracle_recon(const uint8_t* marker, const uint8_t* mask, int W, int H, uint8_t* R,
+                 oracle_recon_stats* stats);
+
+/* The plain definition iterated to stability (slow; small inputs).
+ * Returns the number of iterations that changed something. */
+int oracle_recon_plain(const uint8_t* marker, const uint8_t* mask, int W, int H, uint8_t* R);
+
+/* h-dome: marker = max(hem8 - h, 0), R = recon(marker | hem8),
+ * fg = (hem8 - R >= thr).  R and fg may be NULL. */
+void oracle_hdome(const uint8_t* hem8, int W, int H, int h, int thr, uint8_t* R, uint8_t* fg,
+                  oracle_recon_stats* stats);
+
+/* Fill holes (Table I "FillHoles"): background pixels not 4-connected,
+ * through background, to the image border become foreground. */
+void oracle_fill_holes(const uint8_t* fg, int W, int H, uint8_t* filled);
+
+/* 8-connected components of `filled` (Table I "BWLabel"); components whose
+ * area lies in [amin, amax] (Table I "AreaThreshold") are numbered 1..K in
+ * row-major order of their first pixel, the rest become 0.  Returns K. */
+int oracle_label(const uint8_t* filled, int W, int H, int amin, int amax, int32_t* labels);
+
+/* Exact squared Euclidean distance to the nearest pixel with label 0, over
+ * in-image pixels (Table I "Pre-Watershed" distance transform); 0 on
+ * background; INT32_MAX everywhere when no pixel has label 0.  Algorithm:
+ * Meijster, Roerdink, Hesselink 2000 (separable, exact). */
+void oracle_edt(const int32_t* labels, int W, int H, int32_t* edt);
+
+/* Per-object features for labels 1..K (Sec. II feature families: pixel
+ * statistics, gradient statistics, Haralick texture, morphometry), FP64,
+ * feats[K][15]:
+ *  0 area, 1 perimeter (crack length), 2 mean, 3 std (population) of hem8,
+ *  4 min, 5 max of hem8, 6..9 mean/std/min/max of the Sobel magnitude,
+ *  10..14 GLCM contrast, energy, homogeneity, entropy, correlation, averaged
+ *  over the offsets (dx,dy) in {(1,0),(0,1),(1,1),(1,-1)} with any pair. */
+void oracle_features(const uint8_t* hem8, const int32_t* labels, int W, int H, int K,
+                     double* feats);
+
+/* Whole segmentation: deconv -> h-dome -> fill holes -> label -> EDT.
+ * Any of R, fg, filled may be NULL.  Returns K, or -1 on bad arguments. */
+int oracle_seg(const uint8_t* rgb, int W, int H, size_t pitch, int h, int thr, int amin, int amax,
+               uint8_t* hem8, uint8_t* R, uint8_t* fg, uint8_t* filled, int32_t* labels,
+               int32_t* edt);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
