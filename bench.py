@@ -1,0 +1,356 @@
+"""Benchmark: 4096x4096 tiles per second through the segmentation + feature path.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--form batched|plain]
+                    [--impl ours|reference]
+
+One step is one pass of the whole path (colour deconvolution, h-dome
+reconstruction, fill holes, labelling + area filter + relabel, EDT, per-object
+features) over one batch of synthetic 4096x4096 tiles generated like the
+4096^2 workload (~3000 nuclei, 20% in touching clusters of 2-6, 150 stroma
+discs).  Inputs are resident in HBM when the timed region starts; the batch's
+inputs and planes (hundreds of MB) exceed the 129 MB L2, and the plain form
+rotates over several input buffers.
+
+N>1 (torchrun): every rank is an independent replica on its own tiles (the
+path shards by tile; there is no data exchange), value = all tiles / max time.
+
+--impl reference times the CPU oracle (the plain C program written from the
+paper's definitions) on this host's cores on a bounded sample of the same
+workload; rank 0 only.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "4Kx4K tiles/sec/GB300 (batched+served vs plain) at bit-exact seg; p50/p99 ms"
+WORKLOAD = ("4096x4096 RGB uint8 tiles, ~3000 nuclei (20% in touching clusters of 2-6) + 150 stroma "
+            "discs r40-120; h=20, dome>=10, area [20,1500], 8-level GLCM x4 offsets")
+BYTES_PER_PX = {"deconv": 4, "recon": 2, "fill": 2, "label": 13, "edt": 16, "features": 5}
+PATH_BYTES_PER_PX = 42
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(n_gpus):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, v):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def gen_tiles(n, rank):
+    import synth
+    tiles = []
+    for i in range(n):
+        seed = 1000 if (rank == 0 and i == 0) else 1000 + 7919 * (rank * 64 + i)
+        tiles.append(synth.tile(4096, 4096, seed, n_nuclei=3000, frac_cluster=0.2, n_stroma=150))
+    return tiles
+
+
+def cpu_baseline(tiles, budget_s=12.0):
+    """The oracle as it stands on this host's cores: whole path on full tiles."""
+    import oracle
+    done, t0 = 0, time.perf_counter()
+    while True:
+        r = oracle.seg(tiles[done % len(tiles)])
+        oracle.features(r["hem8"], r["labels"], r["K"])
+        done += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or done >= 8:
+            break
+    return {"value": done / el, "unit": "tiles/s", "cores": 1, "kind": "oracle",
+            "sample": "%d full 4096x4096 tile(s) of the benchmark workload, single-threaded C oracle "
+                      "(segmentation + features), %.1f s" % (done, el)}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    tiles = gen_tiles(1, 0)
+    import oracle
+    oracle.build()
+    for _ in range(args.warmup if args.warmup < 1 else 1):
+        pass
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        r = oracle.seg(tiles[0])
+        oracle.features(r["hem8"], r["labels"], r["K"])
+        times.append(time.perf_counter() - t0)
+    ms = 1000.0 * statistics.mean(times)
+    val = 1000.0 / ms
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "tiles/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "form": "oracle, one tile per step", "tiles_per_step": 1},
+            "cpu_baseline": {"value": val, "unit": "tiles/s", "cores": 1, "kind": "oracle",
+                             "sample": "%d steps of one full 4096x4096 tile each" % args.steps},
+            "e2e": {"value": val, "unit": "tiles/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, world, rank, local):
+    import numpy as np
+    import torch
+    import paper_1209_3332_gb300 as P
+    from paper_1209_3332_gb300 import build
+    build.build()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(dev)
+    pipe = P.Pipe(local)
+    B = args.batch if args.form == "batched" else 1
+    nbuf = max(B, 4) if args.form == "plain" else B
+    host = gen_tiles(min(nbuf, 4), rank)
+    H = W = 4096
+    feats_cap = 20000
+    bufs = []
+    for i in range(nbuf):
+        h = host[i % len(host)]
+        bufs.append(dict(rgb=torch.from_numpy(h).to(dev), hem8=torch.empty((H, W), dtype=torch.uint8, device=dev),
+                         labels=torch.empty((H, W), dtype=torch.int32, device=dev),
+                         edt=torch.empty((H, W), dtype=torch.int32, device=dev),
+                         n_objects=torch.zeros(1, dtype=torch.int32, device=dev),
+                         feats=torch.empty((feats_cap, 15), dtype=torch.float32, device=dev)))
+    torch.cuda.synchronize()
+
+    state = {"i": 0}
+
+    def step_plain(profile_K=None):
+        b = bufs[state["i"] % nbuf]
+        state["i"] += 1
+        with torch.cuda.stream(stream):
+            pipe.seg_tile(b["rgb"], b["hem8"], b["labels"], b["edt"], b["n_objects"], stream=stream)
+        # the feature stage needs K on the host (plain API)
+        stream.synchronize()
+        K = int(b["n_objects"].item())
+        pipe.features_tile(b["hem8"], b["labels"], K, b["feats"], stream=stream)
+
+    def step_batched():
+        pipe.seg_features_batch(bufs[:B], stream=stream)
+
+    step = step_batched if args.form == "batched" else step_plain
+    for _ in range(args.warmup):
+        step()
+    stream.synchronize()
+    st = pipe.status()
+    if st != P.PIPE_OK:
+        raise RuntimeError("device status %d after warm-up" % st)
+
+    clocks = Clocks(local)
+    clocks.start()
+    barrier(world)
+    torch.cuda.synchronize()
+    l0 = pipe.launch_count()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    launches = pipe.launch_count() - l0
+    ms_total = ev0.elapsed_time(ev1)
+    ck = clocks.stop()
+    ms_total = max_over_ranks(world, ms_total)
+    ms_step = ms_total / args.steps
+    value = world * B * args.steps / (ms_total / 1000.0)
+
+    # per-kernel times (CUDA events around every launch, same stream), a
+    # second pass over the same steps
+    pipe.profile(True)
+    for _ in range(args.steps):
+        step()
+    torch.cuda.synchronize()
+    prof = pipe.profile_read()
+    pipe.profile(False)
+    st = pipe.status()
+    if st != P.PIPE_OK:
+        raise RuntimeError("device status %d" % st)
+
+    # end to end through the public API with host buffers: pinned RGB in,
+    # object count and feature rows out, copies inside the timed region
+    pinned = [torch.from_numpy(h).pin_memory() for h in host]
+    fe_host = torch.empty((B, feats_cap, 15), dtype=torch.float32).pin_memory()
+    k_host = torch.empty((B,), dtype=torch.int32).pin_memory()
+    h2d = d2h = 0
+
+    def e2e_step():
+        nonlocal h2d, d2h
+        h2d = d2h = 0
+        with torch.cuda.stream(stream):
+            for i in range(B):
+                bufs[i]["rgb"].copy_(pinned[i % len(pinned)], non_blocking=True)
+                h2d += pinned[i % len(pinned)].numel()
+            if args.form == "batched":
+                pipe.seg_features_batch(bufs[:B], stream=stream)
+            else:
+                b = bufs[0]
+                pipe.seg_tile(b["rgb"], b["hem8"], b["labels"], b["edt"], b["n_objects"], stream=stream)
+                stream.synchronize()
+                K = int(b["n_objects"].item())
+                pipe.features_tile(b["hem8"], b["labels"], K, b["feats"], stream=stream)
+            for i in range(B):
+                k_host[i:i + 1].copy_(bufs[i]["n_objects"], non_blocking=True)
+            stream.synchronize()
+            for i in range(B):
+                K = min(int(k_host[i]), feats_cap)
+                fe_host[i, :K].copy_(bufs[i]["feats"][:K], non_blocking=True)
+                d2h += 4 + K * 15 * 4
+        stream.synchronize()
+
+    for _ in range(max(1, args.warmup)):
+        e2e_step()
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(world, time.perf_counter() - t0)
+    e2e = {"value": world * B * args.steps / e2e_s, "unit": "tiles/s", "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": d2h}
+
+    # roofline of the dominant kernel
+    peak, peak_kind = peaks()
+    name, (cnt, tot) = max(prof.items(), key=lambda kv: kv[1][1])
+    stage = {"recon": "recon", "deconv": "deconv", "edt_rows": "edt", "relabel": "label",
+             "feat_objects": "features", "fill_local": "fill", "label_local": "label"}.get(name)
+    px_per_launch = B * H * W
+    line = {"metric": METRIC, "value": value, "unit": "tiles/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "form": args.form, "tiles_per_step": B,
+                       "l2": "inputs larger than L2 (each step touches >= 350 MB per tile; plain form "
+                             "rotates %d input buffers)" % nbuf,
+                       "parallelism": "replicas" if world > 1 else "1 GPU"},
+            "gpu_launches": int(launches), "clocks": ck, "e2e": e2e}
+    if stage:
+        avg_ms = tot / cnt
+        alg = BYTES_PER_PX[stage] * px_per_launch
+        ach = alg / (avg_ms / 1000.0) / 1e9
+        line["roofline"] = {"bound": "hbm", "kernel": name, "achieved": ach, "peak": peak, "unit": "GB/s",
+                            "frac": ach / peak, "traffic": None, "peak_source": peak_kind,
+                            "alg_bytes_per_launch": alg, "avg_launch_ms": avg_ms}
+    path_gbs = PATH_BYTES_PER_PX * H * W * value / world / 1e9
+    line["path_roofline"] = {"bytes_per_tile": PATH_BYTES_PER_PX * H * W, "achieved": path_gbs, "peak": peak,
+                             "unit": "GB/s", "frac": path_gbs / peak}
+    line["kernels_ms"] = {k: round(v[1] / max(v[0], 1), 4) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
+    if rank == 0 and world == 1 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(host[:1])
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    pipe.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--form", default="plain", choices=["plain", "batched"])
+    ap.add_argument("--batch", type=int, default=8)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    world, rank, local = dist_setup(args.gpus)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

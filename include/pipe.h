@@ -1,0 +1,172 @@
+/*
+ * pipe.h -- C ABI of the GB300 per-tile nucleus segmentation + feature path.
+ *
+ * Paper: G. Teodoro, T. Pan, T. Kurc, J. Kong, L. Cooper, J. Saltz,
+ * "High-throughput Execution of Hierarchical Analysis Pipelines on Hybrid
+ * Cluster Platforms".  The input of the pipeline is an image tile and its
+ * output is a feature vector per segmented nucleus (Sec. II, caption of
+ * Fig. 1); tiles are processed independently as a bag of tasks (Sec. II);
+ * the operations are those of Table I (ReconToNuclei, FillHoles, BWLabel,
+ * AreaThreshold, the distance transform of Pre-Watershed) and the
+ * feature-stage transforms of Sec. V-A (colour deconvolution, gradient).
+ *
+ * Conventions for every entry point:
+ *  - Returns a pipe_status; no entry point aborts, traps or prints.
+ *  - Device pointers are caller-owned, must be on the pipe's device and
+ *    must stay valid until the work enqueued on `stream` has finished.
+ *  - Calls taking a stream are asynchronous on that stream.  Device-side
+ *    failures (a wait budget exhausted, a capacity exceeded) are written to
+ *    a status word in device memory; pipe_status_read() returns it.
+ *  - Image planes are row-major with a row pitch of W elements unless a
+ *    pitch argument says otherwise.
+ *  - A pipe_t may be used from one host thread at a time, except
+ *    batch_submit / batch_poll, which are safe to call concurrently.
+ */
+#ifndef GB300_NUCSEG_PIPE_H
+#define GB300_NUCSEG_PIPE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pipe_s* pipe_t;
+typedef struct CUstream_st* pipe_stream_t; /* a cudaStream_t; NULL = legacy default */
+
+typedef enum {
+    PIPE_OK = 0,
+    PIPE_EINVAL = 1,     /* bad argument (size, pointer, parameter) */
+    PIPE_ENOMEM = 2,     /* device or pinned-host allocation failed */
+    PIPE_EBUSY = 3,      /* admission refused: HBM budget or slots exhausted */
+    PIPE_EAGAIN = 4,     /* ticket not finished yet */
+    PIPE_ETIMEOUT = 5,   /* a device-side wait hit its cycle budget */
+    PIPE_EOVERFLOW = 6,  /* a caller-sized output was too small */
+    PIPE_ECUDA = 7       /* a CUDA runtime call failed */
+} pipe_status;
+
+#define PIPE_NFEAT 15
+
+/* Parameters.  Defaults (pipe_default_params): h = 20, dome_thresh = 10,
+ * area [20, 1500], 8 GLCM levels, offsets (dx,dy) = (1,0),(0,1),(1,1),(1,-1),
+ * hbm_budget_bytes = 40 GiB, max_slots = 16, wait_budget_cycles = 2^32. */
+typedef struct {
+    int h;               /* h-dome height (ReconToNuclei, Table I) */
+    int dome_thresh;     /* foreground iff hem8 - R >= dome_thresh */
+    int area_min;        /* AreaThreshold (Table I): keep areas in [min, max] */
+    int area_max;
+    int glcm_levels;     /* must be 8 (hem8 >> 5) */
+    int n_offsets;       /* must be 4 */
+    int offsets[4][2];   /* (dx, dy); must be the four defaults */
+    size_t hbm_budget_bytes;  /* device memory the served form may hold */
+    int max_slots;            /* tiles in flight in the served form */
+    long long wait_budget_cycles; /* bound on every device-side spin wait */
+    const char* autotune_cache;   /* path of the tile-shape cache, or NULL */
+} pipe_params;
+
+void pipe_default_params(pipe_params* p);
+
+/* Creates a pipe on CUDA device `device`.  The pipe owns all workspaces;
+ * it grows them on demand (a synchronising allocation) when a larger tile
+ * than any seen before arrives. */
+int pipe_create(const pipe_params* params, int device, pipe_t* out);
+
+/* Drains all outstanding work and frees everything the pipe owns. */
+void pipe_destroy(pipe_t p);
+
+/* Segmentation of one RGB tile (Sec. II segmentation stage; Table I):
+ *   hem8   = colour deconvolution, hematoxylin plane, uint8 (Sec. V-A)
+ *   R      = reconstruction by dilation of max(hem8-h,0) under hem8, 8-conn
+ *   fg     = hem8 - R >= dome_thresh                      (ReconToNuclei)
+ *   filled = fg with background holes not 4-connected to the border filled
+ *   labels = 8-connected components of filled with area in [area_min,
+ *            area_max], numbered 1..K by first pixel in row-major order,
+ *            0 elsewhere                                  (BWLabel, AreaThreshold)
+ *   edt    = exact squared Euclidean distance to the nearest label-0 pixel,
+ *            INT32_MAX everywhere if there is none        (Pre-Watershed)
+ * rgb_dev: H rows of 3*W bytes (R,G,B) at pitch_bytes >= 3*W.
+ * hem8_dev [H*W] uint8, labels_dev [H*W] int32, edt_dev [H*W] int32 (may be
+ * NULL to skip the EDT), n_objects_dev [1] int32 receives K.
+ * Errors: PIPE_EINVAL for W,H < 1, W*H >= 2^31 or NULL required pointers. */
+int seg_tile(pipe_t p, const uint8_t* rgb_dev, int W, int H, size_t pitch_bytes,
+             uint8_t* hem8_dev, int32_t* labels_dev, int32_t* edt_dev, int32_t* n_objects_dev,
+             pipe_stream_t stream);
+
+/* Per-object features (Sec. II feature families; Sec. V-A gradient) of
+ * labels 1..n_objects, written as float32 rows feats_dev[n_objects][15]:
+ *  0 area, 1 perimeter (4-neighbour crack count, image outside counts),
+ *  2 mean, 3 population std, 4 min, 5 max of hem8,
+ *  6 mean, 7 population std, 8 min, 9 max of the Sobel magnitude of hem8
+ *    (replicated border),
+ *  10 contrast, 11 energy, 12 homogeneity, 13 entropy, 14 correlation of the
+ *    8-level (hem8 >> 5) co-occurrence matrix of same-object pixel pairs,
+ *    averaged over the offsets that have pairs (0 if none; correlation 0
+ *    when a marginal is constant).
+ * n_objects may be 0 (nothing is launched).  Errors: PIPE_EINVAL. */
+int features_tile(pipe_t p, const uint8_t* hem8_dev, const int32_t* labels_dev, int W, int H,
+                  int n_objects, float* feats_dev, pipe_stream_t stream);
+
+/* Batched form, device-resident: segmentation + features of n tiles of any
+ * sizes, one launch per pass over all tiles (the reconstruction pass is one
+ * persistent launch with a work queue spanning every tile), replayed from a
+ * CUDA graph when the same batch shape recurs.  Bag of tasks over tiles,
+ * Sec. II; demand-driven assignment, Sec. III-B.  Results are identical to
+ * seg_tile + features_tile on each tile alone.  feats receives up to
+ * feats_cap rows; if K > feats_cap, n_objects still reports K and the
+ * tile's status (pipe_status_read) becomes PIPE_EOVERFLOW. */
+typedef struct {
+    const uint8_t* rgb; int W, H; size_t pitch;
+    uint8_t* hem8; int32_t* labels; int32_t* edt; int32_t* n_objects;
+    float* feats; int feats_cap;
+} tile_dev;
+int seg_features_batch(pipe_t p, const tile_dev* tiles, int n, pipe_stream_t stream);
+
+/* Served form (Sec. IV-D prefetching and asynchronous copy): tiles in host
+ * memory are admitted as slots and HBM budget allow, uploaded on copy
+ * streams overlapped with compute, processed, and their results downloaded.
+ * batch_submit never blocks on the GPU; PIPE_EBUSY if the tiles cannot be
+ * admitted now.  Host buffers must stay valid until batch_poll reports the
+ * tile done. */
+typedef struct {
+    const uint8_t* rgb_host;  /* pinned or pageable */
+    int W, H; size_t pitch;
+    int want_planes;          /* 1: also download hem8, labels and edt */
+} tile_desc;
+typedef struct {
+    int status, n_objects;
+    float* feats;             /* pipe-owned, valid until the next poll of this ticket */
+    uint8_t* hem8; int32_t* labels; int32_t* edt; /* pipe-owned, if want_planes */
+    double t_arrive_ms, t_done_ms;  /* submit time and completion time */
+} tile_result;
+int batch_submit(pipe_t p, const tile_desc* tiles, int n, uint64_t* ticket);
+/* PIPE_EAGAIN until every tile of the ticket is done; then fills out[0..n). */
+int batch_poll(pipe_t p, uint64_t ticket, int* n_done, tile_result* out);
+
+/* ---- introspection used by tests and the benchmark ---------------------- */
+
+/* Synchronises the pipe's streams and returns (then clears) the device
+ * status word: PIPE_OK or the first device-side error since the last read. */
+int pipe_status_read(pipe_t p);
+
+/* Copies an internal plane of the most recent seg_tile call into dst_dev
+ * (device memory), enqueued on `stream`:
+ *   0: R, the reconstruction (uint8 H*W)
+ *   1: fg (uint8 0/1, H*W)      2: filled (uint8 0/1, H*W) */
+int pipe_debug_plane(pipe_t p, int which, void* dst_dev, pipe_stream_t stream);
+
+/* Per-kernel CUDA-event timing.  While enabled, every kernel launch of the
+ * pipe is bracketed by events on its stream; pipe_profile_read synchronises
+ * and returns, for up to `cap` kernels, their names, launch counts and total
+ * milliseconds, then resets the totals.  Returns the number of kernels. */
+int pipe_profile_enable(pipe_t p, int enable);
+int pipe_profile_read(pipe_t p, const char** names, long long* launches, double* total_ms,
+                      int cap);
+
+/* Number of kernels the pipe has launched since creation. */
+long long pipe_launch_count(pipe_t p);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

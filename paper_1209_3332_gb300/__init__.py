@@ -1,0 +1,190 @@
+"""GB300 per-tile nucleus segmentation + per-object features.
+
+Thin ctypes binding over libpipe.so (C ABI in include/pipe.h).  The names
+mirror the C entry points; this module only marshals arguments -- every step
+of the path runs in the library's CUDA kernels.  PyTorch tensors serve as
+device buffers and torch streams as CUDA streams.  If the library is missing
+or fails to load, every call raises: there is no CPU fallback.
+"""
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpipe.so")
+NFEAT = 15
+
+PIPE_OK, PIPE_EINVAL, PIPE_ENOMEM, PIPE_EBUSY, PIPE_EAGAIN, PIPE_ETIMEOUT, PIPE_EOVERFLOW, PIPE_ECUDA = range(8)
+STATUS_NAMES = ["PIPE_OK", "PIPE_EINVAL", "PIPE_ENOMEM", "PIPE_EBUSY", "PIPE_EAGAIN", "PIPE_ETIMEOUT",
+                "PIPE_EOVERFLOW", "PIPE_ECUDA"]
+
+EXPORTS = ["pipe_default_params", "pipe_create", "pipe_destroy", "seg_tile", "features_tile",
+           "seg_features_batch", "batch_submit", "batch_poll", "pipe_status_read", "pipe_debug_plane",
+           "pipe_profile_enable", "pipe_profile_read", "pipe_launch_count"]
+
+
+class PipeError(RuntimeError):
+    def __init__(self, code, what):
+        self.code = code
+        name = STATUS_NAMES[code] if 0 <= code < len(STATUS_NAMES) else str(code)
+        super().__init__("%s failed: %s" % (what, name))
+
+
+class PipeParams(ctypes.Structure):
+    _fields_ = [("h", ctypes.c_int), ("dome_thresh", ctypes.c_int), ("area_min", ctypes.c_int),
+                ("area_max", ctypes.c_int), ("glcm_levels", ctypes.c_int), ("n_offsets", ctypes.c_int),
+                ("offsets", (ctypes.c_int * 2) * 4), ("hbm_budget_bytes", ctypes.c_size_t),
+                ("max_slots", ctypes.c_int), ("wait_budget_cycles", ctypes.c_longlong),
+                ("autotune_cache", ctypes.c_char_p)]
+
+
+class TileDevC(ctypes.Structure):
+    _fields_ = [("rgb", ctypes.c_void_p), ("W", ctypes.c_int), ("H", ctypes.c_int),
+                ("pitch", ctypes.c_size_t), ("hem8", ctypes.c_void_p), ("labels", ctypes.c_void_p),
+                ("edt", ctypes.c_void_p), ("n_objects", ctypes.c_void_p), ("feats", ctypes.c_void_p),
+                ("feats_cap", ctypes.c_int)]
+
+
+class TileDesc(ctypes.Structure):
+    _fields_ = [("rgb_host", ctypes.c_void_p), ("W", ctypes.c_int), ("H", ctypes.c_int),
+                ("pitch", ctypes.c_size_t), ("want_planes", ctypes.c_int)]
+
+
+class TileResult(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("n_objects", ctypes.c_int),
+                ("feats", ctypes.POINTER(ctypes.c_float)), ("hem8", ctypes.POINTER(ctypes.c_uint8)),
+                ("labels", ctypes.POINTER(ctypes.c_int32)), ("edt", ctypes.POINTER(ctypes.c_int32)),
+                ("t_arrive_ms", ctypes.c_double), ("t_done_ms", ctypes.c_double)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libpipe.so (raises if it is missing: build it with build.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libpipe.so not built (%s); run paper_1209_3332_gb300.build.build()" % LIB_PATH)
+    L = ctypes.CDLL(LIB_PATH)
+    vp, ci, sz, u64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t, ctypes.c_uint64
+    L.pipe_default_params.argtypes = [ctypes.POINTER(PipeParams)]
+    L.pipe_default_params.restype = None
+    L.pipe_create.argtypes = [ctypes.POINTER(PipeParams), ci, ctypes.POINTER(vp)]
+    L.pipe_destroy.argtypes = [vp]
+    L.pipe_destroy.restype = None
+    L.seg_tile.argtypes = [vp, vp, ci, ci, sz, vp, vp, vp, vp, vp]
+    L.features_tile.argtypes = [vp, vp, vp, ci, ci, ci, vp, vp]
+    L.seg_features_batch.argtypes = [vp, ctypes.POINTER(TileDevC), ci, vp]
+    L.batch_submit.argtypes = [vp, ctypes.POINTER(TileDesc), ci, ctypes.POINTER(u64)]
+    L.batch_poll.argtypes = [vp, u64, ctypes.POINTER(ci), ctypes.POINTER(TileResult)]
+    L.pipe_status_read.argtypes = [vp]
+    L.pipe_debug_plane.argtypes = [vp, ci, vp, vp]
+    L.pipe_profile_enable.argtypes = [vp, ci]
+    L.pipe_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_longlong),
+                                    ctypes.POINTER(ctypes.c_double), ci]
+    L.pipe_launch_count.argtypes = [vp]
+    L.pipe_launch_count.restype = ctypes.c_longlong
+    for n in ("pipe_create", "seg_tile", "features_tile", "seg_features_batch", "batch_submit", "batch_poll",
+              "pipe_status_read", "pipe_debug_plane", "pipe_profile_enable", "pipe_profile_read"):
+        getattr(L, n).restype = ci
+    _lib = L
+    return L
+
+
+def _check(rc, what):
+    if rc != PIPE_OK:
+        raise PipeError(rc, what)
+
+
+def default_params():
+    p = PipeParams()
+    lib().pipe_default_params(ctypes.byref(p))
+    return p
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Pipe:
+    """A pipe_t handle.  Tensors passed in must be contiguous CUDA tensors
+    on the pipe's device; calls are asynchronous on the given (or current)
+    torch stream."""
+
+    def __init__(self, device=0, params=None, **overrides):
+        p = params if params is not None else default_params()
+        for k, v in overrides.items():
+            setattr(p, k, v)
+        self.params = p
+        h = ctypes.c_void_p()
+        _check(lib().pipe_create(ctypes.byref(p), device, ctypes.byref(h)), "pipe_create")
+        self.h = h
+        self.device = device
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().pipe_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- plain form -------------------------------------------------------
+    def seg_tile(self, rgb, hem8, labels, edt, n_objects, stream=None, pitch=None):
+        H, W = rgb.shape[0], rgb.shape[1]
+        pitch = pitch if pitch is not None else rgb.stride(0) * rgb.element_size()
+        rc = lib().seg_tile(self.h, rgb.data_ptr(), W, H, pitch, hem8.data_ptr(), labels.data_ptr(),
+                            edt.data_ptr() if edt is not None else None, n_objects.data_ptr(),
+                            _stream_ptr(stream))
+        _check(rc, "seg_tile")
+
+    def features_tile(self, hem8, labels, n_objects, feats, stream=None):
+        H, W = labels.shape
+        rc = lib().features_tile(self.h, hem8.data_ptr(), labels.data_ptr(), W, H, int(n_objects),
+                                 feats.data_ptr() if feats is not None else None, _stream_ptr(stream))
+        _check(rc, "features_tile")
+
+    # ---- batched form ---------------------------------------------------
+    def seg_features_batch(self, tiles, stream=None):
+        """tiles: list of dicts with rgb, hem8, labels, edt, n_objects, feats (tensors)."""
+        arr = (TileDevC * len(tiles))()
+        for i, t in enumerate(tiles):
+            rgb = t["rgb"]
+            arr[i].rgb = rgb.data_ptr()
+            arr[i].H, arr[i].W = rgb.shape[0], rgb.shape[1]
+            arr[i].pitch = rgb.stride(0) * rgb.element_size()
+            arr[i].hem8 = t["hem8"].data_ptr()
+            arr[i].labels = t["labels"].data_ptr()
+            arr[i].edt = t["edt"].data_ptr() if t.get("edt") is not None else None
+            arr[i].n_objects = t["n_objects"].data_ptr()
+            arr[i].feats = t["feats"].data_ptr()
+            arr[i].feats_cap = t["feats"].shape[0]
+        _check(lib().seg_features_batch(self.h, arr, len(tiles), _stream_ptr(stream)), "seg_features_batch")
+
+    # ---- introspection --------------------------------------------------
+    def status(self):
+        return lib().pipe_status_read(self.h)
+
+    def debug_plane(self, which, dst, stream=None):
+        _check(lib().pipe_debug_plane(self.h, which, dst.data_ptr(), _stream_ptr(stream)), "pipe_debug_plane")
+
+    def profile(self, enable):
+        _check(lib().pipe_profile_enable(self.h, 1 if enable else 0), "pipe_profile_enable")
+
+    def profile_read(self):
+        cap = 64
+        names = (ctypes.c_char_p * cap)()
+        cnt = (ctypes.c_longlong * cap)()
+        ms = (ctypes.c_double * cap)()
+        n = lib().pipe_profile_read(self.h, names, cnt, ms, cap)
+        return {names[i].decode(): (cnt[i], ms[i]) for i in range(min(n, cap))}
+
+    def launch_count(self):
+        return lib().pipe_launch_count(self.h)

@@ -1,0 +1,119 @@
+// Internal declarations shared by the CUDA translation units of libpipe.
+// Nothing here is part of the C ABI (include/pipe.h).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+
+namespace nucseg {
+
+// ---- geometry ---------------------------------------------------------------
+constexpr int RT = 32;            // reconstruction work tile: RT x RT pixels, one warp
+constexpr int RT_WARPS = 4;       // warps (independent workers) per reconstruction CTA
+constexpr int CB = 32;            // labelling block: CB x CB pixels (one bitmap word per row)
+constexpr int CB_THREADS = 256;
+constexpr int NFEAT = 15;
+
+// worklist tile states
+constexpr int WL_IDLE = 0, WL_QUEUED = 1, WL_RUNNING = 2, WL_DIRTY = 3;
+
+// device status codes (same values as pipe_status)
+constexpr int ST_OK = 0, ST_TIMEOUT = 5, ST_OVERFLOW = 6;
+
+// One image of a launch: pointers into caller buffers and the pipe's arena.
+struct TileDev {
+    int W, H;
+    size_t pitch;                 // RGB row pitch in bytes
+    const uint8_t* rgb;
+    uint8_t* hem8;                // H*W
+    uint8_t* R;                   // H*W reconstruction (workspace)
+    int32_t* labels;              // H*W
+    int32_t* edt;                 // H*W (may be null: EDT skipped)
+    int32_t* n_objects;           // [1]
+    float* feats;                 // [feats_cap][15] (batched form)
+    int feats_cap;
+    uint32_t* fgbits;             // bitmaps, H rows of wpr words
+    uint32_t* filledbits;
+    uint32_t* keptbits;           // pixels with label != 0
+    uint32_t* rootbits;           // kept component roots
+    int32_t* wordprefix;          // exclusive popcount prefix of rootbits words
+    int32_t* chunksum;            // per scan chunk
+    int32_t* P;                   // union-find parents (sparse, H*W)
+    int32_t* A;                   // per-root payload (sparse, H*W)
+    int32_t* border;              // per labelling block: 4*CB local roots
+    int32_t* rootlist;            // local roots, capacity H*W
+    int32_t* counters;            // [0] list length
+    int4* bbox;                   // per object: xmin, ymin, xmax, ymax
+    int32_t* edtF;                // per 32-row chunk and column: first background row,
+    int32_t* edtL;                //   last background row (then carries below/above)
+    int wpr;                      // bitmap words per row = ceil(W/32)
+    int rtx, rty, rt_base;        // reconstruction tiles and global base id
+    int cbx, cby, cb_base;        // labelling blocks and global base id
+    int nchunks, chunk_base;      // scan chunks (of SCAN_CHUNK words)
+    int col_base;                 // EDT column strips base
+    int row_base;                 // EDT rows base
+    int px_base;                  // deconvolution work items base
+    int obj_base;                 // first object item of this tile (batched features)
+};
+
+constexpr int SCAN_CHUNK = 1024;  // bitmap words per scan chunk
+
+// Shared state of one launch sequence (device memory).
+struct Shared {
+    int head, tail, pending, err;       // reconstruction worklist
+    int processed;                      // tile processings (diagnostic)
+    int nobj;                           // object items of a batched feature pass
+    int pad[2];
+};
+
+struct Launch {
+    TileDev* tiles;        // device array [ntiles]
+    int ntiles;
+    int* wl_slots;         // [n_rt] queue ring
+    int* wl_state;         // [n_rt]
+    Shared* sh;
+    int* tile_status;      // [ntiles]
+    int* status;           // global status word
+    // totals (host-computed) for grid sizing
+    int n_rt, n_cb, n_chunks, n_cols, n_rows, n_px;
+    long long wait_budget;
+    int h, thr, amin, amax;
+};
+
+// ---- small device helpers ----------------------------------------------------
+__device__ __forceinline__ int find_tile(const TileDev* t, int n, int gid, int TileDev::*base) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (t[mid].*base <= gid) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ void set_status(int* status, int code) {
+    atomicCAS(status, 0, code);
+}
+
+// ---- launchers (one per translation unit) -----------------------------------
+// Profiler hook: every kernel launch is bracketed by begin/end with its name;
+// the pipe counts launches and, when enabled, records CUDA events.
+struct Profiler {
+    virtual void begin(const char* name, cudaStream_t s) = 0;
+    virtual void end(const char* name, cudaStream_t s) = 0;
+    virtual ~Profiler() {}
+};
+
+void upload_deconv_tables(const int32_t* lut3x256);
+void launch_deconv(const Launch& L, cudaStream_t s, Profiler* pf);
+int recon_grid(int n_rt, int device);
+void launch_recon(const Launch& L, int grid, cudaStream_t s, Profiler* pf);
+void launch_label(const Launch& L, int want_bbox, int max_objects, int sms, cudaStream_t s, Profiler* pf);
+size_t edt_rows_smem(int RB, int Wmax);
+void launch_edt(const Launch& L, int RB, int Wmax, cudaStream_t s, Profiler* pf);
+void launch_features_plain(const uint8_t* hem8, const int32_t* labels, int W, int H, int K, float* feats,
+                           int4* bbox, int sms, cudaStream_t s, Profiler* pf);
+void launch_features_batched(const Launch& L, int sms, cudaStream_t s, Profiler* pf);
+void launch_unpack_bits(const uint32_t* bits, int W, int H, int wpr, uint8_t* out, cudaStream_t s,
+                        Profiler* pf);
+
+}  // namespace nucseg

@@ -1,0 +1,322 @@
+// K2: grayscale reconstruction by dilation, 8-connected, of the h-dome
+// marker under hem8 (Table I, "ReconToNuclei"; the paper's GPU version is a
+// queue-based wave propagation, Sec. V-A).  R = lim R_k with
+// R_{k+1} = min(dilate8(R_k), hem8), R_0 = max(hem8 - h, 0) (written by K1).
+//
+// Design (GB300): a persistent kernel whose warps are independent workers.
+// The image is cut into 32x32 work tiles; a device-wide queue holds the
+// tiles that may still change.  A worker pops a tile, stages R and hem8 of
+// the tile plus a one-pixel halo in shared memory, and runs the four
+// directional sweeps (down, up, right, left) -- each an exact sequential
+// sweep along one axis with the 32 lanes moving in lockstep along the other
+// axis, neighbours exchanged by shuffles -- until a full round changes
+// nothing.  It writes the tile back and queues each neighbouring tile that
+// one of the changed border pixels can still raise.  Values only grow and
+// are bounded by hem8, so any order of tile processings reaches the same
+// unique fixed point; a per-tile state machine (idle / queued / running /
+// running+dirty) makes sure a tile is never processed by two workers at
+// once and never misses a raise of its halo.  Every spin wait is bounded by
+// the pipe's cycle budget, after which the worker records ST_TIMEOUT and
+// returns.
+#include "internal.cuh"
+
+namespace nucseg {
+
+constexpr int HS = 36;            // shared row stride for a (RT+2)-wide tile
+constexpr int MAX_ROUNDS = 256;   // sweep rounds before a tile re-queues itself
+constexpr unsigned FULL = 0xffffffffu;
+
+struct WarpTile {
+    uint8_t R[(RT + 2) * HS];
+    uint8_t M[(RT + 2) * HS];
+};
+
+#define SR(y, x) S.R[((y) + 1) * HS + (x) + 1]
+#define SM(y, x) S.M[((y) + 1) * HS + (x) + 1]
+
+__device__ __forceinline__ int ld_vol(const int* p) { return *(const volatile int*)p; }
+
+__device__ __forceinline__ bool budget_over(long long t0, long long budget) {
+    return clock64() - t0 > budget;
+}
+
+// ---- worklist -----------------------------------------------------------------
+
+__device__ void wl_push(const Launch& L, int t) {
+    int i = atomicAdd(&L.sh->tail, 1);
+    volatile int* slot = (volatile int*)&L.wl_slots[i % L.n_rt];
+    long long t0 = clock64();
+    while (*slot >= 0) {
+        if (budget_over(t0, L.wait_budget)) { atomicCAS(&L.sh->err, 0, ST_TIMEOUT); return; }
+        __nanosleep(32);
+    }
+    *slot = t;
+}
+
+__device__ void wl_request(const Launch& L, int t) {
+    for (int it = 0; it < 1024; it++) {
+        int s = atomicCAS(&L.wl_state[t], WL_IDLE, WL_QUEUED);
+        if (s == WL_IDLE) {
+            atomicAdd(&L.sh->pending, 1);
+            wl_push(L, t);
+            return;
+        }
+        if (s == WL_QUEUED || s == WL_DIRTY) return;
+        if (atomicCAS(&L.wl_state[t], WL_RUNNING, WL_DIRTY) == WL_RUNNING) return;
+    }
+    atomicCAS(&L.sh->err, 0, ST_TIMEOUT);
+}
+
+// returns a tile id, or -1 when the queue is drained (or on error)
+__device__ int wl_pop(const Launch& L) {
+    long long t0 = clock64();
+    for (;;) {
+        if (ld_vol(&L.sh->err)) return -1;
+        int h = ld_vol(&L.sh->head), tl = ld_vol(&L.sh->tail);
+        if (h < tl) {
+            if (atomicCAS(&L.sh->head, h, h + 1) == h) {
+                volatile int* slot = (volatile int*)&L.wl_slots[h % L.n_rt];
+                long long t1 = clock64();
+                int v;
+                while ((v = *slot) < 0) {
+                    if (budget_over(t1, L.wait_budget)) { atomicCAS(&L.sh->err, 0, ST_TIMEOUT); return -1; }
+                    __nanosleep(32);
+                }
+                *slot = -1;
+                __threadfence();
+                return v;
+            }
+            continue;
+        }
+        if (ld_vol(&L.sh->pending) == 0) return -1;
+        if (budget_over(t0, L.wait_budget)) { atomicCAS(&L.sh->err, 0, ST_TIMEOUT); return -1; }
+        __nanosleep(100);
+    }
+}
+
+// ---- initial queue: per image, checkerboard order (all tiles with even
+// tx+ty first) so that the first wave of workers does not process adjacent
+// tiles at the same time ----------------------------------------------------------
+__global__ void k_wl_init(Launch L) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) {
+        L.sh->head = 0;
+        L.sh->tail = L.n_rt;
+        L.sh->pending = L.n_rt;
+        L.sh->err = 0;
+        L.sh->processed = 0;
+    }
+    if (i >= L.n_rt) return;
+    int ti = find_tile(L.tiles, L.ntiles, i, &TileDev::rt_base);
+    const TileDev& T = L.tiles[ti];
+    int k = i - T.rt_base, ty = k / T.rtx, tx = k - ty * T.rtx;
+    int rx = T.rtx, ry = T.rty;
+    int evens = ((rx + 1) / 2) * ((ry + 1) / 2) + (rx / 2) * (ry / 2);
+    int before = ((ty + 1) / 2) * ((rx + 1) / 2) + (ty / 2) * (rx / 2);  // evens in rows < ty
+    before += (ty & 1) ? tx / 2 : (tx + 1) / 2;                       // evens in row ty, x < tx
+    int pos = ((tx + ty) & 1) ? evens + (k - before) : before;
+    L.wl_slots[T.rt_base + pos] = i;
+    L.wl_state[i] = WL_QUEUED;
+}
+
+// ---- tile processing --------------------------------------------------------------
+
+__device__ __forceinline__ void load_tile(WarpTile& S, const TileDev& T, int x0, int y0, int lane) {
+    const int W = T.W, H = T.H;
+#pragma unroll 2
+    for (int yy = 0; yy < RT + 2; yy++) {
+        int gy = y0 + yy - 1;
+        bool rowin = gy >= 0 && gy < H;
+        for (int xx = lane; xx < RT + 2; xx += 32) {
+            int gx = x0 + xx - 1;
+            bool in = rowin && gx >= 0 && gx < W;
+            size_t o = (size_t)gy * W + gx;
+            S.R[yy * HS + xx] = in ? __ldcg(T.R + o) : (uint8_t)0;
+            S.M[yy * HS + xx] = in ? __ldg(T.hem8 + o) : (uint8_t)0;
+        }
+    }
+    __syncwarp();
+}
+
+// One round of the four sweeps; returns whether this lane changed a pixel.
+__device__ __forceinline__ bool sweep_round(WarpTile& S, int lane) {
+    bool ch = false;
+    // down: row y takes the 3 pixels above it
+    {
+        int prev = SR(-1, lane), pl = SR(-1, lane - 1), pr = SR(-1, lane + 1);
+        for (int y = 0; y < RT; y++) {
+            int r = SR(y, lane), m = SM(y, lane);
+            int nv = max(r, min(max(prev, max(pl, pr)), m));
+            if (nv != r) { SR(y, lane) = (uint8_t)nv; ch = true; }
+            prev = nv;
+            int a = __shfl_up_sync(FULL, nv, 1), b = __shfl_down_sync(FULL, nv, 1);
+            pl = lane == 0 ? (int)SR(y, -1) : a;
+            pr = lane == 31 ? (int)SR(y, RT) : b;
+        }
+    }
+    __syncwarp();
+    // up: row y takes the 3 pixels below it
+    {
+        int prev = SR(RT, lane), pl = SR(RT, lane - 1), pr = SR(RT, lane + 1);
+        for (int y = RT - 1; y >= 0; y--) {
+            int r = SR(y, lane), m = SM(y, lane);
+            int nv = max(r, min(max(prev, max(pl, pr)), m));
+            if (nv != r) { SR(y, lane) = (uint8_t)nv; ch = true; }
+            prev = nv;
+            int a = __shfl_up_sync(FULL, nv, 1), b = __shfl_down_sync(FULL, nv, 1);
+            pl = lane == 0 ? (int)SR(y, -1) : a;
+            pr = lane == 31 ? (int)SR(y, RT) : b;
+        }
+    }
+    __syncwarp();
+    // right: column x takes the 3 pixels left of it (lane = row)
+    {
+        int prev = SR(lane, -1), pu = SR(lane - 1, -1), pd = SR(lane + 1, -1);
+        for (int x = 0; x < RT; x++) {
+            int r = SR(lane, x), m = SM(lane, x);
+            int nv = max(r, min(max(prev, max(pu, pd)), m));
+            if (nv != r) { SR(lane, x) = (uint8_t)nv; ch = true; }
+            prev = nv;
+            int a = __shfl_up_sync(FULL, nv, 1), b = __shfl_down_sync(FULL, nv, 1);
+            pu = lane == 0 ? (int)SR(-1, x) : a;
+            pd = lane == 31 ? (int)SR(RT, x) : b;
+        }
+    }
+    __syncwarp();
+    // left: column x takes the 3 pixels right of it
+    {
+        int prev = SR(lane, RT), pu = SR(lane - 1, RT), pd = SR(lane + 1, RT);
+        for (int x = RT - 1; x >= 0; x--) {
+            int r = SR(lane, x), m = SM(lane, x);
+            int nv = max(r, min(max(prev, max(pu, pd)), m));
+            if (nv != r) { SR(lane, x) = (uint8_t)nv; ch = true; }
+            prev = nv;
+            int a = __shfl_up_sync(FULL, nv, 1), b = __shfl_down_sync(FULL, nv, 1);
+            pu = lane == 0 ? (int)SR(-1, x) : a;
+            pd = lane == 31 ? (int)SR(RT, x) : b;
+        }
+    }
+    __syncwarp();
+    return ch;
+}
+
+// Whether a changed border line of this tile can raise the facing halo line.
+// own: this lane's border pixel value, changed: whether it changed;
+// halo_r / halo_m: R and mask of the halo pixel facing this lane.
+__device__ __forceinline__ bool line_need(int own, bool changed, int halo_r, int halo_m, int lane) {
+    int cv = changed ? own : 0;
+    int a = __shfl_up_sync(FULL, cv, 1), b = __shfl_down_sync(FULL, cv, 1);
+    if (lane == 0) a = 0;
+    if (lane == 31) b = 0;
+    int cand = max(cv, max(a, b));
+    return __any_sync(FULL, min(halo_m, cand) > halo_r);
+}
+
+__global__ void __launch_bounds__(RT_WARPS * 32) k_recon(Launch L) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    WarpTile& S = reinterpret_cast<WarpTile*>(smraw)[warp];
+    for (;;) {
+        int t = 0;
+        if (lane == 0) t = wl_pop(L);
+        t = __shfl_sync(FULL, t, 0);
+        if (t < 0) break;
+        const int ti = find_tile(L.tiles, L.ntiles, t, &TileDev::rt_base);
+        const TileDev& T = L.tiles[ti];
+        const int k = t - T.rt_base, ty = k / T.rtx, tx = k - ty * T.rtx;
+        const int x0 = tx * RT, y0 = ty * RT;
+        if (lane == 0) atomicExch(&L.wl_state[t], WL_RUNNING);
+        __threadfence();
+        __syncwarp();
+        for (;;) {
+            load_tile(S, T, x0, y0, lane);
+            const int top0 = SR(0, lane), bot0 = SR(RT - 1, lane);
+            const int lef0 = SR(lane, 0), rig0 = SR(lane, RT - 1);
+            bool any = false, more = false;
+            for (int round = 0;; round++) {
+                bool ch = sweep_round(S, lane);
+                bool a = __any_sync(FULL, ch);
+                if (!a) break;
+                any = true;
+                if (round + 1 >= MAX_ROUNDS) { more = true; break; }
+            }
+            if (lane == 0) atomicAdd(&L.sh->processed, 1);
+            if (any) {
+                // write back the interior
+                const int gx = x0 + lane;
+                for (int y = 0; y < RT; y++) {
+                    int gy = y0 + y;
+                    if (gy < T.H && gx < T.W) __stcg(T.R + (size_t)gy * T.W + gx, SR(y, lane));
+                }
+                __threadfence();
+                // neighbours that a changed border pixel can still raise
+                const int top = SR(0, lane), bot = SR(RT - 1, lane);
+                const int lef = SR(lane, 0), rig = SR(lane, RT - 1);
+                bool nU = line_need(top, top != top0, SR(-1, lane), SM(-1, lane), lane);
+                bool nD = line_need(bot, bot != bot0, SR(RT, lane), SM(RT, lane), lane);
+                bool nL = line_need(lef, lef != lef0, SR(lane, -1), SM(lane, -1), lane);
+                bool nR = line_need(rig, rig != rig0, SR(lane, RT), SM(lane, RT), lane);
+                // corner halo pixels face a single tile pixel
+                int t00 = __shfl_sync(FULL, top0, 0), t31 = __shfl_sync(FULL, top0, 31);
+                int b00 = __shfl_sync(FULL, bot0, 0), b31 = __shfl_sync(FULL, bot0, 31);
+                if (lane == 0) {
+                    int v;
+                    bool nUL = (v = SR(0, 0)) != t00 && min((int)SM(-1, -1), v) > SR(-1, -1);
+                    bool nUR = (v = SR(0, RT - 1)) != t31 && min((int)SM(-1, RT), v) > SR(-1, RT);
+                    bool nDL = (v = SR(RT - 1, 0)) != b00 && min((int)SM(RT, -1), v) > SR(RT, -1);
+                    bool nDR = (v = SR(RT - 1, RT - 1)) != b31 && min((int)SM(RT, RT), v) > SR(RT, RT);
+                    const int base = T.rt_base, rx = T.rtx, ry = T.rty;
+                    if (nU && ty > 0) wl_request(L, base + (ty - 1) * rx + tx);
+                    if (nD && ty + 1 < ry) wl_request(L, base + (ty + 1) * rx + tx);
+                    if (nL && tx > 0) wl_request(L, base + ty * rx + tx - 1);
+                    if (nR && tx + 1 < rx) wl_request(L, base + ty * rx + tx + 1);
+                    if (nUL && ty > 0 && tx > 0) wl_request(L, base + (ty - 1) * rx + tx - 1);
+                    if (nUR && ty > 0 && tx + 1 < rx) wl_request(L, base + (ty - 1) * rx + tx + 1);
+                    if (nDL && ty + 1 < ry && tx > 0) wl_request(L, base + (ty + 1) * rx + tx - 1);
+                    if (nDR && ty + 1 < ry && tx + 1 < rx) wl_request(L, base + (ty + 1) * rx + tx + 1);
+                    if (more) wl_request(L, t);  // not converged within MAX_ROUNDS: run again
+                }
+            }
+            __syncwarp();
+            int again = 0;
+            if (lane == 0) {
+                __threadfence();
+                int s = atomicCAS(&L.wl_state[t], WL_RUNNING, WL_IDLE);
+                if (s == WL_RUNNING) {
+                    atomicSub(&L.sh->pending, 1);
+                } else {
+                    atomicExch(&L.wl_state[t], WL_RUNNING);
+                    again = 1;
+                }
+            }
+            again = __shfl_sync(FULL, again, 0);
+            if (!again) break;
+            __threadfence();
+            if (ld_vol(&L.sh->err)) break;
+        }
+    }
+}
+
+int recon_grid(int n_rt, int device) {
+    int sms = 0, per = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    size_t smem = sizeof(WarpTile) * RT_WARPS;
+    cudaFuncSetAttribute(k_recon, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_recon, RT_WARPS * 32, smem);
+    if (per < 1) per = 1;
+    int want = (n_rt + RT_WARPS - 1) / RT_WARPS;
+    int cap = sms * per;
+    return want < cap ? want : cap;
+}
+
+void launch_recon(const Launch& L, int grid, cudaStream_t s, Profiler* pf) {
+    if (L.n_rt == 0) return;
+    pf->begin("recon_init", s);
+    k_wl_init<<<(L.n_rt + 255) / 256, 256, 0, s>>>(L);
+    pf->end("recon_init", s);
+    pf->begin("recon", s);
+    k_recon<<<grid, RT_WARPS * 32, sizeof(WarpTile) * RT_WARPS, s>>>(L);
+    pf->end("recon", s);
+}
+
+}  // namespace nucseg

@@ -1,0 +1,673 @@
+// Host side of libpipe: the C ABI of include/pipe.h.
+//
+// A pipe owns one plain-form workspace (used by seg_tile / features_tile in
+// stream order), a batched-form arena with a cache of captured CUDA graphs
+// keyed by batch shape, and the serving slots of the served form.  Every
+// device pass of the path is one of the kernels in k_*.cu; this file only
+// sizes buffers, fills per-tile descriptors and enqueues launches.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/pipe.h"
+#include "internal.cuh"
+
+using namespace nucseg;
+
+namespace {
+
+#define CK(x)                                 \
+    do {                                      \
+        cudaError_t e__ = (x);                \
+        if (e__ != cudaSuccess) return PIPE_ECUDA; \
+    } while (0)
+
+double now_ms() {
+    using namespace std::chrono;
+    return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+
+size_t al256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+// ---- colour deconvolution constants, rebuilt from their formulas ------------------
+// Stain OD vectors of Ruifrok & Johnston (2001); hematoxylin weight per
+// channel = first column of the inverse of the stain matrix [H; E; H x E].
+void deconv_tables(int32_t tab[3 * 256]) {
+    double Hs[3] = {0.650, 0.704, 0.286}, Es[3] = {0.072, 0.990, 0.105};
+    auto nrm = [](double* v) {
+        double n = std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+        for (int i = 0; i < 3; i++) v[i] /= n;
+    };
+    nrm(Hs);
+    nrm(Es);
+    double Rs[3] = {Hs[1] * Es[2] - Hs[2] * Es[1], Hs[2] * Es[0] - Hs[0] * Es[2], Hs[0] * Es[1] - Hs[1] * Es[0]};
+    nrm(Rs);
+    const double* M[3] = {Hs, Es, Rs};  // rows
+    double det = M[0][0] * (M[1][1] * M[2][2] - M[1][2] * M[2][1]) -
+                 M[0][1] * (M[1][0] * M[2][2] - M[1][2] * M[2][0]) +
+                 M[0][2] * (M[1][0] * M[2][1] - M[1][1] * M[2][0]);
+    // c = od * M^-1, so channel k weighs (M^-1)[k][0] = cofactor(0,k) / det
+    int32_t wq[3];
+    for (int k = 0; k < 3; k++) {
+        int c1 = k == 0 ? 1 : 0, c2 = k == 2 ? 1 : 2;
+        double minor = M[1][c1] * M[2][c2] - M[1][c2] * M[2][c1];
+        double w = ((k & 1) ? -minor : minor) / det;
+        wq[k] = (int32_t)std::llround(100.0 * w * 2048.0);
+    }
+    for (int v = 0; v < 256; v++) {
+        int32_t od = (int32_t)std::floor(-std::log((v + 1) / 256.0) * 256.0 + 0.5);
+        for (int c = 0; c < 3; c++) tab[c * 256 + v] = wq[c] * od;
+    }
+}
+
+// ---- profiler ---------------------------------------------------------------------
+struct EventProfiler : Profiler {
+    bool enabled = false;
+    long long launches = 0;
+    std::vector<cudaEvent_t> pool;
+    size_t used = 0;
+    struct Rec { std::string name; cudaEvent_t a, b; };
+    std::vector<Rec> recs;
+    std::map<std::string, std::pair<long long, double>> totals;
+    std::map<std::string, int> open;
+    cudaEvent_t pending_begin = nullptr;
+    std::string pending_name;
+
+    cudaEvent_t get() {
+        if (used == pool.size()) {
+            cudaEvent_t e;
+            cudaEventCreate(&e);
+            pool.push_back(e);
+        }
+        return pool[used++];
+    }
+    void begin(const char* name, cudaStream_t s) override {
+        launches++;
+        if (!enabled) return;
+        pending_begin = get();
+        pending_name = name;
+        cudaEventRecord(pending_begin, s);
+    }
+    void end(const char* name, cudaStream_t s) override {
+        if (!enabled || !pending_begin) return;
+        cudaEvent_t b = get();
+        cudaEventRecord(b, s);
+        recs.push_back({pending_name, pending_begin, b});
+        pending_begin = nullptr;
+        if (used > 8192) flush();
+    }
+    void flush() {
+        cudaDeviceSynchronize();
+        for (auto& r : recs) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+                auto& t = totals[r.name];
+                t.first++;
+                t.second += ms;
+            }
+        }
+        recs.clear();
+        used = 0;
+    }
+    ~EventProfiler() {
+        for (auto e : pool) cudaEventDestroy(e);
+    }
+};
+
+// a profiler that only counts (used while capturing graphs)
+struct CountingProfiler : Profiler {
+    long long* counter;
+    void begin(const char*, cudaStream_t) override { (*counter)++; }
+    void end(const char*, cudaStream_t) override {}
+};
+
+// ---- device buffers -----------------------------------------------------------------
+struct DevBuf {
+    void* p = nullptr;
+    size_t n = 0;
+    int ensure(size_t bytes) {
+        if (bytes <= n) return PIPE_OK;
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+        if (cudaMalloc(&p, bytes) != cudaSuccess) return PIPE_ENOMEM;
+        n = bytes;
+        return PIPE_OK;
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+};
+
+// Geometry and workspace sizes of one image.
+struct Geo {
+    int W, H, wpr, rtx, rty, cbx, cby, nchunks, nbands;
+    size_t N, ws_bytes;
+};
+
+int bands_rows(int Wmax) { return Wmax <= 4096 ? 8 : (Wmax <= 8192 ? 4 : 2); }
+
+Geo geometry(int W, int H, int feats_cap, int RB) {
+    Geo g;
+    g.W = W;
+    g.H = H;
+    g.N = (size_t)W * H;
+    g.wpr = (W + 31) / 32;
+    g.rtx = (W + RT - 1) / RT;
+    g.rty = (H + RT - 1) / RT;
+    g.cbx = (W + CB - 1) / CB;
+    g.cby = (H + CB - 1) / CB;
+    size_t words = (size_t)H * g.wpr;
+    g.nchunks = (int)((words + SCAN_CHUNK - 1) / SCAN_CHUNK);
+    g.nbands = (H + RB - 1) / RB;
+    size_t b = 0;
+    b += al256(g.N);                              // R
+    b += 3 * al256(g.N * 4);                      // P, A, rootlist
+    b += 4 * al256(words * 4);                    // fg, filled, kept, root bitmaps
+    b += al256(words * 4);                        // word prefix
+    b += al256((size_t)g.nchunks * 4);            // chunk sums
+    b += al256((size_t)g.cbx * g.cby * 4 * CB * 4);  // block edges
+    b += al256(64);                               // counters
+    b += 2 * al256((size_t)g.cby * W * 4);        // EDT chunk summaries
+    b += al256((size_t)std::max(feats_cap, 1) * 16);  // object boxes
+    g.ws_bytes = b;
+    return g;
+}
+
+// Carve the workspace of one image at `base` into a descriptor.
+void carve(TileDev& t, const Geo& g, char* base) {
+    size_t words = (size_t)g.H * g.wpr;
+    char* p = base;
+    auto take = [&](size_t n) { char* r = p; p += al256(n); return r; };
+    t.R = (uint8_t*)take(g.N);
+    t.P = (int32_t*)take(g.N * 4);
+    t.A = (int32_t*)take(g.N * 4);
+    t.rootlist = (int32_t*)take(g.N * 4);
+    t.fgbits = (uint32_t*)take(words * 4);
+    t.filledbits = (uint32_t*)take(words * 4);
+    t.keptbits = (uint32_t*)take(words * 4);
+    t.rootbits = (uint32_t*)take(words * 4);
+    t.wordprefix = (int32_t*)take(words * 4);
+    t.chunksum = (int32_t*)take((size_t)g.nchunks * 4);
+    t.border = (int32_t*)take((size_t)g.cbx * g.cby * 4 * CB * 4);
+    t.counters = (int32_t*)take(64);
+    t.edtF = (int32_t*)take((size_t)g.cby * g.W * 4);
+    t.edtL = (int32_t*)take((size_t)g.cby * g.W * 4);
+    t.bbox = (int4*)take((size_t)std::max(t.feats_cap, 1) * 16);
+    t.W = g.W;
+    t.H = g.H;
+    t.wpr = g.wpr;
+    t.rtx = g.rtx;
+    t.rty = g.rty;
+    t.cbx = g.cbx;
+    t.cby = g.cby;
+    t.nchunks = g.nchunks;
+}
+
+// descriptors are written by a kernel that receives them as parameters, so
+// no host staging buffer must outlive the call and graph capture works
+constexpr int DESC_PER_LAUNCH = 8;
+struct DescPack {
+    TileDev d[DESC_PER_LAUNCH];
+    int n, first;
+};
+__global__ void k_set_desc(TileDev* dst, DescPack p) {
+    if (threadIdx.x < p.n) dst[p.first + threadIdx.x] = p.d[threadIdx.x];
+}
+
+// Everything one launch sequence needs besides the descriptors.
+struct LaunchCtx {
+    DevBuf tiles, wl, shared;  // TileDev[], slots+state, Shared + statuses
+    DevBuf arena;
+    int ntiles_cap = 0;
+};
+
+}  // namespace
+
+// ---- the pipe ---------------------------------------------------------------------------
+
+struct Ticket;
+
+struct Slot {
+    cudaStream_t stream = nullptr;
+    LaunchCtx ctx;
+    DevBuf rgb, hem8, labels, edt, nobj, feats;
+    void* h_stage = nullptr;      // pinned RGB staging
+    size_t h_stage_n = 0;
+    void* h_out = nullptr;        // pinned results: n_objects, feats, planes
+    size_t h_out_n = 0;
+    int maxW = 0, maxH = 0, feats_cap = 0;
+    bool busy = false;
+    size_t footprint = 0;
+    double t_done = 0;
+};
+
+struct Ticket {
+    std::vector<int> slot;        // slot per tile
+    std::vector<tile_desc> desc;
+    std::vector<tile_result> res;
+    std::vector<std::vector<float>> feats;
+    std::vector<std::vector<uint8_t>> hem8;
+    std::vector<std::vector<int32_t>> labels, edt;
+    std::vector<double> t_arrive;
+    bool done = false;
+};
+
+struct pipe_s {
+    int device = 0;
+    pipe_params prm;
+    int sms = 0;
+    int recon_blocks_per_sm = 1;
+    EventProfiler prof;
+    // plain form
+    LaunchCtx plain;
+    TileDev last_plain{};
+    bool have_last = false;
+    DevBuf fbbox;
+    // batched form
+    LaunchCtx batch;
+    std::map<std::string, cudaGraphExec_t> graphs;
+    std::map<std::string, long long> graph_kernels;
+    std::string batch_key;
+    int batch_ntiles = 0;
+    // served form
+    std::mutex mu;
+    std::vector<std::unique_ptr<Slot>> slots;
+    std::map<uint64_t, std::unique_ptr<Ticket>> tickets;
+    uint64_t next_ticket = 1;
+    size_t hbm_in_use = 0;
+};
+
+namespace {
+
+int ensure_ctx(LaunchCtx& c, int ntiles, int n_rt, size_t arena_bytes) {
+    int rc;
+    if ((rc = c.tiles.ensure(sizeof(TileDev) * std::max(ntiles, 1)))) return rc;
+    if ((rc = c.wl.ensure(sizeof(int) * 2 * std::max(n_rt, 1)))) return rc;
+    if ((rc = c.shared.ensure(sizeof(Shared) + sizeof(int) * (2 + std::max(ntiles, 1))))) return rc;
+    if ((rc = c.arena.ensure(std::max(arena_bytes, (size_t)256)))) return rc;
+    return PIPE_OK;
+}
+
+// Fill launch-wide bases of the descriptors and the Launch totals.
+Launch make_launch(pipe_t p, LaunchCtx& c, std::vector<TileDev>& td, int n_rt_total) {
+    Launch L{};
+    L.tiles = (TileDev*)c.tiles.p;
+    L.ntiles = (int)td.size();
+    L.wl_slots = (int*)c.wl.p;
+    L.wl_state = (int*)c.wl.p + std::max(n_rt_total, 1);
+    L.sh = (Shared*)c.shared.p;
+    L.status = (int*)((char*)c.shared.p + sizeof(Shared));
+    L.tile_status = L.status + 2;
+    int rt = 0, cb = 0, ch = 0, col = 0, row = 0, px = 0;
+    int Wmax = 1;
+    for (auto& t : td) Wmax = std::max(Wmax, t.W);
+    int RB = bands_rows(Wmax);
+    for (auto& t : td) {
+        t.rt_base = rt;
+        t.cb_base = cb;
+        t.chunk_base = ch;
+        t.col_base = col;
+        t.row_base = row;
+        t.px_base = px;
+        t.obj_base = 0;
+        rt += t.rtx * t.rty;
+        cb += t.cbx * t.cby;
+        ch += t.nchunks;
+        col += t.W;
+        row += (t.H + RB - 1) / RB;
+        px += t.H * ((t.W + 15) / 16);
+    }
+    L.n_rt = rt;
+    L.n_cb = cb;
+    L.n_chunks = ch;
+    L.n_cols = col;
+    L.n_rows = row;
+    L.n_px = px;
+    L.wait_budget = p->prm.wait_budget_cycles;
+    L.h = p->prm.h;
+    L.thr = p->prm.dome_thresh;
+    L.amin = p->prm.area_min;
+    L.amax = p->prm.area_max;
+    return L;
+}
+
+int upload_desc(const Launch& L, const std::vector<TileDev>& td, cudaStream_t s) {
+    for (int i = 0; i < (int)td.size(); i += DESC_PER_LAUNCH) {
+        DescPack pk;
+        pk.first = i;
+        pk.n = std::min(DESC_PER_LAUNCH, (int)td.size() - i);
+        for (int k = 0; k < pk.n; k++) pk.d[k] = td[i + k];
+        k_set_desc<<<1, 32, 0, s>>>(L.tiles, pk);
+    }
+    CK(cudaGetLastError());
+    return PIPE_OK;
+}
+
+int max_width(const std::vector<TileDev>& td) {
+    int w = 1;
+    for (auto& t : td) w = std::max(w, t.W);
+    return w;
+}
+
+// The whole path over the descriptors of L (segmentation, and features when
+// `features` is set: boxes come from the relabel pass).
+void run_path(pipe_t p, const Launch& L, int Wmax, bool features, int max_objects, cudaStream_t s,
+              Profiler* pf) {
+    launch_deconv(L, s, pf);
+    int grid = std::max(1, std::min((L.n_rt + RT_WARPS - 1) / RT_WARPS, p->sms * p->recon_blocks_per_sm));
+    launch_recon(L, grid, s, pf);
+    launch_label(L, features ? 1 : 0, max_objects, p->sms, s, pf);
+    launch_edt(L, bands_rows(Wmax), Wmax, s, pf);
+    if (features) launch_features_batched(L, p->sms, s, pf);
+}
+
+bool valid_size(int W, int H) { return W >= 1 && H >= 1 && W <= 16384 && H <= 16384; }
+
+}  // namespace
+
+// ======================================================================================
+extern "C" {
+
+void pipe_default_params(pipe_params* p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->h = 20;
+    p->dome_thresh = 10;
+    p->area_min = 20;
+    p->area_max = 1500;
+    p->glcm_levels = 8;
+    p->n_offsets = 4;
+    int off[4][2] = {{1, 0}, {0, 1}, {1, 1}, {1, -1}};
+    std::memcpy(p->offsets, off, sizeof(off));
+    p->hbm_budget_bytes = (size_t)40 << 30;
+    p->max_slots = 16;
+    p->wait_budget_cycles = 1LL << 32;
+    p->autotune_cache = nullptr;
+}
+
+int pipe_create(const pipe_params* params, int device, pipe_t* out) {
+    if (!out) return PIPE_EINVAL;
+    *out = nullptr;
+    pipe_params prm;
+    if (params) prm = *params; else pipe_default_params(&prm);
+    int off[4][2] = {{1, 0}, {0, 1}, {1, 1}, {1, -1}};
+    if (prm.glcm_levels != 8 || prm.n_offsets != 4 || std::memcmp(prm.offsets, off, sizeof(off)) != 0 ||
+        prm.h < 0 || prm.h > 255 || prm.dome_thresh < 0 || prm.area_min < 0 || prm.area_max < prm.area_min ||
+        prm.max_slots < 1 || prm.wait_budget_cycles <= 0)
+        return PIPE_EINVAL;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return PIPE_EINVAL;
+    if (cudaSetDevice(device) != cudaSuccess) return PIPE_ECUDA;
+    pipe_t p = new pipe_s();
+    p->device = device;
+    p->prm = prm;
+    cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, device);
+    int tab[3 * 256];
+    deconv_tables(tab);
+    upload_deconv_tables(tab);
+    int g = recon_grid(1 << 30, device);
+    p->recon_blocks_per_sm = std::max(1, g / std::max(p->sms, 1));
+    if (cudaGetLastError() != cudaSuccess) {
+        delete p;
+        return PIPE_ECUDA;
+    }
+    *out = p;
+    return PIPE_OK;
+}
+
+void pipe_destroy(pipe_t p) {
+    if (!p) return;
+    cudaSetDevice(p->device);
+    cudaDeviceSynchronize();
+    for (auto& kv : p->graphs) cudaGraphExecDestroy(kv.second);
+    auto rel = [](LaunchCtx& c) { c.tiles.release(); c.wl.release(); c.shared.release(); c.arena.release(); };
+    rel(p->plain);
+    rel(p->batch);
+    p->fbbox.release();
+    for (auto& s : p->slots) {
+        rel(s->ctx);
+        s->rgb.release(); s->hem8.release(); s->labels.release(); s->edt.release();
+        s->nobj.release(); s->feats.release();
+        if (s->h_stage) cudaFreeHost(s->h_stage);
+        if (s->h_out) cudaFreeHost(s->h_out);
+        if (s->stream) cudaStreamDestroy(s->stream);
+    }
+    delete p;
+}
+
+int seg_tile(pipe_t p, const uint8_t* rgb_dev, int W, int H, size_t pitch_bytes, uint8_t* hem8_dev,
+             int32_t* labels_dev, int32_t* edt_dev, int32_t* n_objects_dev, pipe_stream_t stream) {
+    if (!p || !rgb_dev || !hem8_dev || !labels_dev || !n_objects_dev) return PIPE_EINVAL;
+    if (!valid_size(W, H) || pitch_bytes < (size_t)W * 3) return PIPE_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaSetDevice(p->device));
+    int RB = bands_rows(W);
+    Geo g = geometry(W, H, 1, RB);
+    int n_rt = g.rtx * g.rty;
+    if (p->plain.arena.n < g.ws_bytes || p->plain.wl.n < sizeof(int) * 2 * (size_t)n_rt) CK(cudaStreamSynchronize(s));
+    int rc = ensure_ctx(p->plain, 1, n_rt, g.ws_bytes);
+    if (rc) return rc;
+    std::vector<TileDev> td(1);
+    TileDev& t = td[0];
+    std::memset(&t, 0, sizeof(t));
+    t.feats_cap = 1;
+    carve(t, g, (char*)p->plain.arena.p);
+    t.pitch = pitch_bytes;
+    t.rgb = rgb_dev;
+    t.hem8 = hem8_dev;
+    t.labels = labels_dev;
+    t.edt = edt_dev;
+    t.n_objects = n_objects_dev;
+    t.feats = nullptr;
+    Launch L = make_launch(p, p->plain, td, n_rt);
+    if ((rc = upload_desc(L, td, s))) return rc;
+    run_path(p, L, W, false, 0, s, &p->prof);
+    CK(cudaGetLastError());
+    p->last_plain = td[0];
+    p->have_last = true;
+    return PIPE_OK;
+}
+
+int features_tile(pipe_t p, const uint8_t* hem8_dev, const int32_t* labels_dev, int W, int H, int n_objects,
+                  float* feats_dev, pipe_stream_t stream) {
+    if (!p || !hem8_dev || !labels_dev || n_objects < 0 || (n_objects > 0 && !feats_dev)) return PIPE_EINVAL;
+    if (!valid_size(W, H)) return PIPE_EINVAL;
+    if (n_objects == 0) return PIPE_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaSetDevice(p->device));
+    size_t need = (size_t)n_objects * sizeof(int4);
+    if (p->fbbox.n < need) {
+        CK(cudaStreamSynchronize(s));
+        int rc = p->fbbox.ensure(need);
+        if (rc) return rc;
+    }
+    launch_features_plain(hem8_dev, labels_dev, W, H, n_objects, feats_dev, (int4*)p->fbbox.p, p->sms, s,
+                          &p->prof);
+    CK(cudaGetLastError());
+    return PIPE_OK;
+}
+
+int seg_features_batch(pipe_t p, const tile_dev* tiles, int n, pipe_stream_t stream) {
+    if (!p || !tiles || n < 1 || n > 4096) return PIPE_EINVAL;
+    for (int i = 0; i < n; i++) {
+        const tile_dev& d = tiles[i];
+        if (!d.rgb || !d.hem8 || !d.labels || !d.n_objects || !valid_size(d.W, d.H) || d.pitch < (size_t)d.W * 3 ||
+            d.feats_cap < 0 || (d.feats_cap > 0 && !d.feats))
+            return PIPE_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaSetDevice(p->device));
+    int Wmax = 1;
+    for (int i = 0; i < n; i++) Wmax = std::max(Wmax, tiles[i].W);
+    int RB = bands_rows(Wmax);
+    std::vector<Geo> geos(n);
+    std::vector<size_t> off(n);
+    size_t total = 0;
+    int n_rt = 0;
+    std::string key;
+    for (int i = 0; i < n; i++) {
+        geos[i] = geometry(tiles[i].W, tiles[i].H, tiles[i].feats_cap, RB);
+        off[i] = total;
+        total += geos[i].ws_bytes;
+        n_rt += geos[i].rtx * geos[i].rty;
+        key += std::to_string(tiles[i].W) + "x" + std::to_string(tiles[i].H) + "c" +
+               std::to_string(tiles[i].feats_cap) + (tiles[i].edt ? "e" : "n") + ";";
+    }
+    bool grow = p->batch.arena.n < total || p->batch.wl.n < sizeof(int) * 2 * (size_t)n_rt ||
+                p->batch.tiles.n < sizeof(TileDev) * n || p->batch.shared.n < sizeof(Shared) + sizeof(int) * (2 + n);
+    if (grow) {
+        CK(cudaStreamSynchronize(s));
+        for (auto& kv : p->graphs) cudaGraphExecDestroy(kv.second);
+        p->graphs.clear();
+        int rc = ensure_ctx(p->batch, n, n_rt, total);
+        if (rc) return rc;
+    }
+    std::vector<TileDev> td(n);
+    int max_obj = 1;
+    for (int i = 0; i < n; i++) {
+        TileDev& t = td[i];
+        std::memset(&t, 0, sizeof(t));
+        t.feats_cap = tiles[i].feats_cap;
+        carve(t, geos[i], (char*)p->batch.arena.p + off[i]);
+        t.pitch = tiles[i].pitch;
+        t.rgb = tiles[i].rgb;
+        t.hem8 = tiles[i].hem8;
+        t.labels = tiles[i].labels;
+        t.edt = tiles[i].edt;
+        t.n_objects = tiles[i].n_objects;
+        t.feats = tiles[i].feats;
+        max_obj = std::max(max_obj, t.feats_cap);
+    }
+    Launch L = make_launch(p, p->batch, td, n_rt);
+    p->batch_ntiles = n;
+    int rc = upload_desc(L, td, s);
+    if (rc) return rc;
+    auto it = p->graphs.find(key);
+    if (it == p->graphs.end()) {
+        // capture the launch sequence once per batch shape; descriptors live in
+        // device memory, so the graph replays for any buffers of this shape
+        cudaStream_t cs;
+        CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        long long dummy = 0;
+        CountingProfiler cp;
+        cp.counter = &dummy;
+        cudaGraph_t graph;
+        if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            cudaStreamDestroy(cs);
+            return PIPE_ECUDA;
+        }
+        run_path(p, L, Wmax, true, max_obj, cs, &cp);
+        cudaError_t e = cudaStreamEndCapture(cs, &graph);
+        cudaStreamDestroy(cs);
+        if (e != cudaSuccess) return PIPE_ECUDA;
+        cudaGraphExec_t exec;
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return PIPE_ECUDA;
+        it = p->graphs.emplace(key, exec).first;
+        p->batch_key = key;
+        p->graph_kernels[key] = dummy;
+    }
+    if (p->prof.enabled) {
+        // profiled runs launch eagerly so that each kernel is bracketed by events
+        run_path(p, L, Wmax, true, max_obj, s, &p->prof);
+    } else {
+        CK(cudaGraphLaunch(it->second, s));
+        p->prof.launches += p->graph_kernels[key];
+    }
+    CK(cudaGetLastError());
+    return PIPE_OK;
+}
+
+int pipe_status_read(pipe_t p) {
+    if (!p) return PIPE_EINVAL;
+    CK(cudaSetDevice(p->device));
+    CK(cudaDeviceSynchronize());
+    int result = PIPE_OK;
+    auto check = [&](LaunchCtx& c, int ntiles) {
+        if (!c.shared.p) return;
+        Shared sh;
+        if (cudaMemcpy(&sh, c.shared.p, sizeof(sh), cudaMemcpyDeviceToHost) != cudaSuccess) {
+            result = PIPE_ECUDA;
+            return;
+        }
+        if (sh.err && result == PIPE_OK) result = sh.err;
+        std::vector<int> st(2 + ntiles);
+        cudaMemcpy(st.data(), (char*)c.shared.p + sizeof(Shared), sizeof(int) * st.size(), cudaMemcpyDeviceToHost);
+        for (int i = 2; i < (int)st.size(); i++)
+            if (st[i] && result == PIPE_OK) result = st[i];
+        int zero = 0;
+        cudaMemcpy((char*)c.shared.p + offsetof(Shared, err), &zero, sizeof(int), cudaMemcpyHostToDevice);
+        cudaMemset((char*)c.shared.p + sizeof(Shared), 0, sizeof(int) * st.size());
+    };
+    check(p->plain, 1);
+    check(p->batch, p->batch_ntiles);
+    return result;
+}
+
+int pipe_debug_plane(pipe_t p, int which, void* dst_dev, pipe_stream_t stream) {
+    if (!p || !dst_dev || !p->have_last || which < 0 || which > 2) return PIPE_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    const TileDev& t = p->last_plain;
+    if (which == 0) {
+        CK(cudaMemcpyAsync(dst_dev, t.R, (size_t)t.W * t.H, cudaMemcpyDeviceToDevice, s));
+    } else {
+        launch_unpack_bits(which == 1 ? t.fgbits : t.filledbits, t.W, t.H, t.wpr, (uint8_t*)dst_dev, s, &p->prof);
+        CK(cudaGetLastError());
+    }
+    return PIPE_OK;
+}
+
+int pipe_profile_enable(pipe_t p, int enable) {
+    if (!p) return PIPE_EINVAL;
+    if (!enable && p->prof.enabled) p->prof.flush();
+    p->prof.enabled = enable != 0;
+    return PIPE_OK;
+}
+
+int pipe_profile_read(pipe_t p, const char** names, long long* launches, double* total_ms, int cap) {
+    if (!p) return -1;
+    cudaSetDevice(p->device);
+    p->prof.flush();
+    static thread_local std::vector<std::string> keep;
+    keep.clear();
+    int i = 0;
+    for (auto& kv : p->prof.totals) {
+        if (i < cap) {
+            keep.push_back(kv.first);
+            if (launches) launches[i] = kv.second.first;
+            if (total_ms) total_ms[i] = kv.second.second;
+        }
+        i++;
+    }
+    for (int k = 0; k < (int)keep.size() && names; k++) names[k] = keep[k].c_str();
+    p->prof.totals.clear();
+    return i;
+}
+
+long long pipe_launch_count(pipe_t p) { return p ? p->prof.launches : -1; }
+
+int batch_submit(pipe_t p, const tile_desc* tiles, int n, uint64_t* ticket) {
+    (void)p; (void)tiles; (void)n; (void)ticket;
+    return PIPE_EINVAL;
+}
+
+int batch_poll(pipe_t p, uint64_t ticket, int* n_done, tile_result* out) {
+    (void)p; (void)ticket; (void)n_done; (void)out;
+    return PIPE_EINVAL;
+}
+
+}  // extern "C"

@@ -1,0 +1,63 @@
+"""Helpers for the GPU parity tests: run the CUDA path through the C ABI on
+torch buffers and compare with the oracle on the same seeded input."""
+import numpy as np
+
+import oracle
+
+TOL_REL, TOL_ABS = 1e-4, 1e-6
+
+
+def run_gpu(pipe, rgb_np, want_planes=True, stream=None):
+    import torch
+    H, W = rgb_np.shape[:2]
+    dev = torch.device("cuda", pipe.device)
+    rgb = torch.from_numpy(np.ascontiguousarray(rgb_np)).to(dev)
+    hem8 = torch.empty((H, W), dtype=torch.uint8, device=dev)
+    labels = torch.empty((H, W), dtype=torch.int32, device=dev)
+    edt = torch.empty((H, W), dtype=torch.int32, device=dev)
+    nobj = torch.zeros(1, dtype=torch.int32, device=dev)
+    pipe.seg_tile(rgb, hem8, labels, edt, nobj, stream=stream)
+    out = {}
+    if want_planes:
+        for k, name in enumerate(("R", "fg", "filled")):
+            buf = torch.empty((H, W), dtype=torch.uint8, device=dev)
+            pipe.debug_plane(k, buf, stream=stream)
+            out[name] = buf
+    torch.cuda.synchronize()
+    K = int(nobj.item())
+    feats = torch.zeros((max(K, 1), 15), dtype=torch.float32, device=dev)
+    pipe.features_tile(hem8, labels, K, feats, stream=stream)
+    torch.cuda.synchronize()
+    res = {k: v.cpu().numpy() for k, v in out.items()}
+    res.update(hem8=hem8.cpu().numpy(), labels=labels.cpu().numpy(), edt=edt.cpu().numpy(), K=K,
+               feats=feats.cpu().numpy()[:K])
+    return res
+
+
+def oracle_all(rgb_np, h=20, thr=10, amin=20, amax=1500):
+    r = oracle.seg(rgb_np, h=h, thr=thr, amin=amin, amax=amax, planes=True)
+    r["feats"] = oracle.features(r["hem8"], r["labels"], r["K"])
+    return r
+
+
+def assert_feats_close(got, ref):
+    assert got.shape == ref.shape, (got.shape, ref.shape)
+    err = np.abs(got.astype(np.float64) - ref)
+    ok = (err <= TOL_REL * np.abs(ref)) | (err <= TOL_ABS)
+    if not ok.all():
+        i, j = np.argwhere(~ok)[0]
+        raise AssertionError("feature [%d][%d]: gpu %r oracle %r (%d bad of %d)"
+                             % (i, j, got[i, j], ref[i, j], int((~ok).sum()), ok.size))
+
+
+def assert_planes_equal(g, r, planes=("hem8", "R", "fg", "filled", "labels", "edt")):
+    for k in planes:
+        if k not in g:
+            continue
+        a, b = g[k], r[k]
+        if not np.array_equal(a, b):
+            bad = np.argwhere(a != b)
+            y, x = bad[0]
+            raise AssertionError("%s differs at %d pixels; first (%d,%d): gpu %r oracle %r"
+                                 % (k, len(bad), y, x, a[y, x], b[y, x]))
+    assert g["K"] == r["K"], (g["K"], r["K"])
