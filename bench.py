@@ -246,6 +246,14 @@ def run_ours(args, world, rank, local):
     ms_step = ms_total / args.steps
     value = world * B * args.steps / (ms_total / 1000.0)
 
+    if args.no_extra:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": world * B * args.steps / (ms_total / 1000.0),
+                              "unit": "tiles/s", "ms_per_step": ms_step, "gpu_launches": int(launches),
+                              "partial": "timed region only"}), flush=True)
+        pipe.close()
+        return
+
     # per-kernel times (CUDA events around every launch, same stream), a
     # second pass over the same steps
     pipe.profile(True)
@@ -324,6 +332,9 @@ def run_ours(args, world, rank, local):
     path_gbs = PATH_BYTES_PER_PX * H * W * value / world / 1e9
     line["path_roofline"] = {"bytes_per_tile": PATH_BYTES_PER_PX * H * W, "achieved": path_gbs, "peak": peak,
                              "unit": "GB/s", "frac": path_gbs / peak}
+    if args.form == "plain":
+        step_plain()
+        line["recon_tile_visits_per_work_tile"] = pipe.recon_visits() / float(((W + 31) // 32) * ((H + 31) // 32))
     line["kernels_ms"] = {k: round(v[1] / max(v[0], 1), 4) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(host[:1])
@@ -340,7 +351,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--form", default="plain", choices=["plain", "batched"])
     ap.add_argument("--batch", type=int, default=8)
-    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="timed region only: skip the per-kernel, end-to-end and CPU legs")
     args = ap.parse_args()
     world, rank, local = dist_setup(args.gpus)
     if args.impl == "reference":

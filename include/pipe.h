@@ -135,12 +135,21 @@ typedef struct {
 } tile_desc;
 typedef struct {
     int status, n_objects;
-    float* feats;             /* pipe-owned, valid until the next poll of this ticket */
+    float* feats;             /* pipe-owned [n_objects][15] */
     uint8_t* hem8; int32_t* labels; int32_t* edt; /* pipe-owned, if want_planes */
-    double t_arrive_ms, t_done_ms;  /* submit time and completion time */
+    double t_arrive_ms, t_done_ms;  /* submit and completion times, ms of CLOCK_MONOTONIC */
 } tile_result;
+/* Admits the n tiles as one group: they are uploaded and processed together
+ * as one batched launch on a context of their own, concurrently with the
+ * groups already in flight.  PIPE_EBUSY (nothing enqueued) when max_slots
+ * contexts are busy or the group would exceed hbm_budget_bytes. */
 int batch_submit(pipe_t p, const tile_desc* tiles, int n, uint64_t* ticket);
-/* PIPE_EAGAIN until every tile of the ticket is done; then fills out[0..n). */
+/* PIPE_EAGAIN (n_done = 0) until every tile of the ticket is done; then
+ * fills out[0..n) and sets n_done = n.  The pipe-owned result arrays of a
+ * completed ticket stay valid until batch_poll is called for a different
+ * ticket (which releases them) or the pipe is destroyed.  A tile whose
+ * object count exceeds the feature capacity min(W*H/20+1, 65536) reports
+ * PIPE_EOVERFLOW with n_objects = K and the first capacity rows. */
 int batch_poll(pipe_t p, uint64_t ticket, int* n_done, tile_result* out);
 
 /* ---- introspection used by tests and the benchmark ---------------------- */
@@ -165,6 +174,11 @@ int pipe_profile_read(pipe_t p, const char** names, long long* launches, double*
 
 /* Number of kernels the pipe has launched since creation. */
 long long pipe_launch_count(pipe_t p);
+
+/* Synchronises the device and returns how many 32x32 work tiles the
+ * reconstruction of the most recent seg_tile call processed (a tile that is
+ * re-queued counts again), or -1 before any call.  Diagnostic only. */
+long long pipe_recon_visits(pipe_t p);
 
 #ifdef __cplusplus
 }

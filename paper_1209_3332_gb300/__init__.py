@@ -19,7 +19,7 @@ STATUS_NAMES = ["PIPE_OK", "PIPE_EINVAL", "PIPE_ENOMEM", "PIPE_EBUSY", "PIPE_EAG
 
 EXPORTS = ["pipe_default_params", "pipe_create", "pipe_destroy", "seg_tile", "features_tile",
            "seg_features_batch", "batch_submit", "batch_poll", "pipe_status_read", "pipe_debug_plane",
-           "pipe_profile_enable", "pipe_profile_read", "pipe_launch_count"]
+           "pipe_profile_enable", "pipe_profile_read", "pipe_launch_count", "pipe_recon_visits"]
 
 
 class PipeError(RuntimeError):
@@ -85,6 +85,8 @@ def lib():
                                     ctypes.POINTER(ctypes.c_double), ci]
     L.pipe_launch_count.argtypes = [vp]
     L.pipe_launch_count.restype = ctypes.c_longlong
+    L.pipe_recon_visits.argtypes = [vp]
+    L.pipe_recon_visits.restype = ctypes.c_longlong
     for n in ("pipe_create", "seg_tile", "features_tile", "seg_features_batch", "batch_submit", "batch_poll",
               "pipe_status_read", "pipe_debug_plane", "pipe_profile_enable", "pipe_profile_read"):
         getattr(L, n).restype = ci
@@ -168,6 +170,55 @@ class Pipe:
             arr[i].feats_cap = t["feats"].shape[0]
         _check(lib().seg_features_batch(self.h, arr, len(tiles), _stream_ptr(stream)), "seg_features_batch")
 
+    # ---- served form ----------------------------------------------------
+    def submit(self, tiles, want_planes=False):
+        """tiles: list of (H, W, 3) uint8 host arrays (numpy or pinned CPU
+        tensors).  Returns a ticket, or None when admission is refused now."""
+        arr = (TileDesc * len(tiles))()
+        keep = []
+        for i, t in enumerate(tiles):
+            if hasattr(t, "data_ptr"):
+                ptr, H, W, pitch = t.data_ptr(), t.shape[0], t.shape[1], t.stride(0)
+            else:
+                ptr, H, W, pitch = t.ctypes.data, t.shape[0], t.shape[1], t.strides[0]
+            keep.append(t)
+            arr[i].rgb_host, arr[i].W, arr[i].H, arr[i].pitch = ptr, W, H, pitch
+            arr[i].want_planes = 1 if want_planes else 0
+        tk = ctypes.c_uint64()
+        rc = lib().batch_submit(self.h, arr, len(tiles), ctypes.byref(tk))
+        if rc == PIPE_EBUSY:
+            return None
+        _check(rc, "batch_submit")
+        self._keep = getattr(self, "_keep", {})
+        self._keep[tk.value] = (keep, len(tiles), want_planes)
+        return tk.value
+
+    def poll(self, ticket, copy=True):
+        """None while the ticket runs; then a list of per-tile dicts."""
+        import numpy as np
+        keep, n, planes = self._keep[ticket]
+        out = (TileResult * n)()
+        nd = ctypes.c_int()
+        rc = lib().batch_poll(self.h, ticket, ctypes.byref(nd), out)
+        if rc == PIPE_EAGAIN:
+            return None
+        _check(rc, "batch_poll")
+        res = []
+        for i in range(n):
+            r = out[i]
+            H, W = keep[i].shape[0], keep[i].shape[1]
+            rows = min(r.n_objects, max(1, min(W * H // 20 + 1, 65536)))
+            d = dict(status=r.status, n_objects=r.n_objects, t_arrive_ms=r.t_arrive_ms, t_done_ms=r.t_done_ms)
+            d["feats"] = (np.ctypeslib.as_array(r.feats, (rows, NFEAT)).copy() if rows > 0 and r.feats
+                          else np.zeros((0, NFEAT), np.float32))
+            if planes:
+                d["hem8"] = np.ctypeslib.as_array(r.hem8, (H, W)).copy()
+                d["labels"] = np.ctypeslib.as_array(r.labels, (H, W)).copy()
+                d["edt"] = np.ctypeslib.as_array(r.edt, (H, W)).copy()
+            res.append(d)
+        del self._keep[ticket]
+        return res
+
     # ---- introspection --------------------------------------------------
     def status(self):
         return lib().pipe_status_read(self.h)
@@ -188,3 +239,6 @@ class Pipe:
 
     def launch_count(self):
         return lib().pipe_launch_count(self.h)
+
+    def recon_visits(self):
+        return lib().pipe_recon_visits(self.h)

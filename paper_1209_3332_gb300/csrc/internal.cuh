@@ -69,8 +69,9 @@ struct Shared {
 struct Launch {
     TileDev* tiles;        // device array [ntiles]
     int ntiles;
-    int* wl_slots;         // [n_rt] queue ring
-    int* wl_state;         // [n_rt]
+    int* wl_slots;         // [n_rt] queue ring: tile ids
+    int* wl_seq;           // [n_rt] queue ring: slot sequence numbers
+    int* wl_state;         // [n_rt] per-tile state
     Shared* sh;
     int* tile_status;      // [ntiles]
     int* status;           // global status word

@@ -114,11 +114,12 @@ __device__ void object_features(const ObjJob& J, int obj, int* glcm, long long* 
     const int l = obj + 1;
     const int4 box = J.bbox[obj];
     float* out = J.feats + (size_t)obj * NFEAT;
-    if (box.z < 0) {  // no pixel carries this label
+    const int W = J.W, H = J.H;
+    // a box outside the image (no pixel carries this label) yields zeros
+    if (box.x < 0 || box.y < 0 || box.z >= W || box.w >= H || box.x > box.z || box.y > box.w) {
         if (threadIdx.x < NFEAT) out[threadIdx.x] = 0.f;
         return;
     }
-    const int W = J.W, H = J.H;
     const int bw = box.z - box.x + 1, bh = box.w - box.y + 1;
     const long long npx = (long long)bw * bh;
     for (int i = threadIdx.x; i < 4 * 64; i += FT) glcm[i] = 0;

@@ -450,11 +450,12 @@ __global__ void __launch_bounds__(CB_THREADS) k_relabel(Launch L, int want_bbox)
     }
 }
 
-__global__ void k_bbox_init(Launch L, int max_objects) {
+// every box slot a tile can use (feats_cap of them) starts empty
+__global__ void k_bbox_init(Launch L) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     for (int ti = 0; ti < L.ntiles; ti++) {
         const TileDev& T = L.tiles[ti];
-        int n = min(T.feats_cap, max_objects);
+        int n = T.feats_cap;
         for (int j = i; j < n; j += gridDim.x * blockDim.x)
             T.bbox[j] = make_int4(0x7fffffff, 0x7fffffff, -1, -1);
     }
@@ -492,7 +493,7 @@ void launch_label(const Launch& L, int want_bbox, int max_objects, int sms, cuda
     pf->end("label_reset", s);
     if (want_bbox) {
         pf->begin("bbox_init", s);
-        k_bbox_init<<<rgrid, 256, 0, s>>>(L, max_objects);
+        k_bbox_init<<<rgrid, 256, 0, s>>>(L);
         pf->end("bbox_init", s);
     }
     pf->begin("fill_local", s);

@@ -22,7 +22,7 @@
 
 namespace nucseg {
 
-constexpr int HS = 36;            // shared row stride for a (RT+2)-wide tile
+constexpr int HS = 44;            // shared row stride: 11 words (odd: column sweeps are conflict-free)
 constexpr int MAX_ROUNDS = 256;   // sweep rounds before a tile re-queues itself
 constexpr unsigned FULL = 0xffffffffu;
 
@@ -31,8 +31,9 @@ struct WarpTile {
     uint8_t M[(RT + 2) * HS];
 };
 
-#define SR(y, x) S.R[((y) + 1) * HS + (x) + 1]
-#define SM(y, x) S.M[((y) + 1) * HS + (x) + 1]
+// pixel (y, x), y and x in [-1, RT]; interior column 0 sits on a 4-byte boundary
+#define SR(y, x) S.R[((y) + 1) * HS + (x) + 4]
+#define SM(y, x) S.M[((y) + 1) * HS + (x) + 4]
 
 __device__ __forceinline__ int ld_vol(const int* p) { return *(const volatile int*)p; }
 
@@ -41,16 +42,26 @@ __device__ __forceinline__ bool budget_over(long long t0, long long budget) {
 }
 
 // ---- worklist -----------------------------------------------------------------
+// A ticket queue: producers and consumers take indices with atomicAdd (no
+// compare-and-swap retries under contention).  Slot k carries a sequence
+// number: seq == i means "free for producer index i", seq == i+1 means
+// "holds the item of index i"; the consumer of index i hands the slot to
+// producer index i+cap.  A consumer holding a ticket waits until its item
+// arrives or until no tile is queued or running any more.
 
 __device__ void wl_push(const Launch& L, int t) {
+    const int cap = L.n_rt;
     int i = atomicAdd(&L.sh->tail, 1);
-    volatile int* slot = (volatile int*)&L.wl_slots[i % L.n_rt];
+    int k = i % cap;
+    volatile int* seq = (volatile int*)(L.wl_seq + k);
     long long t0 = clock64();
-    while (*slot >= 0) {
+    while (*seq != i) {
         if (budget_over(t0, L.wait_budget)) { atomicCAS(&L.sh->err, 0, ST_TIMEOUT); return; }
         __nanosleep(32);
     }
-    *slot = t;
+    L.wl_slots[k] = t;
+    __threadfence();
+    *seq = i + 1;
 }
 
 __device__ void wl_request(const Launch& L, int t) {
@@ -69,28 +80,21 @@ __device__ void wl_request(const Launch& L, int t) {
 
 // returns a tile id, or -1 when the queue is drained (or on error)
 __device__ int wl_pop(const Launch& L) {
+    const int cap = L.n_rt;
+    int h = atomicAdd(&L.sh->head, 1);
+    int k = h % cap;
+    volatile int* seq = (volatile int*)(L.wl_seq + k);
     long long t0 = clock64();
     for (;;) {
-        if (ld_vol(&L.sh->err)) return -1;
-        int h = ld_vol(&L.sh->head), tl = ld_vol(&L.sh->tail);
-        if (h < tl) {
-            if (atomicCAS(&L.sh->head, h, h + 1) == h) {
-                volatile int* slot = (volatile int*)&L.wl_slots[h % L.n_rt];
-                long long t1 = clock64();
-                int v;
-                while ((v = *slot) < 0) {
-                    if (budget_over(t1, L.wait_budget)) { atomicCAS(&L.sh->err, 0, ST_TIMEOUT); return -1; }
-                    __nanosleep(32);
-                }
-                *slot = -1;
-                __threadfence();
-                return v;
-            }
-            continue;
+        if (*seq == h + 1) {
+            __threadfence();
+            int v = *(volatile int*)(L.wl_slots + k);
+            *seq = h + cap;
+            return v;
         }
-        if (ld_vol(&L.sh->pending) == 0) return -1;
+        if (ld_vol(&L.sh->pending) == 0 || ld_vol(&L.sh->err)) return -1;
         if (budget_over(t0, L.wait_budget)) { atomicCAS(&L.sh->err, 0, ST_TIMEOUT); return -1; }
-        __nanosleep(100);
+        __nanosleep(64);
     }
 }
 
@@ -114,8 +118,9 @@ __global__ void k_wl_init(Launch L) {
     int evens = ((rx + 1) / 2) * ((ry + 1) / 2) + (rx / 2) * (ry / 2);
     int before = ((ty + 1) / 2) * ((rx + 1) / 2) + (ty / 2) * (rx / 2);  // evens in rows < ty
     before += (ty & 1) ? tx / 2 : (tx + 1) / 2;                       // evens in row ty, x < tx
-    int pos = ((tx + ty) & 1) ? evens + (k - before) : before;
-    L.wl_slots[T.rt_base + pos] = i;
+    int pos = T.rt_base + (((tx + ty) & 1) ? evens + (k - before) : before);
+    L.wl_slots[pos] = i;
+    L.wl_seq[pos] = pos + 1;
     L.wl_state[i] = WL_QUEUED;
 }
 
@@ -123,17 +128,54 @@ __global__ void k_wl_init(Launch L) {
 
 __device__ __forceinline__ void load_tile(WarpTile& S, const TileDev& T, int x0, int y0, int lane) {
     const int W = T.W, H = T.H;
-#pragma unroll 2
-    for (int yy = 0; yy < RT + 2; yy++) {
-        int gy = y0 + yy - 1;
-        bool rowin = gy >= 0 && gy < H;
-        for (int xx = lane; xx < RT + 2; xx += 32) {
-            int gx = x0 + xx - 1;
-            bool in = rowin && gx >= 0 && gx < W;
-            size_t o = (size_t)gy * W + gx;
-            S.R[yy * HS + xx] = in ? __ldcg(T.R + o) : (uint8_t)0;
-            S.M[yy * HS + xx] = in ? __ldg(T.hem8 + o) : (uint8_t)0;
+    // halo: q=0 row -1, q=1 row RT (columns lane-1), q=2 column -1, q=3 column RT (rows lane),
+    // q=4 the four halo-row pixels of columns RT-1 and RT (lanes 0..3)
+    uint8_t hr[5], hm[5];
+#pragma unroll
+    for (int q = 0; q < 5; q++) {
+        int gy, gx;
+        if (q < 2) { gy = q == 0 ? y0 - 1 : y0 + RT; gx = x0 + lane - 1; }
+        else if (q < 4) { gy = y0 + lane; gx = q == 2 ? x0 - 1 : x0 + RT; }
+        else { gy = (lane & 1) ? y0 + RT : y0 - 1; gx = x0 + RT - 1 + ((lane >> 1) & 1); }
+        bool in = gy >= 0 && gy < H && gx >= 0 && gx < W && (q < 4 || lane < 4);
+        size_t o = (size_t)gy * W + gx;
+        hr[q] = in ? __ldcg(T.R + o) : (uint8_t)0;
+        hm[q] = in ? __ldg(T.hem8 + o) : (uint8_t)0;
+    }
+    if ((W & 3) == 0 && x0 + RT <= W) {
+        // interior: 8 lanes x 4 bytes per row, 4 rows per step, all loads issued first
+        const int r4 = lane >> 3, c4 = (lane & 7) * 4;
+        uint32_t rv[RT / 4], mv[RT / 4];
+#pragma unroll
+        for (int j = 0; j < RT / 4; j++) {
+            int gy = y0 + j * 4 + r4;
+            bool in = gy < H;
+            size_t o = (size_t)gy * W + x0 + c4;
+            rv[j] = in ? __ldcg(reinterpret_cast<const unsigned int*>(T.R + o)) : 0u;
+            mv[j] = in ? __ldg(reinterpret_cast<const unsigned int*>(T.hem8 + o)) : 0u;
         }
+#pragma unroll
+        for (int j = 0; j < RT / 4; j++) {
+            int yy = j * 4 + r4;
+            *reinterpret_cast<uint32_t*>(&SR(yy, c4)) = rv[j];
+            *reinterpret_cast<uint32_t*>(&SM(yy, c4)) = mv[j];
+        }
+    } else {
+        for (int yy = 0; yy < RT; yy++) {
+            int gy = y0 + yy, gx = x0 + lane;
+            bool in = gy < H && gx < W;
+            size_t o = (size_t)gy * W + gx;
+            SR(yy, lane) = in ? __ldcg(T.R + o) : (uint8_t)0;
+            SM(yy, lane) = in ? __ldg(T.hem8 + o) : (uint8_t)0;
+        }
+    }
+    SR(-1, lane - 1) = hr[0]; SM(-1, lane - 1) = hm[0];
+    SR(RT, lane - 1) = hr[1]; SM(RT, lane - 1) = hm[1];
+    SR(lane, -1) = hr[2]; SM(lane, -1) = hm[2];
+    SR(lane, RT) = hr[3]; SM(lane, RT) = hm[3];
+    if (lane < 4) {
+        int yy = (lane & 1) ? RT : -1, xx = RT - 1 + ((lane >> 1) & 1);
+        SR(yy, xx) = hr[4]; SM(yy, xx) = hm[4];
     }
     __syncwarp();
 }

@@ -238,31 +238,37 @@ struct LaunchCtx {
 
 // ---- the pipe ---------------------------------------------------------------------------
 
-struct Ticket;
-
-struct Slot {
+// One served-form context: buffers for a group of tiles submitted together,
+// processed as one batched launch on the context's own stream.
+struct Ctx {
     cudaStream_t stream = nullptr;
-    LaunchCtx ctx;
-    DevBuf rgb, hem8, labels, edt, nobj, feats;
-    void* h_stage = nullptr;      // pinned RGB staging
-    size_t h_stage_n = 0;
-    void* h_out = nullptr;        // pinned results: n_objects, feats, planes
+    cudaEvent_t done = nullptr;
+    LaunchCtx lc;
+    DevBuf dev;                    // rgb, hem8, labels, edt, n_objects, feats of all tiles
+    void* h_in = nullptr;          // pinned RGB staging (pageable inputs)
+    size_t h_in_n = 0;
+    void* h_out = nullptr;         // pinned results
     size_t h_out_n = 0;
-    int maxW = 0, maxH = 0, feats_cap = 0;
+    size_t bytes = 0;              // device bytes held (budget accounting)
     bool busy = false;
-    size_t footprint = 0;
     double t_done = 0;
+    int status_dev_off = 0;
+};
+
+struct TicketTile {
+    int W, H, want;
+    size_t out_off, nobj_off, st_off;
 };
 
 struct Ticket {
-    std::vector<int> slot;        // slot per tile
-    std::vector<tile_desc> desc;
-    std::vector<tile_result> res;
+    int ctx = -1;
+    std::vector<TicketTile> tiles;
+    double t_submit = 0;
+    bool done = false;
+    double t_done_ms = 0;
     std::vector<std::vector<float>> feats;
     std::vector<std::vector<uint8_t>> hem8;
     std::vector<std::vector<int32_t>> labels, edt;
-    std::vector<double> t_arrive;
-    bool done = false;
 };
 
 struct pipe_s {
@@ -284,10 +290,12 @@ struct pipe_s {
     int batch_ntiles = 0;
     // served form
     std::mutex mu;
-    std::vector<std::unique_ptr<Slot>> slots;
+    std::vector<std::unique_ptr<Ctx>> ctxs;
     std::map<uint64_t, std::unique_ptr<Ticket>> tickets;
     uint64_t next_ticket = 1;
+    uint64_t last_polled = 0;      // completed ticket whose results are still held
     size_t hbm_in_use = 0;
+    EventProfiler serve_prof;      // launches of the served form (counted, not timed)
 };
 
 namespace {
@@ -295,7 +303,7 @@ namespace {
 int ensure_ctx(LaunchCtx& c, int ntiles, int n_rt, size_t arena_bytes) {
     int rc;
     if ((rc = c.tiles.ensure(sizeof(TileDev) * std::max(ntiles, 1)))) return rc;
-    if ((rc = c.wl.ensure(sizeof(int) * 2 * std::max(n_rt, 1)))) return rc;
+    if ((rc = c.wl.ensure(sizeof(int) * 3 * std::max(n_rt, 1)))) return rc;
     if ((rc = c.shared.ensure(sizeof(Shared) + sizeof(int) * (2 + std::max(ntiles, 1))))) return rc;
     if ((rc = c.arena.ensure(std::max(arena_bytes, (size_t)256)))) return rc;
     return PIPE_OK;
@@ -307,7 +315,8 @@ Launch make_launch(pipe_t p, LaunchCtx& c, std::vector<TileDev>& td, int n_rt_to
     L.tiles = (TileDev*)c.tiles.p;
     L.ntiles = (int)td.size();
     L.wl_slots = (int*)c.wl.p;
-    L.wl_state = (int*)c.wl.p + std::max(n_rt_total, 1);
+    L.wl_seq = (int*)c.wl.p + std::max(n_rt_total, 1);
+    L.wl_state = (int*)c.wl.p + 2 * std::max(n_rt_total, 1);
     L.sh = (Shared*)c.shared.p;
     L.status = (int*)((char*)c.shared.p + sizeof(Shared));
     L.tile_status = L.status + 2;
@@ -437,13 +446,13 @@ void pipe_destroy(pipe_t p) {
     rel(p->plain);
     rel(p->batch);
     p->fbbox.release();
-    for (auto& s : p->slots) {
-        rel(s->ctx);
-        s->rgb.release(); s->hem8.release(); s->labels.release(); s->edt.release();
-        s->nobj.release(); s->feats.release();
-        if (s->h_stage) cudaFreeHost(s->h_stage);
-        if (s->h_out) cudaFreeHost(s->h_out);
-        if (s->stream) cudaStreamDestroy(s->stream);
+    for (auto& c : p->ctxs) {
+        rel(c->lc);
+        c->dev.release();
+        if (c->h_in) cudaFreeHost(c->h_in);
+        if (c->h_out) cudaFreeHost(c->h_out);
+        if (c->done) cudaEventDestroy(c->done);
+        if (c->stream) cudaStreamDestroy(c->stream);
     }
     delete p;
 }
@@ -457,7 +466,7 @@ int seg_tile(pipe_t p, const uint8_t* rgb_dev, int W, int H, size_t pitch_bytes,
     int RB = bands_rows(W);
     Geo g = geometry(W, H, 1, RB);
     int n_rt = g.rtx * g.rty;
-    if (p->plain.arena.n < g.ws_bytes || p->plain.wl.n < sizeof(int) * 2 * (size_t)n_rt) CK(cudaStreamSynchronize(s));
+    if (p->plain.arena.n < g.ws_bytes || p->plain.wl.n < sizeof(int) * 3 * (size_t)n_rt) CK(cudaStreamSynchronize(s));
     int rc = ensure_ctx(p->plain, 1, n_rt, g.ws_bytes);
     if (rc) return rc;
     std::vector<TileDev> td(1);
@@ -526,7 +535,7 @@ int seg_features_batch(pipe_t p, const tile_dev* tiles, int n, pipe_stream_t str
         key += std::to_string(tiles[i].W) + "x" + std::to_string(tiles[i].H) + "c" +
                std::to_string(tiles[i].feats_cap) + (tiles[i].edt ? "e" : "n") + ";";
     }
-    bool grow = p->batch.arena.n < total || p->batch.wl.n < sizeof(int) * 2 * (size_t)n_rt ||
+    bool grow = p->batch.arena.n < total || p->batch.wl.n < sizeof(int) * 3 * (size_t)n_rt ||
                 p->batch.tiles.n < sizeof(TileDev) * n || p->batch.shared.n < sizeof(Shared) + sizeof(int) * (2 + n);
     if (grow) {
         CK(cudaStreamSynchronize(s));
@@ -658,16 +667,237 @@ int pipe_profile_read(pipe_t p, const char** names, long long* launches, double*
     return i;
 }
 
-long long pipe_launch_count(pipe_t p) { return p ? p->prof.launches : -1; }
+long long pipe_launch_count(pipe_t p) { return p ? p->prof.launches + p->serve_prof.launches : -1; }
+
+long long pipe_recon_visits(pipe_t p) {
+    if (!p || !p->plain.shared.p) return -1;
+    if (cudaSetDevice(p->device) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) return -1;
+    Shared sh;
+    if (cudaMemcpy(&sh, p->plain.shared.p, sizeof(sh), cudaMemcpyDeviceToHost) != cudaSuccess) return -1;
+    return sh.processed;
+}
+
+static void CUDART_CB stamp_done(void* arg) { static_cast<Ctx*>(arg)->t_done = now_ms(); }
 
 int batch_submit(pipe_t p, const tile_desc* tiles, int n, uint64_t* ticket) {
-    (void)p; (void)tiles; (void)n; (void)ticket;
-    return PIPE_EINVAL;
+    if (!p || !tiles || n < 1 || n > 1024 || !ticket) return PIPE_EINVAL;
+    for (int i = 0; i < n; i++)
+        if (!tiles[i].rgb_host || !valid_size(tiles[i].W, tiles[i].H) || tiles[i].pitch < (size_t)tiles[i].W * 3)
+            return PIPE_EINVAL;
+    std::lock_guard<std::mutex> lk(p->mu);
+    CK(cudaSetDevice(p->device));
+    const double t_submit = now_ms();
+    // sizes of this group
+    int Wmax = 1;
+    for (int i = 0; i < n; i++) Wmax = std::max(Wmax, tiles[i].W);
+    const int RB = bands_rows(Wmax);
+    std::vector<Geo> geos(n);
+    std::vector<int> caps(n);
+    size_t ws = 0, io = 0, hin = 0, hout = 0;
+    int n_rt = 0;
+    for (int i = 0; i < n; i++) {
+        size_t N = (size_t)tiles[i].W * tiles[i].H;
+        caps[i] = (int)std::min<size_t>(N / 20 + 1, 65536);
+        geos[i] = geometry(tiles[i].W, tiles[i].H, caps[i], RB);
+        ws += geos[i].ws_bytes;
+        io += al256(3 * N) + al256(N) + 2 * al256(4 * N) + al256(16) + al256((size_t)caps[i] * NFEAT * 4);
+        hin += al256(3 * N);
+        hout += al256(16) + al256((size_t)caps[i] * NFEAT * 4) +
+                (tiles[i].want_planes ? al256(N) + 2 * al256(4 * N) : 0);
+        n_rt += geos[i].rtx * geos[i].rty;
+    }
+    // admission: a free context (reused if large enough) within the HBM budget
+    int ci = -1;
+    for (int k = 0; k < (int)p->ctxs.size(); k++) {
+        Ctx& c = *p->ctxs[k];
+        if (c.busy) continue;
+        if (c.dev.n >= io && c.lc.arena.n >= ws && c.h_in_n >= hin && c.h_out_n >= hout &&
+            c.lc.wl.n >= sizeof(int) * 3 * (size_t)n_rt && c.lc.tiles.n >= sizeof(TileDev) * n &&
+            c.lc.shared.n >= sizeof(Shared) + sizeof(int) * (2 + n)) {
+            ci = k;
+            break;
+        }
+        if (ci < 0) ci = k;  // a free context to grow if nothing fits
+    }
+    size_t need = io + ws + sizeof(TileDev) * n + sizeof(int) * 3 * n_rt;
+    if (ci < 0) {
+        if ((int)p->ctxs.size() >= p->prm.max_slots) return PIPE_EBUSY;
+        p->ctxs.emplace_back(new Ctx());
+        ci = (int)p->ctxs.size() - 1;
+        Ctx& c = *p->ctxs[ci];
+        CK(cudaStreamCreateWithFlags(&c.stream, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&c.done, cudaEventDisableTiming));
+    }
+    Ctx& c = *p->ctxs[ci];
+    size_t have = c.bytes;
+    size_t grow_to = std::max(have, need);
+    if (p->hbm_in_use + grow_to > p->prm.hbm_budget_bytes) return PIPE_EBUSY;
+    int rc;
+    if ((rc = c.dev.ensure(io))) return rc;
+    if ((rc = ensure_ctx(c.lc, n, n_rt, ws))) return rc;
+    c.bytes = c.dev.n + c.lc.arena.n + c.lc.tiles.n + c.lc.wl.n + c.lc.shared.n;
+    if (c.h_in_n < hin) {
+        if (c.h_in) cudaFreeHost(c.h_in);
+        c.h_in = nullptr;
+        c.h_in_n = 0;
+        CK(cudaHostAlloc(&c.h_in, hin, cudaHostAllocDefault));
+        c.h_in_n = hin;
+    }
+    if (c.h_out_n < hout) {
+        if (c.h_out) cudaFreeHost(c.h_out);
+        c.h_out = nullptr;
+        c.h_out_n = 0;
+        CK(cudaHostAlloc(&c.h_out, hout, cudaHostAllocDefault));
+        c.h_out_n = hout;
+    }
+    // carve device buffers and fill descriptors
+    std::unique_ptr<Ticket> tk(new Ticket());
+    tk->ctx = ci;
+    tk->t_submit = t_submit;
+    std::vector<TileDev> td(n);
+    char* d = (char*)c.dev.p;
+    char* hi = (char*)c.h_in;
+    size_t wsoff = 0, hoff = 0;
+    for (int i = 0; i < n; i++) {
+        const tile_desc& t = tiles[i];
+        size_t N = (size_t)t.W * t.H;
+        TileDev& x = td[i];
+        std::memset(&x, 0, sizeof(x));
+        x.feats_cap = caps[i];
+        carve(x, geos[i], (char*)c.lc.arena.p + wsoff);
+        wsoff += geos[i].ws_bytes;
+        uint8_t* rgb = (uint8_t*)d; d += al256(3 * N);
+        x.hem8 = (uint8_t*)d; d += al256(N);
+        x.labels = (int32_t*)d; d += al256(4 * N);
+        x.edt = (int32_t*)d; d += al256(4 * N);
+        x.n_objects = (int32_t*)d; d += al256(16);
+        x.feats = (float*)d; d += al256((size_t)caps[i] * NFEAT * 4);
+        x.rgb = rgb;
+        x.pitch = (size_t)t.W * 3;
+        // upload: pinned source directly, pageable through the staging buffer
+        cudaPointerAttributes pa;
+        bool pinned = cudaPointerGetAttributes(&pa, t.rgb_host) == cudaSuccess && pa.type == cudaMemoryTypeHost;
+        cudaGetLastError();
+        const void* src = t.rgb_host;
+        size_t spitch = t.pitch;
+        if (!pinned) {
+            for (int y = 0; y < t.H; y++) std::memcpy(hi + (size_t)y * t.W * 3, t.rgb_host + (size_t)y * t.pitch, (size_t)t.W * 3);
+            src = hi;
+            spitch = (size_t)t.W * 3;
+        }
+        hi += al256(3 * N);
+        CK(cudaMemcpy2DAsync(rgb, (size_t)t.W * 3, src, spitch, (size_t)t.W * 3, t.H, cudaMemcpyHostToDevice, c.stream));
+        TicketTile tt{t.W, t.H, t.want_planes, 0, 0, 0};
+        tt.nobj_off = hoff; hoff += al256(16);
+        tt.out_off = hoff; hoff += al256((size_t)caps[i] * NFEAT * 4);
+        if (t.want_planes) hoff += al256(N) + 2 * al256(4 * N);
+        tk->tiles.push_back(tt);
+    }
+    Launch L = make_launch(p, c.lc, td, n_rt);
+    if ((rc = upload_desc(L, td, c.stream))) return rc;
+    run_path(p, L, Wmax, true, *std::max_element(caps.begin(), caps.end()), c.stream, &p->serve_prof);
+    // download: count + device status word, feature rows (all cap rows), planes
+    char* ho = (char*)c.h_out;
+    for (int i = 0; i < n; i++) {
+        const TicketTile& tt = tk->tiles[i];
+        size_t N = (size_t)tt.W * tt.H;
+        CK(cudaMemcpyAsync(ho + tt.nobj_off, td[i].n_objects, 4, cudaMemcpyDeviceToHost, c.stream));
+        CK(cudaMemcpyAsync(ho + tt.nobj_off + 4, L.tile_status + i, 4, cudaMemcpyDeviceToHost, c.stream));
+        CK(cudaMemcpyAsync(ho + tt.nobj_off + 8, &L.sh->err, 4, cudaMemcpyDeviceToHost, c.stream));
+        CK(cudaMemcpyAsync(ho + tt.out_off, td[i].feats, (size_t)caps[i] * NFEAT * 4, cudaMemcpyDeviceToHost, c.stream));
+        if (tt.want) {
+            char* q = ho + tt.out_off + al256((size_t)caps[i] * NFEAT * 4);
+            CK(cudaMemcpyAsync(q, td[i].hem8, N, cudaMemcpyDeviceToHost, c.stream));
+            CK(cudaMemcpyAsync(q + al256(N), td[i].labels, 4 * N, cudaMemcpyDeviceToHost, c.stream));
+            CK(cudaMemcpyAsync(q + al256(N) + al256(4 * N), td[i].edt, 4 * N, cudaMemcpyDeviceToHost, c.stream));
+        }
+    }
+    CK(cudaLaunchHostFunc(c.stream, stamp_done, &c));
+    CK(cudaEventRecord(c.done, c.stream));
+    CK(cudaGetLastError());
+    c.busy = true;
+    p->hbm_in_use += c.bytes;
+    p->prof.launches += 0;
+    uint64_t id = p->next_ticket++;
+    p->tickets[id] = std::move(tk);
+    *ticket = id;
+    return PIPE_OK;
 }
 
 int batch_poll(pipe_t p, uint64_t ticket, int* n_done, tile_result* out) {
-    (void)p; (void)ticket; (void)n_done; (void)out;
-    return PIPE_EINVAL;
+    if (!p || !n_done) return PIPE_EINVAL;
+    std::lock_guard<std::mutex> lk(p->mu);
+    auto it = p->tickets.find(ticket);
+    if (it == p->tickets.end()) return PIPE_EINVAL;
+    Ticket& tk = *it->second;
+    const int n = (int)tk.tiles.size();
+    if (!tk.done) {
+        Ctx& c = *p->ctxs[tk.ctx];
+        cudaError_t q = cudaEventQuery(c.done);
+        if (q == cudaErrorNotReady) {
+            *n_done = 0;
+            return PIPE_EAGAIN;
+        }
+        if (q != cudaSuccess) return PIPE_ECUDA;
+        // copy results out of the context so that it can take new work
+        const char* ho = (const char*)c.h_out;
+        tk.feats.resize(n);
+        tk.hem8.resize(n);
+        tk.labels.resize(n);
+        tk.edt.resize(n);
+        std::vector<int> st(n), K(n);
+        for (int i = 0; i < n; i++) {
+            const TicketTile& tt = tk.tiles[i];
+            int vals[3];
+            std::memcpy(vals, ho + tt.nobj_off, sizeof(vals));
+            K[i] = vals[0];
+            st[i] = vals[1] ? vals[1] : vals[2];
+            int rows = std::min(K[i], (int)((tt.W * (size_t)tt.H) / 20 + 1 < 65536 ? (tt.W * (size_t)tt.H) / 20 + 1 : 65536));
+            const float* f = (const float*)(ho + tt.out_off);
+            tk.feats[i].assign(f, f + (size_t)std::max(rows, 0) * NFEAT);
+            if (tt.want) {
+                size_t N = (size_t)tt.W * tt.H;
+                size_t cap = std::min<size_t>(N / 20 + 1, 65536);
+                const char* q = ho + tt.out_off + al256(cap * NFEAT * 4);
+                tk.hem8[i].assign((const uint8_t*)q, (const uint8_t*)q + N);
+                tk.labels[i].assign((const int32_t*)(q + al256(N)), (const int32_t*)(q + al256(N)) + N);
+                tk.edt[i].assign((const int32_t*)(q + al256(N) + al256(4 * N)), (const int32_t*)(q + al256(N) + al256(4 * N)) + N);
+            }
+            tk.tiles[i].st_off = (size_t)st[i];
+            tk.tiles[i].nobj_off = (size_t)K[i];  // reuse the fields for the host copies
+        }
+        tk.done = true;
+        double td = c.t_done;
+        c.busy = false;
+        p->hbm_in_use -= std::min(p->hbm_in_use, c.bytes);
+        for (int i = 0; i < n; i++) tk.tiles[i].out_off = 0;
+        tk.t_submit = tk.t_submit;
+        tk.ctx = -1;
+        tk.feats.shrink_to_fit();
+        // completion time of the whole group
+        tk.tiles.shrink_to_fit();
+        tk.done = true;
+        tk.t_done_ms = td;
+    }
+    if (out) {
+        for (int i = 0; i < n; i++) {
+            tile_result& r = out[i];
+            r.status = (int)tk.tiles[i].st_off;
+            r.n_objects = (int)tk.tiles[i].nobj_off;
+            if (r.status == PIPE_OK && r.n_objects > (int)(tk.feats[i].size() / NFEAT)) r.status = PIPE_EOVERFLOW;
+            r.feats = tk.feats[i].empty() ? nullptr : tk.feats[i].data();
+            r.hem8 = tk.hem8[i].empty() ? nullptr : tk.hem8[i].data();
+            r.labels = tk.labels[i].empty() ? nullptr : tk.labels[i].data();
+            r.edt = tk.edt[i].empty() ? nullptr : tk.edt[i].data();
+            r.t_arrive_ms = tk.t_submit;
+            r.t_done_ms = tk.t_done_ms;
+        }
+    }
+    *n_done = n;
+    // results of the previously polled ticket are released now
+    if (p->last_polled && p->last_polled != ticket) p->tickets.erase(p->last_polled);
+    p->last_polled = ticket;
+    return PIPE_OK;
 }
 
 }  // extern "C"

@@ -1,0 +1,144 @@
+"""Batched and served forms: each tile's result equals the plain form's on
+the same tile alone (bit for bit, features included) and the oracle's, while
+tiles of uneven size and density share launches and run concurrently."""
+import time
+
+import numpy as np
+import pytest
+
+import synth
+from tests.gpu_util import assert_feats_close, assert_planes_equal, oracle_all, run_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pipe():
+    import torch
+    import paper_1209_3332_gb300 as P
+    from paper_1209_3332_gb300 import build
+    build.build()
+    torch.cuda.init()
+    p = P.Pipe(0, max_slots=4)
+    yield p
+    assert p.status() == P.PIPE_OK
+    p.close()
+
+
+def mixed_tiles():
+    tiles = [synth.tile(640, 480, 21, n_nuclei=0),                                    # empty
+             synth.tile(1024, 1024, 22, n_nuclei=300, frac_cluster=0.2, n_stroma=10),  # dense
+             synth.tile(333, 517, 23, n_nuclei=40, frac_overlap=0.1),                 # ragged
+             synth.tile(1, 77, 24),
+             synth.tile(2048, 1536, 25, n_nuclei=700, frac_chain=0.5, corridor=True)]
+    return tiles
+
+
+def run_batched(pipe, tiles, caps=None):
+    import torch
+    dev = torch.device("cuda", 0)
+    bufs = []
+    for i, t in enumerate(tiles):
+        H, W = t.shape[:2]
+        cap = caps[i] if caps else max(1, W * H // 20 + 1)
+        bufs.append(dict(rgb=torch.from_numpy(t).to(dev), hem8=torch.empty((H, W), dtype=torch.uint8, device=dev),
+                         labels=torch.empty((H, W), dtype=torch.int32, device=dev),
+                         edt=torch.empty((H, W), dtype=torch.int32, device=dev),
+                         n_objects=torch.zeros(1, dtype=torch.int32, device=dev),
+                         feats=torch.zeros((cap, 15), dtype=torch.float32, device=dev)))
+    pipe.seg_features_batch(bufs)
+    torch.cuda.synchronize()
+    out = []
+    for b in bufs:
+        K = int(b["n_objects"].item())
+        out.append(dict(hem8=b["hem8"].cpu().numpy(), labels=b["labels"].cpu().numpy(),
+                        edt=b["edt"].cpu().numpy(), K=K, feats=b["feats"][:min(K, b["feats"].shape[0])].cpu().numpy()))
+    return out
+
+
+def test_batched_equals_plain_and_oracle(pipe):
+    tiles = mixed_tiles()
+    got = run_batched(pipe, tiles)
+    for t, g in zip(tiles, got):
+        alone = run_gpu(pipe, t, want_planes=False)
+        assert_planes_equal(g, alone, planes=("hem8", "labels", "edt"))
+        assert np.array_equal(g["feats"], alone["feats"])
+        r = oracle_all(t)
+        assert_planes_equal(g, r, planes=("hem8", "labels", "edt"))
+        assert_feats_close(g["feats"], r["feats"])
+
+
+def test_batched_graph_replay_and_shape_change(pipe):
+    tiles = mixed_tiles()[:3]
+    a = run_batched(pipe, tiles)
+    b = run_batched(pipe, tiles)          # replayed from the captured graph
+    c = run_batched(pipe, tiles[::-1])    # another shape -> another graph
+    for x, y in zip(a, b):
+        assert_planes_equal(x, y, planes=("hem8", "labels", "edt"))
+        assert np.array_equal(x["feats"], y["feats"])
+    for x, y in zip(a, c[::-1]):
+        assert_planes_equal(x, y, planes=("hem8", "labels", "edt"))
+
+
+def test_batched_feature_capacity_overflow_is_reported(pipe):
+    import paper_1209_3332_gb300 as P
+    t = synth.tile(512, 512, 31, n_nuclei=80)
+    got = run_batched(pipe, [t], caps=[3])
+    assert got[0]["K"] > 3
+    assert pipe.status() == P.PIPE_EOVERFLOW
+    r = oracle_all(t)
+    assert_feats_close(got[0]["feats"], r["feats"][:3])
+
+
+def wait(pipe, tk, timeout=60):
+    t0 = time.time()
+    while True:
+        r = pipe.poll(tk)
+        if r is not None:
+            return r
+        assert time.time() - t0 < timeout
+        time.sleep(0.001)
+
+
+def test_served_alone_and_in_the_mix(pipe):
+    import torch
+    tiles = mixed_tiles()
+    alone = []
+    for t in tiles:
+        tk = pipe.submit([t], want_planes=True)
+        alone.append(wait(pipe, tk)[0])
+    # in the mix: several groups in flight at once, pinned and pageable inputs
+    pinned = [torch.from_numpy(t).pin_memory() for t in tiles[:2]]
+    tks = [pipe.submit(pinned, want_planes=True), pipe.submit(tiles[2:4], want_planes=True),
+           pipe.submit([tiles[4]], want_planes=True)]
+    assert all(tk is not None for tk in tks)
+    mixed = []
+    for tk in tks:
+        mixed.extend(wait(pipe, tk))
+    for t, a, m in zip(tiles, alone, mixed):
+        assert a["status"] == 0 and m["status"] == 0
+        for k in ("hem8", "labels", "edt"):
+            assert np.array_equal(a[k], m[k]), k
+        assert a["n_objects"] == m["n_objects"]
+        assert np.array_equal(a["feats"], m["feats"])
+        r = oracle_all(t)
+        assert a["n_objects"] == r["K"]
+        for k in ("hem8", "labels", "edt"):
+            assert np.array_equal(a[k], r[k]), k
+        assert_feats_close(a["feats"], r["feats"])
+        assert m["t_done_ms"] >= m["t_arrive_ms"]
+
+
+def test_served_admission_refused_when_slots_full(pipe):
+    t = synth.tile(256, 256, 41, n_nuclei=10)
+    tks = []
+    for _ in range(4):
+        tk = pipe.submit([t])
+        assert tk is not None
+        tks.append(tk)
+    assert pipe.submit([t]) is None       # max_slots=4 contexts are busy until polled
+    for tk in tks:
+        wait(pipe, tk)
+    tk = pipe.submit([t])
+    assert tk is not None
+    assert wait(pipe, tk)[0]["status"] == 0
