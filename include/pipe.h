@@ -107,6 +107,26 @@ int seg_tile(pipe_t p, const uint8_t* rgb_dev, int W, int H, size_t pitch_bytes,
 int features_tile(pipe_t p, const uint8_t* hem8_dev, const int32_t* labels_dev, int W, int H,
                   int n_objects, float* feats_dev, pipe_stream_t stream);
 
+/* features_tile without a pipe and without any device allocation.  The paper
+ * has no counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc -- code that runs under a framework's own caching allocator
+ * (where a raw allocation would bypass its accounting or fail because the
+ * pool already holds the memory), or a serving loop that must not take the
+ * implicit device synchronisation an allocation can cause.  Inputs, outputs
+ * and results are exactly those of features_tile.  Its only scratch, one
+ * box per object, is a static device array of PIPE_NOALLOC_MAX_OBJECTS
+ * entries (1 MiB) that every GPU loading this library holds until exit.
+ *  - Uses the current CUDA device.  The first call on a device looks up the
+ *    array's device address (cudaGetSymbolAddress); make that first call
+ *    before any stream capture.
+ *  - n_objects > PIPE_NOALLOC_MAX_OBJECTS: PIPE_EINVAL, nothing launched.
+ *  - All calls share the one array (each call first resets the entries it
+ *    uses): calls that overlap on the GPU -- on different streams, or from
+ *    different threads -- race and must be serialised by the caller. */
+#define PIPE_NOALLOC_MAX_OBJECTS 65536
+int features_tile_noalloc(const uint8_t* hem8_dev, const int32_t* labels_dev, int W, int H,
+                          int n_objects, float* feats_dev, pipe_stream_t stream);
+
 /* Batched form, device-resident: segmentation + features of n tiles of any
  * sizes, one launch per pass over all tiles (the reconstruction pass is one
  * persistent launch with a work queue spanning every tile), replayed from a

@@ -19,7 +19,9 @@ STATUS_NAMES = ["PIPE_OK", "PIPE_EINVAL", "PIPE_ENOMEM", "PIPE_EBUSY", "PIPE_EAG
 
 EXPORTS = ["pipe_default_params", "pipe_create", "pipe_destroy", "seg_tile", "features_tile",
            "seg_features_batch", "batch_submit", "batch_poll", "pipe_status_read", "pipe_debug_plane",
-           "pipe_profile_enable", "pipe_profile_read", "pipe_launch_count", "pipe_recon_visits"]
+           "pipe_profile_enable", "pipe_profile_read", "pipe_launch_count", "pipe_recon_visits",
+           "features_tile_noalloc"]
+NOALLOC_MAX_OBJECTS = 65536
 
 
 class PipeError(RuntimeError):
@@ -85,6 +87,8 @@ def lib():
                                     ctypes.POINTER(ctypes.c_double), ci]
     L.pipe_launch_count.argtypes = [vp]
     L.pipe_launch_count.restype = ctypes.c_longlong
+    L.features_tile_noalloc.argtypes = [vp, vp, ci, ci, ci, vp, vp]
+    L.features_tile_noalloc.restype = ci
     L.pipe_recon_visits.argtypes = [vp]
     L.pipe_recon_visits.restype = ctypes.c_longlong
     for n in ("pipe_create", "seg_tile", "features_tile", "seg_features_batch", "batch_submit", "batch_poll",
@@ -97,6 +101,14 @@ def lib():
 def _check(rc, what):
     if rc != PIPE_OK:
         raise PipeError(rc, what)
+
+
+def features_tile_noalloc(hem8, labels, n_objects, feats, stream=None):
+    """features_tile on the current device with no allocation (static scratch)."""
+    H, W = labels.shape
+    rc = lib().features_tile_noalloc(hem8.data_ptr(), labels.data_ptr(), W, H, int(n_objects),
+                                     feats.data_ptr() if feats is not None else None, _stream_ptr(stream))
+    _check(rc, "features_tile_noalloc")
 
 
 def default_params():
