@@ -10,8 +10,11 @@ namespace nucseg {
 // ---- geometry ---------------------------------------------------------------
 constexpr int RT = 32;            // reconstruction work tile: RT x RT pixels, one warp
 constexpr int RT_WARPS = 4;       // warps (independent workers) per reconstruction CTA
+constexpr int RECON_MIN_BLOCKS = 8;   // resident reconstruction CTAs per SM the register budget must allow
 constexpr int CB = 32;            // labelling block: CB x CB pixels (one bitmap word per row)
 constexpr int CB_THREADS = 256;
+constexpr int CCL_WARPS = 4;      // labelling blocks (one per warp) per CTA
+constexpr int RL_CAP = 512;       // root-list slots per labelling block
 constexpr int NFEAT = 15;
 
 // worklist tile states
@@ -41,11 +44,10 @@ struct TileDev {
     int32_t* P;                   // union-find parents (sparse, H*W)
     int32_t* A;                   // per-root payload (sparse, H*W)
     int32_t* border;              // per labelling block: 4*CB local roots
-    int32_t* rootlist;            // local roots, capacity H*W
-    int32_t* counters;            // [0] list length
+    int32_t* rootlist;            // local roots, RL_CAP per labelling block
+    int32_t* blkroots;            // local roots recorded per labelling block
     int4* bbox;                   // per object: xmin, ymin, xmax, ymax
-    int32_t* edtF;                // per 32-row chunk and column: first background row,
-    int32_t* edtL;                //   last background row (then carries below/above)
+    uint32_t* colbits;            // per 32-row chunk and column: kept bits of the 32 rows
     int wpr;                      // bitmap words per row = ceil(W/32)
     int rtx, rty, rt_base;        // reconstruction tiles and global base id
     int cbx, cby, cb_base;        // labelling blocks and global base id
@@ -105,9 +107,11 @@ struct Profiler {
 };
 
 void upload_deconv_tables(const int32_t* lut3x256);
+// fills the feature pass's constant tables on `device` (current) once; 0 on success
+int features_tables_ready(int device);
 void launch_deconv(const Launch& L, cudaStream_t s, Profiler* pf);
-int recon_grid(int n_rt, int device);
-void launch_recon(const Launch& L, int grid, cudaStream_t s, Profiler* pf);
+int recon_grid(int device);
+void launch_recon(const Launch& L, int grid_cap, cudaStream_t s, Profiler* pf);
 void launch_label(const Launch& L, int want_bbox, int max_objects, int sms, cudaStream_t s, Profiler* pf);
 size_t edt_rows_smem(int RB, int Wmax);
 void launch_edt(const Launch& L, int RB, int Wmax, cudaStream_t s, Profiler* pf);

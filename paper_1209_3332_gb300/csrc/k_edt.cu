@@ -5,14 +5,14 @@
 // distance along column x to the nearest background pixel, and
 // D(y,x) = min_q (x-q)^2 + g(y,q)^2 along row y.
 //
-// GB300 layout: the relabel pass leaves the kept-pixel bitmap (2 MB for a
-// 4K tile) and, per 32-row chunk and column, the first and last background
-// row.  k_edt_carry turns those into, per chunk, the nearest background row
-// above and below the chunk (a short sequential scan per column).  k_edt_rows
-// then handles a band of rows per CTA: it rebuilds g for the band from the
-// bitmap (a 32x32 bit transpose by warp shuffles) and the carries, keeps the
-// band's g rows in shared memory and solves every row there, so the only
-// full-plane traffic is the single int32 write of D.  Rows whose g stays
+// GB300 layout: the relabel pass leaves, per 32-row chunk and column, one
+// word with the chunk's 32 kept bits of that column (2 MB for a 4K tile).
+// k_edt_rows handles a band of rows per CTA: for each column it finds the
+// nearest background row within the chunk with bit scans, and above/below
+// the chunk by walking to the nearest chunk that has background (almost
+// always the adjacent one), keeps the band's g rows in shared memory and
+// solves every row there, so the only full-plane traffic is the single
+// int32 write of D.  Rows whose g stays
 // within WMAX use an exact windowed search (a candidate at distance r costs
 // at least r^2, so the search stops once r^2 >= the best value); other rows
 // run Meijster's lower-envelope scan on one thread.
@@ -24,32 +24,8 @@ constexpr int INFG = 32767;       // "no background in this column"
 constexpr int WMAX = 128;
 constexpr unsigned FULLE = 0xffffffffu;
 
-// per column: carryL[c] <- last background row above chunk c (or -1),
-//             carryF[c] <- first background row below chunk c (or -1)
-__global__ void __launch_bounds__(256) k_edt_carry(Launch L) {
-    int gid = blockIdx.x * blockDim.x + threadIdx.x;
-    if (gid >= L.n_cols) return;
-    int ti = find_tile(L.tiles, L.ntiles, gid, &TileDev::col_base);
-    const TileDev& T = L.tiles[ti];
-    if (!T.edt) return;
-    int x = gid - T.col_base;
-    int above = -1;
-    for (int c = 0; c < T.cby; c++) {
-        size_t o = (size_t)c * T.W + x;
-        int lb = T.edtL[o];
-        T.edtL[o] = above;
-        if (lb >= 0) above = lb;
-    }
-    int below = -1;
-    for (int c = T.cby - 1; c >= 0; c--) {
-        size_t o = (size_t)c * T.W + x;
-        int fb = T.edtF[o];
-        T.edtF[o] = below;
-        if (fb >= 0) below = fb;
-    }
-}
-
 __device__ __forceinline__ int sq(int v) { return v * v; }
+__device__ __forceinline__ uint32_t below_or_at(int k) { return (2u << k) - 1u; }  // bits 0..k
 
 __device__ void meijster_row(const uint16_t* g, int W, int16_t* s, int16_t* t, int32_t* out) {
     // lower envelope of f_i(u) = (u-i)^2 + g_i^2
@@ -88,7 +64,7 @@ __global__ void __launch_bounds__(256) k_edt_rows(Launch L, int RB, int Wmax) {
     uint16_t* gs = reinterpret_cast<uint16_t*>(smraw);                 // [RB][Wmax]
     int16_t* ms = reinterpret_cast<int16_t*>(gs + (size_t)RB * Wmax);  // [Wmax]
     int16_t* mt = ms + Wmax;                                           // [Wmax]
-    __shared__ int rowmax[32];
+    __shared__ int rowslow[32];
     const int gbnd = blockIdx.x;
     const int ti = find_tile(L.tiles, L.ntiles, gbnd, &TileDev::row_base);
     const TileDev& T = L.tiles[ti];
@@ -97,49 +73,45 @@ __global__ void __launch_bounds__(256) k_edt_rows(Launch L, int RB, int Wmax) {
     const int y0 = (gbnd - T.row_base) * RB;
     const int c = y0 / CB, r0 = c * CB;
     const int nrow = min(RB, H - y0);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int kmax = min(CB, H - r0);  // valid rows in this chunk
-    const uint32_t rowvalid = kmax >= 32 ? FULLE : ((1u << kmax) - 1u);
-    // g for the band: one warp per 32-column strip
-    for (int sidx = warp; sidx < T.wpr; sidx += nw) {
-        uint32_t word = lane < kmax ? T.keptbits[(size_t)(r0 + lane) * T.wpr + sidx] : 0xffffffffu;
-        uint32_t col = 0;  // bit k: row r0+k of column (32*sidx+lane) is kept (foreground)
-#pragma unroll
-        for (int k = 0; k < 32; k++) {
-            uint32_t w = __shfl_sync(FULLE, word, k);
-            col |= ((w >> lane) & 1u) << k;
-        }
-        const int x = sidx * 32 + lane;
-        if (x >= W) continue;
-        const uint32_t bg = ~col & rowvalid;
-        const int above = T.edtL[(size_t)c * W + x], below = T.edtF[(size_t)c * W + x];
+    const int nchunk = T.cby;
+    if (threadIdx.x < 32) rowslow[threadIdx.x] = 0;
+    __syncthreads();
+    auto rows_valid = [&](int cc) -> uint32_t {
+        int k = min(CB, H - cc * CB);
+        return k >= 32 ? FULLE : ((1u << k) - 1u);
+    };
+    const uint32_t rv = rows_valid(c);
+    // g for the band, one column per thread
+    for (int x = threadIdx.x; x < W; x += blockDim.x) {
+        const uint32_t bg = ~T.colbits[(size_t)c * W + x] & rv;
+        int above = -1, below = -1;  // nearest background row above / below this chunk
+        const int k0 = y0 - r0, k1 = y0 + nrow - 1 - r0;
+        if (!(bg & below_or_at(k0)))
+            for (int cc = c - 1; cc >= 0; cc--) {
+                uint32_t b2 = ~T.colbits[(size_t)cc * W + x] & rows_valid(cc);
+                if (b2) { above = cc * CB + 31 - __clz(b2); break; }
+            }
+        if (!(bg & ~((1u << k1) - 1u)))
+            for (int cc = c + 1; cc < nchunk; cc++) {
+                uint32_t b2 = ~T.colbits[(size_t)cc * W + x] & rows_valid(cc);
+                if (b2) { below = cc * CB + __ffs(b2) - 1; break; }
+            }
         for (int j = 0; j < nrow; j++) {
-            int y = y0 + j, k = y - r0;
-            uint32_t mu = bg & ((2u << k) - 1u);
-            int du = mu ? k - (31 - __clz(mu)) : (above >= 0 ? y - above : INFG);
-            uint32_t md = bg & ~((1u << k) - 1u);
-            int dd = md ? (__ffs(md) - 1) - k : (below >= 0 ? below - y : INFG);
-            int gv = min(min(du, dd), INFG);
+            const int y = y0 + j, k = y - r0;
+            const uint32_t mu = bg & below_or_at(k);
+            const int du = mu ? k - (31 - __clz(mu)) : (above >= 0 ? y - above : INFG);
+            const uint32_t md = bg & ~((1u << k) - 1u);
+            const int dd = md ? (__ffs(md) - 1) - k : (below >= 0 ? below - y : INFG);
+            const int gv = min(min(du, dd), INFG);
             gs[(size_t)j * Wmax + x] = (uint16_t)gv;
+            if (gv > WMAX) rowslow[j] = 1;
         }
     }
     __syncthreads();
     for (int j = 0; j < nrow; j++) {
         const uint16_t* g = gs + (size_t)j * Wmax;
-        int m = 0;
-        for (int x = threadIdx.x; x < W; x += blockDim.x) m = max(m, (int)g[x]);
-        m = __reduce_max_sync(FULLE, m);
-        if (lane == 0) rowmax[warp] = m;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            int mm = 0;
-            for (int i = 0; i < nw; i++) mm = max(mm, rowmax[i]);
-            rowmax[31] = mm;
-        }
-        __syncthreads();
-        const int mm = rowmax[31];
         int32_t* out = T.edt + (size_t)(y0 + j) * W;
-        if (mm <= WMAX) {
+        if (!rowslow[j]) {
             for (int x = threadIdx.x; x < W; x += blockDim.x) {
                 int g0 = g[x];
                 int D = sq(g0);
@@ -153,7 +125,6 @@ __global__ void __launch_bounds__(256) k_edt_rows(Launch L, int RB, int Wmax) {
         } else if (threadIdx.x == 0) {
             meijster_row(g, W, ms, mt, out);
         }
-        __syncthreads();
     }
 }
 
@@ -161,9 +132,6 @@ size_t edt_rows_smem(int RB, int Wmax) { return (size_t)RB * Wmax * 2 + (size_t)
 
 void launch_edt(const Launch& L, int RB, int Wmax, cudaStream_t s, Profiler* pf) {
     if (L.n_rows == 0) return;
-    pf->begin("edt_carry", s);
-    k_edt_carry<<<(L.n_cols + 255) / 256, 256, 0, s>>>(L);
-    pf->end("edt_carry", s);
     size_t smem = edt_rows_smem(RB, Wmax);
     cudaFuncSetAttribute(k_edt_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     pf->begin("edt_rows", s);

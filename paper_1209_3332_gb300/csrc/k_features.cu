@@ -15,38 +15,74 @@
 // order-free); the gradient sums are FP64 in a fixed thread order; the
 // co-occurrence counts are shared-memory histograms.  The FP64 finishing
 // math runs once per object, never per pixel.
+#include <cmath>
+#include <mutex>
+
 #include "internal.cuh"
 
 namespace nucseg {
 
-constexpr int FT = 128;  // threads per object CTA
 constexpr unsigned FULLF = 0xffffffffu;
+
+// c * ln(c) for c < CLNC_N in FP64: a static device table (no allocation),
+// copied from the host once per device by features_tables_ready()
+constexpr int CLNC_N = 4096;
+static __device__ double g_clnc[CLNC_N];
+
+__device__ __forceinline__ double clnc(int c) {
+    return c < CLNC_N ? g_clnc[c] : (double)c * log((double)c);
+}
 
 __global__ void k_fbbox_init(int4* bbox, int K) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < K) bbox[i] = make_int4(0x7fffffff, 0x7fffffff, -1, -1);
 }
 
-// one warp per 32 consecutive pixels of a row
+// One warp per row segment of 32*4*FB_STEPS pixels: each lane reads 4 labels
+// at a time; the lanes holding the same label (one __match_any_sync group per
+// label value) combine their column range and one lane updates the box.
+constexpr int FB_STEPS = 8;
 __global__ void __launch_bounds__(256) k_fbbox(const int32_t* __restrict__ labels, int W, int H, int K,
                                                int4* bbox) {
     const int lane = threadIdx.x & 31;
-    const int spr = (W + 31) >> 5;
+    const int seg = 32 * 4 * FB_STEPS;
+    const int spr = (W + seg - 1) / seg;
     long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (gw >= (long long)spr * H) return;
-    int y = (int)(gw / spr), x = (int)(gw - (long long)y * spr) * 32 + lane;
-    int lab = x < W ? __ldcs(labels + (size_t)y * W + x) : 0;
-    if (lab < 1 || lab > K) lab = 0;
-    if (__ballot_sync(FULLF, lab != 0) == 0) return;
-    unsigned grp = __match_any_sync(FULLF, lab);
-    if (lab == 0) return;
-    int mn = __reduce_min_sync(grp, (unsigned)x), mx = __reduce_max_sync(grp, (unsigned)x);
-    if (lane == __ffs(grp) - 1) {
-        int4* b = bbox + (lab - 1);
-        atomicMin(&b->x, mn);
-        atomicMax(&b->z, mx);
-        atomicMin(&b->y, y);
-        atomicMax(&b->w, y);
+    const int y = (int)(gw / spr), xs = (int)(gw - (long long)y * spr) * seg;
+    const int32_t* row = labels + (size_t)y * W;
+    const bool vec = (W & 3) == 0;
+    for (int step = 0; step < FB_STEPS; step++) {
+        const int x0 = xs + (step * 32 + lane) * 4;
+        int v[4] = {0, 0, 0, 0};
+        if (vec && x0 + 3 < W) {
+            int4 q = __ldcs(reinterpret_cast<const int4*>(row + x0));
+            v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+        } else {
+            for (int k = 0; k < 4; k++) v[k] = x0 + k < W ? __ldcs(row + x0 + k) : 0;
+        }
+        if (__ballot_sync(FULLF, (v[0] | v[1] | v[2] | v[3]) != 0) == 0) continue;
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            int lab = (v[k] >= 1 && v[k] <= K) ? v[k] : 0;
+            // the other pixels of this lane with the same label join this update
+            int mn = 0x7fffffff, mx = -1;
+            if (lab) {
+                for (int j = k; j < 4; j++)
+                    if (v[j] == lab) { mn = min(mn, x0 + j); mx = max(mx, x0 + j); v[j] = 0; }
+            }
+            unsigned grp = __match_any_sync(FULLF, lab);
+            if (lab) {
+                int gmn = __reduce_min_sync(grp, (unsigned)mn), gmx = __reduce_max_sync(grp, (unsigned)mx);
+                if (lane == __ffs(grp) - 1) {
+                    int4* b = bbox + (lab - 1);
+                    atomicMin(&b->x, gmn);
+                    atomicMax(&b->z, gmx);
+                    atomicMin(&b->y, y);
+                    atomicMax(&b->w, y);
+                }
+            }
+        }
     }
 }
 
@@ -78,61 +114,42 @@ __device__ __forceinline__ T warp_sum(T v) {
     return v;
 }
 
-// block reduction of a sum in fixed order: lanes (xor tree), then warps in index order
-template <typename T>
-__device__ T block_sum(T v, T* tmp) {
-    v = warp_sum(v);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0) tmp[warp] = v;
-    __syncthreads();
-    T s = 0;
-    for (int i = 0; i < FT / 32; i++) s += tmp[i];
-    __syncthreads();
-    return s;
-}
-__device__ int block_min(int v, int* tmp) {
-    v = __reduce_min_sync(FULLF, v);
-    if ((threadIdx.x & 31) == 0) tmp[threadIdx.x >> 5] = v;
-    __syncthreads();
-    int s = tmp[0];
-    for (int i = 1; i < FT / 32; i++) s = min(s, tmp[i]);
-    __syncthreads();
-    return s;
-}
-__device__ int block_max(int v, int* tmp) {
-    v = __reduce_max_sync(FULLF, v);
-    if ((threadIdx.x & 31) == 0) tmp[threadIdx.x >> 5] = v;
-    __syncthreads();
-    int s = tmp[0];
-    for (int i = 1; i < FT / 32; i++) s = max(s, tmp[i]);
-    __syncthreads();
-    return s;
+// |Sobel| as a double: sqrtf (correctly rounded) refined by one Newton step
+// in FP64, s + (m2 - s^2) / (2 s), whose residual m2 - s^2 is exact in FP64;
+// relative error ~1e-14, at two FP64 operations per pixel.
+__device__ __forceinline__ double grad_mag(int m2) {
+    if (m2 == 0) return 0.0;
+    float sf = sqrtf((float)m2);
+    double sd = (double)sf;
+    double r = fma(-sd, sd, (double)m2);
+    return sd + (double)((float)r * (0.5f / sf));
 }
 
-__device__ void object_features(const ObjJob& J, int obj, int* glcm, long long* tl, double* td,
-                                int* ti, double* ostat) {
+// Features of object `obj` by one warp; glcm: this warp's 4x64 counters.
+__device__ void object_features(const ObjJob& J, int obj, int* glcm) {
+    const int lane = threadIdx.x & 31;
     const int l = obj + 1;
     const int4 box = J.bbox[obj];
     float* out = J.feats + (size_t)obj * NFEAT;
     const int W = J.W, H = J.H;
     // a box outside the image (no pixel carries this label) yields zeros
     if (box.x < 0 || box.y < 0 || box.z >= W || box.w >= H || box.x > box.z || box.y > box.w) {
-        if (threadIdx.x < NFEAT) out[threadIdx.x] = 0.f;
+        if (lane < NFEAT) out[lane] = 0.f;
         return;
     }
     const int bw = box.z - box.x + 1, bh = box.w - box.y + 1;
     const long long npx = (long long)bw * bh;
-    for (int i = threadIdx.x; i < 4 * 64; i += FT) glcm[i] = 0;
-    __syncthreads();
+    for (int i = lane; i < 4 * 64; i += 32) glcm[i] = 0;
+    __syncwarp();
     int cnt = 0, per = 0, mn = 255, mx = 0, gmn = 0x7fffffff, gmx = 0;
     long long S = 0, Q = 0;
     double gs = 0.0;
     const int odx[4] = {1, 0, 1, 1}, ody[4] = {0, 1, 1, -1};
-    for (long long idx = threadIdx.x; idx < npx; idx += FT) {
-        int y = box.y + (int)(idx / bw), x = box.x + (int)(idx % bw);
-        size_t p = (size_t)y * W + x;
+    for (long long idx = lane; idx < npx; idx += 32) {
+        const int y = box.y + (int)(idx / bw), x = box.x + (int)(idx % bw);
+        const size_t p = (size_t)y * W + x;
         if (J.labels[p] != l) continue;
-        int v = J.hem8[p];
+        const int v = J.hem8[p];
         cnt++;
         S += v;
         Q += v * v;
@@ -142,76 +159,76 @@ __device__ void object_features(const ObjJob& J, int obj, int* glcm, long long* 
         per += (y == H - 1 || J.labels[p + W] != l);
         per += (x == 0 || J.labels[p - 1] != l);
         per += (x == W - 1 || J.labels[p + 1] != l);
-        int m2 = sobel_m2(J.hem8, W, H, y, x);
-        gs += sqrt((double)m2);
+        const int m2 = sobel_m2(J.hem8, W, H, y, x);
+        gs += grad_mag(m2);
         gmn = min(gmn, m2);
         gmx = max(gmx, m2);
 #pragma unroll
         for (int o = 0; o < 4; o++) {
-            int yy = y + ody[o], xx = x + odx[o];
+            const int yy = y + ody[o], xx = x + odx[o];
             if (yy < 0 || yy >= H || xx >= W) continue;
-            size_t q = (size_t)yy * W + xx;
+            const size_t q = (size_t)yy * W + xx;
             if (J.labels[q] != l) continue;
             atomicAdd(&glcm[o * 64 + (v >> 5) * 8 + (J.hem8[q] >> 5)], 1);
         }
     }
-    const long long N = block_sum<long long>(cnt, tl);
-    const long long Ssum = block_sum<long long>(S, tl);
-    const long long Qsum = block_sum<long long>(Q, tl);
-    const long long Per = block_sum<long long>(per, tl);
-    const int Mn = block_min(mn, ti), Mx = block_max(mx, ti);
-    const int Gmn = block_min(gmn, ti), Gmx = block_max(gmx, ti);
-    const double Gs = block_sum<double>(gs, td);
+    const long long N = warp_sum<long long>(cnt);
+    const long long Ssum = warp_sum<long long>(S), Qsum = warp_sum<long long>(Q);
+    const long long Per = warp_sum<long long>(per);
+    const int Mn = __reduce_min_sync(FULLF, mn), Mx = __reduce_max_sync(FULLF, mx);
+    const int Gmn = __reduce_min_sync(FULLF, gmn), Gmx = __reduce_max_sync(FULLF, gmx);
+    const double Gs = warp_sum<double>(gs);
     if (N == 0) {
-        if (threadIdx.x < NFEAT) out[threadIdx.x] = 0.f;
-        __syncthreads();
+        if (lane < NFEAT) out[lane] = 0.f;
+        __syncwarp();
         return;
     }
     const double gmean = Gs / (double)N;
     double gss = 0.0;
-    for (long long idx = threadIdx.x; idx < npx; idx += FT) {
-        int y = box.y + (int)(idx / bw), x = box.x + (int)(idx % bw);
+    for (long long idx = lane; idx < npx; idx += 32) {
+        const int y = box.y + (int)(idx / bw), x = box.x + (int)(idx % bw);
         if (J.labels[(size_t)y * W + x] != l) continue;
-        double d = sqrt((double)sobel_m2(J.hem8, W, H, y, x)) - gmean;
+        const double d = grad_mag(sobel_m2(J.hem8, W, H, y, x)) - gmean;
         gss += d * d;
     }
-    const double Gss = block_sum<double>(gss, td);
-    // co-occurrence statistics: warp o handles offset o (bins lane, lane+32)
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (warp < 4) {
-        const int* c = glcm + warp * 64;
-        long long T = 0, si = 0, sj = 0, sii = 0, sjj = 0, sij = 0;
-        for (int b = lane; b < 64; b += 32) {
-            long long v = c[b];
-            int i = b >> 3, j = b & 7;
-            T += v; si += i * v; sj += j * v; sii += i * i * v; sjj += j * j * v; sij += i * j * v;
-        }
-        T = warp_sum(T); si = warp_sum(si); sj = warp_sum(sj);
-        sii = warp_sum(sii); sjj = warp_sum(sjj); sij = warp_sum(sij);
-        double con = 0, ene = 0, hom = 0, ent = 0;
-        if (T > 0) {
-            for (int b = lane; b < 64; b += 32) {
-                int v = c[b];
-                if (!v) continue;
-                int i = b >> 3, j = b & 7;
-                double P = (double)v / (double)T;
-                con += (double)((i - j) * (i - j)) * P;
-                ene += P * P;
-                hom += P / (1.0 + (double)((i - j) * (i - j)));
-                ent -= P * log(P);
-            }
-        }
-        con = warp_sum(con); ene = warp_sum(ene); hom = warp_sum(hom); ent = warp_sum(ent);
-        if (lane == 0) {
-            long long vi = T * sii - si * si, vj = T * sjj - sj * sj, cv = T * sij - si * sj;
-            double cor = (vi == 0 || vj == 0) ? 0.0 : (double)cv / sqrt((double)vi * (double)vj);
-            double* os = ostat + warp * 6;
-            os[0] = T > 0 ? 1.0 : 0.0;
-            os[1] = con; os[2] = ene; os[3] = hom; os[4] = ent; os[5] = cor;
-        }
+    const double Gss = warp_sum<double>(gss);
+    __syncwarp();
+    // co-occurrence statistics per offset: lanes hold bins lane and lane+32.
+    // With counts C_ij and T = sum C_ij: contrast = sum (i-j)^2 C / T, energy =
+    // sum C^2 / T^2, homogeneity = sum C/(1+(i-j)^2) / T (integer numerator over
+    // the common multiple 408850 of the denominators 1+(i-j)^2), entropy =
+    // ln T - sum C ln C / T, correlation from integer moments.  Only a few
+    // FP64 operations per offset remain (the GPU's FP64 rate is low).
+    double acc[5] = {0, 0, 0, 0, 0};
+    int used = 0;
+    const int i0 = lane >> 3, j0 = lane & 7, i1 = i0 + 4, j1 = j0;
+    const int d0 = (i0 - j0) * (i0 - j0), d1 = (i1 - j1) * (i1 - j1);
+    const long long HL = 408850;  // lcm of 1+d^2 for d = 0..7
+#pragma unroll
+    for (int o = 0; o < 4; o++) {
+        const int* c = glcm + o * 64;
+        const long long v0 = c[lane], v1 = c[lane + 32];
+        const long long T = warp_sum<long long>(v0 + v1);
+        if (T == 0) continue;
+        used++;
+        const long long si = warp_sum<long long>(i0 * v0 + i1 * v1);
+        const long long sj = warp_sum<long long>(j0 * v0 + j1 * v1);
+        const long long sii = warp_sum<long long>(i0 * i0 * v0 + i1 * i1 * v1);
+        const long long sjj = warp_sum<long long>(j0 * j0 * v0 + j1 * j1 * v1);
+        const long long sij = warp_sum<long long>(i0 * j0 * v0 + i1 * j1 * v1);
+        const long long scon = warp_sum<long long>(d0 * v0 + d1 * v1);
+        const long long sene = warp_sum<long long>(v0 * v0 + v1 * v1);
+        const long long shom = warp_sum<long long>((HL / (1 + d0)) * v0 + (HL / (1 + d1)) * v1);
+        const double sent = warp_sum<double>(clnc((int)v0) + clnc((int)v1));
+        const double Td = (double)T;
+        const long long vi = T * sii - si * si, vj = T * sjj - sj * sj, cv = T * sij - si * sj;
+        acc[0] += (double)scon / Td;
+        acc[1] += (double)sene / (Td * Td);
+        acc[2] += (double)shom / ((double)HL * Td);
+        acc[3] += log(Td) - sent / Td;
+        acc[4] += (vi == 0 || vj == 0) ? 0.0 : (double)cv / sqrt((double)vi * (double)vj);
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
+    if (lane == 0) {
         const double n = (double)N;
         __int128 var_num = (__int128)N * Qsum - (__int128)Ssum * Ssum;
         double f[NFEAT];
@@ -225,29 +242,19 @@ __device__ void object_features(const ObjJob& J, int obj, int* glcm, long long* 
         f[7] = sqrt(Gss / n);
         f[8] = sqrt((double)Gmn);
         f[9] = sqrt((double)Gmx);
-        double acc[5] = {0, 0, 0, 0, 0};
-        int used = 0;
-        for (int o = 0; o < 4; o++) {
-            const double* os = ostat + o * 6;
-            if (os[0] == 0.0) continue;
-            used++;
-            for (int k = 0; k < 5; k++) acc[k] += os[1 + k];
-        }
         for (int k = 0; k < 5; k++) f[10 + k] = used ? acc[k] / used : 0.0;
         for (int k = 0; k < NFEAT; k++) out[k] = (float)f[k];
     }
-    __syncthreads();
+    __syncwarp();
 }
 
-// Object CTAs.  Plain form: one tile, objects [0, K).  Batched form: the
-// objects of all tiles, item -> (tile, object) through obj_base prefixes.
-__global__ void __launch_bounds__(FT) k_fobj_plain(ObjJob J, int K) {
-    __shared__ int glcm[4 * 64];
-    __shared__ long long tl[FT / 32];
-    __shared__ double td[FT / 32];
-    __shared__ int ti[FT / 32];
-    __shared__ double ostat[4 * 6];
-    for (int obj = blockIdx.x; obj < K; obj += gridDim.x) object_features(J, obj, glcm, tl, td, ti, ostat);
+constexpr int FW = 4;  // object warps per CTA
+
+// Plain form: objects [0, K) of one tile, one warp each.
+__global__ void __launch_bounds__(FW * 32) k_fobj_plain(ObjJob J, int K) {
+    __shared__ int glcm[FW][4 * 64];
+    const int warp = threadIdx.x >> 5;
+    for (int obj = blockIdx.x * FW + warp; obj < K; obj += gridDim.x * FW) object_features(J, obj, glcm[warp]);
 }
 
 __global__ void k_obj_prefix(Launch L) {
@@ -264,20 +271,31 @@ __global__ void k_obj_prefix(Launch L) {
     L.sh->nobj = run;
 }
 
-__global__ void __launch_bounds__(FT) k_fobj_batched(Launch L) {
-    __shared__ int glcm[4 * 64];
-    __shared__ long long tl[FT / 32];
-    __shared__ double td[FT / 32];
-    __shared__ int tis[FT / 32];
-    __shared__ double ostat[4 * 6];
+// Batched form: the objects of all tiles, item -> (tile, object) through the
+// obj_base prefixes (the last tile whose base is <= item owns it).
+__global__ void __launch_bounds__(FW * 32) k_fobj_batched(Launch L) {
+    __shared__ int glcm[FW][4 * 64];
+    const int warp = threadIdx.x >> 5;
     const int total = L.sh->nobj;
-    for (int item = blockIdx.x; item < total; item += gridDim.x) {
-        int t = find_tile(L.tiles, L.ntiles, item, &TileDev::obj_base);
-        // skip tiles that contribute no object (equal bases): take the last with base <= item
+    for (int item = blockIdx.x * FW + warp; item < total; item += gridDim.x * FW) {
+        const int t = find_tile(L.tiles, L.ntiles, item, &TileDev::obj_base);
         const TileDev& T = L.tiles[t];
         ObjJob J{T.hem8, T.labels, T.W, T.H, T.bbox, T.feats};
-        object_features(J, item - T.obj_base, glcm, tl, td, tis, ostat);
+        object_features(J, item - T.obj_base, glcm[warp]);
     }
+}
+
+int features_tables_ready(int device) {
+    static std::mutex mu;
+    static bool done[64] = {false};
+    if (device < 0 || device >= 64) return 1;
+    std::lock_guard<std::mutex> lk(mu);
+    if (done[device]) return 0;
+    static double tab[CLNC_N];
+    for (int c = 0; c < CLNC_N; c++) tab[c] = c > 0 ? (double)c * std::log((double)c) : 0.0;
+    if (cudaMemcpyToSymbol(g_clnc, tab, sizeof(tab)) != cudaSuccess) return 1;
+    done[device] = true;
+    return 0;
 }
 
 void launch_features_plain(const uint8_t* hem8, const int32_t* labels, int W, int H, int K, float* feats,
@@ -287,13 +305,13 @@ void launch_features_plain(const uint8_t* hem8, const int32_t* labels, int W, in
     k_fbbox_init<<<(K + 255) / 256, 256, 0, s>>>(bbox, K);
     pf->end("feat_bbox_init", s);
     pf->begin("feat_bbox", s);
-    long long warps = (long long)((W + 31) / 32) * H;
+    long long warps = (long long)((W + 32 * 4 * FB_STEPS - 1) / (32 * 4 * FB_STEPS)) * H;
     k_fbbox<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, s>>>(labels, W, H, K, bbox);
     pf->end("feat_bbox", s);
     ObjJob J{hem8, labels, W, H, bbox, feats};
-    int grid = K < sms * 16 ? K : sms * 16;
+    int grid = (K + FW - 1) / FW < sms * 16 ? (K + FW - 1) / FW : sms * 16;
     pf->begin("feat_objects", s);
-    k_fobj_plain<<<grid, FT, 0, s>>>(J, K);
+    k_fobj_plain<<<grid, FW * 32, 0, s>>>(J, K);
     pf->end("feat_objects", s);
 }
 
@@ -302,7 +320,7 @@ void launch_features_batched(const Launch& L, int sms, cudaStream_t s, Profiler*
     k_obj_prefix<<<1, 32, 0, s>>>(L);
     pf->end("feat_prefix", s);
     pf->begin("feat_objects", s);
-    k_fobj_batched<<<sms * 16, FT, 0, s>>>(L);
+    k_fobj_batched<<<sms * 16, FW * 32, 0, s>>>(L);
     pf->end("feat_objects", s);
 }
 

@@ -4,10 +4,11 @@
 //
 // Both steps are connected-component problems solved with the same block
 // union-find scheme:
-//  * a 32x32 labelling block stages its class bits (one 32-bit word per
-//    row) and labels its local components in shared memory with union-find
-//    whose links always point to the smaller index, so every local root is
-//    the first pixel (row-major) of its local component;
+//  * one warp labels a 32x32 block: lane y holds the 32-bit class word of
+//    row y, runs of set bits are the union-find nodes, and only runs of
+//    adjacent rows that touch are unioned (links point to the smaller
+//    index, so every local root is the first pixel, row-major, of its local
+//    component);
 //  * local roots get a slot in the sparse global arrays P (parent) and A
 //    (payload) at their own pixel index and are appended to a root list;
 //  * block edges publish the local roots of their edge pixels; a merge
@@ -53,9 +54,16 @@ __device__ __forceinline__ void s_union(int* par, int a, int b) {
 }
 
 // ---- global union-find -----------------------------------------------------------
+// find with path halving; the shortcut is written with atomicMin, so it can
+// only lower a link to an ancestor and never undoes a concurrent union
 __device__ __forceinline__ int g_find(int* P, int a) {
     int p = __ldcg(P + a);
-    while (p != a) { a = p; p = __ldcg(P + a); }
+    while (p != a) {
+        int gp = __ldcg(P + p);
+        if (gp != p) atomicMin(P + a, gp);
+        a = p;
+        p = gp;
+    }
     return a;
 }
 __device__ __forceinline__ void g_union(int* P, int a, int b) {
@@ -77,41 +85,63 @@ __device__ __forceinline__ void g_union(int* P, int a, int b) {
     } while (!done);
 }
 
-// Local components of the class bits cls[CB] (bit x of word y = pixel (y,x))
-// of one block.  On return par[i] is the local root (first pixel) of pixel i,
-// or -1 when i is not in the class.
+// ---- run-based local labelling, one warp per 32x32 block --------------------------
+// Lane y holds the class word of row y (bit x = pixel (y, x)).  Runs of
+// consecutive set bits are the nodes: a run is named by the pixel index of
+// its first bit, par[] (per-warp shared memory, 1024 ints) holds union-find
+// links at run starts only, and links always point to the smaller index, so
+// a root is the first pixel (row-major) of its local component.  Only runs of
+// adjacent rows that touch are unioned: a run of the row above covering
+// columns [a, e] touches the runs of this row that meet [a, e] (4-conn) or
+// [a-1, e+1] (8-conn).
+
+__device__ __forceinline__ uint32_t below_or_at(int x) { return (2u << x) - 1u; }  // bits 0..x
+
+// first bit of the run (of starts `st`) containing column x
+__device__ __forceinline__ int run_start(uint32_t st, int x) { return 31 - __clz(st & below_or_at(x)); }
+
 template <int CONN>
-__device__ void local_ccl(const uint32_t* cls, int* par) {
-    for (int i = threadIdx.x; i < CB * CB; i += blockDim.x) {
-        int y = i >> 5, x = i & 31;
-        par[i] = ((cls[y] >> x) & 1u) ? i : -1;
+__device__ __forceinline__ void warp_ccl(uint32_t w, uint32_t st, int lane, int* par) {
+    for (uint32_t m = st; m; m &= m - 1) {
+        int i = lane * CB + __ffs(m) - 1;
+        par[i] = i;
     }
-    __syncthreads();
-    for (int i = threadIdx.x; i < CB * CB; i += blockDim.x) {
-        int y = i >> 5, x = i & 31;
-        uint32_t row = cls[y];
-        if (!((row >> x) & 1u)) continue;
-        if (x > 0 && ((row >> (x - 1)) & 1u)) s_union(par, i, i - 1);
-        if (y > 0) {
-            uint32_t up = cls[y - 1];
-            if ((up >> x) & 1u) s_union(par, i, i - CB);
-            if (CONN == 8) {
-                if (x > 0 && ((up >> (x - 1)) & 1u)) s_union(par, i, i - CB - 1);
-                if (x < CB - 1 && ((up >> (x + 1)) & 1u)) s_union(par, i, i - CB + 1);
-            }
-        }
+    __syncwarp();
+    uint32_t wu = __shfl_up_sync(FULLM, w, 1);
+    if (lane == 0) wu = 0u;
+    const uint32_t stu = wu & ~(wu << 1);
+    for (uint32_t m = stu; m; m &= m - 1) {
+        const int a = __ffs(m) - 1;
+        const uint32_t rest = ~wu & (0xffffffffu << a);
+        const int e = rest ? __ffs(rest) - 2 : 31;
+        const int lo = CONN == 8 ? max(a - 1, 0) : a, hi = CONN == 8 ? min(e + 1, 31) : e;
+        const uint32_t t = w & below_or_at(hi) & (0xffffffffu << lo);
+        if (!t) continue;
+        const int up = (lane - 1) * CB + a;
+        const int s0 = run_start(st, __ffs(t) - 1);
+        s_union(par, up, lane * CB + s0);
+        for (uint32_t m2 = st & t & ~(1u << s0); m2; m2 &= m2 - 1) s_union(par, up, lane * CB + __ffs(m2) - 1);
     }
-    __syncthreads();
-    for (int i = threadIdx.x; i < CB * CB; i += blockDim.x)
-        if (par[i] >= 0) par[i] = s_find(par, i);
-    __syncthreads();
+    __syncwarp();
+    for (uint32_t m = st; m; m &= m - 1) {
+        int i = lane * CB + __ffs(m) - 1;
+        par[i] = s_find(par, i);
+    }
+    __syncwarp();
 }
 
-struct BlockGeo {
-    int ti, bx, by, x0, y0, bw, bh, lb;  // lb: block index within its tile
+// mask of the run starting at bit s in word w
+__device__ __forceinline__ uint32_t run_mask(uint32_t w, int s) {
+    uint32_t rest = ~w & (0xffffffffu << s);
+    int e = rest ? __ffs(rest) - 2 : 31;
+    return below_or_at(e) & (0xffffffffu << s);
+}
+
+struct WarpGeo {
+    int ti, bx, by, x0, y0, bw, bh, lb;
 };
-__device__ __forceinline__ BlockGeo block_geo(const Launch& L, int gb) {
-    BlockGeo g;
+__device__ __forceinline__ WarpGeo warp_geo(const Launch& L, int gb) {
+    WarpGeo g;
     g.ti = find_tile(L.tiles, L.ntiles, gb, &TileDev::cb_base);
     const TileDev& T = L.tiles[g.ti];
     g.lb = gb - T.cb_base;
@@ -124,79 +154,110 @@ __device__ __forceinline__ BlockGeo block_geo(const Launch& L, int gb) {
     return g;
 }
 __device__ __forceinline__ uint32_t valid_mask(int bw) { return bw >= 32 ? FULLM : ((1u << bw) - 1u); }
+__device__ __forceinline__ int gidx(const TileDev& T, const WarpGeo& g, int li) {
+    return (g.y0 + (li >> 5)) * T.W + g.x0 + (li & 31);
+}
 
-// Publish edge local roots: [0,CB) left column, [CB,2CB) right column (x=31),
-// [2CB,3CB) top row, [3CB,4CB) bottom row (y=31); -1 = not in class.
-__device__ void publish_edges(const TileDev& T, const BlockGeo& g, const int* par) {
+// Edge roots: [0,CB) left column, [CB,2CB) right column (x=31), [2CB,3CB)
+// top row, [3CB,4CB) bottom row (y=31); -1 where the pixel is not in the class.
+__device__ __forceinline__ void publish_edges(const TileDev& T, const WarpGeo& g, uint32_t w, uint32_t st,
+                                              const int* par, int lane) {
     int* e = T.border + (size_t)g.lb * 4 * CB;
-    for (int k = threadIdx.x; k < 4 * CB; k += blockDim.x) {
-        int side = k / CB, j = k % CB;
-        int ly = side == 0 || side == 1 ? j : (side == 2 ? 0 : CB - 1);
-        int lx = side == 2 || side == 3 ? j : (side == 0 ? 0 : CB - 1);
-        int r = par[ly * CB + lx];
-        int v = -1;
-        if (r >= 0) v = (g.y0 + (r >> 5)) * T.W + g.x0 + (r & 31);
-        e[k] = v;
-    }
+    e[lane] = (w & 1u) ? gidx(T, g, par[lane * CB]) : -1;
+    e[CB + lane] = (w >> 31) ? gidx(T, g, par[lane * CB + run_start(st, 31)]) : -1;
+    uint32_t w0 = __shfl_sync(FULLM, w, 0), s0 = __shfl_sync(FULLM, st, 0);
+    uint32_t w31 = __shfl_sync(FULLM, w, 31), s31 = __shfl_sync(FULLM, st, 31);
+    e[2 * CB + lane] = ((w0 >> lane) & 1u) ? gidx(T, g, par[run_start(s0, lane)]) : -1;
+    e[3 * CB + lane] = ((w31 >> lane) & 1u) ? gidx(T, g, par[31 * CB + run_start(s31, lane)]) : -1;
 }
 
-// Append local roots (pixels with par[i]==i) to the tile's root list and
-// initialise P/A at their global index with payload pay[i].
-__device__ void register_roots(const TileDev& T, const BlockGeo& g, const int* par, const int* pay,
-                               int counter) {
-    for (int i = threadIdx.x; i < CB * CB; i += blockDim.x) {
-        bool root = par[i] == i;
-        unsigned m = __ballot_sync(FULLM, root);
-        if (!m) continue;
-        int lane = threadIdx.x & 31;
-        int base = 0;
-        if (lane == __ffs(m) - 1) base = atomicAdd(T.counters + counter, __popc(m));
-        base = __shfl_sync(FULLM, base, __ffs(m) - 1);
-        if (root) {
-            int gi = (g.y0 + (i >> 5)) * T.W + g.x0 + (i & 31);
-            T.P[gi] = gi;
-            T.A[gi] = pay[i];
-            T.rootlist[base + __popc(m & ((1u << lane) - 1u))] = gi;
-        }
+// Record this block's local roots (run starts that are roots) in the block's
+// own slice of the root list (RL_CAP entries: a 32x32 block has at most 512
+// 4-connected and 256 8-connected components) and initialise P/A at their
+// global index with payload pay[root].  No global counter is involved.
+__device__ __forceinline__ void register_roots(const TileDev& T, const WarpGeo& g, uint32_t st, const int* par,
+                                               const int* pay, int lane) {
+    uint32_t rs = 0;
+    for (uint32_t m = st; m; m &= m - 1) {
+        int s = __ffs(m) - 1;
+        if (par[lane * CB + s] == lane * CB + s) rs |= 1u << s;
     }
+    int n = __popc(rs), incl = n;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(FULLM, incl, o);
+        if (lane >= o) incl += y;
+    }
+    int* list = T.rootlist + (size_t)g.lb * RL_CAP;
+    int k = incl - n;
+    for (uint32_t m = rs; m; m &= m - 1) {
+        int li = lane * CB + __ffs(m) - 1;
+        int gi = gidx(T, g, li);
+        T.P[gi] = gi;
+        T.A[gi] = pay[li];
+        list[k++] = gi;
+    }
+    if (lane == 31) T.blkroots[g.lb] = incl;
 }
+
+struct WarpSmem {
+    int par[CB * CB];
+    int aux[CB * CB];
+};
 
 // ---- K3a: foreground from the h-dome, background local components ---------------
-__global__ void __launch_bounds__(CB_THREADS) k_fill_local(Launch L) {
-    __shared__ uint32_t fgw[CB], bgw[CB];
-    __shared__ int par[CB * CB];
-    __shared__ int flag[CB * CB];
-    const BlockGeo g = block_geo(L, blockIdx.x);
-    const TileDev& T = L.tiles[g.ti];
+__global__ void __launch_bounds__(CCL_WARPS * 32) k_fill_local(Launch L) {
+    __shared__ WarpSmem sm[CCL_WARPS];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int gb = blockIdx.x * CCL_WARPS + warp;
+    if (gb >= L.n_cb) return;
+    WarpSmem& S = sm[warp];
+    const WarpGeo g = warp_geo(L, gb);
+    const TileDev& T = L.tiles[g.ti];
     const uint32_t vm = valid_mask(g.bw);
-    for (int ly = warp; ly < CB; ly += CB_THREADS / 32) {
-        bool in = ly < g.bh && lane < g.bw;
-        bool fg = false;
-        if (in) {
-            size_t o = (size_t)(g.y0 + ly) * T.W + g.x0 + lane;
-            fg = (int)__ldg(T.hem8 + o) - (int)__ldcg(T.R + o) >= L.thr;
+    uint32_t fg = 0;
+    if (lane < g.bh) {
+        const size_t o = (size_t)(g.y0 + lane) * T.W + g.x0;
+        const uint8_t* hp = T.hem8 + o;
+        const uint8_t* rp = T.R + o;
+        const uint32_t thr4 = (uint32_t)L.thr * 0x01010101u;
+        if (g.bw == 32 && ((reinterpret_cast<uintptr_t>(hp) | reinterpret_cast<uintptr_t>(rp)) & 15) == 0) {
+#pragma unroll
+            for (int q = 0; q < 2; q++) {
+                uint4 hv = __ldg(reinterpret_cast<const uint4*>(hp) + q);
+                uint4 rv = __ldcg(reinterpret_cast<const uint4*>(rp) + q);
+                uint32_t hw[4] = {hv.x, hv.y, hv.z, hv.w}, rw[4] = {rv.x, rv.y, rv.z, rv.w};
+#pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    // R <= hem8 bytewise, so the bytewise difference does not wrap
+                    uint32_t ge = __vcmpgeu4(__vsub4(hw[k], rw[k]), thr4);
+                    uint32_t bits = (ge & 1u) | ((ge >> 7) & 2u) | ((ge >> 14) & 4u) | ((ge >> 21) & 8u);
+                    fg |= bits << (q * 16 + k * 4);
+                }
+            }
+        } else {
+            for (int x = 0; x < g.bw; x++)
+                if ((int)hp[x] - (int)__ldcg(rp + x) >= L.thr) fg |= 1u << x;
         }
-        uint32_t b = __ballot_sync(FULLM, fg);
-        if (lane == 0) {
-            fgw[ly] = b;
-            bgw[ly] = ly < g.bh ? (~b & vm) : 0u;
-            if (ly < g.bh) T.fgbits[(size_t)(g.y0 + ly) * T.wpr + g.bx] = b;
-        }
+        T.fgbits[(size_t)(g.y0 + lane) * T.wpr + g.bx] = fg;
     }
-    for (int i = threadIdx.x; i < CB * CB; i += blockDim.x) flag[i] = 0;
-    __syncthreads();
-    local_ccl<4>(bgw, par);
-    // a local component touching the image border marks its root
-    for (int i = threadIdx.x; i < CB * CB; i += blockDim.x) {
-        int r = par[i];
-        if (r < 0) continue;
-        int gy = g.y0 + (i >> 5), gx = g.x0 + (i & 31);
-        if (gy == 0 || gx == 0 || gy == T.H - 1 || gx == T.W - 1) flag[r] = 1;
+    const uint32_t bg = lane < g.bh ? (~fg & vm) : 0u;
+    const uint32_t st = bg & ~(bg << 1);
+    warp_ccl<4>(bg, st, lane, S.par);
+    for (uint32_t m = st; m; m &= m - 1) S.aux[lane * CB + __ffs(m) - 1] = 0;
+    __syncwarp();
+    // a component touching the image border marks its root
+    const int gy = g.y0 + lane;
+    for (uint32_t m = st; m; m &= m - 1) {
+        int s = __ffs(m) - 1;
+        uint32_t rm = run_mask(bg, s);
+        bool touch = gy == 0 || gy == T.H - 1 || (g.x0 == 0 && (rm & 1u)) ||
+                     (T.W - 1 - g.x0 < 32 && ((rm >> (T.W - 1 - g.x0)) & 1u));
+        if (touch) S.aux[S.par[lane * CB + s]] = 1;
     }
-    __syncthreads();
-    register_roots(T, g, par, flag, 0);
-    publish_edges(T, g, par);
+    __syncwarp();
+    register_roots(T, g, st, S.par, S.aux, lane);
+    publish_edges(T, g, bg, st, S.par, lane);
 }
 
 // ---- merge facing edge pixels of neighbouring blocks ------------------------------
@@ -206,40 +267,49 @@ __device__ __forceinline__ int edge_root(const TileDev& T, int bx, int by, int s
     return T.border[(size_t)(by * T.cbx + bx) * 4 * CB + side * CB + j];
 }
 
+// One warp per block: lanes walk the right column and then the bottom row.
+// Consecutive edge pixels mostly repeat the same pair of local roots, so a
+// lane unions only when its pair differs from the previous lane's.
+__device__ __forceinline__ void union_dedup(int* P, int a, int b, int lane) {
+    int pa = __shfl_up_sync(FULLM, a, 1), pb = __shfl_up_sync(FULLM, b, 1);
+    bool same = lane > 0 && pa == a && pb == b;
+    if (a >= 0 && b >= 0 && !same) g_union(P, a, b);
+}
+
 template <int CONN>
-__global__ void __launch_bounds__(256) k_merge(Launch L) {
-    int gid = blockIdx.x * blockDim.x + threadIdx.x;
-    int gb = gid / (2 * CB), k = gid % (2 * CB);
+__global__ void __launch_bounds__(CCL_WARPS * 32) k_merge(Launch L) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int gb = blockIdx.x * CCL_WARPS + warp;
     if (gb >= L.n_cb) return;
-    const BlockGeo g = block_geo(L, gb);
+    const WarpGeo g = warp_geo(L, gb);
     const TileDev& T = L.tiles[g.ti];
     const int* e = T.border + (size_t)g.lb * 4 * CB;
-    if (k < CB) {  // right column pixel (k, 31) against the next block(s) to the right
-        int a = e[CB + k];
-        if (a < 0) return;
-        int b = edge_root<CONN>(T, g.bx + 1, g.by, 0, k);
-        if (b >= 0) g_union(T.P, a, b);
+    // right column pixel (lane, 31) against the next block(s) to the right
+    {
+        int a = e[CB + lane];
+        int b = edge_root<CONN>(T, g.bx + 1, g.by, 0, lane);
+        union_dedup(T.P, a, b, lane);
         if (CONN == 8) {
-            int up = k == 0 ? edge_root<CONN>(T, g.bx + 1, g.by - 1, 0, CB - 1)
-                            : edge_root<CONN>(T, g.bx + 1, g.by, 0, k - 1);
-            if (up >= 0) g_union(T.P, a, up);
-            int dn = k == CB - 1 ? edge_root<CONN>(T, g.bx + 1, g.by + 1, 0, 0)
-                                 : edge_root<CONN>(T, g.bx + 1, g.by, 0, k + 1);
-            if (dn >= 0) g_union(T.P, a, dn);
+            int up = lane == 0 ? edge_root<CONN>(T, g.bx + 1, g.by - 1, 0, CB - 1)
+                               : edge_root<CONN>(T, g.bx + 1, g.by, 0, lane - 1);
+            union_dedup(T.P, a, up, lane);
+            int dn = lane == CB - 1 ? edge_root<CONN>(T, g.bx + 1, g.by + 1, 0, 0)
+                                    : edge_root<CONN>(T, g.bx + 1, g.by, 0, lane + 1);
+            union_dedup(T.P, a, dn, lane);
         }
-    } else {  // bottom row pixel (31, j) against the block(s) below
-        int j = k - CB;
-        int a = e[3 * CB + j];
-        if (a < 0) return;
-        int b = edge_root<CONN>(T, g.bx, g.by + 1, 2, j);
-        if (b >= 0) g_union(T.P, a, b);
+    }
+    // bottom row pixel (31, lane) against the block(s) below
+    {
+        int a = e[3 * CB + lane];
+        int b = edge_root<CONN>(T, g.bx, g.by + 1, 2, lane);
+        union_dedup(T.P, a, b, lane);
         if (CONN == 8) {
-            int l = j == 0 ? edge_root<CONN>(T, g.bx - 1, g.by + 1, 2, CB - 1)
-                           : edge_root<CONN>(T, g.bx, g.by + 1, 2, j - 1);
-            if (l >= 0) g_union(T.P, a, l);
-            int r = j == CB - 1 ? edge_root<CONN>(T, g.bx + 1, g.by + 1, 2, 0)
-                                : edge_root<CONN>(T, g.bx, g.by + 1, 2, j + 1);
-            if (r >= 0) g_union(T.P, a, r);
+            int l = lane == 0 ? edge_root<CONN>(T, g.bx - 1, g.by + 1, 2, CB - 1)
+                              : edge_root<CONN>(T, g.bx, g.by + 1, 2, lane - 1);
+            union_dedup(T.P, a, l, lane);
+            int r = lane == CB - 1 ? edge_root<CONN>(T, g.bx + 1, g.by + 1, 2, 0)
+                                   : edge_root<CONN>(T, g.bx, g.by + 1, 2, lane + 1);
+            union_dedup(T.P, a, r, lane);
         }
     }
 }
@@ -249,37 +319,40 @@ __global__ void __launch_bounds__(256) k_merge(Launch L) {
 // mode 1: copy the global root's flag back to every local root; compress P
 // mode 2: add local areas into the global root; compress P
 // mode 3: mark kept global roots in the root bitmap
-__global__ void __launch_bounds__(256) k_roots(Launch L, int counter, int mode) {
-    const int stride = gridDim.x * blockDim.x;
-    for (int ti = 0; ti < L.ntiles; ti++) {
-        const TileDev& T = L.tiles[ti];
-        const int n = __ldcg(T.counters + counter);
-        for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
-            int r = T.rootlist[j];
-            if (mode == 0) {
-                if (T.A[r]) {
-                    int g = g_find(T.P, r);
-                    if (g != r) T.A[g] = 1;
-                }
-            } else if (mode == 1) {
+__global__ void __launch_bounds__(CCL_WARPS * 32) k_roots(Launch L, int mode) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int gb = blockIdx.x * CCL_WARPS + warp;
+    if (gb >= L.n_cb) return;
+    const int ti = find_tile(L.tiles, L.ntiles, gb, &TileDev::cb_base);
+    const TileDev& T = L.tiles[ti];
+    const int lb = gb - T.cb_base;
+    const int n = T.blkroots[lb];
+    const int* list = T.rootlist + (size_t)lb * RL_CAP;
+    for (int j = lane; j < n; j += 32) {
+        int r = list[j];
+        if (mode == 0) {
+            if (T.A[r]) {
                 int g = g_find(T.P, r);
-                if (g != r) {
-                    T.A[r] = __ldcg(T.A + g);
-                    T.P[r] = g;
-                }
-            } else if (mode == 2) {
-                int g = g_find(T.P, r);
-                if (g != r) {
-                    atomicAdd(T.A + g, T.A[r]);
-                    T.P[r] = g;
-                }
-            } else {
-                if (T.P[r] == r) {
-                    int a = T.A[r];
-                    if (a >= L.amin && a <= L.amax) {
-                        int y = r / T.W, x = r - y * T.W;
-                        atomicOr(T.rootbits + (size_t)y * T.wpr + (x >> 5), 1u << (x & 31));
-                    }
+                if (g != r) T.A[g] = 1;
+            }
+        } else if (mode == 1) {
+            int g = g_find(T.P, r);
+            if (g != r) {
+                T.A[r] = __ldcg(T.A + g);
+                T.P[r] = g;
+            }
+        } else if (mode == 2) {
+            int g = g_find(T.P, r);
+            if (g != r) {
+                atomicAdd(T.A + g, T.A[r]);
+                T.P[r] = g;
+            }
+        } else {
+            if (T.P[r] == r) {
+                int a = T.A[r];
+                if (a >= L.amin && a <= L.amax) {
+                    int y = r / T.W, x = r - y * T.W;
+                    atomicOr(T.rootbits + (size_t)y * T.wpr + (x >> 5), 1u << (x & 31));
                 }
             }
         }
@@ -287,41 +360,43 @@ __global__ void __launch_bounds__(256) k_roots(Launch L, int counter, int mode) 
 }
 
 // ---- K4a: holes -> filled; foreground local components ----------------------------
-__global__ void __launch_bounds__(CB_THREADS) k_label_local(Launch L) {
-    __shared__ uint32_t fgw[CB], bgw[CB], flw[CB];
-    __shared__ int par[CB * CB];
-    __shared__ int cnt[CB * CB];
-    const BlockGeo g = block_geo(L, blockIdx.x);
+__global__ void __launch_bounds__(CCL_WARPS * 32) k_label_local(Launch L) {
+    __shared__ WarpSmem sm[CCL_WARPS];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int gb = blockIdx.x * CCL_WARPS + warp;
+    if (gb >= L.n_cb) return;
+    WarpSmem& S = sm[warp];
+    const WarpGeo g = warp_geo(L, gb);
     const TileDev& T = L.tiles[g.ti];
     const uint32_t vm = valid_mask(g.bw);
-    for (int ly = threadIdx.x; ly < CB; ly += blockDim.x) {
-        uint32_t b = ly < g.bh ? T.fgbits[(size_t)(g.y0 + ly) * T.wpr + g.bx] : 0u;
-        fgw[ly] = b;
-        bgw[ly] = ly < g.bh ? (~b & vm) : 0u;
-        flw[ly] = b;
+    const size_t wrow = (size_t)(g.y0 + lane) * T.wpr + g.bx;
+    const uint32_t fg = lane < g.bh ? T.fgbits[wrow] : 0u;
+    const uint32_t bg = lane < g.bh ? (~fg & vm) : 0u;
+    uint32_t st = bg & ~(bg << 1);
+    warp_ccl<4>(bg, st, lane, S.par);
+    // background runs whose component does not reach the border are holes
+    uint32_t filled = fg;
+    for (uint32_t m = st; m; m &= m - 1) {
+        int s = __ffs(m) - 1;
+        int gr = gidx(T, g, S.par[lane * CB + s]);
+        if (!__ldcg(T.A + gr)) filled |= run_mask(bg, s);
     }
-    for (int i = threadIdx.x; i < CB * CB; i += blockDim.x) cnt[i] = 0;
-    __syncthreads();
-    local_ccl<4>(bgw, par);
-    // background pixels whose component does not reach the border are holes
-    for (int i = threadIdx.x; i < CB * CB; i += blockDim.x) {
-        int r = par[i];
-        if (r < 0) continue;
-        int gr = (g.y0 + (r >> 5)) * T.W + g.x0 + (r & 31);
-        if (!__ldcg(T.A + gr)) atomicOr(&flw[i >> 5], 1u << (i & 31));
+    if (lane < g.bh) {
+        T.filledbits[wrow] = filled;
+        T.rootbits[wrow] = 0u;
     }
-    __syncthreads();
-    for (int ly = threadIdx.x; ly < g.bh; ly += blockDim.x) {
-        size_t w = (size_t)(g.y0 + ly) * T.wpr + g.bx;
-        T.filledbits[w] = flw[ly];
-        T.rootbits[w] = 0u;
+    __syncwarp();
+    st = filled & ~(filled << 1);
+    warp_ccl<8>(filled, st, lane, S.par);
+    for (uint32_t m = st; m; m &= m - 1) S.aux[lane * CB + __ffs(m) - 1] = 0;
+    __syncwarp();
+    for (uint32_t m = st; m; m &= m - 1) {
+        int s = __ffs(m) - 1;
+        atomicAdd(&S.aux[S.par[lane * CB + s]], __popc(run_mask(filled, s)));
     }
-    local_ccl<8>(flw, par);
-    for (int i = threadIdx.x; i < CB * CB; i += blockDim.x)
-        if (par[i] >= 0) atomicAdd(&cnt[par[i]], 1);
-    __syncthreads();
-    register_roots(T, g, par, cnt, 1);
-    publish_edges(T, g, par);
+    __syncwarp();
+    register_roots(T, g, st, S.par, S.aux, lane);
+    publish_edges(T, g, filled, st, S.par, lane);
 }
 
 // ---- K4e: exclusive popcount prefix of the root bitmap ----------------------------
@@ -387,66 +462,60 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(Launch L) {
 }
 
 // ---- K4f: final labels, kept bitmap, EDT column summaries, object boxes ----------
-__global__ void __launch_bounds__(CB_THREADS) k_relabel(Launch L, int want_bbox) {
-    __shared__ uint32_t flw[CB], keep[CB];
-    __shared__ int par[CB * CB];
-    const BlockGeo g = block_geo(L, blockIdx.x);
+struct RelabelSmem {
+    int par[CB * CB];
+    int lab[CB * (CB + 1)];
+};
+
+__global__ void __launch_bounds__(CCL_WARPS * 32) k_relabel(Launch L, int want_bbox) {
+    __shared__ RelabelSmem sm[CCL_WARPS];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int gb = blockIdx.x * CCL_WARPS + warp;
+    if (gb >= L.n_cb) return;
+    RelabelSmem& S = sm[warp];
+    const WarpGeo g = warp_geo(L, gb);
     const TileDev& T = L.tiles[g.ti];
-    for (int ly = threadIdx.x; ly < CB; ly += blockDim.x) {
-        flw[ly] = ly < g.bh ? T.filledbits[(size_t)(g.y0 + ly) * T.wpr + g.bx] : 0u;
-        keep[ly] = 0u;
+    const size_t wrow = (size_t)(g.y0 + lane) * T.wpr + g.bx;
+    const uint32_t filled = lane < g.bh ? T.filledbits[wrow] : 0u;
+    const uint32_t st = filled & ~(filled << 1);
+    warp_ccl<8>(filled, st, lane, S.par);
+    int* labrow = S.lab + lane * (CB + 1);
+    for (int x = 0; x < CB; x++) labrow[x] = 0;
+    uint32_t kept = 0;
+    const int gy = g.y0 + lane;
+    for (uint32_t m = st; m; m &= m - 1) {
+        const int s = __ffs(m) - 1;
+        const uint32_t rm = run_mask(filled, s);
+        const int gl = gidx(T, g, S.par[lane * CB + s]);
+        const int gr = __ldcg(T.P + gl);
+        const int yy = gr / T.W, xx = gr - yy * T.W;
+        const size_t w = (size_t)yy * T.wpr + (xx >> 5);
+        const uint32_t bits = T.rootbits[w];
+        if (!((bits >> (xx & 31)) & 1u)) continue;
+        const int lab = T.wordprefix[w] + __popc(bits & ((1u << (xx & 31)) - 1u)) + 1;
+        kept |= rm;
+        const int e = 31 - __clz(rm);
+        for (int x = s; x <= e; x++) labrow[x] = lab;
+        if (want_bbox && lab <= T.feats_cap) {
+            int4* b = T.bbox + (lab - 1);
+            atomicMin(&b->x, g.x0 + s);
+            atomicMax(&b->z, g.x0 + e);
+            atomicMin(&b->y, gy);
+            atomicMax(&b->w, gy);
+        }
     }
-    __syncthreads();
-    local_ccl<8>(flw, par);
-    const int lane = threadIdx.x & 31;
-    for (int i = threadIdx.x; i < CB * CB; i += blockDim.x) {
-        int ly = i >> 5, lx = i & 31;
-        int lab = 0;
-        int r = par[i];
-        if (r >= 0) {
-            int gl = (g.y0 + (r >> 5)) * T.W + g.x0 + (r & 31);
-            int gr = __ldcg(T.P + gl);
-            int yy = gr / T.W, xx = gr - yy * T.W;
-            size_t w = (size_t)yy * T.wpr + (xx >> 5);
-            uint32_t bits = T.rootbits[w];
-            if ((bits >> (xx & 31)) & 1u) lab = T.wordprefix[w] + __popc(bits & ((1u << (xx & 31)) - 1u)) + 1;
-        }
-        if (ly < g.bh && lx < g.bw) {
-            T.labels[(size_t)(g.y0 + ly) * T.W + g.x0 + lx] = lab;
-            if (want_bbox && lab > 0) {
-                // warp-aggregated box update per label
-                unsigned grp = __match_any_sync(__activemask(), lab);
-                int gx = g.x0 + lx, gy = g.y0 + ly;
-                int mnx = __reduce_min_sync(grp, (unsigned)gx), mxx = __reduce_max_sync(grp, (unsigned)gx);
-                int mny = __reduce_min_sync(grp, (unsigned)gy), mxy = __reduce_max_sync(grp, (unsigned)gy);
-                if (lane == __ffs(grp) - 1 && lab <= T.feats_cap) {
-                    int4* b = T.bbox + (lab - 1);
-                    atomicMin(&b->x, mnx); atomicMin(&b->y, mny);
-                    atomicMax(&b->z, mxx); atomicMax(&b->w, mxy);
-                }
-            }
-        }
-        unsigned kb = __ballot_sync(FULLM, lab > 0);
-        if (lane == 0) keep[ly] = kb;
+    if (lane < g.bh) T.keptbits[wrow] = kept;
+    __syncwarp();
+    // coalesced label rows: lane = column
+    if (lane < g.bw) {
+        int32_t* dst = T.labels + (size_t)g.y0 * T.W + g.x0 + lane;
+        for (int y = 0; y < g.bh; y++) dst[(size_t)y * T.W] = S.lab[y * (CB + 1) + lane];
     }
-    __syncthreads();
-    for (int ly = threadIdx.x; ly < g.bh; ly += blockDim.x)
-        T.keptbits[(size_t)(g.y0 + ly) * T.wpr + g.bx] = keep[ly];
-    // EDT column summaries of this 32-row chunk: first and last background row
-    if (T.edt && threadIdx.x < 32) {
-        int lx = threadIdx.x;
-        int fb = -1, lb = -1;
-        if (lx < g.bw) {
-            for (int ly = 0; ly < g.bh; ly++) {
-                if (!((keep[ly] >> lx) & 1u)) {
-                    if (fb < 0) fb = g.y0 + ly;
-                    lb = g.y0 + ly;
-                }
-            }
-            size_t o = (size_t)g.by * T.W + g.x0 + lx;
-            T.edtF[o] = fb;
-            T.edtL[o] = lb;
-        }
+    // EDT input: this chunk's 32 kept bits of each column, as one word per column
+    if (T.edt) {
+        uint32_t col = 0;
+        for (int y = 0; y < CB; y++) col |= ((__shfl_sync(FULLM, kept, y) >> lane) & 1u) << y;
+        if (lane < g.bw) T.colbits[(size_t)g.by * T.W + g.x0 + lane] = col;
     }
 }
 
@@ -462,11 +531,7 @@ __global__ void k_bbox_init(Launch L) {
 }
 
 __global__ void k_counters_reset(Launch L) {
-    for (int i = threadIdx.x; i < L.ntiles; i += blockDim.x) {
-        L.tiles[i].counters[0] = 0;
-        L.tiles[i].counters[1] = 0;
-        L.tile_status[i] = 0;
-    }
+    for (int i = threadIdx.x; i < L.ntiles; i += blockDim.x) L.tile_status[i] = 0;
 }
 
 __global__ void k_unpack_bits(const uint32_t* bits, int W, int H, int wpr, uint8_t* out) {
@@ -497,29 +562,29 @@ void launch_label(const Launch& L, int want_bbox, int max_objects, int sms, cuda
         pf->end("bbox_init", s);
     }
     pf->begin("fill_local", s);
-    k_fill_local<<<L.n_cb, CB_THREADS, 0, s>>>(L);
+    k_fill_local<<<(L.n_cb + CCL_WARPS - 1) / CCL_WARPS, CCL_WARPS * 32, 0, s>>>(L);
     pf->end("fill_local", s);
-    int mg = (L.n_cb * 2 * CB + 255) / 256;
+    const int wg = (L.n_cb + CCL_WARPS - 1) / CCL_WARPS;
     pf->begin("fill_merge", s);
-    k_merge<4><<<mg, 256, 0, s>>>(L);
+    k_merge<4><<<wg, CCL_WARPS * 32, 0, s>>>(L);
     pf->end("fill_merge", s);
     pf->begin("fill_roots_flag", s);
-    k_roots<<<rgrid, 256, 0, s>>>(L, 0, 0);
+    k_roots<<<wg, CCL_WARPS * 32, 0, s>>>(L, 0);
     pf->end("fill_roots_flag", s);
     pf->begin("fill_roots_copy", s);
-    k_roots<<<rgrid, 256, 0, s>>>(L, 0, 1);
+    k_roots<<<wg, CCL_WARPS * 32, 0, s>>>(L, 1);
     pf->end("fill_roots_copy", s);
     pf->begin("label_local", s);
-    k_label_local<<<L.n_cb, CB_THREADS, 0, s>>>(L);
+    k_label_local<<<(L.n_cb + CCL_WARPS - 1) / CCL_WARPS, CCL_WARPS * 32, 0, s>>>(L);
     pf->end("label_local", s);
     pf->begin("label_merge", s);
-    k_merge<8><<<mg, 256, 0, s>>>(L);
+    k_merge<8><<<wg, CCL_WARPS * 32, 0, s>>>(L);
     pf->end("label_merge", s);
     pf->begin("label_roots_area", s);
-    k_roots<<<rgrid, 256, 0, s>>>(L, 1, 2);
+    k_roots<<<wg, CCL_WARPS * 32, 0, s>>>(L, 2);
     pf->end("label_roots_area", s);
     pf->begin("label_roots_keep", s);
-    k_roots<<<rgrid, 256, 0, s>>>(L, 1, 3);
+    k_roots<<<wg, CCL_WARPS * 32, 0, s>>>(L, 3);
     pf->end("label_roots_keep", s);
     pf->begin("scan_chunks", s);
     k_scan_chunks<<<L.n_chunks, SCAN_CHUNK, 0, s>>>(L, 0);
@@ -531,7 +596,7 @@ void launch_label(const Launch& L, int want_bbox, int max_objects, int sms, cuda
     k_scan_chunks<<<L.n_chunks, SCAN_CHUNK, 0, s>>>(L, 1);
     pf->end("scan_words", s);
     pf->begin("relabel", s);
-    k_relabel<<<L.n_cb, CB_THREADS, 0, s>>>(L, want_bbox);
+    k_relabel<<<(L.n_cb + CCL_WARPS - 1) / CCL_WARPS, CCL_WARPS * 32, 0, s>>>(L, want_bbox);
     pf->end("relabel", s);
 }
 

@@ -6,18 +6,19 @@
 // Design (GB300): a persistent kernel whose warps are independent workers.
 // The image is cut into 32x32 work tiles; a device-wide queue holds the
 // tiles that may still change.  A worker pops a tile, stages R and hem8 of
-// the tile plus a one-pixel halo in shared memory, and runs the four
-// directional sweeps (down, up, right, left) -- each an exact sequential
-// sweep along one axis with the 32 lanes moving in lockstep along the other
-// axis, neighbours exchanged by shuffles -- until a full round changes
-// nothing.  It writes the tile back and queues each neighbouring tile that
-// one of the changed border pixels can still raise.  Values only grow and
-// are bounded by hem8, so any order of tile processings reaches the same
-// unique fixed point; a per-tile state machine (idle / queued / running /
-// running+dirty) makes sure a tile is never processed by two workers at
-// once and never misses a raise of its halo.  Every spin wait is bounded by
-// the pipe's cycle budget, after which the worker records ST_TIMEOUT and
-// returns.
+// the tile plus a one-pixel halo in shared memory (bytes, 2.4 KB per warp,
+// so that many workers fit on an SM and hide the queue and L2 latencies),
+// and while an exact, chain-free test says some pixel can still be raised it
+// runs four directional sweeps (down, up, right, left) -- each an exact
+// sequential sweep along one axis with the 32 lanes moving in lockstep along
+// the other axis, neighbours exchanged by shuffles.  It writes the tile back
+// and queues each neighbouring tile that one of the changed border pixels
+// can still raise.  Values only grow and are bounded by hem8, so any order
+// of tile processings reaches the same unique fixed point; a per-tile state
+// machine (idle / queued / running / running+dirty) makes sure a tile is
+// never processed by two workers at once and never misses a raise of its
+// halo.  Every spin wait is bounded by the pipe's cycle budget, after which
+// the worker records ST_TIMEOUT and returns.
 #include "internal.cuh"
 
 namespace nucseg {
@@ -126,17 +127,32 @@ __global__ void k_wl_init(Launch L) {
 
 // ---- tile processing --------------------------------------------------------------
 
+// halo pixel q of this lane: q=0 row -1 and q=1 row RT (columns lane-1), q=2
+// column -1 and q=3 column RT (rows lane), q=4 the halo-row pixels of columns
+// RT-1 and RT (lanes 0..3)
+__device__ __forceinline__ void halo_coord(int q, int lane, int x0, int y0, int& gy, int& gx) {
+    if (q < 2) { gy = q == 0 ? y0 - 1 : y0 + RT; gx = x0 + lane - 1; }
+    else if (q < 4) { gy = y0 + lane; gx = q == 2 ? x0 - 1 : x0 + RT; }
+    else { gy = (lane & 1) ? y0 + RT : y0 - 1; gx = x0 + RT - 1 + ((lane >> 1) & 1); }
+}
+__device__ __forceinline__ uint8_t& halo_ref(WarpTile& S, int q, int lane, bool mask) {
+    uint8_t* A = mask ? S.M : S.R;
+#define AX(y, x) A[((y) + 1) * HS + (x) + 4]
+    if (q == 0) return AX(-1, lane - 1);
+    if (q == 1) return AX(RT, lane - 1);
+    if (q == 2) return AX(lane, -1);
+    if (q == 3) return AX(lane, RT);
+    return AX((lane & 1) ? RT : -1, RT - 1 + ((lane >> 1) & 1));
+#undef AX
+}
+
 __device__ __forceinline__ void load_tile(WarpTile& S, const TileDev& T, int x0, int y0, int lane) {
     const int W = T.W, H = T.H;
-    // halo: q=0 row -1, q=1 row RT (columns lane-1), q=2 column -1, q=3 column RT (rows lane),
-    // q=4 the four halo-row pixels of columns RT-1 and RT (lanes 0..3)
     uint8_t hr[5], hm[5];
 #pragma unroll
     for (int q = 0; q < 5; q++) {
         int gy, gx;
-        if (q < 2) { gy = q == 0 ? y0 - 1 : y0 + RT; gx = x0 + lane - 1; }
-        else if (q < 4) { gy = y0 + lane; gx = q == 2 ? x0 - 1 : x0 + RT; }
-        else { gy = (lane & 1) ? y0 + RT : y0 - 1; gx = x0 + RT - 1 + ((lane >> 1) & 1); }
+        halo_coord(q, lane, x0, y0, gy, gx);
         bool in = gy >= 0 && gy < H && gx >= 0 && gx < W && (q < 4 || lane < 4);
         size_t o = (size_t)gy * W + gx;
         hr[q] = in ? __ldcg(T.R + o) : (uint8_t)0;
@@ -169,27 +185,22 @@ __device__ __forceinline__ void load_tile(WarpTile& S, const TileDev& T, int x0,
             SM(yy, lane) = in ? __ldg(T.hem8 + o) : (uint8_t)0;
         }
     }
-    SR(-1, lane - 1) = hr[0]; SM(-1, lane - 1) = hm[0];
-    SR(RT, lane - 1) = hr[1]; SM(RT, lane - 1) = hm[1];
-    SR(lane, -1) = hr[2]; SM(lane, -1) = hm[2];
-    SR(lane, RT) = hr[3]; SM(lane, RT) = hm[3];
-    if (lane < 4) {
-        int yy = (lane & 1) ? RT : -1, xx = RT - 1 + ((lane >> 1) & 1);
-        SR(yy, xx) = hr[4]; SM(yy, xx) = hm[4];
+#pragma unroll
+    for (int q = 0; q < 5; q++) {
+        if (q == 4 && lane >= 4) continue;
+        halo_ref(S, q, lane, false) = hr[q];
+        halo_ref(S, q, lane, true) = hm[q];
     }
     __syncwarp();
 }
 
-// One round of the four sweeps; returns whether this lane changed a pixel.
-__device__ __forceinline__ bool sweep_round(WarpTile& S, int lane) {
-    bool ch = false;
-    // down: row y takes the 3 pixels above it
-    {
+// One round of the four sweeps.
+__device__ __forceinline__ void sweep_round(WarpTile& S, int lane) {
+    {   // down: row y takes the 3 pixels above it
         int prev = SR(-1, lane), pl = SR(-1, lane - 1), pr = SR(-1, lane + 1);
         for (int y = 0; y < RT; y++) {
-            int r = SR(y, lane), m = SM(y, lane);
-            int nv = max(r, min(max(prev, max(pl, pr)), m));
-            if (nv != r) { SR(y, lane) = (uint8_t)nv; ch = true; }
+            int nv = max((int)SR(y, lane), min(__vimax3_s32(prev, pl, pr), (int)SM(y, lane)));
+            SR(y, lane) = (uint8_t)nv;
             prev = nv;
             int a = __shfl_up_sync(FULL, nv, 1), b = __shfl_down_sync(FULL, nv, 1);
             pl = lane == 0 ? (int)SR(y, -1) : a;
@@ -197,13 +208,11 @@ __device__ __forceinline__ bool sweep_round(WarpTile& S, int lane) {
         }
     }
     __syncwarp();
-    // up: row y takes the 3 pixels below it
-    {
+    {   // up: row y takes the 3 pixels below it
         int prev = SR(RT, lane), pl = SR(RT, lane - 1), pr = SR(RT, lane + 1);
         for (int y = RT - 1; y >= 0; y--) {
-            int r = SR(y, lane), m = SM(y, lane);
-            int nv = max(r, min(max(prev, max(pl, pr)), m));
-            if (nv != r) { SR(y, lane) = (uint8_t)nv; ch = true; }
+            int nv = max((int)SR(y, lane), min(__vimax3_s32(prev, pl, pr), (int)SM(y, lane)));
+            SR(y, lane) = (uint8_t)nv;
             prev = nv;
             int a = __shfl_up_sync(FULL, nv, 1), b = __shfl_down_sync(FULL, nv, 1);
             pl = lane == 0 ? (int)SR(y, -1) : a;
@@ -211,13 +220,11 @@ __device__ __forceinline__ bool sweep_round(WarpTile& S, int lane) {
         }
     }
     __syncwarp();
-    // right: column x takes the 3 pixels left of it (lane = row)
-    {
+    {   // right: column x takes the 3 pixels left of it (lane = row)
         int prev = SR(lane, -1), pu = SR(lane - 1, -1), pd = SR(lane + 1, -1);
         for (int x = 0; x < RT; x++) {
-            int r = SR(lane, x), m = SM(lane, x);
-            int nv = max(r, min(max(prev, max(pu, pd)), m));
-            if (nv != r) { SR(lane, x) = (uint8_t)nv; ch = true; }
+            int nv = max((int)SR(lane, x), min(__vimax3_s32(prev, pu, pd), (int)SM(lane, x)));
+            SR(lane, x) = (uint8_t)nv;
             prev = nv;
             int a = __shfl_up_sync(FULL, nv, 1), b = __shfl_down_sync(FULL, nv, 1);
             pu = lane == 0 ? (int)SR(-1, x) : a;
@@ -225,13 +232,11 @@ __device__ __forceinline__ bool sweep_round(WarpTile& S, int lane) {
         }
     }
     __syncwarp();
-    // left: column x takes the 3 pixels right of it
-    {
+    {   // left: column x takes the 3 pixels right of it
         int prev = SR(lane, RT), pu = SR(lane - 1, RT), pd = SR(lane + 1, RT);
         for (int x = RT - 1; x >= 0; x--) {
-            int r = SR(lane, x), m = SM(lane, x);
-            int nv = max(r, min(max(prev, max(pu, pd)), m));
-            if (nv != r) { SR(lane, x) = (uint8_t)nv; ch = true; }
+            int nv = max((int)SR(lane, x), min(__vimax3_s32(prev, pu, pd), (int)SM(lane, x)));
+            SR(lane, x) = (uint8_t)nv;
             prev = nv;
             int a = __shfl_up_sync(FULL, nv, 1), b = __shfl_down_sync(FULL, nv, 1);
             pu = lane == 0 ? (int)SR(-1, x) : a;
@@ -239,22 +244,35 @@ __device__ __forceinline__ bool sweep_round(WarpTile& S, int lane) {
         }
     }
     __syncwarp();
-    return ch;
+}
+
+// Whether some pixel of the tile can still be raised by one of its 8
+// neighbours: the exact convergence test, evaluated for all pixels in
+// parallel (lane = column), so it has no dependent chain.
+__device__ __forceinline__ bool can_raise(WarpTile& S, int lane) {
+    bool v = false;
+    int a = __vimax3_s32(SR(-1, lane - 1), SR(-1, lane), SR(-1, lane + 1));
+    int b = __vimax3_s32(SR(0, lane - 1), SR(0, lane), SR(0, lane + 1));
+#pragma unroll 4
+    for (int y = 0; y < RT; y++) {
+        int c = __vimax3_s32(SR(y + 1, lane - 1), SR(y + 1, lane), SR(y + 1, lane + 1));
+        v |= min(__vimax3_s32(a, b, c), (int)SM(y, lane)) > (int)SR(y, lane);
+        a = b;
+        b = c;
+    }
+    return __any_sync(FULL, v);
 }
 
 // Whether a changed border line of this tile can raise the facing halo line.
-// own: this lane's border pixel value, changed: whether it changed;
-// halo_r / halo_m: R and mask of the halo pixel facing this lane.
 __device__ __forceinline__ bool line_need(int own, bool changed, int halo_r, int halo_m, int lane) {
     int cv = changed ? own : 0;
     int a = __shfl_up_sync(FULL, cv, 1), b = __shfl_down_sync(FULL, cv, 1);
     if (lane == 0) a = 0;
     if (lane == 31) b = 0;
-    int cand = max(cv, max(a, b));
-    return __any_sync(FULL, min(halo_m, cand) > halo_r);
+    return __any_sync(FULL, min(halo_m, __vimax3_s32(cv, a, b)) > halo_r);
 }
 
-__global__ void __launch_bounds__(RT_WARPS * 32) k_recon(Launch L) {
+__global__ void __launch_bounds__(RT_WARPS * 32, RECON_MIN_BLOCKS) k_recon(Launch L) {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     WarpTile& S = reinterpret_cast<WarpTile*>(smraw)[warp];
@@ -275,49 +293,67 @@ __global__ void __launch_bounds__(RT_WARPS * 32) k_recon(Launch L) {
             const int top0 = SR(0, lane), bot0 = SR(RT - 1, lane);
             const int lef0 = SR(lane, 0), rig0 = SR(lane, RT - 1);
             bool any = false, more = false;
-            for (int round = 0;; round++) {
-                bool ch = sweep_round(S, lane);
-                bool a = __any_sync(FULL, ch);
-                if (!a) break;
+            for (int round = 0; can_raise(S, lane); round++) {
+                if (round >= MAX_ROUNDS) { more = true; break; }
+                sweep_round(S, lane);
                 any = true;
-                if (round + 1 >= MAX_ROUNDS) { more = true; break; }
             }
             if (lane == 0) atomicAdd(&L.sh->processed, 1);
             if (any) {
-                // write back the interior
                 const int gx = x0 + lane;
                 for (int y = 0; y < RT; y++) {
                     int gy = y0 + y;
                     if (gy < T.H && gx < T.W) __stcg(T.R + (size_t)gy * T.W + gx, SR(y, lane));
                 }
                 __threadfence();
-                // neighbours that a changed border pixel can still raise
+                // judge the neighbours against the halo as it is now: values only
+                // grow, so a fresh read can only remove needless requests
+                uint8_t hr[5];
+#pragma unroll
+                for (int q = 0; q < 5; q++) {
+                    int gy, hx;
+                    halo_coord(q, lane, x0, y0, gy, hx);
+                    bool in = gy >= 0 && gy < T.H && hx >= 0 && hx < T.W && (q < 4 || lane < 4);
+                    hr[q] = in ? __ldcg(T.R + (size_t)gy * T.W + hx) : (uint8_t)0;
+                }
+                __syncwarp();
+#pragma unroll
+                for (int q = 0; q < 5; q++) {
+                    if (q == 4 && lane >= 4) continue;
+                    uint8_t& h = halo_ref(S, q, lane, false);
+                    h = max(h, hr[q]);
+                }
+                __syncwarp();
                 const int top = SR(0, lane), bot = SR(RT - 1, lane);
                 const int lef = SR(lane, 0), rig = SR(lane, RT - 1);
-                bool nU = line_need(top, top != top0, SR(-1, lane), SM(-1, lane), lane);
-                bool nD = line_need(bot, bot != bot0, SR(RT, lane), SM(RT, lane), lane);
-                bool nL = line_need(lef, lef != lef0, SR(lane, -1), SM(lane, -1), lane);
-                bool nR = line_need(rig, rig != rig0, SR(lane, RT), SM(lane, RT), lane);
+                const bool nU = line_need(top, top != top0, SR(-1, lane), SM(-1, lane), lane);
+                const bool nD = line_need(bot, bot != bot0, SR(RT, lane), SM(RT, lane), lane);
+                const bool nL = line_need(lef, lef != lef0, SR(lane, -1), SM(lane, -1), lane);
+                const bool nR = line_need(rig, rig != rig0, SR(lane, RT), SM(lane, RT), lane);
                 // corner halo pixels face a single tile pixel
-                int t00 = __shfl_sync(FULL, top0, 0), t31 = __shfl_sync(FULL, top0, 31);
-                int b00 = __shfl_sync(FULL, bot0, 0), b31 = __shfl_sync(FULL, bot0, 31);
-                if (lane == 0) {
-                    int v;
-                    bool nUL = (v = SR(0, 0)) != t00 && min((int)SM(-1, -1), v) > SR(-1, -1);
-                    bool nUR = (v = SR(0, RT - 1)) != t31 && min((int)SM(-1, RT), v) > SR(-1, RT);
-                    bool nDL = (v = SR(RT - 1, 0)) != b00 && min((int)SM(RT, -1), v) > SR(RT, -1);
-                    bool nDR = (v = SR(RT - 1, RT - 1)) != b31 && min((int)SM(RT, RT), v) > SR(RT, RT);
-                    const int base = T.rt_base, rx = T.rtx, ry = T.rty;
-                    if (nU && ty > 0) wl_request(L, base + (ty - 1) * rx + tx);
-                    if (nD && ty + 1 < ry) wl_request(L, base + (ty + 1) * rx + tx);
-                    if (nL && tx > 0) wl_request(L, base + ty * rx + tx - 1);
-                    if (nR && tx + 1 < rx) wl_request(L, base + ty * rx + tx + 1);
-                    if (nUL && ty > 0 && tx > 0) wl_request(L, base + (ty - 1) * rx + tx - 1);
-                    if (nUR && ty > 0 && tx + 1 < rx) wl_request(L, base + (ty - 1) * rx + tx + 1);
-                    if (nDL && ty + 1 < ry && tx > 0) wl_request(L, base + (ty + 1) * rx + tx - 1);
-                    if (nDR && ty + 1 < ry && tx + 1 < rx) wl_request(L, base + (ty + 1) * rx + tx + 1);
-                    if (more) wl_request(L, t);  // not converged within MAX_ROUNDS: run again
+                const int t00 = __shfl_sync(FULL, top0, 0), t31 = __shfl_sync(FULL, top0, 31);
+                const int b00 = __shfl_sync(FULL, bot0, 0), b31 = __shfl_sync(FULL, bot0, 31);
+                int v;
+                const bool nUL = (v = SR(0, 0)) != t00 && min((int)SM(-1, -1), v) > SR(-1, -1);
+                const bool nUR = (v = SR(0, RT - 1)) != t31 && min((int)SM(-1, RT), v) > SR(-1, RT);
+                const bool nDL = (v = SR(RT - 1, 0)) != b00 && min((int)SM(RT, -1), v) > SR(RT, -1);
+                const bool nDR = (v = SR(RT - 1, RT - 1)) != b31 && min((int)SM(RT, RT), v) > SR(RT, RT);
+                // lane j issues request j, so the requests overlap instead of queueing
+                const int base = T.rt_base, rx = T.rtx, ry = T.rty;
+                int target = -1;
+                switch (lane) {
+                    case 0: if (nU && ty > 0) target = base + (ty - 1) * rx + tx; break;
+                    case 1: if (nD && ty + 1 < ry) target = base + (ty + 1) * rx + tx; break;
+                    case 2: if (nL && tx > 0) target = base + ty * rx + tx - 1; break;
+                    case 3: if (nR && tx + 1 < rx) target = base + ty * rx + tx + 1; break;
+                    case 4: if (nUL && ty > 0 && tx > 0) target = base + (ty - 1) * rx + tx - 1; break;
+                    case 5: if (nUR && ty > 0 && tx + 1 < rx) target = base + (ty - 1) * rx + tx + 1; break;
+                    case 6: if (nDL && ty + 1 < ry && tx > 0) target = base + (ty + 1) * rx + tx - 1; break;
+                    case 7: if (nDR && ty + 1 < ry && tx + 1 < rx) target = base + (ty + 1) * rx + tx + 1; break;
+                    case 8: if (more) target = t; break;  // not converged within MAX_ROUNDS: run again
+                    default: break;
                 }
+                if (target >= 0) wl_request(L, target);
             }
             __syncwarp();
             int again = 0;
@@ -339,23 +375,23 @@ __global__ void __launch_bounds__(RT_WARPS * 32) k_recon(Launch L) {
     }
 }
 
-int recon_grid(int n_rt, int device) {
+// resident CTAs of the reconstruction kernel
+int recon_grid(int device) {
     int sms = 0, per = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
     size_t smem = sizeof(WarpTile) * RT_WARPS;
     cudaFuncSetAttribute(k_recon, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_recon, RT_WARPS * 32, smem);
-    if (per < 1) per = 1;
-    int want = (n_rt + RT_WARPS - 1) / RT_WARPS;
-    int cap = sms * per;
-    return want < cap ? want : cap;
+    return sms * (per < 1 ? 1 : per);
 }
 
-void launch_recon(const Launch& L, int grid, cudaStream_t s, Profiler* pf) {
+void launch_recon(const Launch& L, int grid_cap, cudaStream_t s, Profiler* pf) {
     if (L.n_rt == 0) return;
     pf->begin("recon_init", s);
     k_wl_init<<<(L.n_rt + 255) / 256, 256, 0, s>>>(L);
     pf->end("recon_init", s);
+    const int want = (L.n_rt + RT_WARPS - 1) / RT_WARPS;
+    const int grid = want < grid_cap ? want : grid_cap;
     pf->begin("recon", s);
     k_recon<<<grid, RT_WARPS * 32, sizeof(WarpTile) * RT_WARPS, s>>>(L);
     pf->end("recon", s);

@@ -174,13 +174,14 @@ Geo geometry(int W, int H, int feats_cap, int RB) {
     g.nbands = (H + RB - 1) / RB;
     size_t b = 0;
     b += al256(g.N);                              // R
-    b += 3 * al256(g.N * 4);                      // P, A, rootlist
+    b += 2 * al256(g.N * 4);                      // P, A
+    b += al256((size_t)g.cbx * g.cby * RL_CAP * 4);  // per-block root lists
+    b += al256((size_t)g.cbx * g.cby * 4);        // per-block root counts
     b += 4 * al256(words * 4);                    // fg, filled, kept, root bitmaps
     b += al256(words * 4);                        // word prefix
     b += al256((size_t)g.nchunks * 4);            // chunk sums
     b += al256((size_t)g.cbx * g.cby * 4 * CB * 4);  // block edges
-    b += al256(64);                               // counters
-    b += 2 * al256((size_t)g.cby * W * 4);        // EDT chunk summaries
+    b += al256((size_t)g.cby * W * 4);            // EDT column bits per chunk
     b += al256((size_t)std::max(feats_cap, 1) * 16);  // object boxes
     g.ws_bytes = b;
     return g;
@@ -194,7 +195,8 @@ void carve(TileDev& t, const Geo& g, char* base) {
     t.R = (uint8_t*)take(g.N);
     t.P = (int32_t*)take(g.N * 4);
     t.A = (int32_t*)take(g.N * 4);
-    t.rootlist = (int32_t*)take(g.N * 4);
+    t.rootlist = (int32_t*)take((size_t)g.cbx * g.cby * RL_CAP * 4);
+    t.blkroots = (int32_t*)take((size_t)g.cbx * g.cby * 4);
     t.fgbits = (uint32_t*)take(words * 4);
     t.filledbits = (uint32_t*)take(words * 4);
     t.keptbits = (uint32_t*)take(words * 4);
@@ -202,9 +204,7 @@ void carve(TileDev& t, const Geo& g, char* base) {
     t.wordprefix = (int32_t*)take(words * 4);
     t.chunksum = (int32_t*)take((size_t)g.nchunks * 4);
     t.border = (int32_t*)take((size_t)g.cbx * g.cby * 4 * CB * 4);
-    t.counters = (int32_t*)take(64);
-    t.edtF = (int32_t*)take((size_t)g.cby * g.W * 4);
-    t.edtL = (int32_t*)take((size_t)g.cby * g.W * 4);
+    t.colbits = (uint32_t*)take((size_t)g.cby * g.W * 4);
     t.bbox = (int4*)take((size_t)std::max(t.feats_cap, 1) * 16);
     t.W = g.W;
     t.H = g.H;
@@ -275,7 +275,7 @@ struct pipe_s {
     int device = 0;
     pipe_params prm;
     int sms = 0;
-    int recon_blocks_per_sm = 1;
+    int recon_cap = 1;
     EventProfiler prof;
     // plain form
     LaunchCtx plain;
@@ -376,8 +376,7 @@ int max_width(const std::vector<TileDev>& td) {
 void run_path(pipe_t p, const Launch& L, int Wmax, bool features, int max_objects, cudaStream_t s,
               Profiler* pf) {
     launch_deconv(L, s, pf);
-    int grid = std::max(1, std::min((L.n_rt + RT_WARPS - 1) / RT_WARPS, p->sms * p->recon_blocks_per_sm));
-    launch_recon(L, grid, s, pf);
+    launch_recon(L, p->recon_cap, s, pf);
     launch_label(L, features ? 1 : 0, max_objects, p->sms, s, pf);
     launch_edt(L, bands_rows(Wmax), Wmax, s, pf);
     if (features) launch_features_batched(L, p->sms, s, pf);
@@ -417,6 +416,7 @@ int pipe_create(const pipe_params* params, int device, pipe_t* out) {
         prm.h < 0 || prm.h > 255 || prm.dome_thresh < 0 || prm.area_min < 0 || prm.area_max < prm.area_min ||
         prm.max_slots < 1 || prm.wait_budget_cycles <= 0)
         return PIPE_EINVAL;
+
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return PIPE_EINVAL;
     if (cudaSetDevice(device) != cudaSuccess) return PIPE_ECUDA;
@@ -427,8 +427,11 @@ int pipe_create(const pipe_params* params, int device, pipe_t* out) {
     int tab[3 * 256];
     deconv_tables(tab);
     upload_deconv_tables(tab);
-    int g = recon_grid(1 << 30, device);
-    p->recon_blocks_per_sm = std::max(1, g / std::max(p->sms, 1));
+    if (features_tables_ready(device) != 0) {
+        delete p;
+        return PIPE_ECUDA;
+    }
+    p->recon_cap = std::max(1, recon_grid(device));
     if (cudaGetLastError() != cudaSuccess) {
         delete p;
         return PIPE_ECUDA;
