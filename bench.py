@@ -1,26 +1,37 @@
 """Benchmark: 4096x4096 tiles per second through the segmentation + feature path.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--form batched|plain]
-                    [--impl ours|reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--batch B]
+                    [--impl ours|reference] [--no-cpu] [--no-extra]
 
-One step is one pass of the whole path (colour deconvolution, h-dome
-reconstruction, fill holes, labelling + area filter + relabel, EDT, per-object
-features) over one batch of synthetic 4096x4096 tiles generated like the
-4096^2 workload (~3000 nuclei, 20% in touching clusters of 2-6, 150 stroma
-discs).  Inputs are resident in HBM when the timed region starts; the batch's
-inputs and planes (hundreds of MB) exceed the 129 MB L2, and the plain form
-rotates over several input buffers.
+One step is one pass of the whole path -- colour deconvolution, h-dome
+reconstruction, fill holes, labelling + area filter + relabel, EDT and
+per-object features -- over one batch of B synthetic 4096x4096 tiles in the
+batched form (one launch per pass over all tiles, replayed from a CUDA
+graph).  Tiles are generated like the 4096^2 workload (~3000 nuclei, 20% in
+touching clusters of 2-6, 150 stroma discs), each with its own seed.  Inputs
+are resident in HBM when the timed region starts; a batch's inputs alone
+(B x 48 MiB) and its planes exceed the 129 MB L2.
+
+Reported beside the batched value: the plain form (seg_tile + features_tile,
+one tile per call) on the same tiles; the served form (batch_submit /
+batch_poll under Poisson arrivals at 80% of the batched rate, with p50/p99
+latency); an end-to-end figure (whole batches submitted from pinned host
+memory through the served API and polled to completion); per-kernel CUDA
+event times; the roofline of the dominant kernel; and the CPU oracle.
 
 N>1 (torchrun): every rank is an independent replica on its own tiles (the
 path shards by tile; there is no data exchange), value = all tiles / max time.
 
 --impl reference times the CPU oracle (the plain C program written from the
-paper's definitions) on this host's cores on a bounded sample of the same
+paper's definitions) on this host's cores on full tiles of the same
 workload; rank 0 only.
 """
 import argparse
+import hashlib
 import json
+import math
 import os
+import random
 import statistics
 import subprocess
 import sys
@@ -33,8 +44,13 @@ sys.path.insert(0, ROOT)
 METRIC = "4Kx4K tiles/sec/GB300 (batched+served vs plain) at bit-exact seg; p50/p99 ms"
 WORKLOAD = ("4096x4096 RGB uint8 tiles, ~3000 nuclei (20% in touching clusters of 2-6) + 150 stroma "
             "discs r40-120; h=20, dome>=10, area [20,1500], 8-level GLCM x4 offsets")
+# algorithmic HBM bytes per pixel of each step (each step reads its inputs and
+# writes its outputs once)
 BYTES_PER_PX = {"deconv": 4, "recon": 2, "fill": 2, "label": 13, "edt": 16, "features": 5}
+KERNEL_STAGE = {"recon": "recon", "deconv": "deconv", "edt_rows": "edt", "relabel": "label",
+                "feat_objects": "features", "fill_local": "fill", "label_local": "label"}
 PATH_BYTES_PER_PX = 42
+H = W = 4096
 
 
 def peaks():
@@ -44,6 +60,21 @@ def peaks():
         return float(d["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
+
+
+def kernel_traffic(name):
+    """DRAM bytes per 4096^2 launch from the committed ncu summary, if the
+    kernel's source is unchanged since the capture (else None)."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            d = json.load(f)
+        ent = d[name]
+        src = os.path.join(ROOT, "paper_1209_3332_gb300", "csrc", ent["source"])
+        if hashlib.sha256(open(src, "rb").read()).hexdigest() != ent["source_sha256"]:
+            return None
+        return float(ent["dram_bytes_per_launch"])
+    except Exception:
+        return None
 
 
 class Clocks:
@@ -60,7 +91,7 @@ class Clocks:
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -97,7 +128,7 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def dist_setup(n_gpus):
+def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -127,13 +158,15 @@ def max_over_ranks(world, v):
     return float(t.item())
 
 
+def tile_seed(rank, i):
+    """Seed of tile i of rank `rank`; rank 0's first tile is the 4096^2 workload tile."""
+    return 1000 if (rank == 0 and i == 0) else 1000 + 7919 * (rank * 256 + i)
+
+
 def gen_tiles(n, rank):
     import synth
-    tiles = []
-    for i in range(n):
-        seed = 1000 if (rank == 0 and i == 0) else 1000 + 7919 * (rank * 64 + i)
-        tiles.append(synth.tile(4096, 4096, seed, n_nuclei=3000, frac_cluster=0.2, n_stroma=150))
-    return tiles
+    return [synth.tile(W, H, tile_seed(rank, i), n_nuclei=3000, frac_cluster=0.2, n_stroma=150)
+            for i in range(n)]
 
 
 def cpu_baseline(tiles, budget_s=12.0):
@@ -155,11 +188,9 @@ def cpu_baseline(tiles, budget_s=12.0):
 def run_reference(args, world, rank):
     if rank != 0:
         return
-    tiles = gen_tiles(1, 0)
     import oracle
     oracle.build()
-    for _ in range(args.warmup if args.warmup < 1 else 1):
-        pass
+    tiles = gen_tiles(1, 0)
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
@@ -171,15 +202,89 @@ def run_reference(args, world, rank):
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "tiles/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "form": "oracle, one tile per step", "tiles_per_step": 1},
+            "config": {"workload": WORKLOAD, "form": "CPU oracle, one tile per step", "tiles_per_step": 1},
             "cpu_baseline": {"value": val, "unit": "tiles/s", "cores": 1, "kind": "oracle",
                              "sample": "%d steps of one full 4096x4096 tile each" % args.steps},
             "e2e": {"value": val, "unit": "tiles/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
+def device_buffers(torch, dev, host, feats_cap):
+    bufs = []
+    for h in host:
+        bufs.append(dict(rgb=torch.from_numpy(h).to(dev), hem8=torch.empty((H, W), dtype=torch.uint8, device=dev),
+                         labels=torch.empty((H, W), dtype=torch.int32, device=dev),
+                         edt=torch.empty((H, W), dtype=torch.int32, device=dev),
+                         n_objects=torch.zeros(1, dtype=torch.int32, device=dev),
+                         feats=torch.empty((feats_cap, 15), dtype=torch.float32, device=dev)))
+    return bufs
+
+
+def timed(torch, stream, fn, steps):
+    """CUDA-event time of `steps` calls of fn on `stream`, ms."""
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def serve_run(pipe, pinned, n_requests, rate, seed=3999, max_group=16, limit_s=120.0):
+    """Poisson arrivals at `rate` tiles/s; each request is one pool tile.
+    Requests that arrived while the device was busy are admitted together, in
+    groups of at most max_group, as soon as a context frees up (continuous
+    batching)."""
+    rng = random.Random(seed)
+    arrivals, t = [], 0.0
+    for _ in range(n_requests):
+        t += rng.expovariate(rate)
+        arrivals.append(t)
+    waiting, inflight, lat, done_t = [], [], [], []
+    i = 0
+    t0 = time.monotonic()
+    while len(lat) < n_requests:
+        now = time.monotonic() - t0
+        while i < n_requests and arrivals[i] <= now:
+            waiting.append(i)
+            i += 1
+        while waiting:
+            group = waiting[:max_group]
+            tk = pipe.submit([pinned[r % len(pinned)] for r in group])
+            if tk is None:
+                break
+            inflight.append((tk, group))
+            waiting = waiting[len(group):]
+        if time.monotonic() - t0 > limit_s:
+            raise RuntimeError("served leg exceeded %.0f s" % limit_s)
+        still = []
+        for tk, reqs in inflight:
+            res = pipe.poll(tk)
+            if res is None:
+                still.append((tk, reqs))
+                continue
+            for r, out in zip(reqs, res):
+                if out["status"] != 0:
+                    raise RuntimeError("served tile status %d" % out["status"])
+                done_ms = out["t_done_ms"] - t0 * 1000.0
+                lat.append(done_ms - arrivals[r] * 1000.0)
+                done_t.append(done_ms / 1000.0)
+        inflight = still
+        if not waiting and not inflight and i < n_requests:
+            time.sleep(max(0.0, min(0.0005, arrivals[i] - (time.monotonic() - t0))))
+    lat.sort()
+    span = max(done_t) - arrivals[0]
+
+    def pct(p):
+        return lat[min(len(lat) - 1, int(math.ceil(p / 100.0 * len(lat))) - 1)]
+    return {"value": n_requests / span, "unit": "tiles/s", "p50_ms": pct(50), "p99_ms": pct(99),
+            "requests": n_requests, "arrival_rate": rate, "pool_tiles": len(pinned)}
+
+
 def run_ours(args, world, rank, local):
-    import numpy as np
     import torch
     import paper_1209_3332_gb300 as P
     from paper_1209_3332_gb300 import build
@@ -188,154 +293,127 @@ def run_ours(args, world, rank, local):
     torch.cuda.set_device(dev)
     stream = torch.cuda.Stream(dev)
     pipe = P.Pipe(local)
-    B = args.batch if args.form == "batched" else 1
-    nbuf = max(B, 4) if args.form == "plain" else B
-    host = gen_tiles(min(nbuf, 4), rank)
-    H = W = 4096
+    B = args.batch
     feats_cap = 20000
-    bufs = []
-    for i in range(nbuf):
-        h = host[i % len(host)]
-        bufs.append(dict(rgb=torch.from_numpy(h).to(dev), hem8=torch.empty((H, W), dtype=torch.uint8, device=dev),
-                         labels=torch.empty((H, W), dtype=torch.int32, device=dev),
-                         edt=torch.empty((H, W), dtype=torch.int32, device=dev),
-                         n_objects=torch.zeros(1, dtype=torch.int32, device=dev),
-                         feats=torch.empty((feats_cap, 15), dtype=torch.float32, device=dev)))
+    host = gen_tiles(B, rank)
+    bufs = device_buffers(torch, dev, host, feats_cap)
     torch.cuda.synchronize()
 
-    state = {"i": 0}
-
-    def step_plain(profile_K=None):
-        b = bufs[state["i"] % nbuf]
-        state["i"] += 1
-        with torch.cuda.stream(stream):
-            pipe.seg_tile(b["rgb"], b["hem8"], b["labels"], b["edt"], b["n_objects"], stream=stream)
-        # the feature stage needs K on the host (plain API)
-        stream.synchronize()
-        K = int(b["n_objects"].item())
-        pipe.features_tile(b["hem8"], b["labels"], K, b["feats"], stream=stream)
-
     def step_batched():
-        pipe.seg_features_batch(bufs[:B], stream=stream)
+        pipe.seg_features_batch(bufs, stream=stream)
 
-    step = step_batched if args.form == "batched" else step_plain
+    def plain_tile(b):
+        pipe.seg_tile(b["rgb"], b["hem8"], b["labels"], b["edt"], b["n_objects"], stream=stream)
+        stream.synchronize()  # the plain feature call takes K from the host
+        pipe.features_tile(b["hem8"], b["labels"], int(b["n_objects"].item()), b["feats"], stream=stream)
+
+    def step_plain():
+        for b in bufs:
+            plain_tile(b)
+
+    # ---- batched form: the timed region -----------------------------------
     for _ in range(args.warmup):
-        step()
+        step_batched()
     stream.synchronize()
     st = pipe.status()
     if st != P.PIPE_OK:
         raise RuntimeError("device status %d after warm-up" % st)
-
     clocks = Clocks(local)
     clocks.start()
     barrier(world)
     torch.cuda.synchronize()
     l0 = pipe.launch_count()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    for _ in range(args.steps):
-        step()
-    ev1.record(stream)
-    torch.cuda.synchronize()
+    ms_total = timed(torch, stream, step_batched, args.steps)
     barrier(world)
     launches = pipe.launch_count() - l0
-    ms_total = ev0.elapsed_time(ev1)
     ck = clocks.stop()
     ms_total = max_over_ranks(world, ms_total)
     ms_step = ms_total / args.steps
     value = world * B * args.steps / (ms_total / 1000.0)
-
-    if args.no_extra:
-        if rank == 0:
-            print(json.dumps({"metric": METRIC, "value": world * B * args.steps / (ms_total / 1000.0),
-                              "unit": "tiles/s", "ms_per_step": ms_step, "gpu_launches": int(launches),
-                              "partial": "timed region only"}), flush=True)
-        pipe.close()
-        return
-
-    # per-kernel times (CUDA events around every launch, same stream), a
-    # second pass over the same steps
-    pipe.profile(True)
-    for _ in range(args.steps):
-        step()
-    torch.cuda.synchronize()
-    prof = pipe.profile_read()
-    pipe.profile(False)
     st = pipe.status()
     if st != P.PIPE_OK:
         raise RuntimeError("device status %d" % st)
-
-    # end to end through the public API with host buffers: pinned RGB in,
-    # object count and feature rows out, copies inside the timed region
-    pinned = [torch.from_numpy(h).pin_memory() for h in host]
-    fe_host = torch.empty((B, feats_cap, 15), dtype=torch.float32).pin_memory()
-    k_host = torch.empty((B,), dtype=torch.int32).pin_memory()
-    h2d = d2h = 0
-
-    def e2e_step():
-        nonlocal h2d, d2h
-        h2d = d2h = 0
-        with torch.cuda.stream(stream):
-            for i in range(B):
-                bufs[i]["rgb"].copy_(pinned[i % len(pinned)], non_blocking=True)
-                h2d += pinned[i % len(pinned)].numel()
-            if args.form == "batched":
-                pipe.seg_features_batch(bufs[:B], stream=stream)
-            else:
-                b = bufs[0]
-                pipe.seg_tile(b["rgb"], b["hem8"], b["labels"], b["edt"], b["n_objects"], stream=stream)
-                stream.synchronize()
-                K = int(b["n_objects"].item())
-                pipe.features_tile(b["hem8"], b["labels"], K, b["feats"], stream=stream)
-            for i in range(B):
-                k_host[i:i + 1].copy_(bufs[i]["n_objects"], non_blocking=True)
-            stream.synchronize()
-            for i in range(B):
-                K = min(int(k_host[i]), feats_cap)
-                fe_host[i, :K].copy_(bufs[i]["feats"][:K], non_blocking=True)
-                d2h += 4 + K * 15 * 4
-        stream.synchronize()
-
-    for _ in range(max(1, args.warmup)):
-        e2e_step()
-    barrier(world)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        e2e_step()
-    torch.cuda.synchronize()
-    e2e_s = max_over_ranks(world, time.perf_counter() - t0)
-    e2e = {"value": world * B * args.steps / e2e_s, "unit": "tiles/s", "h2d_bytes_per_step": h2d,
-           "d2h_bytes_per_step": d2h}
-
-    # roofline of the dominant kernel
-    peak, peak_kind = peaks()
-    name, (cnt, tot) = max(prof.items(), key=lambda kv: kv[1][1])
-    stage = {"recon": "recon", "deconv": "deconv", "edt_rows": "edt", "relabel": "label",
-             "feat_objects": "features", "fill_local": "fill", "label_local": "label"}.get(name)
-    px_per_launch = B * H * W
     line = {"metric": METRIC, "value": value, "unit": "tiles/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "form": args.form, "tiles_per_step": B,
-                       "l2": "inputs larger than L2 (each step touches >= 350 MB per tile; plain form "
-                             "rotates %d input buffers)" % nbuf,
+            "config": {"workload": WORKLOAD, "form": "batched (one launch per pass over the batch, CUDA graph)",
+                       "tiles_per_step": B, "l2": "inputs larger than L2 (%d x 48 MiB RGB per step)" % B,
                        "parallelism": "replicas" if world > 1 else "1 GPU"},
-            "gpu_launches": int(launches), "clocks": ck, "e2e": e2e}
+            "gpu_launches": int(launches), "clocks": ck}
+    if args.no_extra:
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        pipe.close()
+        return
+
+    # ---- per-kernel times (events around every launch, same stream) ---------
+    pipe.profile(True)
+    for _ in range(args.steps):
+        step_batched()
+    torch.cuda.synchronize()
+    prof = pipe.profile_read()
+    pipe.profile(False)
+
+    # ---- plain form on the same tiles ---------------------------------------
+    step_plain()
+    n_plain = max(1, args.steps // 2)
+    ms_plain = timed(torch, stream, step_plain, n_plain)
+    line["plain"] = {"value": world * B * n_plain / (max_over_ranks(world, ms_plain) / 1000.0), "unit": "tiles/s",
+                     "form": "seg_tile + features_tile per tile (host reads K between them)"}
+    plain_tile(bufs[0])
+    line["plain"]["recon_tile_visits_per_work_tile"] = pipe.recon_visits() / float(
+        ((W + 31) // 32) * ((H + 31) // 32))
+
+    # ---- end to end through the served API with host buffers ----------------
+    pinned = [torch.from_numpy(h).pin_memory() for h in host]
+    h2d = B * H * W * 3
+
+    def e2e_step(limit_s=60.0):
+        t0 = time.monotonic()
+        tk = None
+        while tk is None:
+            tk = pipe.submit(pinned)
+            if time.monotonic() - t0 > limit_s:
+                raise RuntimeError("e2e submit not admitted within %.0f s" % limit_s)
+        while True:
+            res = pipe.poll(tk)
+            if res is not None:
+                return sum(4 * 3 + r["n_objects"] * 15 * 4 for r in res)
+            if time.monotonic() - t0 > limit_s:
+                raise RuntimeError("e2e batch not done within %.0f s" % limit_s)
+    d2h = e2e_step()
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        d2h = e2e_step()
+    e2e_s = max_over_ranks(world, time.perf_counter() - t0)
+    line["e2e"] = {"value": world * B * args.steps / e2e_s, "unit": "tiles/s", "h2d_bytes_per_step": h2d,
+                   "d2h_bytes_per_step": d2h,
+                   "path": "batch_submit (pinned host RGB) -> batch_poll (count + feature rows)"}
+
+    # ---- served form: Poisson arrivals at 80% of the batched rate ----------
+    rate = 0.8 * value / world
+    serve_run(pipe, pinned, min(32, 4 * B), rate)  # warm the contexts
+    line["served"] = serve_run(pipe, pinned, args.requests, rate)
+
+    # ---- roofline of the dominant kernel ------------------------------------
+    peak, peak_kind = peaks()
+    name, (cnt, tot) = max(prof.items(), key=lambda kv: kv[1][1])
+    stage = KERNEL_STAGE.get(name)
     if stage:
         avg_ms = tot / cnt
-        alg = BYTES_PER_PX[stage] * px_per_launch
+        alg = BYTES_PER_PX[stage] * B * H * W
         ach = alg / (avg_ms / 1000.0) / 1e9
+        tr = kernel_traffic(name)
         line["roofline"] = {"bound": "hbm", "kernel": name, "achieved": ach, "peak": peak, "unit": "GB/s",
-                            "frac": ach / peak, "traffic": None, "peak_source": peak_kind,
+                            "frac": ach / peak, "traffic": tr * B if tr is not None else None,
+                            "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)",
                             "alg_bytes_per_launch": alg, "avg_launch_ms": avg_ms}
     path_gbs = PATH_BYTES_PER_PX * H * W * value / world / 1e9
     line["path_roofline"] = {"bytes_per_tile": PATH_BYTES_PER_PX * H * W, "achieved": path_gbs, "peak": peak,
                              "unit": "GB/s", "frac": path_gbs / peak}
-    if args.form == "plain":
-        step_plain()
-        line["recon_tile_visits_per_work_tile"] = pipe.recon_visits() / float(((W + 31) // 32) * ((H + 31) // 32))
-    line["kernels_ms"] = {k: round(v[1] / max(v[0], 1), 4) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
+    line["kernels_ms"] = {k: round(v[1] / max(v[0], 1), 4)
+                          for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(host[:1])
     if rank == 0:
@@ -349,13 +427,12 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--form", default="plain", choices=["plain", "batched"])
-    ap.add_argument("--batch", type=int, default=8)
+    ap.add_argument("--batch", type=int, default=16, help="4096^2 tiles per batched step")
+    ap.add_argument("--requests", type=int, default=400, help="requests in the served leg")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
-    ap.add_argument("--no-extra", action="store_true",
-                    help="timed region only: skip the per-kernel, end-to-end and CPU legs")
+    ap.add_argument("--no-extra", action="store_true", help="timed region only")
     args = ap.parse_args()
-    world, rank, local = dist_setup(args.gpus)
+    world, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, world, rank)
     else:

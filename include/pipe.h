@@ -162,7 +162,8 @@ typedef struct {
 /* Admits the n tiles as one group: they are uploaded and processed together
  * as one batched launch on a context of their own, concurrently with the
  * groups already in flight.  PIPE_EBUSY (nothing enqueued) when max_slots
- * contexts are busy or the group would exceed hbm_budget_bytes. */
+ * contexts are busy or the group would exceed hbm_budget_bytes together with
+ * the groups in flight; PIPE_ENOMEM when the group alone exceeds it. */
 int batch_submit(pipe_t p, const tile_desc* tiles, int n, uint64_t* ticket);
 /* PIPE_EAGAIN (n_done = 0) until every tile of the ticket is done; then
  * fills out[0..n) and sets n_done = n.  The pipe-owned result arrays of a

@@ -106,7 +106,7 @@ struct Profiler {
     virtual ~Profiler() {}
 };
 
-void upload_deconv_tables(const int32_t* lut3x256);
+void upload_deconv_tables(const int32_t* lut256, const int32_t* wq3);
 // fills the feature pass's constant tables on `device` (current) once; 0 on success
 int features_tables_ready(int device);
 void launch_deconv(const Launch& L, cudaStream_t s, Profiler* pf);

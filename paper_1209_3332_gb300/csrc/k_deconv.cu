@@ -3,8 +3,10 @@
 // marker: R0 = max(hem8 - h, 0) seeds the reconstruction plane (Table I,
 // ReconToNuclei).
 //
-// hem8 = clamp((sum_c T_c[rgb_c] + 2^18) >> 19, 0, 255) with the premultiplied
-// integer tables T_c[v] = wq_c * od_lut[v] built on the host at pipe creation.
+// hem8 = clamp((sum_c wq_c * od_lut[rgb_c] + 2^18) >> 19, 0, 255) with the
+// integer tables built on the host at pipe creation.  The 256-entry od_lut
+// (u16) is replicated once per lane in shared memory, entry v of lane l at
+// v*32 + l, so 32 data-dependent lookups hit at most two lanes per bank.
 // One thread converts 16 consecutive pixels of a row: three 16-byte loads of
 // interleaved RGB, one 16-byte store to each output plane, when the row is
 // 16-byte aligned; byte accesses otherwise.  HBM-bound: 3 B read + 2 B
@@ -13,25 +15,39 @@
 
 namespace nucseg {
 
-__constant__ int32_t c_tab[3 * 256];
+__constant__ int32_t c_lut[256];  // od_lut
+__constant__ int32_t c_wq[3];     // channel weights
 
-void upload_deconv_tables(const int32_t* lut3x256) {
-    cudaMemcpyToSymbol(c_tab, lut3x256, sizeof(int32_t) * 3 * 256);
+void upload_deconv_tables(const int32_t* lut256, const int32_t* wq3) {
+    cudaMemcpyToSymbol(c_lut, lut256, sizeof(int32_t) * 256);
+    cudaMemcpyToSymbol(c_wq, wq3, sizeof(int32_t) * 3);
 }
 
-__device__ __forceinline__ uint32_t hem_of(const int32_t* T, uint32_t r, uint32_t g, uint32_t b) {
-    int32_t acc = T[r] + T[256 + g] + T[512 + b];
-    int32_t v = acc < 0 ? 0 : (acc + (1 << 18)) >> 19;
-    return (uint32_t)(v > 255 ? 255 : v);
-}
+struct DeconvLut {
+    const uint16_t* t;  // t[v * 32 + lane]
+    int lane, w0, w1, w2;
+    __device__ __forceinline__ uint32_t hem(uint32_t r, uint32_t g, uint32_t b) const {
+        int32_t acc = w0 * (int32_t)t[r * 32 + lane] + w1 * (int32_t)t[g * 32 + lane] + w2 * (int32_t)t[b * 32 + lane];
+        int32_t v = acc < 0 ? 0 : (acc + (1 << 18)) >> 19;
+        return (uint32_t)(v > 255 ? 255 : v);
+    }
+};
+
+__device__ __forceinline__ void deconv_item(const TileDev* __restrict__ tiles, int ntiles, int gid, int h,
+                                            const DeconvLut& lut);
 
 __global__ void __launch_bounds__(256) k_deconv(const TileDev* __restrict__ tiles, int ntiles,
                                                 int n_items, int h) {
-    __shared__ int32_t T[3 * 256];
-    for (int i = threadIdx.x; i < 3 * 256; i += blockDim.x) T[i] = c_tab[i];
+    __shared__ uint16_t T[256 * 32];
+    for (int i = threadIdx.x; i < 256 * 32; i += blockDim.x) T[i] = (uint16_t)c_lut[i >> 5];
     __syncthreads();
-    int gid = blockIdx.x * blockDim.x + threadIdx.x;
-    if (gid >= n_items) return;
+    const DeconvLut lut{T, (int)(threadIdx.x & 31), c_wq[0], c_wq[1], c_wq[2]};
+    for (int gid = blockIdx.x * blockDim.x + threadIdx.x; gid < n_items; gid += gridDim.x * blockDim.x)
+        deconv_item(tiles, ntiles, gid, h, lut);
+}
+
+__device__ __forceinline__ void deconv_item(const TileDev* __restrict__ tiles, int ntiles, int gid, int h,
+                                            const DeconvLut& lut) {
     int ti = find_tile(tiles, ntiles, gid, &TileDev::px_base);
     const TileDev& t = tiles[ti];
     int item = gid - t.px_base;
@@ -54,7 +70,7 @@ __global__ void __launch_bounds__(256) k_deconv(const TileDev* __restrict__ tile
             uint32_t r = (w[o >> 2] >> ((o & 3) * 8)) & 255;
             uint32_t g = (w[(o + 1) >> 2] >> (((o + 1) & 3) * 8)) & 255;
             uint32_t bb = (w[(o + 2) >> 2] >> (((o + 2) & 3) * 8)) & 255;
-            uint32_t hm = hem_of(T, r, g, bb);
+            uint32_t hm = lut.hem(r, g, bb);
             uint32_t mk = hm > (uint32_t)h ? hm - h : 0;
             hv[p >> 2] |= hm << ((p & 3) * 8);
             rv[p >> 2] |= mk << ((p & 3) * 8);
@@ -72,7 +88,7 @@ __global__ void __launch_bounds__(256) k_deconv(const TileDev* __restrict__ tile
     } else {
         int n = min(16, t.W - x0);
         for (int p = 0; p < n; p++) {
-            uint32_t hm = hem_of(T, src[3 * p], src[3 * p + 1], src[3 * p + 2]);
+            uint32_t hm = lut.hem(src[3 * p], src[3 * p + 1], src[3 * p + 2]);
             dh[p] = (uint8_t)hm;
             dr[p] = (uint8_t)(hm > (uint32_t)h ? hm - h : 0);
         }
@@ -82,7 +98,12 @@ __global__ void __launch_bounds__(256) k_deconv(const TileDev* __restrict__ tile
 void launch_deconv(const Launch& L, cudaStream_t s, Profiler* pf) {
     if (L.n_px == 0) return;
     pf->begin("deconv", s);
-    k_deconv<<<(L.n_px + 255) / 256, 256, 0, s>>>(L.tiles, L.ntiles, L.n_px, L.h);
+    int sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int blocks = (L.n_px + 255) / 256;
+    if (blocks > sms * 8) blocks = sms * 8;  // the per-block table setup is amortised over a grid-stride loop
+    k_deconv<<<blocks, 256, 0, s>>>(L.tiles, L.ntiles, L.n_px, L.h);
     pf->end("deconv", s);
 }
 

@@ -15,7 +15,9 @@
 // int32 write of D.  Rows whose g stays
 // within WMAX use an exact windowed search (a candidate at distance r costs
 // at least r^2, so the search stops once r^2 >= the best value); other rows
-// run Meijster's lower-envelope scan on one thread.
+// run Meijster's lower-envelope scan on one thread.  Shared memory holds
+// only the band (4 rows of u16 for a 4096-wide tile), so several CTAs fit on
+// an SM.
 #include "internal.cuh"
 
 namespace nucseg {
@@ -27,19 +29,24 @@ constexpr unsigned FULLE = 0xffffffffu;
 __device__ __forceinline__ int sq(int v) { return v * v; }
 __device__ __forceinline__ uint32_t below_or_at(int k) { return (2u << k) - 1u; }  // bits 0..k
 
-__device__ void meijster_row(const uint16_t* g, int W, int16_t* s, int16_t* t, int32_t* out) {
-    // lower envelope of f_i(u) = (u-i)^2 + g_i^2
+// Meijster's row pass for rows whose column distances exceed WMAX (rare:
+// long stretches of foreground).  The stack of (site s, start t) pairs lives
+// in the output row itself, packed as (s << 16) | t: in the backward pass the
+// live stack index q satisfies q <= t[q] <= u, and entry q is read before
+// out[u] is written, so no scratch memory is needed.
+__device__ void meijster_row(const uint16_t* g, int W, int32_t* out) {
     auto F = [&](int u, int i) -> long long { return (long long)(u - i) * (u - i) + (long long)g[i] * g[i]; };
+    auto S = [&](int k) -> int { return (int)((uint32_t)out[k] >> 16); };
+    auto Tt = [&](int k) -> int { return (int)(out[k] & 0xffff); };
     int q = 0;
-    s[0] = 0;
-    t[0] = 0;
+    out[0] = 0;
     for (int u = 1; u < W; u++) {
-        while (q >= 0 && F(t[q], s[q]) > F(t[q], u)) q--;
+        while (q >= 0 && F(Tt(q), S(q)) > F(Tt(q), u)) q--;
         if (q < 0) {
             q = 0;
-            s[0] = (int16_t)u;
+            out[0] = (int32_t)((uint32_t)u << 16);
         } else {
-            int i = s[q];
+            int i = S(q);
             long long num = (long long)u * u - (long long)i * i + (long long)g[u] * g[u] - (long long)g[i] * g[i];
             long long den = 2LL * (u - i);
             long long fl = num / den;
@@ -47,23 +54,21 @@ __device__ void meijster_row(const uint16_t* g, int W, int16_t* s, int16_t* t, i
             long long w = 1 + fl;
             if (w < W) {
                 q++;
-                s[q] = (int16_t)u;
-                t[q] = (int16_t)w;
+                out[q] = (int32_t)(((uint32_t)u << 16) | (uint32_t)w);
             }
         }
     }
     for (int u = W - 1; u >= 0; u--) {
-        long long d = F(u, s[q]);
+        const int su = S(q), tu = Tt(q);
+        long long d = F(u, su);
         out[u] = d >= (long long)INFG * INFG ? 0x7fffffff : (int32_t)d;
-        if (u == t[q]) q--;
+        if (u == tu) q--;
     }
 }
 
 __global__ void __launch_bounds__(256) k_edt_rows(Launch L, int RB, int Wmax) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    uint16_t* gs = reinterpret_cast<uint16_t*>(smraw);                 // [RB][Wmax]
-    int16_t* ms = reinterpret_cast<int16_t*>(gs + (size_t)RB * Wmax);  // [Wmax]
-    int16_t* mt = ms + Wmax;                                           // [Wmax]
+    uint16_t* gs = reinterpret_cast<uint16_t*>(smraw);  // [RB][Wmax]
     __shared__ int rowslow[32];
     const int gbnd = blockIdx.x;
     const int ti = find_tile(L.tiles, L.ntiles, gbnd, &TileDev::row_base);
@@ -123,12 +128,12 @@ __global__ void __launch_bounds__(256) k_edt_rows(Launch L, int RB, int Wmax) {
                 out[x] = D;
             }
         } else if (threadIdx.x == 0) {
-            meijster_row(g, W, ms, mt, out);
+            meijster_row(g, W, out);
         }
     }
 }
 
-size_t edt_rows_smem(int RB, int Wmax) { return (size_t)RB * Wmax * 2 + (size_t)2 * Wmax * 2; }
+size_t edt_rows_smem(int RB, int Wmax) { return (size_t)RB * Wmax * 2; }
 
 void launch_edt(const Launch& L, int RB, int Wmax, cudaStream_t s, Profiler* pf) {
     if (L.n_rows == 0) return;

@@ -125,8 +125,16 @@ __device__ __forceinline__ double grad_mag(int m2) {
     return sd + (double)((float)r * (0.5f / sf));
 }
 
-// Features of object `obj` by one warp; glcm: this warp's 4x64 counters.
-__device__ void object_features(const ObjJob& J, int obj, int* glcm) {
+constexpr int STAGE_PX = 5120;  // staged region (box + 1-px margin) capacity per warp
+
+// Features of object `obj` by one warp; glcm: this warp's 4x64 counters;
+// smask / shem: this warp's staging buffers.  When the object's box plus a
+// 1-pixel margin (clipped to the image) fits, it is staged once with
+// coalesced row loads as an in-object byte mask and hem8, and every
+// neighbourhood read comes from shared memory; larger boxes read global
+// memory directly.  Sobel neighbours (clamped to the image), 4-neighbours and
+// co-occurrence partners of box pixels all lie inside that region.
+__device__ void object_features(const ObjJob& J, int obj, int* glcm, uint8_t* smask, uint8_t* shem) {
     const int lane = threadIdx.x & 31;
     const int l = obj + 1;
     const int4 box = J.bbox[obj];
@@ -139,37 +147,65 @@ __device__ void object_features(const ObjJob& J, int obj, int* glcm) {
     }
     const int bw = box.z - box.x + 1, bh = box.w - box.y + 1;
     const long long npx = (long long)bw * bh;
+    const int rx0 = max(box.x - 1, 0), ry0 = max(box.y - 1, 0);
+    const int rw = min(box.z + 1, W - 1) - rx0 + 1, rh = min(box.w + 1, H - 1) - ry0 + 1;
+    const bool staged = (long long)rw * rh <= STAGE_PX;
     for (int i = lane; i < 4 * 64; i += 32) glcm[i] = 0;
+    if (staged) {
+        for (int yy = 0; yy < rh; yy++) {
+            const size_t row = (size_t)(ry0 + yy) * W + rx0;
+            for (int xx = lane; xx < rw; xx += 32) {
+                smask[yy * rw + xx] = J.labels[row + xx] == l;
+                shem[yy * rw + xx] = J.hem8[row + xx];
+            }
+        }
+    }
     __syncwarp();
+    auto IN = [&](int y, int x) -> bool {
+        return staged ? smask[(y - ry0) * rw + (x - rx0)] != 0 : J.labels[(size_t)y * W + x] == l;
+    };
+    auto HV = [&](int y, int x) -> int {
+        return staged ? (int)shem[(y - ry0) * rw + (x - rx0)] : (int)J.hem8[(size_t)y * W + x];
+    };
+    auto SOBEL = [&](int y, int x) -> int {
+        const int ym = max(y - 1, 0), yp = min(y + 1, H - 1), xm = max(x - 1, 0), xp = min(x + 1, W - 1);
+        const int a = HV(ym, xm), b = HV(ym, x), c = HV(ym, xp), d = HV(y, xm), f = HV(y, xp);
+        const int g = HV(yp, xm), h = HV(yp, x), i = HV(yp, xp);
+        const int gx = (c + 2 * f + i) - (a + 2 * d + g);
+        const int gy = (g + 2 * h + i) - (a + 2 * b + c);
+        return gx * gx + gy * gy;
+    };
     int cnt = 0, per = 0, mn = 255, mx = 0, gmn = 0x7fffffff, gmx = 0;
     long long S = 0, Q = 0;
     double gs = 0.0;
     const int odx[4] = {1, 0, 1, 1}, ody[4] = {0, 1, 1, -1};
+    // lane walks the box row-major with stride 32, advancing (y, x) without divisions
+    int y = box.y + lane / bw, x = box.x + lane % bw;
     for (long long idx = lane; idx < npx; idx += 32) {
-        const int y = box.y + (int)(idx / bw), x = box.x + (int)(idx % bw);
-        const size_t p = (size_t)y * W + x;
-        if (J.labels[p] != l) continue;
-        const int v = J.hem8[p];
+        const int cy = y, cx = x;
+        x += 32;
+        while (x > box.z) { x -= bw; y++; }
+        if (!IN(cy, cx)) continue;
+        const int v = HV(cy, cx);
         cnt++;
         S += v;
         Q += v * v;
         mn = min(mn, v);
         mx = max(mx, v);
-        per += (y == 0 || J.labels[p - W] != l);
-        per += (y == H - 1 || J.labels[p + W] != l);
-        per += (x == 0 || J.labels[p - 1] != l);
-        per += (x == W - 1 || J.labels[p + 1] != l);
-        const int m2 = sobel_m2(J.hem8, W, H, y, x);
+        per += (cy == 0 || !IN(cy - 1, cx));
+        per += (cy == H - 1 || !IN(cy + 1, cx));
+        per += (cx == 0 || !IN(cy, cx - 1));
+        per += (cx == W - 1 || !IN(cy, cx + 1));
+        const int m2 = SOBEL(cy, cx);
         gs += grad_mag(m2);
         gmn = min(gmn, m2);
         gmx = max(gmx, m2);
 #pragma unroll
         for (int o = 0; o < 4; o++) {
-            const int yy = y + ody[o], xx = x + odx[o];
+            const int yy = cy + ody[o], xx = cx + odx[o];
             if (yy < 0 || yy >= H || xx >= W) continue;
-            const size_t q = (size_t)yy * W + xx;
-            if (J.labels[q] != l) continue;
-            atomicAdd(&glcm[o * 64 + (v >> 5) * 8 + (J.hem8[q] >> 5)], 1);
+            if (!IN(yy, xx)) continue;
+            atomicAdd(&glcm[o * 64 + (v >> 5) * 8 + (HV(yy, xx) >> 5)], 1);
         }
     }
     const long long N = warp_sum<long long>(cnt);
@@ -185,10 +221,14 @@ __device__ void object_features(const ObjJob& J, int obj, int* glcm) {
     }
     const double gmean = Gs / (double)N;
     double gss = 0.0;
+    y = box.y + lane / bw;
+    x = box.x + lane % bw;
     for (long long idx = lane; idx < npx; idx += 32) {
-        const int y = box.y + (int)(idx / bw), x = box.x + (int)(idx % bw);
-        if (J.labels[(size_t)y * W + x] != l) continue;
-        const double d = grad_mag(sobel_m2(J.hem8, W, H, y, x)) - gmean;
+        const int cy = y, cx = x;
+        x += 32;
+        while (x > box.z) { x -= bw; y++; }
+        if (!IN(cy, cx)) continue;
+        const double d = grad_mag(SOBEL(cy, cx)) - gmean;
         gss += d * d;
     }
     const double Gss = warp_sum<double>(gss);
@@ -251,10 +291,18 @@ __device__ void object_features(const ObjJob& J, int obj, int* glcm) {
 constexpr int FW = 4;  // object warps per CTA
 
 // Plain form: objects [0, K) of one tile, one warp each.
+struct ObjSmem {
+    int glcm[4 * 64];
+    uint8_t mask[STAGE_PX];
+    uint8_t hem[STAGE_PX];
+};
+
 __global__ void __launch_bounds__(FW * 32) k_fobj_plain(ObjJob J, int K) {
-    __shared__ int glcm[FW][4 * 64];
+    __shared__ ObjSmem sm[FW];
     const int warp = threadIdx.x >> 5;
-    for (int obj = blockIdx.x * FW + warp; obj < K; obj += gridDim.x * FW) object_features(J, obj, glcm[warp]);
+    ObjSmem& S = sm[warp];
+    for (int obj = blockIdx.x * FW + warp; obj < K; obj += gridDim.x * FW)
+        object_features(J, obj, S.glcm, S.mask, S.hem);
 }
 
 __global__ void k_obj_prefix(Launch L) {
@@ -274,14 +322,15 @@ __global__ void k_obj_prefix(Launch L) {
 // Batched form: the objects of all tiles, item -> (tile, object) through the
 // obj_base prefixes (the last tile whose base is <= item owns it).
 __global__ void __launch_bounds__(FW * 32) k_fobj_batched(Launch L) {
-    __shared__ int glcm[FW][4 * 64];
+    __shared__ ObjSmem sm[FW];
     const int warp = threadIdx.x >> 5;
+    ObjSmem& S = sm[warp];
     const int total = L.sh->nobj;
     for (int item = blockIdx.x * FW + warp; item < total; item += gridDim.x * FW) {
         const int t = find_tile(L.tiles, L.ntiles, item, &TileDev::obj_base);
         const TileDev& T = L.tiles[t];
         ObjJob J{T.hem8, T.labels, T.W, T.H, T.bbox, T.feats};
-        object_features(J, item - T.obj_base, glcm[warp]);
+        object_features(J, item - T.obj_base, S.glcm, S.mask, S.hem);
     }
 }
 

@@ -42,7 +42,7 @@ size_t al256(size_t v) { return (v + 255) & ~(size_t)255; }
 // ---- colour deconvolution constants, rebuilt from their formulas ------------------
 // Stain OD vectors of Ruifrok & Johnston (2001); hematoxylin weight per
 // channel = first column of the inverse of the stain matrix [H; E; H x E].
-void deconv_tables(int32_t tab[3 * 256]) {
+void deconv_tables(int32_t lut[256], int32_t wq[3]) {
     double Hs[3] = {0.650, 0.704, 0.286}, Es[3] = {0.072, 0.990, 0.105};
     auto nrm = [](double* v) {
         double n = std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
@@ -57,17 +57,13 @@ void deconv_tables(int32_t tab[3 * 256]) {
                  M[0][1] * (M[1][0] * M[2][2] - M[1][2] * M[2][0]) +
                  M[0][2] * (M[1][0] * M[2][1] - M[1][1] * M[2][0]);
     // c = od * M^-1, so channel k weighs (M^-1)[k][0] = cofactor(0,k) / det
-    int32_t wq[3];
     for (int k = 0; k < 3; k++) {
         int c1 = k == 0 ? 1 : 0, c2 = k == 2 ? 1 : 2;
         double minor = M[1][c1] * M[2][c2] - M[1][c2] * M[2][c1];
         double w = ((k & 1) ? -minor : minor) / det;
         wq[k] = (int32_t)std::llround(100.0 * w * 2048.0);
     }
-    for (int v = 0; v < 256; v++) {
-        int32_t od = (int32_t)std::floor(-std::log((v + 1) / 256.0) * 256.0 + 0.5);
-        for (int c = 0; c < 3; c++) tab[c * 256 + v] = wq[c] * od;
-    }
+    for (int v = 0; v < 256; v++) lut[v] = (int32_t)std::floor(-std::log((v + 1) / 256.0) * 256.0 + 0.5);
 }
 
 // ---- profiler ---------------------------------------------------------------------
@@ -157,7 +153,7 @@ struct Geo {
     size_t N, ws_bytes;
 };
 
-int bands_rows(int Wmax) { return Wmax <= 4096 ? 8 : (Wmax <= 8192 ? 4 : 2); }
+int bands_rows(int Wmax) { return Wmax <= 4096 ? 4 : (Wmax <= 8192 ? 2 : 1); }
 
 Geo geometry(int W, int H, int feats_cap, int RB) {
     Geo g;
@@ -384,6 +380,46 @@ void run_path(pipe_t p, const Launch& L, int Wmax, bool features, int max_object
 
 bool valid_size(int W, int H) { return W >= 1 && H >= 1 && W <= 16384 && H <= 16384; }
 
+// where one tile's results go in mapped host memory
+struct ResultSlot {
+    int32_t* head;   // [0] K, [1] tile status, [2] launch status
+    float* feats;    // [cap][15]
+};
+constexpr int RESULTS_PER_LAUNCH = 64;
+struct ResultPack {
+    ResultSlot r[RESULTS_PER_LAUNCH];
+    int n, first;
+};
+// one CTA per tile: count, status words and exactly min(K, cap) feature rows
+__global__ void k_results(Launch L, ResultPack pk) {
+    const int i = blockIdx.x;
+    if (i >= pk.n) return;
+    const TileDev& T = L.tiles[pk.first + i];
+    const int K = *T.n_objects;
+    const int rows = K < T.feats_cap ? K : T.feats_cap;
+    if (threadIdx.x == 0) {
+        pk.r[i].head[0] = K;
+        pk.r[i].head[1] = L.tile_status[pk.first + i];
+        pk.r[i].head[2] = L.sh->err;
+    }
+    const int n = rows * NFEAT;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) pk.r[i].feats[j] = T.feats[j];
+}
+
+int launch_results(const Launch& L, const ResultSlot* rs, int n, cudaStream_t s, Profiler* pf) {
+    for (int i = 0; i < n; i += RESULTS_PER_LAUNCH) {
+        ResultPack pk;
+        pk.first = i;
+        pk.n = std::min(RESULTS_PER_LAUNCH, n - i);
+        for (int k = 0; k < pk.n; k++) pk.r[k] = rs[i + k];
+        pf->begin("results", s);
+        k_results<<<pk.n, 256, 0, s>>>(L, pk);
+        pf->end("results", s);
+    }
+    CK(cudaGetLastError());
+    return PIPE_OK;
+}
+
 }  // namespace
 
 // ======================================================================================
@@ -424,9 +460,9 @@ int pipe_create(const pipe_params* params, int device, pipe_t* out) {
     p->device = device;
     p->prm = prm;
     cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, device);
-    int tab[3 * 256];
-    deconv_tables(tab);
-    upload_deconv_tables(tab);
+    int32_t lut[256], wq[3];
+    deconv_tables(lut, wq);
+    upload_deconv_tables(lut, wq);
     if (features_tables_ready(device) != 0) {
         delete p;
         return PIPE_ECUDA;
@@ -723,6 +759,7 @@ int batch_submit(pipe_t p, const tile_desc* tiles, int n, uint64_t* ticket) {
         if (ci < 0) ci = k;  // a free context to grow if nothing fits
     }
     size_t need = io + ws + sizeof(TileDev) * n + sizeof(int) * 3 * n_rt;
+    if (need > p->prm.hbm_budget_bytes) return PIPE_ENOMEM;  // never admissible as one group
     if (ci < 0) {
         if ((int)p->ctxs.size() >= p->prm.max_slots) return PIPE_EBUSY;
         p->ctxs.emplace_back(new Ctx());
@@ -750,7 +787,7 @@ int batch_submit(pipe_t p, const tile_desc* tiles, int n, uint64_t* ticket) {
         if (c.h_out) cudaFreeHost(c.h_out);
         c.h_out = nullptr;
         c.h_out_n = 0;
-        CK(cudaHostAlloc(&c.h_out, hout, cudaHostAllocDefault));
+        CK(cudaHostAlloc(&c.h_out, hout, cudaHostAllocMapped));
         c.h_out_n = hout;
     }
     // carve device buffers and fill descriptors
@@ -799,15 +836,22 @@ int batch_submit(pipe_t p, const tile_desc* tiles, int n, uint64_t* ticket) {
     Launch L = make_launch(p, c.lc, td, n_rt);
     if ((rc = upload_desc(L, td, c.stream))) return rc;
     run_path(p, L, Wmax, true, *std::max_element(caps.begin(), caps.end()), c.stream, &p->serve_prof);
-    // download: count + device status word, feature rows (all cap rows), planes
+    // download: a kernel writes count, status and exactly min(K, cap) feature
+    // rows of every tile into the mapped pinned result buffer; planes by copy
     char* ho = (char*)c.h_out;
+    char* ho_dev = nullptr;
+    CK(cudaHostGetDevicePointer((void**)&ho_dev, c.h_out, 0));
+    {
+        std::vector<ResultSlot> rs(n);
+        for (int i = 0; i < n; i++) {
+            rs[i].head = (int32_t*)(ho_dev + tk->tiles[i].nobj_off);
+            rs[i].feats = (float*)(ho_dev + tk->tiles[i].out_off);
+        }
+        if ((rc = launch_results(L, rs.data(), n, c.stream, &p->serve_prof))) return rc;
+    }
     for (int i = 0; i < n; i++) {
         const TicketTile& tt = tk->tiles[i];
         size_t N = (size_t)tt.W * tt.H;
-        CK(cudaMemcpyAsync(ho + tt.nobj_off, td[i].n_objects, 4, cudaMemcpyDeviceToHost, c.stream));
-        CK(cudaMemcpyAsync(ho + tt.nobj_off + 4, L.tile_status + i, 4, cudaMemcpyDeviceToHost, c.stream));
-        CK(cudaMemcpyAsync(ho + tt.nobj_off + 8, &L.sh->err, 4, cudaMemcpyDeviceToHost, c.stream));
-        CK(cudaMemcpyAsync(ho + tt.out_off, td[i].feats, (size_t)caps[i] * NFEAT * 4, cudaMemcpyDeviceToHost, c.stream));
         if (tt.want) {
             char* q = ho + tt.out_off + al256((size_t)caps[i] * NFEAT * 4);
             CK(cudaMemcpyAsync(q, td[i].hem8, N, cudaMemcpyDeviceToHost, c.stream));
