@@ -134,7 +134,9 @@ constexpr int STAGE_PX = 5120;  // staged region (box + 1-px margin) capacity pe
 // neighbourhood read comes from shared memory; larger boxes read global
 // memory directly.  Sobel neighbours (clamped to the image), 4-neighbours and
 // co-occurrence partners of box pixels all lie inside that region.
-__device__ void object_features(const ObjJob& J, int obj, int* glcm, uint8_t* smask, uint8_t* shem) {
+template <bool STAGED>
+__device__ __forceinline__ void object_features_impl(const ObjJob& J, int obj, int* glcm, uint8_t* smask,
+                                                     uint8_t* shem) {
     const int lane = threadIdx.x & 31;
     const int l = obj + 1;
     const int4 box = J.bbox[obj];
@@ -149,7 +151,7 @@ __device__ void object_features(const ObjJob& J, int obj, int* glcm, uint8_t* sm
     const long long npx = (long long)bw * bh;
     const int rx0 = max(box.x - 1, 0), ry0 = max(box.y - 1, 0);
     const int rw = min(box.z + 1, W - 1) - rx0 + 1, rh = min(box.w + 1, H - 1) - ry0 + 1;
-    const bool staged = (long long)rw * rh <= STAGE_PX;
+    constexpr bool staged = STAGED;
     for (int i = lane; i < 4 * 64; i += 32) glcm[i] = 0;
     if (staged) {
         for (int yy = 0; yy < rh; yy++) {
@@ -286,6 +288,23 @@ __device__ void object_features(const ObjJob& J, int obj, int* glcm, uint8_t* sm
         for (int k = 0; k < NFEAT; k++) out[k] = (float)f[k];
     }
     __syncwarp();
+}
+
+// boxes larger than the stage read global memory; that rare path is kept out
+// of line so the common one stays small in the instruction cache
+__device__ __noinline__ void object_features_global(const ObjJob& J, int obj, int* glcm) {
+    object_features_impl<false>(J, obj, glcm, nullptr, nullptr);
+}
+
+__device__ __forceinline__ void object_features(const ObjJob& J, int obj, int* glcm, uint8_t* smask,
+                                                uint8_t* shem) {
+    const int4 box = J.bbox[obj];
+    const int rx0 = max(box.x - 1, 0), ry0 = max(box.y - 1, 0);
+    const long long rw = (long long)min(box.z + 1, J.W - 1) - rx0 + 1, rh = (long long)min(box.w + 1, J.H - 1) - ry0 + 1;
+    if (rw > 0 && rh > 0 && rw * rh <= STAGE_PX)
+        object_features_impl<true>(J, obj, glcm, smask, shem);
+    else
+        object_features_global(J, obj, glcm);
 }
 
 constexpr int FW = 4;  // object warps per CTA

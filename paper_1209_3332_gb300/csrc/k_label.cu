@@ -102,6 +102,28 @@ __device__ __forceinline__ int run_start(uint32_t st, int x) { return 31 - __clz
 
 template <int CONN>
 __device__ __forceinline__ void warp_ccl(uint32_t w, uint32_t st, int lane, int* par) {
+    // Uniform fast path: every class row is one run, the class rows are
+    // contiguous and each overlaps (CONN-adjacency) the row above -- the whole
+    // block is one component whose root is its first pixel.  Typical for the
+    // background of a block, and for blocks without any class pixel.
+    {
+        uint32_t wu = __shfl_up_sync(FULLM, w, 1);
+        if (lane == 0) wu = 0u;
+        const uint32_t adj = CONN == 8 ? (wu | (wu << 1) | (wu >> 1)) : wu;
+        const unsigned has = __ballot_sync(FULLM, w != 0u);
+        if (has == 0u) return;
+        const int lo = __ffs(has) - 1;
+        const uint32_t span = has >> lo;
+        const bool contiguous = (span & (span + 1u)) == 0u;
+        const bool bad = (w != 0u) && (__popc(st) != 1 || (lane != lo && (w & adj) == 0u));
+        if (contiguous && __ballot_sync(FULLM, bad) == 0u) {
+            const uint32_t w0 = __shfl_sync(FULLM, w, lo);
+            const int root = lo * CB + __ffs(w0) - 1;
+            if (st) par[lane * CB + __ffs(st) - 1] = root;
+            __syncwarp();
+            return;
+        }
+    }
     for (uint32_t m = st; m; m &= m - 1) {
         int i = lane * CB + __ffs(m) - 1;
         par[i] = i;
