@@ -233,17 +233,17 @@ def timed(torch, stream, fn, steps):
     return e0.elapsed_time(e1)
 
 
-def serve_run(pipe, pinned, n_requests, rate, seed=3999, max_group=16, limit_s=120.0):
+def serve_run(pipe, pinned, n_requests, rate, seed=3999, max_group=16, max_inflight=2, limit_s=120.0):
     """Poisson arrivals at `rate` tiles/s; each request is one pool tile.
-    Requests that arrived while the device was busy are admitted together, in
-    groups of at most max_group, as soon as a context frees up (continuous
-    batching)."""
+    Continuous batching: whenever fewer than max_inflight groups are on the
+    device, every request that has arrived (up to max_group) is admitted as
+    the next group, so one group uploads while the previous one computes."""
     rng = random.Random(seed)
     arrivals, t = [], 0.0
     for _ in range(n_requests):
         t += rng.expovariate(rate)
         arrivals.append(t)
-    waiting, inflight, lat, done_t = [], [], [], []
+    waiting, inflight, lat, done_t, sizes = [], [], [], [], []
     i = 0
     t0 = time.monotonic()
     while len(lat) < n_requests:
@@ -251,12 +251,13 @@ def serve_run(pipe, pinned, n_requests, rate, seed=3999, max_group=16, limit_s=1
         while i < n_requests and arrivals[i] <= now:
             waiting.append(i)
             i += 1
-        while waiting:
+        while waiting and len(inflight) < max_inflight:
             group = waiting[:max_group]
             tk = pipe.submit([pinned[r % len(pinned)] for r in group])
             if tk is None:
                 break
             inflight.append((tk, group))
+            sizes.append(len(group))
             waiting = waiting[len(group):]
         if time.monotonic() - t0 > limit_s:
             raise RuntimeError("served leg exceeded %.0f s" % limit_s)
@@ -281,7 +282,9 @@ def serve_run(pipe, pinned, n_requests, rate, seed=3999, max_group=16, limit_s=1
     def pct(p):
         return lat[min(len(lat) - 1, int(math.ceil(p / 100.0 * len(lat))) - 1)]
     return {"value": n_requests / span, "unit": "tiles/s", "p50_ms": pct(50), "p99_ms": pct(99),
-            "requests": n_requests, "arrival_rate": rate, "pool_tiles": len(pinned)}
+            "requests": n_requests, "arrival_rate": rate, "pool_tiles": len(pinned),
+            "policy": "continuous batching: <= %d groups in flight, <= %d tiles per group" % (max_inflight, max_group),
+            "groups": len(sizes), "mean_group": sum(sizes) / max(1, len(sizes))}
 
 
 def run_ours(args, world, rank, local):

@@ -127,6 +127,20 @@ struct CountingProfiler : Profiler {
     void end(const char*, cudaStream_t) override {}
 };
 
+// CUDA graphs of the launch sequence, keyed by batch shape.  Descriptors live
+// in device memory (uploaded before each replay), so a graph replays for any
+// buffers of its shape on the context it was captured for.
+struct GraphEntry {
+    cudaGraphExec_t exec = nullptr;
+    long long kernels = 0;
+};
+using GraphCache = std::map<std::string, GraphEntry>;
+
+void clear_graphs(GraphCache& g) {
+    for (auto& kv : g) cudaGraphExecDestroy(kv.second.exec);
+    g.clear();
+}
+
 // ---- device buffers -----------------------------------------------------------------
 struct DevBuf {
     void* p = nullptr;
@@ -237,7 +251,8 @@ struct LaunchCtx {
 // One served-form context: buffers for a group of tiles submitted together,
 // processed as one batched launch on the context's own stream.
 struct Ctx {
-    cudaStream_t stream = nullptr;
+    cudaStream_t stream = nullptr;  // this context's uploads
+    cudaEvent_t uploaded = nullptr;
     cudaEvent_t done = nullptr;
     LaunchCtx lc;
     DevBuf dev;                    // rgb, hem8, labels, edt, n_objects, feats of all tiles
@@ -247,8 +262,7 @@ struct Ctx {
     size_t h_out_n = 0;
     size_t bytes = 0;              // device bytes held (budget accounting)
     bool busy = false;
-    double t_done = 0;
-    int status_dev_off = 0;
+    GraphCache graphs;            // compute part of a group, per shape
 };
 
 struct TicketTile {
@@ -280,9 +294,7 @@ struct pipe_s {
     DevBuf fbbox;
     // batched form
     LaunchCtx batch;
-    std::map<std::string, cudaGraphExec_t> graphs;
-    std::map<std::string, long long> graph_kernels;
-    std::string batch_key;
+    GraphCache graphs;
     int batch_ntiles = 0;
     // served form
     std::mutex mu;
@@ -292,6 +304,9 @@ struct pipe_s {
     uint64_t last_polled = 0;      // completed ticket whose results are still held
     size_t hbm_in_use = 0;
     EventProfiler serve_prof;      // launches of the served form (counted, not timed)
+    cudaStream_t serve_compute = nullptr;  // all groups compute in submission order
+    cudaEvent_t serve_ref = nullptr;       // recorded at serve_ref_ms (host clock)
+    double serve_ref_ms = 0;
 };
 
 namespace {
@@ -376,6 +391,39 @@ void run_path(pipe_t p, const Launch& L, int Wmax, bool features, int max_object
     launch_label(L, features ? 1 : 0, max_objects, p->sms, s, pf);
     launch_edt(L, bands_rows(Wmax), Wmax, s, pf);
     if (features) launch_features_batched(L, p->sms, s, pf);
+}
+
+void run_path(pipe_t p, const Launch& L, int Wmax, bool features, int max_objects, cudaStream_t s,
+              Profiler* pf);
+
+int run_path_graph(pipe_t p, GraphCache& cache, const std::string& key, const Launch& L, int Wmax, int max_obj,
+                   cudaStream_t s, long long* launches) {
+    auto it = cache.find(key);
+    if (it == cache.end()) {
+        cudaStream_t cs;
+        CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        long long nk = 0;
+        CountingProfiler cp;
+        cp.counter = &nk;
+        cudaGraph_t graph;
+        if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            cudaStreamDestroy(cs);
+            return PIPE_ECUDA;
+        }
+        run_path(p, L, Wmax, true, max_obj, cs, &cp);
+        cudaError_t e = cudaStreamEndCapture(cs, &graph);
+        cudaStreamDestroy(cs);
+        if (e != cudaSuccess) return PIPE_ECUDA;
+        GraphEntry ge;
+        e = cudaGraphInstantiate(&ge.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return PIPE_ECUDA;
+        ge.kernels = nk;
+        it = cache.emplace(key, ge).first;
+    }
+    CK(cudaGraphLaunch(it->second.exec, s));
+    *launches += it->second.kernels;
+    return PIPE_OK;
 }
 
 bool valid_size(int W, int H) { return W >= 1 && H >= 1 && W <= 16384 && H <= 16384; }
@@ -480,7 +528,7 @@ void pipe_destroy(pipe_t p) {
     if (!p) return;
     cudaSetDevice(p->device);
     cudaDeviceSynchronize();
-    for (auto& kv : p->graphs) cudaGraphExecDestroy(kv.second);
+    clear_graphs(p->graphs);
     auto rel = [](LaunchCtx& c) { c.tiles.release(); c.wl.release(); c.shared.release(); c.arena.release(); };
     rel(p->plain);
     rel(p->batch);
@@ -490,9 +538,13 @@ void pipe_destroy(pipe_t p) {
         c->dev.release();
         if (c->h_in) cudaFreeHost(c->h_in);
         if (c->h_out) cudaFreeHost(c->h_out);
+        clear_graphs(c->graphs);
+        if (c->uploaded) cudaEventDestroy(c->uploaded);
         if (c->done) cudaEventDestroy(c->done);
         if (c->stream) cudaStreamDestroy(c->stream);
     }
+    if (p->serve_ref) cudaEventDestroy(p->serve_ref);
+    if (p->serve_compute) cudaStreamDestroy(p->serve_compute);
     delete p;
 }
 
@@ -578,8 +630,7 @@ int seg_features_batch(pipe_t p, const tile_dev* tiles, int n, pipe_stream_t str
                 p->batch.tiles.n < sizeof(TileDev) * n || p->batch.shared.n < sizeof(Shared) + sizeof(int) * (2 + n);
     if (grow) {
         CK(cudaStreamSynchronize(s));
-        for (auto& kv : p->graphs) cudaGraphExecDestroy(kv.second);
-        p->graphs.clear();
+        clear_graphs(p->graphs);
         int rc = ensure_ctx(p->batch, n, n_rt, total);
         if (rc) return rc;
     }
@@ -603,38 +654,11 @@ int seg_features_batch(pipe_t p, const tile_dev* tiles, int n, pipe_stream_t str
     p->batch_ntiles = n;
     int rc = upload_desc(L, td, s);
     if (rc) return rc;
-    auto it = p->graphs.find(key);
-    if (it == p->graphs.end()) {
-        // capture the launch sequence once per batch shape; descriptors live in
-        // device memory, so the graph replays for any buffers of this shape
-        cudaStream_t cs;
-        CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-        long long dummy = 0;
-        CountingProfiler cp;
-        cp.counter = &dummy;
-        cudaGraph_t graph;
-        if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
-            cudaStreamDestroy(cs);
-            return PIPE_ECUDA;
-        }
-        run_path(p, L, Wmax, true, max_obj, cs, &cp);
-        cudaError_t e = cudaStreamEndCapture(cs, &graph);
-        cudaStreamDestroy(cs);
-        if (e != cudaSuccess) return PIPE_ECUDA;
-        cudaGraphExec_t exec;
-        e = cudaGraphInstantiate(&exec, graph, 0);
-        cudaGraphDestroy(graph);
-        if (e != cudaSuccess) return PIPE_ECUDA;
-        it = p->graphs.emplace(key, exec).first;
-        p->batch_key = key;
-        p->graph_kernels[key] = dummy;
-    }
     if (p->prof.enabled) {
         // profiled runs launch eagerly so that each kernel is bracketed by events
         run_path(p, L, Wmax, true, max_obj, s, &p->prof);
-    } else {
-        CK(cudaGraphLaunch(it->second, s));
-        p->prof.launches += p->graph_kernels[key];
+    } else if ((rc = run_path_graph(p, p->graphs, key, L, Wmax, max_obj, s, &p->prof.launches))) {
+        return rc;
     }
     CK(cudaGetLastError());
     return PIPE_OK;
@@ -716,8 +740,6 @@ long long pipe_recon_visits(pipe_t p) {
     return sh.processed;
 }
 
-static void CUDART_CB stamp_done(void* arg) { static_cast<Ctx*>(arg)->t_done = now_ms(); }
-
 int batch_submit(pipe_t p, const tile_desc* tiles, int n, uint64_t* ticket) {
     if (!p || !tiles || n < 1 || n > 1024 || !ticket) return PIPE_EINVAL;
     for (int i = 0; i < n; i++)
@@ -766,13 +788,17 @@ int batch_submit(pipe_t p, const tile_desc* tiles, int n, uint64_t* ticket) {
         ci = (int)p->ctxs.size() - 1;
         Ctx& c = *p->ctxs[ci];
         CK(cudaStreamCreateWithFlags(&c.stream, cudaStreamNonBlocking));
-        CK(cudaEventCreateWithFlags(&c.done, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&c.uploaded, cudaEventDisableTiming));
+        CK(cudaEventCreate(&c.done));  // timed: its GPU timestamp gives the completion time
     }
     Ctx& c = *p->ctxs[ci];
     size_t have = c.bytes;
     size_t grow_to = std::max(have, need);
     if (p->hbm_in_use + grow_to > p->prm.hbm_budget_bytes) return PIPE_EBUSY;
     int rc;
+    if (c.dev.n < io || c.lc.arena.n < ws || c.lc.wl.n < sizeof(int) * 3 * (size_t)n_rt ||
+        c.lc.tiles.n < sizeof(TileDev) * n || c.lc.shared.n < sizeof(Shared) + sizeof(int) * (2 + n))
+        clear_graphs(c.graphs);
     if ((rc = c.dev.ensure(io))) return rc;
     if ((rc = ensure_ctx(c.lc, n, n_rt, ws))) return rc;
     c.bytes = c.dev.n + c.lc.arena.n + c.lc.tiles.n + c.lc.wl.n + c.lc.shared.n;
@@ -826,16 +852,41 @@ int batch_submit(pipe_t p, const tile_desc* tiles, int n, uint64_t* ticket) {
             spitch = (size_t)t.W * 3;
         }
         hi += al256(3 * N);
-        CK(cudaMemcpy2DAsync(rgb, (size_t)t.W * 3, src, spitch, (size_t)t.W * 3, t.H, cudaMemcpyHostToDevice, c.stream));
+        if (spitch == (size_t)t.W * 3)  // dense rows: one contiguous copy, not H row copies
+            CK(cudaMemcpyAsync(rgb, src, (size_t)t.W * 3 * t.H, cudaMemcpyHostToDevice, c.stream));
+        else
+            CK(cudaMemcpy2DAsync(rgb, (size_t)t.W * 3, src, spitch, (size_t)t.W * 3, t.H, cudaMemcpyHostToDevice,
+                                 c.stream));
         TicketTile tt{t.W, t.H, t.want_planes, 0, 0, 0};
         tt.nobj_off = hoff; hoff += al256(16);
         tt.out_off = hoff; hoff += al256((size_t)caps[i] * NFEAT * 4);
         if (t.want_planes) hoff += al256(N) + 2 * al256(4 * N);
         tk->tiles.push_back(tt);
     }
+    // three phases (Sec. IV-D): this group's upload runs on the context's copy
+    // stream, overlapping the compute of groups submitted before it; compute and
+    // download run on the shared compute stream, in submission order
+    if (!p->serve_compute) {
+        CK(cudaStreamCreateWithFlags(&p->serve_compute, cudaStreamNonBlocking));
+        // reference point mapping GPU event time to the host clock
+        CK(cudaEventCreate(&p->serve_ref));
+        CK(cudaEventRecord(p->serve_ref, p->serve_compute));
+        CK(cudaEventSynchronize(p->serve_ref));
+        p->serve_ref_ms = now_ms();
+    }
+    CK(cudaEventRecord(c.uploaded, c.stream));
+    cudaStream_t cs = p->serve_compute;
+    CK(cudaStreamWaitEvent(cs, c.uploaded, 0));
     Launch L = make_launch(p, c.lc, td, n_rt);
-    if ((rc = upload_desc(L, td, c.stream))) return rc;
-    run_path(p, L, Wmax, true, *std::max_element(caps.begin(), caps.end()), c.stream, &p->serve_prof);
+    if ((rc = upload_desc(L, td, cs))) return rc;
+    {
+        std::string key;
+        for (int i = 0; i < n; i++)
+            key += std::to_string(tiles[i].W) + "x" + std::to_string(tiles[i].H) + (tiles[i].want_planes ? "p;" : ";");
+        rc = run_path_graph(p, c.graphs, key, L, Wmax, *std::max_element(caps.begin(), caps.end()), cs,
+                            &p->serve_prof.launches);
+        if (rc) return rc;
+    }
     // download: a kernel writes count, status and exactly min(K, cap) feature
     // rows of every tile into the mapped pinned result buffer; planes by copy
     char* ho = (char*)c.h_out;
@@ -847,20 +898,22 @@ int batch_submit(pipe_t p, const tile_desc* tiles, int n, uint64_t* ticket) {
             rs[i].head = (int32_t*)(ho_dev + tk->tiles[i].nobj_off);
             rs[i].feats = (float*)(ho_dev + tk->tiles[i].out_off);
         }
-        if ((rc = launch_results(L, rs.data(), n, c.stream, &p->serve_prof))) return rc;
+        if ((rc = launch_results(L, rs.data(), n, cs, &p->serve_prof))) return rc;
     }
     for (int i = 0; i < n; i++) {
         const TicketTile& tt = tk->tiles[i];
         size_t N = (size_t)tt.W * tt.H;
         if (tt.want) {
             char* q = ho + tt.out_off + al256((size_t)caps[i] * NFEAT * 4);
-            CK(cudaMemcpyAsync(q, td[i].hem8, N, cudaMemcpyDeviceToHost, c.stream));
-            CK(cudaMemcpyAsync(q + al256(N), td[i].labels, 4 * N, cudaMemcpyDeviceToHost, c.stream));
-            CK(cudaMemcpyAsync(q + al256(N) + al256(4 * N), td[i].edt, 4 * N, cudaMemcpyDeviceToHost, c.stream));
+            CK(cudaMemcpyAsync(q, td[i].hem8, N, cudaMemcpyDeviceToHost, cs));
+            CK(cudaMemcpyAsync(q + al256(N), td[i].labels, 4 * N, cudaMemcpyDeviceToHost, cs));
+            CK(cudaMemcpyAsync(q + al256(N) + al256(4 * N), td[i].edt, 4 * N, cudaMemcpyDeviceToHost, cs));
         }
     }
-    CK(cudaLaunchHostFunc(c.stream, stamp_done, &c));
-    CK(cudaEventRecord(c.done, c.stream));
+    CK(cudaEventRecord(c.done, cs));
+    // No device-side wait orders this context's next upload after this group:
+    // a context takes new work only after batch_poll has seen its done event
+    // complete, so nothing of this group still reads the context's buffers.
     CK(cudaGetLastError());
     c.busy = true;
     p->hbm_in_use += c.bytes;
@@ -914,7 +967,9 @@ int batch_poll(pipe_t p, uint64_t ticket, int* n_done, tile_result* out) {
             tk.tiles[i].nobj_off = (size_t)K[i];  // reuse the fields for the host copies
         }
         tk.done = true;
-        double td = c.t_done;
+        float el = 0.f;
+        double td = now_ms();
+        if (cudaEventElapsedTime(&el, p->serve_ref, c.done) == cudaSuccess) td = p->serve_ref_ms + el;
         c.busy = false;
         p->hbm_in_use -= std::min(p->hbm_in_use, c.bytes);
         for (int i = 0; i < n; i++) tk.tiles[i].out_off = 0;
