@@ -48,6 +48,8 @@ def _load():
         L.oracle_recon.restype = ci
         L.oracle_recon_plain.argtypes = [vp, vp, ci, ci, vp]
         L.oracle_recon_plain.restype = ci
+        L.oracle_recon_rounds.argtypes = [vp, vp, ci, ci, vp, vp]
+        L.oracle_recon_rounds.restype = ci
         L.oracle_hdome.argtypes = [vp, ci, ci, ci, ci, vp, vp, vp]
         L.oracle_fill_holes.argtypes = [vp, ci, ci, vp]
         L.oracle_label.argtypes = [vp, ci, ci, ci, ci, vp]
@@ -100,6 +102,19 @@ def recon_plain(marker, mask):
     out = np.empty((H, W), np.uint8)
     it = _load().oracle_recon_plain(pm, pk, W, H, out.ctypes.data)
     return out, it
+
+
+def recon_rounds(marker, mask):
+    """The plain iteration evaluated only where it can change; returns
+    (R, steps, pixel evaluations).  steps is the front distance in
+    8-connected steps."""
+    marker, pm = _c(marker, np.uint8)
+    mask, pk = _c(mask, np.uint8)
+    H, W = mask.shape
+    out = np.empty((H, W), np.uint8)
+    ev = ctypes.c_longlong(0)
+    it = _load().oracle_recon_rounds(pm, pk, W, H, out.ctypes.data, ctypes.addressof(ev))
+    return out, it, ev.value
 
 
 def hdome(hem8, h=20, thr=10):

@@ -192,6 +192,64 @@ int oracle_recon_plain(const uint8_t* marker, const uint8_t* mask, int W, int H,
     return iters;
 }
 
+/* The same synchronous iteration as oracle_recon_plain, R_{k+1} =
+ * min(dilate8(R_k), mask), evaluated only where it can change: a pixel's
+ * value in R_{k+1} differs from R_k only if some pixel of its 3x3
+ * neighbourhood changed in step k, so after the first full step only the
+ * neighbourhoods of the previous step's changes are re-evaluated (against
+ * an unmodified R_k; changes are applied after the step).  Every R_k, and
+ * hence the number of steps that change something, equals the plain
+ * iteration's.  That number is the distance, in 8-connected steps, that the
+ * slowest reconstruction front travels. */
+int oracle_recon_rounds(const uint8_t* marker, const uint8_t* mask, int W, int H, uint8_t* R,
+                        long long* evaluated) {
+    size_t N = (size_t)W * H;
+    int32_t* cand = (int32_t*)malloc((N ? N : 1) * sizeof(int32_t));
+    int32_t* next = (int32_t*)malloc((N ? N : 1) * sizeof(int32_t));
+    int32_t* chg = (int32_t*)malloc((N ? N : 1) * sizeof(int32_t));
+    uint8_t* val = (uint8_t*)malloc(N ? N : 1);
+    int32_t* stamp = (int32_t*)malloc((N ? N : 1) * sizeof(int32_t));
+    for (size_t i = 0; i < N; i++) { R[i] = marker[i]; cand[i] = (int32_t)i; stamp[i] = 0; }
+    size_t nc = N;
+    long long evals = 0;
+    int steps = 0;
+    for (;;) {
+        size_t nch = 0;
+        for (size_t c = 0; c < nc; c++) {
+            int p = cand[c], y = p / W, x = p % W, m = 0;
+            for (int dy = -1; dy <= 1; dy++)
+                for (int dx = -1; dx <= 1; dx++) {
+                    int yy = y + dy, xx = x + dx;
+                    if (yy < 0 || yy >= H || xx < 0 || xx >= W) continue;
+                    int v = R[(size_t)yy * W + xx];
+                    if (v > m) m = v;
+                }
+            int v = m < mask[p] ? m : mask[p];
+            if (v != R[p]) { chg[nch] = p; val[nch] = (uint8_t)v; nch++; }
+        }
+        evals += (long long)nc;
+        if (nch == 0) break;
+        steps++;
+        for (size_t k = 0; k < nch; k++) R[chg[k]] = val[k];
+        size_t nn = 0;
+        for (size_t k = 0; k < nch; k++) {
+            int p = chg[k], y = p / W, x = p % W;
+            for (int dy = -1; dy <= 1; dy++)
+                for (int dx = -1; dx <= 1; dx++) {
+                    int yy = y + dy, xx = x + dx;
+                    if (yy < 0 || yy >= H || xx < 0 || xx >= W) continue;
+                    int q = yy * W + xx;
+                    if (stamp[q] != steps) { stamp[q] = steps; next[nn++] = q; }
+                }
+        }
+        int32_t* t = cand; cand = next; next = t;
+        nc = nn;
+    }
+    if (evaluated) *evaluated = evals;
+    free(cand); free(next); free(chg); free(val); free(stamp);
+    return steps;
+}
+
 void oracle_hdome(const uint8_t* hem8, int W, int H, int h, int thr, uint8_t* R, uint8_t* fg,
                   oracle_recon_stats* st) {
     size_t N = (size_t)W * H;

@@ -52,6 +52,14 @@ int oracle_recon(const uint8_t* marker, const uint8_t* mask, int W, int H, uint8
  * Returns the number of iterations that changed something. */
 int oracle_recon_plain(const uint8_t* marker, const uint8_t* mask, int W, int H, uint8_t* R);
 
+/* The plain iteration of oracle_recon_plain, restricted after its first
+ * step to the 3x3 neighbourhoods of the previous step's changes (exactly
+ * the same sequence R_k).  Returns the number of steps that changed
+ * something: the distance, in 8-connected steps, that the slowest front
+ * travels.  *evaluated (may be NULL) receives the pixel evaluations. */
+int oracle_recon_rounds(const uint8_t* marker, const uint8_t* mask, int W, int H, uint8_t* R,
+                        long long* evaluated);
+
 /* h-dome: marker = max(hem8 - h, 0), R = recon(marker | hem8),
  * fg = (hem8 - R >= thr).  R and fg may be NULL. */
 void oracle_hdome(const uint8_t* hem8, int W, int H, int h, int thr, uint8_t* R, uint8_t* fg,

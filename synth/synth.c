@@ -13,7 +13,7 @@
  * bytes are the same on every host architecture; only the ellipse geometry
  * uses libm cos/sin.
  *
- * Paint order: background -> stroma blobs -> serpentine corridor -> nuclei
+ * Paint order: background -> stroma blobs -> nuclei -> serpentine corridor
  * -> per-channel noise (Irwin-Hall sum of 12 uniforms, sd 6) -> separable
  * Gaussian blur sigma 1 (radius 3, mirror border) -> round half to even and
  * clamp to uint8.
@@ -107,33 +107,36 @@ static void paint_nuc(canvas* cv, rstream* rs, const nuc* n) {
 }
 static double nuc_rad(const nuc* n) { return 0.5 * (n->a + n->b); }
 
-static void paint_corridor(canvas* cv, int W, int H) {
-    /* Serpentine band: horizontal runs joined by short vertical runs, colour
-       ramped linearly along the arc length from STROMA to CORR_END. */
-    int runs = 5, run_len = W - 2 * 64 < 700 ? W - 2 * 64 : 700, step = 100;
-    if (run_len < 16 || H < runs * step + 128) return;
-    double total = runs * run_len + (runs - 1) * step;
+/* Serpentine band: `runs` horizontal runs 128 px in from the left and right
+   edges, joined by vertical runs of 256 px, its colour ramped linearly (in
+   RGB) along the arc length from STROMA to CORR_END.  It is painted after
+   the nuclei, over a clearance strip of background 14 px wide on each side
+   of its centre line, so no nucleus touches it and the reconstruction front
+   entering at its high end has to travel along it. */
+static void corridor_pass(canvas* cv, int W, int H, double rad, int ramp) {
+    const int runs = 3, margin = 128, step = 256;
+    const int run_len = W - 2 * margin;
+    if (run_len < 16 || H < (runs - 1) * step + 2 * margin) return;
+    const double total = (double)runs * run_len + (runs - 1) * step;
     double s = 0.0;
-    int x = 64, y = 64, dir = 1;
-    double half = 4.0;
+    int x = margin, y = margin, dir = 1;
     for (int r = 0; r < runs; r++) {
-        for (int i = 0; i < run_len; i++) {
+        for (int i = 0; i < run_len + (r == runs - 1 ? 0 : step); i++) {
             int32_t colq[3];
             for (int c = 0; c < 3; c++)
-                colq[c] = (int32_t)llround((STROMA[c] + (CORR_END[c] - STROMA[c]) * (s / total)) * Q);
-            fill_disc_q(cv, x, y, half, colq);
-            x += dir; s += 1.0;
-        }
-        if (r == runs - 1) break;
-        for (int i = 0; i < step; i++) {
-            int32_t colq[3];
-            for (int c = 0; c < 3; c++)
-                colq[c] = (int32_t)llround((STROMA[c] + (CORR_END[c] - STROMA[c]) * (s / total)) * Q);
-            fill_disc_q(cv, x, y, half, colq);
-            y += 1; s += 1.0;
+                colq[c] = ramp ? (int32_t)llround((STROMA[c] + (CORR_END[c] - STROMA[c]) * (s / total)) * Q)
+                               : BG[c] * Q;
+            fill_disc_q(cv, x, y, rad, colq);
+            if (i < run_len) x += dir; else y += 1;
+            s += 1.0;
         }
         dir = -dir;
     }
+}
+
+static void paint_corridor(canvas* cv, int W, int H) {
+    corridor_pass(cv, W, H, 14.0, 0);
+    corridor_pass(cv, W, H, 4.0, 1);
 }
 
 /* Q16 taps of exp(-k^2/2), k=-3..3, normalised to sum 65536 */
@@ -170,7 +173,6 @@ int synth_tile(const synth_cfg* cfg, uint8_t* out, size_t pitch) {
         for (int c = 0; c < 3; c++) colq[c] = (STROMA[c] + rs_int(&geo, -5, 5)) * Q;
         fill_disc_q(&cv, cx, cy, rad, colq);
     }
-    if (cfg->corridor) paint_corridor(&cv, W, H);
 
     /* nuclei: singles, overlapping pairs, touching clusters (2..6), chains */
     int placed = 0;
@@ -223,6 +225,8 @@ int synth_tile(const synth_cfg* cfg, uint8_t* out, size_t pitch) {
             have_prev = 1;
         }
     }
+
+    if (cfg->corridor) paint_corridor(&cv, W, H);
 
     /* noise: per pixel and channel, 12 16-bit uniforms from 3 counter draws;
        (sum - 12*32767.5) / 65536 has sd 1; scaled by 6 into Q8 units */

@@ -61,3 +61,52 @@ def assert_planes_equal(g, r, planes=("hem8", "R", "fg", "filled", "labels", "ed
             raise AssertionError("%s differs at %d pixels; first (%d,%d): gpu %r oracle %r"
                                  % (k, len(bad), y, x, a[y, x], b[y, x]))
     assert g["K"] == r["K"], (g["K"], r["K"])
+
+
+# ---- many tiles: oracle outputs computed in a process pool ------------------
+
+def plane_digest(a):
+    import hashlib
+    return hashlib.sha256(np.ascontiguousarray(a).tobytes()).hexdigest()
+
+
+def make_tile(spec):
+    """spec: ("cfg2"|"cfg3"|"cfg4", i) for the synth presets, or
+    ("bench", seed) for a tile of the 4096^2 benchmark workload."""
+    import synth
+    kind, i = spec
+    if kind == "bench":
+        return synth.tile(4096, 4096, i, n_nuclei=3000, frac_cluster=0.2, n_stroma=150)
+    return getattr(synth, kind)(i)
+
+
+def oracle_digest(spec):
+    """Oracle result of one seeded tile: K, FP64 features and a SHA-256
+    digest of each integer plane (compared bit for bit with the GPU's)."""
+    rgb = make_tile(spec)
+    r = oracle.seg(rgb, planes=False)
+    feats = oracle.features(r["hem8"], r["labels"], r["K"])
+    return dict(K=r["K"], feats=feats, hem8=plane_digest(r["hem8"]), labels=plane_digest(r["labels"]),
+                edt=plane_digest(r["edt"]))
+
+
+def oracle_digests(specs):
+    """oracle_digest over a spawn-started process pool (fork after CUDA
+    initialisation is unsafe)."""
+    import concurrent.futures
+    import multiprocessing
+    import os
+    n = max(1, min(len(specs), os.cpu_count() or 1))
+    with concurrent.futures.ProcessPoolExecutor(n, mp_context=multiprocessing.get_context("spawn")) as ex:
+        return list(ex.map(oracle_digest, specs))
+
+
+def assert_matches_digest(got, ref, rgb=None, what=""):
+    """got: dict with K, feats and (optionally) hem8/labels/edt planes."""
+    assert got["K"] == ref["K"], (what, got["K"], ref["K"])
+    for k in ("hem8", "labels", "edt"):
+        if k in got and got[k] is not None and plane_digest(got[k]) != ref[k]:
+            if rgb is not None:  # locate the first difference
+                assert_planes_equal(got, oracle_all(rgb), planes=(k,))
+            raise AssertionError("%s: plane %s differs from the oracle" % (what, k))
+    assert_feats_close(got["feats"], ref["feats"])

@@ -105,3 +105,49 @@ def test_hdome_threshold_is_inclusive():
     assert fg[4, 4] == 1 and fg.sum() == 9
     _, fg = oracle.hdome(hem, h=10, thr=11)
     assert fg.sum() == 0
+
+
+# ---- the front-distance instrument (plain iteration, evaluated where it can change)
+
+@pytest.mark.parametrize("seed", range(8))
+def test_rounds_equals_iterated_definition(seed):
+    rng = np.random.default_rng(300 + seed)
+    H, W = int(rng.integers(1, 48)), int(rng.integers(1, 48))
+    mask = rng.integers(0, 256, (H, W)).astype(np.uint8)
+    if seed % 2:
+        mask = (rng.integers(0, 3, (H, W)) * 100).astype(np.uint8)
+    marker = np.where(rng.random((H, W)) < 0.05, mask, 0).astype(np.uint8)
+    ref, it = brute.recon_iterated(marker, mask)
+    got, steps, evals = oracle.recon_rounds(marker, mask)
+    assert np.array_equal(got, ref)
+    assert steps == it
+    assert evals >= H * W
+
+
+@pytest.mark.parametrize("N", [1, 2, 9, 40])
+def test_rounds_front_distance_closed_form(N):
+    """One seed in the corner of a flat square mask: the front needs the
+    chessboard distance to the far corner, N-1 steps (2N-2 if propagation
+    were 4-connected); along a single row it needs W-1 steps."""
+    mask = np.full((N, N), 100, np.uint8)
+    marker = np.zeros((N, N), np.uint8)
+    marker[0, 0] = 100
+    R, steps, _ = oracle.recon_rounds(marker, mask)
+    assert (R == 100).all() and steps == N - 1
+    row = np.full((1, 3 * N), 7, np.uint8)
+    mrow = np.zeros_like(row)
+    mrow[0, -1] = 7
+    R, steps, _ = oracle.recon_rounds(mrow, row)
+    assert (R == 7).all() and steps == 3 * N - 1
+
+
+def test_worst_case_front_travels_beyond_2000px():
+    """Acceptance of the worst-case workload: in its h-dome reconstruction
+    (h = 20) the slowest front travels more than 2000 px, and the result
+    equals Vincent's."""
+    import synth
+    hem8 = oracle.deconv(synth.cfg4(0))
+    marker = np.maximum(hem8.astype(np.int32) - 20, 0).astype(np.uint8)
+    R, steps, _ = oracle.recon_rounds(marker, hem8)
+    assert steps > 2000, steps
+    assert np.array_equal(R, oracle.recon(marker, hem8))
