@@ -409,6 +409,7 @@ def run_ours(args, world, rank, local):
     barrier(world)
     launches = pipe.launch_count() - l0
     ck = clocks.stop()
+    shapes = pipe.autotune_info()
     ms_total = max_over_ranks(world, ms_total)
     ms_step = ms_total / args.steps
     value = world * B * args.steps / (ms_total / 1000.0)
@@ -420,7 +421,10 @@ def run_ours(args, world, rank, local):
             "vs_baseline": None, "dtype": "u8", "data": "synthetic",
             "config": {"workload": WORKLOAD, "form": "batched (one launch per pass over the batch, CUDA graph)",
                        "tiles_per_step": B, "l2": "inputs larger than L2 (%d x 48 MiB RGB per step)" % B,
-                       "parallelism": "replicas" if world > 1 else "1 GPU"},
+                       "parallelism": "replicas" if world > 1 else "1 GPU",
+                       "launch_shapes": {"recon_workers": shapes["recon_workers"], "edt_rows": shapes["edt_rows"],
+                                         "feat_blocks": shapes["feat_blocks"],
+                                         "tuned_in_warmup_passes": shapes["tune_runs"]}},
             "gpu_launches": int(launches), "clocks": ck}
     if args.no_extra:
         if rank == 0:
@@ -514,7 +518,7 @@ def run_ours(args, world, rank, local):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--batch", type=int, default=16, help="4096^2 tiles per batched step")

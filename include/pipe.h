@@ -50,7 +50,8 @@ typedef enum {
 
 /* Parameters.  Defaults (pipe_default_params): h = 20, dome_thresh = 10,
  * area [20, 1500], 8 GLCM levels, offsets (dx,dy) = (1,0),(0,1),(1,1),(1,-1),
- * hbm_budget_bytes = 40 GiB, max_slots = 16, wait_budget_cycles = 2^32. */
+ * hbm_budget_bytes = 40 GiB, max_slots = 16, wait_budget_cycles = 2^32,
+ * autotune_cache = NULL, autotune = 1. */
 typedef struct {
     int h;               /* h-dome height (ReconToNuclei, Table I) */
     int dome_thresh;     /* foreground iff hem8 - R >= dome_thresh */
@@ -62,7 +63,8 @@ typedef struct {
     size_t hbm_budget_bytes;  /* device memory the served form may hold */
     int max_slots;            /* tiles in flight in the served form */
     long long wait_budget_cycles; /* bound on every device-side spin wait */
-    const char* autotune_cache;   /* path of the tile-shape cache, or NULL */
+    const char* autotune_cache;   /* path of the launch-shape cache file, or NULL */
+    int autotune;                 /* 1: tune the launch shapes of new batch shapes */
 } pipe_params;
 
 void pipe_default_params(pipe_params* p);
@@ -140,6 +142,17 @@ typedef struct {
     uint8_t* hem8; int32_t* labels; int32_t* edt; int32_t* n_objects;
     float* feats; int feats_cap;
 } tile_dev;
+/* Launch shapes (the number of persistent reconstruction workers, the rows
+ * one distance-transform block solves, the blocks of the feature pass)
+ * never change a result.  With params.autotune set, the first call with a
+ * new list of tile sizes synchronises `stream` and picks them by timing the
+ * whole path on this batch (about 30 extra passes; the outputs are
+ * rewritten with identical values); the choice is kept per tile-size list
+ * for the pipe's lifetime and, if params.autotune_cache names a file,
+ * appended to it ("<key> <workers> <rows> <blocks>" per line) and read back
+ * by later pipes.  Such a first call cannot be captured into a CUDA graph.
+ * The served form uses a shape's tuned values when it has them and the
+ * defaults otherwise; it never tunes. */
 int seg_features_batch(pipe_t p, const tile_dev* tiles, int n, pipe_stream_t stream);
 
 /* Served form (Sec. IV-D prefetching and asynchronous copy): tiles in host
@@ -192,6 +205,10 @@ int pipe_debug_plane(pipe_t p, int which, void* dst_dev, pipe_stream_t stream);
 int pipe_profile_enable(pipe_t p, int enable);
 int pipe_profile_read(pipe_t p, const char** names, long long* launches, double* total_ms,
                       int cap);
+
+/* Launch shapes used by the most recent seg_features_batch call, and the
+ * number of timed passes the autotuner has run since creation. */
+int pipe_autotune_info(pipe_t p, int* recon_workers, int* edt_rows, int* feat_blocks, long long* tune_runs);
 
 /* Number of kernels the pipe has launched since creation. */
 long long pipe_launch_count(pipe_t p);

@@ -20,7 +20,7 @@ STATUS_NAMES = ["PIPE_OK", "PIPE_EINVAL", "PIPE_ENOMEM", "PIPE_EBUSY", "PIPE_EAG
 EXPORTS = ["pipe_default_params", "pipe_create", "pipe_destroy", "seg_tile", "features_tile",
            "seg_features_batch", "batch_submit", "batch_poll", "pipe_status_read", "pipe_debug_plane",
            "pipe_profile_enable", "pipe_profile_read", "pipe_launch_count", "pipe_recon_visits",
-           "features_tile_noalloc"]
+           "features_tile_noalloc", "pipe_autotune_info"]
 NOALLOC_MAX_OBJECTS = 65536
 
 
@@ -36,7 +36,7 @@ class PipeParams(ctypes.Structure):
                 ("area_max", ctypes.c_int), ("glcm_levels", ctypes.c_int), ("n_offsets", ctypes.c_int),
                 ("offsets", (ctypes.c_int * 2) * 4), ("hbm_budget_bytes", ctypes.c_size_t),
                 ("max_slots", ctypes.c_int), ("wait_budget_cycles", ctypes.c_longlong),
-                ("autotune_cache", ctypes.c_char_p)]
+                ("autotune_cache", ctypes.c_char_p), ("autotune", ctypes.c_int)]
 
 
 class TileDevC(ctypes.Structure):
@@ -91,6 +91,8 @@ def lib():
     L.features_tile_noalloc.restype = ci
     L.pipe_recon_visits.argtypes = [vp]
     L.pipe_recon_visits.restype = ctypes.c_longlong
+    L.pipe_autotune_info.argtypes = [vp, ctypes.POINTER(ci), ctypes.POINTER(ci), ctypes.POINTER(ci),
+                                     ctypes.POINTER(ctypes.c_longlong)]
     for n in ("pipe_create", "seg_tile", "features_tile", "seg_features_batch", "batch_submit", "batch_poll",
               "pipe_status_read", "pipe_debug_plane", "pipe_profile_enable", "pipe_profile_read"):
         getattr(L, n).restype = ci
@@ -132,6 +134,9 @@ class Pipe:
     def __init__(self, device=0, params=None, **overrides):
         p = params if params is not None else default_params()
         for k, v in overrides.items():
+            if k == "autotune_cache" and isinstance(v, str):
+                v = v.encode()
+                self._cache_path = v  # keeps the bytes alive while the pipe reads them
             setattr(p, k, v)
         self.params = p
         h = ctypes.c_void_p()
@@ -254,3 +259,12 @@ class Pipe:
 
     def recon_visits(self):
         return lib().pipe_recon_visits(self.h)
+
+    def autotune_info(self):
+        """Launch shapes of the latest batched call and the autotuner's timed
+        passes so far: dict(recon_workers, edt_rows, feat_blocks, tune_runs)."""
+        a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        r = ctypes.c_longlong()
+        _check(lib().pipe_autotune_info(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(r)),
+               "pipe_autotune_info")
+        return dict(recon_workers=a.value, edt_rows=b.value, feat_blocks=c.value, tune_runs=r.value)

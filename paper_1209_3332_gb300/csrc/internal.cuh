@@ -117,7 +117,7 @@ size_t edt_rows_smem(int RB, int Wmax);
 void launch_edt(const Launch& L, int RB, int Wmax, cudaStream_t s, Profiler* pf);
 void launch_features_plain(const uint8_t* hem8, const int32_t* labels, int W, int H, int K, float* feats,
                            int4* bbox, int sms, cudaStream_t s, Profiler* pf);
-void launch_features_batched(const Launch& L, int sms, cudaStream_t s, Profiler* pf);
+void launch_features_batched(const Launch& L, int grid, cudaStream_t s, Profiler* pf);
 void launch_unpack_bits(const uint32_t* bits, int W, int H, int wpr, uint8_t* out, cudaStream_t s,
                         Profiler* pf);
 

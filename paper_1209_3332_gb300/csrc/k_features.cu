@@ -383,12 +383,12 @@ void launch_features_plain(const uint8_t* hem8, const int32_t* labels, int W, in
     pf->end("feat_objects", s);
 }
 
-void launch_features_batched(const Launch& L, int sms, cudaStream_t s, Profiler* pf) {
+void launch_features_batched(const Launch& L, int grid, cudaStream_t s, Profiler* pf) {
     pf->begin("feat_prefix", s);
     k_obj_prefix<<<1, 32, 0, s>>>(L);
     pf->end("feat_prefix", s);
     pf->begin("feat_objects", s);
-    k_fobj_batched<<<sms * 16, FW * 32, 0, s>>>(L);
+    k_fobj_batched<<<grid, FW * 32, 0, s>>>(L);
     pf->end("feat_objects", s);
 }
 

@@ -163,13 +163,24 @@ struct DevBuf {
 
 // Geometry and workspace sizes of one image.
 struct Geo {
-    int W, H, wpr, rtx, rty, cbx, cby, nchunks, nbands;
+    int W, H, wpr, rtx, rty, cbx, cby, nchunks;
     size_t N, ws_bytes;
 };
 
 int bands_rows(int Wmax) { return Wmax <= 4096 ? 4 : (Wmax <= 8192 ? 2 : 1); }
 
-Geo geometry(int W, int H, int feats_cap, int RB) {
+// Launch shapes of one batch.  None of them changes any result: they set how
+// many persistent reconstruction workers run, how many rows one EDT block
+// solves (a divisor of the 32-row chunk), and how many blocks the feature
+// pass spreads the objects over.
+struct Tune {
+    int recon_grid, edt_rb, feat_grid;
+};
+std::string tune_str(const Tune& t) {
+    return std::to_string(t.recon_grid) + " " + std::to_string(t.edt_rb) + " " + std::to_string(t.feat_grid);
+}
+
+Geo geometry(int W, int H, int feats_cap) {
     Geo g;
     g.W = W;
     g.H = H;
@@ -181,7 +192,6 @@ Geo geometry(int W, int H, int feats_cap, int RB) {
     g.cby = (H + CB - 1) / CB;
     size_t words = (size_t)H * g.wpr;
     g.nchunks = (int)((words + SCAN_CHUNK - 1) / SCAN_CHUNK);
-    g.nbands = (H + RB - 1) / RB;
     size_t b = 0;
     b += al256(g.N);                              // R
     b += 2 * al256(g.N * 4);                      // P, A
@@ -307,6 +317,12 @@ struct pipe_s {
     cudaStream_t serve_compute = nullptr;  // all groups compute in submission order
     cudaEvent_t serve_ref = nullptr;       // recorded at serve_ref_ms (host clock)
     double serve_ref_ms = 0;
+    // launch shapes per batch shape: tuned by the batched form on first sight
+    // of a shape, or read from the autotune cache file
+    std::map<std::string, Tune> tuned;
+    std::string tune_file;
+    long long tune_runs = 0;
+    Tune last_tune{0, 0, 0};
 };
 
 namespace {
@@ -321,7 +337,7 @@ int ensure_ctx(LaunchCtx& c, int ntiles, int n_rt, size_t arena_bytes) {
 }
 
 // Fill launch-wide bases of the descriptors and the Launch totals.
-Launch make_launch(pipe_t p, LaunchCtx& c, std::vector<TileDev>& td, int n_rt_total) {
+Launch make_launch(pipe_t p, LaunchCtx& c, std::vector<TileDev>& td, int n_rt_total, int RB) {
     Launch L{};
     L.tiles = (TileDev*)c.tiles.p;
     L.ntiles = (int)td.size();
@@ -332,9 +348,6 @@ Launch make_launch(pipe_t p, LaunchCtx& c, std::vector<TileDev>& td, int n_rt_to
     L.status = (int*)((char*)c.shared.p + sizeof(Shared));
     L.tile_status = L.status + 2;
     int rt = 0, cb = 0, ch = 0, col = 0, row = 0, px = 0;
-    int Wmax = 1;
-    for (auto& t : td) Wmax = std::max(Wmax, t.W);
-    int RB = bands_rows(Wmax);
     for (auto& t : td) {
         t.rt_base = rt;
         t.cb_base = cb;
@@ -384,20 +397,18 @@ int max_width(const std::vector<TileDev>& td) {
 
 // The whole path over the descriptors of L (segmentation, and features when
 // `features` is set: boxes come from the relabel pass).
-void run_path(pipe_t p, const Launch& L, int Wmax, bool features, int max_objects, cudaStream_t s,
-              Profiler* pf) {
+void run_path(pipe_t p, const Launch& L, int Wmax, bool features, int max_objects, const Tune& tu,
+              cudaStream_t s, Profiler* pf) {
     launch_deconv(L, s, pf);
-    launch_recon(L, p->recon_cap, s, pf);
+    launch_recon(L, tu.recon_grid, s, pf);
     launch_label(L, features ? 1 : 0, max_objects, p->sms, s, pf);
-    launch_edt(L, bands_rows(Wmax), Wmax, s, pf);
-    if (features) launch_features_batched(L, p->sms, s, pf);
+    launch_edt(L, tu.edt_rb, Wmax, s, pf);
+    if (features) launch_features_batched(L, tu.feat_grid, s, pf);
 }
 
-void run_path(pipe_t p, const Launch& L, int Wmax, bool features, int max_objects, cudaStream_t s,
-              Profiler* pf);
-
-int run_path_graph(pipe_t p, GraphCache& cache, const std::string& key, const Launch& L, int Wmax, int max_obj,
-                   cudaStream_t s, long long* launches) {
+int run_path_graph(pipe_t p, GraphCache& cache, const std::string& shape_key, const Launch& L, int Wmax,
+                   int max_obj, const Tune& tu, cudaStream_t s, long long* launches) {
+    const std::string key = shape_key + "|" + tune_str(tu);
     auto it = cache.find(key);
     if (it == cache.end()) {
         cudaStream_t cs;
@@ -410,7 +421,7 @@ int run_path_graph(pipe_t p, GraphCache& cache, const std::string& key, const La
             cudaStreamDestroy(cs);
             return PIPE_ECUDA;
         }
-        run_path(p, L, Wmax, true, max_obj, cs, &cp);
+        run_path(p, L, Wmax, true, max_obj, tu, cs, &cp);
         cudaError_t e = cudaStreamEndCapture(cs, &graph);
         cudaStreamDestroy(cs);
         if (e != cudaSuccess) return PIPE_ECUDA;
@@ -424,6 +435,126 @@ int run_path_graph(pipe_t p, GraphCache& cache, const std::string& key, const La
     CK(cudaGraphLaunch(it->second.exec, s));
     *launches += it->second.kernels;
     return PIPE_OK;
+}
+
+Tune default_tune(pipe_t p, int Wmax) { return Tune{p->recon_cap, bands_rows(Wmax), p->sms * 16}; }
+
+constexpr size_t EDT_SMEM_MAX = 96 * 1024;
+
+bool tune_ok(pipe_t p, const Tune& t, int Wmax) {
+    return t.recon_grid >= 1 && t.recon_grid <= p->recon_cap && (t.edt_rb == 1 || t.edt_rb == 2 || t.edt_rb == 4 ||
+           t.edt_rb == 8) && edt_rows_smem(t.edt_rb, Wmax) <= EDT_SMEM_MAX && t.feat_grid >= 1 &&
+           t.feat_grid <= p->sms * 64;
+}
+
+// Tuning key: the device's SM count and the tile sizes, in batch order.
+std::string tune_key(pipe_t p, const std::vector<Geo>& geos) {
+    std::string k = std::to_string(p->sms) + "sm:";
+    for (const Geo& g : geos) k += std::to_string(g.W) + "x" + std::to_string(g.H) + ";";
+    return k;
+}
+
+// The cache file holds one line per key: "<key> <recon_grid> <edt_rb> <feat_grid>".
+void load_tune_file(pipe_t p) {
+    FILE* f = std::fopen(p->tune_file.c_str(), "r");
+    if (!f) return;
+    std::vector<char> line(1 << 20);
+    while (std::fgets(line.data(), (int)line.size(), f)) {
+        char* sp = std::strchr(line.data(), ' ');
+        if (!sp) continue;
+        Tune t;
+        if (std::sscanf(sp + 1, "%d %d %d", &t.recon_grid, &t.edt_rb, &t.feat_grid) != 3) continue;
+        p->tuned[std::string(line.data(), sp)] = t;
+    }
+    std::fclose(f);
+}
+
+void save_tune(pipe_t p, const std::string& key, const Tune& t) {
+    if (p->tune_file.empty()) return;
+    FILE* f = std::fopen(p->tune_file.c_str(), "a");
+    if (!f) return;
+    std::fprintf(f, "%s %s\n", key.c_str(), tune_str(t).c_str());
+    std::fclose(f);
+}
+
+// Picks the launch shapes of a batch by timing the whole batched path on the
+// batch itself, one parameter at a time (coordinate descent from the
+// defaults); each candidate runs once to warm and is timed as the fastest of
+// two runs with CUDA events.  Every candidate computes the same results, so
+// the runs only rewrite the caller's outputs with identical values.  A
+// candidate replaces the current choice only if it is 2% faster.
+int autotune(pipe_t p, LaunchCtx& c, std::vector<TileDev>& td, int n_rt, int Wmax, int max_obj, cudaStream_t s,
+             Tune* out) {
+    Tune best = default_tune(p, Wmax);
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return PIPE_ECUDA;
+    }
+    CountingProfiler cp;
+    cp.counter = &p->prof.launches;
+    int rc = PIPE_OK;
+    auto timeit = [&](const Tune& tu, float* ms) -> int {
+        Launch L = make_launch(p, c, td, n_rt, tu.edt_rb);
+        int r = upload_desc(L, td, s);
+        if (r) return r;
+        float b = 1e30f;
+        for (int k = 0; k < 3; k++) {
+            if (cudaEventRecord(e0, s) != cudaSuccess) return PIPE_ECUDA;
+            run_path(p, L, Wmax, true, max_obj, tu, s, &cp);
+            if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) return PIPE_ECUDA;
+            float t = 0;
+            if (cudaEventElapsedTime(&t, e0, e1) != cudaSuccess) return PIPE_ECUDA;
+            if (k > 0) b = std::min(b, t);
+        }
+        p->tune_runs += 3;
+        *ms = b;
+        return PIPE_OK;
+    };
+    float cur = 0;
+    auto consider = [&](Tune t) -> int {
+        if (!tune_ok(p, t, Wmax)) return PIPE_OK;
+        float ms = 0;
+        int r = timeit(t, &ms);
+        if (r) return r;
+        if (ms < 0.98f * cur) {
+            best = t;
+            cur = ms;
+        }
+        return PIPE_OK;
+    };
+    if ((rc = timeit(best, &cur))) goto done;
+    {
+        const int per = std::max(1, p->recon_cap / std::max(p->sms, 1));
+        const int fr[3] = {per / 4, per / 2, (3 * per) / 4};
+        Tune base = best;
+        for (int f : fr)
+            if (f >= 1 && f < per) {
+                Tune t = base;
+                t.recon_grid = f * p->sms;
+                if ((rc = consider(t))) goto done;
+            }
+        base = best;
+        for (int rb : {1, 2, 8})
+            if (rb != base.edt_rb) {
+                Tune t = base;
+                t.edt_rb = rb;
+                if ((rc = consider(t))) goto done;
+            }
+        base = best;
+        for (int fg : {4, 8, 32})
+            if (fg * p->sms != base.feat_grid) {
+                Tune t = base;
+                t.feat_grid = fg * p->sms;
+                if ((rc = consider(t))) goto done;
+            }
+    }
+done:
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc == PIPE_OK) *out = best;
+    return rc;
 }
 
 bool valid_size(int W, int H) { return W >= 1 && H >= 1 && W <= 16384 && H <= 16384; }
@@ -488,6 +619,7 @@ void pipe_default_params(pipe_params* p) {
     p->max_slots = 16;
     p->wait_budget_cycles = 1LL << 32;
     p->autotune_cache = nullptr;
+    p->autotune = 1;
 }
 
 int pipe_create(const pipe_params* params, int device, pipe_t* out) {
@@ -516,6 +648,10 @@ int pipe_create(const pipe_params* params, int device, pipe_t* out) {
         return PIPE_ECUDA;
     }
     p->recon_cap = std::max(1, recon_grid(device));
+    if (prm.autotune_cache) {
+        p->tune_file = prm.autotune_cache;
+        load_tune_file(p);
+    }
     if (cudaGetLastError() != cudaSuccess) {
         delete p;
         return PIPE_ECUDA;
@@ -554,8 +690,7 @@ int seg_tile(pipe_t p, const uint8_t* rgb_dev, int W, int H, size_t pitch_bytes,
     if (!valid_size(W, H) || pitch_bytes < (size_t)W * 3) return PIPE_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     CK(cudaSetDevice(p->device));
-    int RB = bands_rows(W);
-    Geo g = geometry(W, H, 1, RB);
+    Geo g = geometry(W, H, 1);
     int n_rt = g.rtx * g.rty;
     if (p->plain.arena.n < g.ws_bytes || p->plain.wl.n < sizeof(int) * 3 * (size_t)n_rt) CK(cudaStreamSynchronize(s));
     int rc = ensure_ctx(p->plain, 1, n_rt, g.ws_bytes);
@@ -572,9 +707,10 @@ int seg_tile(pipe_t p, const uint8_t* rgb_dev, int W, int H, size_t pitch_bytes,
     t.edt = edt_dev;
     t.n_objects = n_objects_dev;
     t.feats = nullptr;
-    Launch L = make_launch(p, p->plain, td, n_rt);
+    const Tune tu = default_tune(p, W);
+    Launch L = make_launch(p, p->plain, td, n_rt, tu.edt_rb);
     if ((rc = upload_desc(L, td, s))) return rc;
-    run_path(p, L, W, false, 0, s, &p->prof);
+    run_path(p, L, W, false, 0, tu, s, &p->prof);
     CK(cudaGetLastError());
     p->last_plain = td[0];
     p->have_last = true;
@@ -612,14 +748,13 @@ int seg_features_batch(pipe_t p, const tile_dev* tiles, int n, pipe_stream_t str
     CK(cudaSetDevice(p->device));
     int Wmax = 1;
     for (int i = 0; i < n; i++) Wmax = std::max(Wmax, tiles[i].W);
-    int RB = bands_rows(Wmax);
     std::vector<Geo> geos(n);
     std::vector<size_t> off(n);
     size_t total = 0;
     int n_rt = 0;
     std::string key;
     for (int i = 0; i < n; i++) {
-        geos[i] = geometry(tiles[i].W, tiles[i].H, tiles[i].feats_cap, RB);
+        geos[i] = geometry(tiles[i].W, tiles[i].H, tiles[i].feats_cap);
         off[i] = total;
         total += geos[i].ws_bytes;
         n_rt += geos[i].rtx * geos[i].rty;
@@ -650,14 +785,27 @@ int seg_features_batch(pipe_t p, const tile_dev* tiles, int n, pipe_stream_t str
         t.feats = tiles[i].feats;
         max_obj = std::max(max_obj, t.feats_cap);
     }
-    Launch L = make_launch(p, p->batch, td, n_rt);
     p->batch_ntiles = n;
-    int rc = upload_desc(L, td, s);
-    if (rc) return rc;
+    int rc;
+    Tune tu = default_tune(p, Wmax);
+    {
+        const std::string tk = tune_key(p, geos);
+        auto it = p->tuned.find(tk);
+        if (it != p->tuned.end() && tune_ok(p, it->second, Wmax)) {
+            tu = it->second;
+        } else if (p->prm.autotune) {
+            if ((rc = autotune(p, p->batch, td, n_rt, Wmax, max_obj, s, &tu))) return rc;
+            p->tuned[tk] = tu;
+            save_tune(p, tk, tu);
+        }
+    }
+    p->last_tune = tu;
+    Launch L = make_launch(p, p->batch, td, n_rt, tu.edt_rb);
+    if ((rc = upload_desc(L, td, s))) return rc;
     if (p->prof.enabled) {
         // profiled runs launch eagerly so that each kernel is bracketed by events
-        run_path(p, L, Wmax, true, max_obj, s, &p->prof);
-    } else if ((rc = run_path_graph(p, p->graphs, key, L, Wmax, max_obj, s, &p->prof.launches))) {
+        run_path(p, L, Wmax, true, max_obj, tu, s, &p->prof);
+    } else if ((rc = run_path_graph(p, p->graphs, key, L, Wmax, max_obj, tu, s, &p->prof.launches))) {
         return rc;
     }
     CK(cudaGetLastError());
@@ -732,6 +880,15 @@ int pipe_profile_read(pipe_t p, const char** names, long long* launches, double*
 
 long long pipe_launch_count(pipe_t p) { return p ? p->prof.launches + p->serve_prof.launches : -1; }
 
+int pipe_autotune_info(pipe_t p, int* recon_grid, int* edt_rows, int* feat_grid, long long* tune_runs) {
+    if (!p) return PIPE_EINVAL;
+    if (recon_grid) *recon_grid = p->last_tune.recon_grid;
+    if (edt_rows) *edt_rows = p->last_tune.edt_rb;
+    if (feat_grid) *feat_grid = p->last_tune.feat_grid;
+    if (tune_runs) *tune_runs = p->tune_runs;
+    return PIPE_OK;
+}
+
 long long pipe_recon_visits(pipe_t p) {
     if (!p || !p->plain.shared.p) return -1;
     if (cudaSetDevice(p->device) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) return -1;
@@ -751,7 +908,6 @@ int batch_submit(pipe_t p, const tile_desc* tiles, int n, uint64_t* ticket) {
     // sizes of this group
     int Wmax = 1;
     for (int i = 0; i < n; i++) Wmax = std::max(Wmax, tiles[i].W);
-    const int RB = bands_rows(Wmax);
     std::vector<Geo> geos(n);
     std::vector<int> caps(n);
     size_t ws = 0, io = 0, hin = 0, hout = 0;
@@ -759,7 +915,7 @@ int batch_submit(pipe_t p, const tile_desc* tiles, int n, uint64_t* ticket) {
     for (int i = 0; i < n; i++) {
         size_t N = (size_t)tiles[i].W * tiles[i].H;
         caps[i] = (int)std::min<size_t>(N / 20 + 1, 65536);
-        geos[i] = geometry(tiles[i].W, tiles[i].H, caps[i], RB);
+        geos[i] = geometry(tiles[i].W, tiles[i].H, caps[i]);
         ws += geos[i].ws_bytes;
         io += al256(3 * N) + al256(N) + 2 * al256(4 * N) + al256(16) + al256((size_t)caps[i] * NFEAT * 4);
         hin += al256(3 * N);
@@ -877,13 +1033,20 @@ int batch_submit(pipe_t p, const tile_desc* tiles, int n, uint64_t* ticket) {
     CK(cudaEventRecord(c.uploaded, c.stream));
     cudaStream_t cs = p->serve_compute;
     CK(cudaStreamWaitEvent(cs, c.uploaded, 0));
-    Launch L = make_launch(p, c.lc, td, n_rt);
+    // launch shapes: those tuned for this shape by the batched form, if any
+    // (the served form never blocks to tune)
+    Tune tu = default_tune(p, Wmax);
+    {
+        auto it = p->tuned.find(tune_key(p, geos));
+        if (it != p->tuned.end() && tune_ok(p, it->second, Wmax)) tu = it->second;
+    }
+    Launch L = make_launch(p, c.lc, td, n_rt, tu.edt_rb);
     if ((rc = upload_desc(L, td, cs))) return rc;
     {
         std::string key;
         for (int i = 0; i < n; i++)
             key += std::to_string(tiles[i].W) + "x" + std::to_string(tiles[i].H) + (tiles[i].want_planes ? "p;" : ";");
-        rc = run_path_graph(p, c.graphs, key, L, Wmax, *std::max_element(caps.begin(), caps.end()), cs,
+        rc = run_path_graph(p, c.graphs, key, L, Wmax, *std::max_element(caps.begin(), caps.end()), tu, cs,
                             &p->serve_prof.launches);
         if (rc) return rc;
     }

@@ -142,3 +142,34 @@ def test_served_admission_refused_when_slots_full(pipe):
     tk = pipe.submit([t])
     assert tk is not None
     assert wait(pipe, tk)[0]["status"] == 0
+
+
+def test_autotune_keeps_results_and_cache_file_round_trip(tmp_path):
+    """Launch shapes change no result; a second pipe reads the tuned shapes
+    from the cache file instead of tuning again."""
+    import paper_1209_3332_gb300 as P
+    tiles = mixed_tiles()[:3]
+    cache = str(tmp_path / "shapes.txt")
+    a = P.Pipe(0, autotune=1, autotune_cache=cache)
+    got_a = run_batched(a, tiles)
+    info_a = a.autotune_info()
+    assert info_a["tune_runs"] > 0
+    a.close()
+    lines = open(cache).read().splitlines()
+    assert len(lines) == 1 and lines[0].split(" ")[0].endswith("640x480;1024x1024;333x517;")
+    b = P.Pipe(0, autotune=0)
+    got_b = run_batched(b, tiles)
+    assert b.autotune_info()["tune_runs"] == 0
+    b.close()
+    c = P.Pipe(0, autotune=1, autotune_cache=cache)
+    got_c = run_batched(c, tiles)
+    info_c = c.autotune_info()
+    assert info_c["tune_runs"] == 0
+    assert {k: info_c[k] for k in ("recon_workers", "edt_rows", "feat_blocks")} == \
+        {k: info_a[k] for k in ("recon_workers", "edt_rows", "feat_blocks")}
+    assert c.status() == P.PIPE_OK
+    c.close()
+    for x, y, z in zip(got_a, got_b, got_c):
+        for k in ("hem8", "labels", "edt"):
+            assert np.array_equal(x[k], y[k]) and np.array_equal(x[k], z[k]), k
+        assert np.array_equal(x["feats"], y["feats"]) and np.array_equal(x["feats"], z["feats"])
