@@ -62,17 +62,16 @@ constexpr int SCAN_CHUNK = 1024;  // bitmap words per scan chunk
 
 // Shared state of one launch sequence (device memory).
 struct Shared {
-    int head, tail, pending, err;       // reconstruction worklist
+    unsigned long long tp;              // reconstruction worklist: tail << 32 | pending
+    int head, err;                      // worklist head; first device-side error
     int processed;                      // tile processings (diagnostic)
     int nobj;                           // object items of a batched feature pass
-    int pad[2];
 };
 
 struct Launch {
     TileDev* tiles;        // device array [ntiles]
     int ntiles;
-    int* wl_slots;         // [n_rt] queue ring: tile ids
-    int* wl_seq;           // [n_rt] queue ring: slot sequence numbers
+    unsigned long long* wl_slots;  // [n_rt] queue ring: sequence << 32 | item
     int* wl_state;         // [n_rt] per-tile state
     Shared* sh;
     int* tile_status;      // [ntiles]

@@ -44,33 +44,45 @@ __device__ __forceinline__ bool budget_over(long long t0, long long budget) {
 
 // ---- worklist -----------------------------------------------------------------
 // A ticket queue: producers and consumers take indices with atomicAdd (no
-// compare-and-swap retries under contention).  Slot k carries a sequence
-// number: seq == i means "free for producer index i", seq == i+1 means
-// "holds the item of index i"; the consumer of index i hands the slot to
-// producer index i+cap.  A consumer holding a ticket waits until its item
-// arrives or until no tile is queued or running any more.
+// compare-and-swap retries under contention).  Slot k is one 64-bit word,
+// sequence << 32 | item: sequence i means "free for producer index i",
+// i + 1 means "holds the item of index i"; the consumer of index i hands the
+// slot to producer index i + cap.  One word per slot, so an item and its
+// sequence number become visible together.  An item is the image index
+// << ITEM_BITS | the work tile's index within its image.  The tail and the
+// count of queued-or-running tiles (pending) share one 64-bit word, so a push
+// moves both with one atomic.  A consumer holding a ticket waits until its
+// item arrives or until no tile is queued or running any more.
 
-__device__ void wl_push(const Launch& L, int t) {
-    const int cap = L.n_rt;
-    int i = atomicAdd(&L.sh->tail, 1);
-    int k = i % cap;
-    volatile int* seq = (volatile int*)(L.wl_seq + k);
+constexpr int ITEM_BITS = 18;  // work tiles per image <= (16384 / 32)^2 = 2^18
+constexpr unsigned ITEM_MASK = (1u << ITEM_BITS) - 1;
+
+__device__ __forceinline__ unsigned long long ld_vol64(const unsigned long long* p) {
+    return *(const volatile unsigned long long*)p;
+}
+__device__ __forceinline__ void st_vol64(unsigned long long* p, unsigned long long v) {
+    *(volatile unsigned long long*)p = v;
+}
+
+__device__ void wl_push(const Launch& L, unsigned item) {
+    const unsigned cap = (unsigned)L.n_rt;
+    const unsigned i = (unsigned)(atomicAdd(&L.sh->tp, (1ull << 32) | 1ull) >> 32);
+    unsigned long long* slot = L.wl_slots + i % cap;
     long long t0 = clock64();
-    while (*seq != i) {
+    while ((unsigned)(ld_vol64(slot) >> 32) != i) {
         if (budget_over(t0, L.wait_budget)) { atomicCAS(&L.sh->err, 0, ST_TIMEOUT); return; }
         __nanosleep(32);
     }
-    L.wl_slots[k] = t;
-    __threadfence();
-    *seq = i + 1;
+    st_vol64(slot, ((unsigned long long)(i + 1) << 32) | item);
 }
 
-__device__ void wl_request(const Launch& L, int t) {
+// work tile k of image ti, whose first work tile has global index base
+__device__ void wl_request(const Launch& L, int ti, int base, int k) {
+    const int t = base + k;
     for (int it = 0; it < 1024; it++) {
         int s = atomicCAS(&L.wl_state[t], WL_IDLE, WL_QUEUED);
         if (s == WL_IDLE) {
-            atomicAdd(&L.sh->pending, 1);
-            wl_push(L, t);
+            wl_push(L, ((unsigned)ti << ITEM_BITS) | (unsigned)k);
             return;
         }
         if (s == WL_QUEUED || s == WL_DIRTY) return;
@@ -79,22 +91,21 @@ __device__ void wl_request(const Launch& L, int t) {
     atomicCAS(&L.sh->err, 0, ST_TIMEOUT);
 }
 
-// returns a tile id, or -1 when the queue is drained (or on error)
-__device__ int wl_pop(const Launch& L) {
-    const int cap = L.n_rt;
-    int h = atomicAdd(&L.sh->head, 1);
-    int k = h % cap;
-    volatile int* seq = (volatile int*)(L.wl_seq + k);
+// takes the next item; false when the queue is drained (or on error)
+__device__ bool wl_pop(const Launch& L, unsigned* item) {
+    const unsigned cap = (unsigned)L.n_rt;
+    const unsigned h = (unsigned)atomicAdd(&L.sh->head, 1);
+    unsigned long long* slot = L.wl_slots + h % cap;
     long long t0 = clock64();
     for (;;) {
-        if (*seq == h + 1) {
-            __threadfence();
-            int v = *(volatile int*)(L.wl_slots + k);
-            *seq = h + cap;
-            return v;
+        const unsigned long long v = ld_vol64(slot);
+        if ((unsigned)(v >> 32) == h + 1) {
+            st_vol64(slot, (unsigned long long)(h + cap) << 32);
+            *item = (unsigned)v;
+            return true;
         }
-        if (ld_vol(&L.sh->pending) == 0 || ld_vol(&L.sh->err)) return -1;
-        if (budget_over(t0, L.wait_budget)) { atomicCAS(&L.sh->err, 0, ST_TIMEOUT); return -1; }
+        if ((unsigned)ld_vol64(&L.sh->tp) == 0u || ld_vol(&L.sh->err)) return false;
+        if (budget_over(t0, L.wait_budget)) { atomicCAS(&L.sh->err, 0, ST_TIMEOUT); return false; }
         __nanosleep(64);
     }
 }
@@ -106,8 +117,7 @@ __global__ void k_wl_init(Launch L) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i == 0) {
         L.sh->head = 0;
-        L.sh->tail = L.n_rt;
-        L.sh->pending = L.n_rt;
+        L.sh->tp = ((unsigned long long)(unsigned)L.n_rt << 32) | (unsigned)L.n_rt;
         L.sh->err = 0;
         L.sh->processed = 0;
     }
@@ -120,8 +130,7 @@ __global__ void k_wl_init(Launch L) {
     int before = ((ty + 1) / 2) * ((rx + 1) / 2) + (ty / 2) * (rx / 2);  // evens in rows < ty
     before += (ty & 1) ? tx / 2 : (tx + 1) / 2;                       // evens in row ty, x < tx
     int pos = T.rt_base + (((tx + ty) & 1) ? evens + (k - before) : before);
-    L.wl_slots[pos] = i;
-    L.wl_seq[pos] = pos + 1;
+    L.wl_slots[pos] = ((unsigned long long)(unsigned)(pos + 1) << 32) | (((unsigned)ti << ITEM_BITS) | (unsigned)k);
     L.wl_state[i] = WL_QUEUED;
 }
 
@@ -146,8 +155,20 @@ __device__ __forceinline__ uint8_t& halo_ref(WarpTile& S, int q, int lane, bool 
 #undef AX
 }
 
-__device__ __forceinline__ void load_tile(WarpTile& S, const TileDev& T, int x0, int y0, int lane) {
-    const int W = T.W, H = T.H;
+// R of the halo pixels of this lane (see halo_coord), 0 outside the image
+__device__ __forceinline__ void load_halo(uint8_t hr[5], const uint8_t* Rg, int W, int H, int x0, int y0,
+                                          int lane) {
+#pragma unroll
+    for (int q = 0; q < 5; q++) {
+        int gy, gx;
+        halo_coord(q, lane, x0, y0, gy, gx);
+        bool in = gy >= 0 && gy < H && gx >= 0 && gx < W && (q < 4 || lane < 4);
+        hr[q] = in ? __ldcg(Rg + (size_t)gy * W + gx) : (uint8_t)0;
+    }
+}
+
+__device__ __forceinline__ void load_tile(WarpTile& S, const uint8_t* Rg, const uint8_t* Mg, int W, int H,
+                                          int x0, int y0, int lane) {
     uint8_t hr[5], hm[5];
 #pragma unroll
     for (int q = 0; q < 5; q++) {
@@ -155,8 +176,8 @@ __device__ __forceinline__ void load_tile(WarpTile& S, const TileDev& T, int x0,
         halo_coord(q, lane, x0, y0, gy, gx);
         bool in = gy >= 0 && gy < H && gx >= 0 && gx < W && (q < 4 || lane < 4);
         size_t o = (size_t)gy * W + gx;
-        hr[q] = in ? __ldcg(T.R + o) : (uint8_t)0;
-        hm[q] = in ? __ldg(T.hem8 + o) : (uint8_t)0;
+        hr[q] = in ? __ldcg(Rg + o) : (uint8_t)0;
+        hm[q] = in ? __ldg(Mg + o) : (uint8_t)0;
     }
     if ((W & 3) == 0 && x0 + RT <= W) {
         // interior: 8 lanes x 4 bytes per row, 4 rows per step, all loads issued first
@@ -167,8 +188,8 @@ __device__ __forceinline__ void load_tile(WarpTile& S, const TileDev& T, int x0,
             int gy = y0 + j * 4 + r4;
             bool in = gy < H;
             size_t o = (size_t)gy * W + x0 + c4;
-            rv[j] = in ? __ldcg(reinterpret_cast<const unsigned int*>(T.R + o)) : 0u;
-            mv[j] = in ? __ldg(reinterpret_cast<const unsigned int*>(T.hem8 + o)) : 0u;
+            rv[j] = in ? __ldcg(reinterpret_cast<const unsigned int*>(Rg + o)) : 0u;
+            mv[j] = in ? __ldg(reinterpret_cast<const unsigned int*>(Mg + o)) : 0u;
         }
 #pragma unroll
         for (int j = 0; j < RT / 4; j++) {
@@ -181,8 +202,8 @@ __device__ __forceinline__ void load_tile(WarpTile& S, const TileDev& T, int x0,
             int gy = y0 + yy, gx = x0 + lane;
             bool in = gy < H && gx < W;
             size_t o = (size_t)gy * W + gx;
-            SR(yy, lane) = in ? __ldcg(T.R + o) : (uint8_t)0;
-            SM(yy, lane) = in ? __ldg(T.hem8 + o) : (uint8_t)0;
+            SR(yy, lane) = in ? __ldcg(Rg + o) : (uint8_t)0;
+            SM(yy, lane) = in ? __ldg(Mg + o) : (uint8_t)0;
         }
     }
 #pragma unroll
@@ -192,6 +213,42 @@ __device__ __forceinline__ void load_tile(WarpTile& S, const TileDev& T, int x0,
         halo_ref(S, q, lane, true) = hm[q];
     }
     __syncwarp();
+}
+
+// Writes the tile's R back: 4-byte stores where rows are word aligned.
+__device__ __forceinline__ void store_tile(WarpTile& S, uint8_t* Rg, int W, int H, int x0, int y0, int lane) {
+    if ((W & 3) == 0 && x0 + RT <= W) {
+        const int r4 = lane >> 3, c4 = (lane & 7) * 4;
+#pragma unroll
+        for (int j = 0; j < RT / 4; j++) {
+            int yy = j * 4 + r4, gy = y0 + yy;
+            if (gy < H)
+                __stcg(reinterpret_cast<unsigned int*>(Rg + (size_t)gy * W + x0 + c4),
+                       *reinterpret_cast<const uint32_t*>(&SR(yy, c4)));
+        }
+    } else {
+        const int gx = x0 + lane;
+        for (int y = 0; y < RT; y++) {
+            int gy = y0 + y;
+            if (gy < H && gx < W) __stcg(Rg + (size_t)gy * W + gx, SR(y, lane));
+        }
+    }
+}
+
+// Raises the staged halo to the values just read; true if any grew.
+__device__ __forceinline__ bool merge_halo(WarpTile& S, const uint8_t hr[5], int lane) {
+    bool grew = false;
+#pragma unroll
+    for (int q = 0; q < 5; q++) {
+        if (q == 4 && lane >= 4) continue;
+        uint8_t& h = halo_ref(S, q, lane, false);
+        if (hr[q] > h) {
+            h = hr[q];
+            grew = true;
+        }
+    }
+    __syncwarp();
+    return __any_sync(FULL, grew);
 }
 
 // One round of the four sweeps.
@@ -277,53 +334,48 @@ __global__ void __launch_bounds__(RT_WARPS * 32, RECON_MIN_BLOCKS) k_recon(Launc
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     WarpTile& S = reinterpret_cast<WarpTile*>(smraw)[warp];
     for (;;) {
-        int t = 0;
-        if (lane == 0) t = wl_pop(L);
-        t = __shfl_sync(FULL, t, 0);
-        if (t < 0) break;
-        const int ti = find_tile(L.tiles, L.ntiles, t, &TileDev::rt_base);
+        unsigned item = 0;
+        int ok = 0;
+        if (lane == 0) ok = wl_pop(L, &item) ? 1 : 0;
+        ok = __shfl_sync(FULL, ok, 0);
+        if (!ok) break;
+        item = __shfl_sync(FULL, item, 0);
+        const int ti = (int)(item >> ITEM_BITS), k = (int)(item & ITEM_MASK);
         const TileDev& T = L.tiles[ti];
-        const int k = t - T.rt_base, ty = k / T.rtx, tx = k - ty * T.rtx;
+        const int W = T.W, H = T.H, rx = T.rtx, ry = T.rty, base = T.rt_base;
+        uint8_t* const Rg = T.R;
+        const uint8_t* const Mg = T.hem8;
+        const int t = base + k, ty = k / rx, tx = k - ty * rx;
         const int x0 = tx * RT, y0 = ty * RT;
-        if (lane == 0) atomicExch(&L.wl_state[t], WL_RUNNING);
+        if (lane == 0) {
+            atomicExch(&L.wl_state[t], WL_RUNNING);
+            atomicAdd(&L.sh->processed, 1);
+        }
         __threadfence();
         __syncwarp();
+        load_tile(S, Rg, Mg, W, H, x0, y0, lane);
+        // border values as last written (or as loaded): a request is due
+        // only for border pixels changed since
+        int top0 = SR(0, lane), bot0 = SR(RT - 1, lane);
+        int lef0 = SR(lane, 0), rig0 = SR(lane, RT - 1);
         for (;;) {
-            load_tile(S, T, x0, y0, lane);
-            const int top0 = SR(0, lane), bot0 = SR(RT - 1, lane);
-            const int lef0 = SR(lane, 0), rig0 = SR(lane, RT - 1);
-            bool any = false, more = false;
-            for (int round = 0; can_raise(S, lane); round++) {
-                if (round >= MAX_ROUNDS) { more = true; break; }
+            int nr = 0;
+            bool more = false;
+            while (can_raise(S, lane)) {
+                if (nr >= MAX_ROUNDS) { more = true; break; }
                 sweep_round(S, lane);
-                any = true;
+                nr++;
             }
-            if (lane == 0) atomicAdd(&L.sh->processed, 1);
-            if (any) {
-                const int gx = x0 + lane;
-                for (int y = 0; y < RT; y++) {
-                    int gy = y0 + y;
-                    if (gy < T.H && gx < T.W) __stcg(T.R + (size_t)gy * T.W + gx, SR(y, lane));
-                }
-                __threadfence();
-                // judge the neighbours against the halo as it is now: values only
-                // grow, so a fresh read can only remove needless requests
+            bool grew = false;
+            if (nr > 0) {
+                // the halo read only decides which neighbours to queue; it is
+                // issued before the write-back so that the two overlap (a stale
+                // value can only cause a needless request)
                 uint8_t hr[5];
-#pragma unroll
-                for (int q = 0; q < 5; q++) {
-                    int gy, hx;
-                    halo_coord(q, lane, x0, y0, gy, hx);
-                    bool in = gy >= 0 && gy < T.H && hx >= 0 && hx < T.W && (q < 4 || lane < 4);
-                    hr[q] = in ? __ldcg(T.R + (size_t)gy * T.W + hx) : (uint8_t)0;
-                }
-                __syncwarp();
-#pragma unroll
-                for (int q = 0; q < 5; q++) {
-                    if (q == 4 && lane >= 4) continue;
-                    uint8_t& h = halo_ref(S, q, lane, false);
-                    h = max(h, hr[q]);
-                }
-                __syncwarp();
+                load_halo(hr, Rg, W, H, x0, y0, lane);
+                store_tile(S, Rg, W, H, x0, y0, lane);
+                __threadfence();  // this tile's pixels before any request
+                grew = merge_halo(S, hr, lane);
                 const int top = SR(0, lane), bot = SR(RT - 1, lane);
                 const int lef = SR(lane, 0), rig = SR(lane, RT - 1);
                 const bool nU = line_need(top, top != top0, SR(-1, lane), SM(-1, lane), lane);
@@ -339,31 +391,39 @@ __global__ void __launch_bounds__(RT_WARPS * 32, RECON_MIN_BLOCKS) k_recon(Launc
                 const bool nDL = (v = SR(RT - 1, 0)) != b00 && min((int)SM(RT, -1), v) > SR(RT, -1);
                 const bool nDR = (v = SR(RT - 1, RT - 1)) != b31 && min((int)SM(RT, RT), v) > SR(RT, RT);
                 // lane j issues request j, so the requests overlap instead of queueing
-                const int base = T.rt_base, rx = T.rtx, ry = T.rty;
                 int target = -1;
                 switch (lane) {
-                    case 0: if (nU && ty > 0) target = base + (ty - 1) * rx + tx; break;
-                    case 1: if (nD && ty + 1 < ry) target = base + (ty + 1) * rx + tx; break;
-                    case 2: if (nL && tx > 0) target = base + ty * rx + tx - 1; break;
-                    case 3: if (nR && tx + 1 < rx) target = base + ty * rx + tx + 1; break;
-                    case 4: if (nUL && ty > 0 && tx > 0) target = base + (ty - 1) * rx + tx - 1; break;
-                    case 5: if (nUR && ty > 0 && tx + 1 < rx) target = base + (ty - 1) * rx + tx + 1; break;
-                    case 6: if (nDL && ty + 1 < ry && tx > 0) target = base + (ty + 1) * rx + tx - 1; break;
-                    case 7: if (nDR && ty + 1 < ry && tx + 1 < rx) target = base + (ty + 1) * rx + tx + 1; break;
-                    case 8: if (more) target = t; break;  // not converged within MAX_ROUNDS: run again
+                    case 0: if (nU && ty > 0) target = k - rx; break;
+                    case 1: if (nD && ty + 1 < ry) target = k + rx; break;
+                    case 2: if (nL && tx > 0) target = k - 1; break;
+                    case 3: if (nR && tx + 1 < rx) target = k + 1; break;
+                    case 4: if (nUL && ty > 0 && tx > 0) target = k - rx - 1; break;
+                    case 5: if (nUR && ty > 0 && tx + 1 < rx) target = k - rx + 1; break;
+                    case 6: if (nDL && ty + 1 < ry && tx > 0) target = k + rx - 1; break;
+                    case 7: if (nDR && ty + 1 < ry && tx + 1 < rx) target = k + rx + 1; break;
+                    case 8: if (more) target = k; break;  // not converged within MAX_ROUNDS: run again
                     default: break;
                 }
-                if (target >= 0) wl_request(L, target);
+                if (target >= 0) wl_request(L, ti, base, target);
+                top0 = top;
+                bot0 = bot;
+                lef0 = lef;
+                rig0 = rig;
             }
+            // every lane's requests (and the pending counts they add) come
+            // before this tile stops counting as running
             __syncwarp();
+            if (grew) continue;  // the fresher halo may raise pixels: check again
             int again = 0;
             if (lane == 0) {
                 __threadfence();
-                int s = atomicCAS(&L.wl_state[t], WL_RUNNING, WL_IDLE);
-                if (s == WL_RUNNING) {
-                    atomicSub(&L.sh->pending, 1);
+                int st = atomicCAS(&L.wl_state[t], WL_RUNNING, WL_IDLE);
+                if (st == WL_RUNNING) {
+                    atomicAdd(&L.sh->tp, ~0ull);  // pending - 1
                 } else {
+                    // a neighbour raised the halo meanwhile: take the tile again
                     atomicExch(&L.wl_state[t], WL_RUNNING);
+                    atomicAdd(&L.sh->processed, 1);
                     again = 1;
                 }
             }
@@ -371,6 +431,10 @@ __global__ void __launch_bounds__(RT_WARPS * 32, RECON_MIN_BLOCKS) k_recon(Launc
             if (!again) break;
             __threadfence();
             if (ld_vol(&L.sh->err)) break;
+            // only the halo can have changed: the interior belongs to this worker
+            uint8_t hr[5];
+            load_halo(hr, Rg, W, H, x0, y0, lane);
+            merge_halo(S, hr, lane);
         }
     }
 }

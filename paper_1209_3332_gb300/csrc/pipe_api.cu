@@ -341,8 +341,7 @@ Launch make_launch(pipe_t p, LaunchCtx& c, std::vector<TileDev>& td, int n_rt_to
     Launch L{};
     L.tiles = (TileDev*)c.tiles.p;
     L.ntiles = (int)td.size();
-    L.wl_slots = (int*)c.wl.p;
-    L.wl_seq = (int*)c.wl.p + std::max(n_rt_total, 1);
+    L.wl_slots = (unsigned long long*)c.wl.p;
     L.wl_state = (int*)c.wl.p + 2 * std::max(n_rt_total, 1);
     L.sh = (Shared*)c.shared.p;
     L.status = (int*)((char*)c.shared.p + sizeof(Shared));
