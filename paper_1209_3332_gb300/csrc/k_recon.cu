@@ -251,56 +251,58 @@ __device__ __forceinline__ bool merge_halo(WarpTile& S, const uint8_t hr[5], int
     return __any_sync(FULL, grew);
 }
 
-// One round of the four sweeps.
+// One round of the four sweeps.  A sweep step updates one line of the tile
+// (a row, lanes = columns; or a column, lanes = rows) from the three pixels
+// of the line before it, which the previous step stored: each lane reads its
+// two diagonal neighbours from shared memory, where the edge lanes find the
+// halo, so no lane needs a special case.  With R <= M everywhere,
+// max(R, min(m, M)) = min(max(R, m), M).  __syncwarp orders each step's
+// stores before the next step's loads.
 __device__ __forceinline__ void sweep_round(WarpTile& S, int lane) {
     {   // down: row y takes the 3 pixels above it
-        int prev = SR(-1, lane), pl = SR(-1, lane - 1), pr = SR(-1, lane + 1);
+        int prev = SR(-1, lane);
+#pragma unroll
         for (int y = 0; y < RT; y++) {
-            int nv = max((int)SR(y, lane), min(__vimax3_s32(prev, pl, pr), (int)SM(y, lane)));
+            const int a = SR(y - 1, lane - 1), b = SR(y - 1, lane + 1);
+            const int nv = min(max((int)SR(y, lane), __vimax3_s32(prev, a, b)), (int)SM(y, lane));
             SR(y, lane) = (uint8_t)nv;
             prev = nv;
-            int a = __shfl_up_sync(FULL, nv, 1), b = __shfl_down_sync(FULL, nv, 1);
-            pl = lane == 0 ? (int)SR(y, -1) : a;
-            pr = lane == 31 ? (int)SR(y, RT) : b;
+            __syncwarp();
         }
     }
-    __syncwarp();
     {   // up: row y takes the 3 pixels below it
-        int prev = SR(RT, lane), pl = SR(RT, lane - 1), pr = SR(RT, lane + 1);
+        int prev = SR(RT, lane);
+#pragma unroll
         for (int y = RT - 1; y >= 0; y--) {
-            int nv = max((int)SR(y, lane), min(__vimax3_s32(prev, pl, pr), (int)SM(y, lane)));
+            const int a = SR(y + 1, lane - 1), b = SR(y + 1, lane + 1);
+            const int nv = min(max((int)SR(y, lane), __vimax3_s32(prev, a, b)), (int)SM(y, lane));
             SR(y, lane) = (uint8_t)nv;
             prev = nv;
-            int a = __shfl_up_sync(FULL, nv, 1), b = __shfl_down_sync(FULL, nv, 1);
-            pl = lane == 0 ? (int)SR(y, -1) : a;
-            pr = lane == 31 ? (int)SR(y, RT) : b;
+            __syncwarp();
         }
     }
-    __syncwarp();
     {   // right: column x takes the 3 pixels left of it (lane = row)
-        int prev = SR(lane, -1), pu = SR(lane - 1, -1), pd = SR(lane + 1, -1);
+        int prev = SR(lane, -1);
+#pragma unroll
         for (int x = 0; x < RT; x++) {
-            int nv = max((int)SR(lane, x), min(__vimax3_s32(prev, pu, pd), (int)SM(lane, x)));
+            const int a = SR(lane - 1, x - 1), b = SR(lane + 1, x - 1);
+            const int nv = min(max((int)SR(lane, x), __vimax3_s32(prev, a, b)), (int)SM(lane, x));
             SR(lane, x) = (uint8_t)nv;
             prev = nv;
-            int a = __shfl_up_sync(FULL, nv, 1), b = __shfl_down_sync(FULL, nv, 1);
-            pu = lane == 0 ? (int)SR(-1, x) : a;
-            pd = lane == 31 ? (int)SR(RT, x) : b;
+            __syncwarp();
         }
     }
-    __syncwarp();
     {   // left: column x takes the 3 pixels right of it
-        int prev = SR(lane, RT), pu = SR(lane - 1, RT), pd = SR(lane + 1, RT);
+        int prev = SR(lane, RT);
+#pragma unroll
         for (int x = RT - 1; x >= 0; x--) {
-            int nv = max((int)SR(lane, x), min(__vimax3_s32(prev, pu, pd), (int)SM(lane, x)));
+            const int a = SR(lane - 1, x + 1), b = SR(lane + 1, x + 1);
+            const int nv = min(max((int)SR(lane, x), __vimax3_s32(prev, a, b)), (int)SM(lane, x));
             SR(lane, x) = (uint8_t)nv;
             prev = nv;
-            int a = __shfl_up_sync(FULL, nv, 1), b = __shfl_down_sync(FULL, nv, 1);
-            pu = lane == 0 ? (int)SR(-1, x) : a;
-            pd = lane == 31 ? (int)SR(RT, x) : b;
+            __syncwarp();
         }
     }
-    __syncwarp();
 }
 
 // Whether some pixel of the tile can still be raised by one of its 8
