@@ -49,13 +49,16 @@ __device__ __forceinline__ bool budget_over(long long t0, long long budget) {
 // i + 1 means "holds the item of index i"; the consumer of index i hands the
 // slot to producer index i + cap.  One word per slot, so an item and its
 // sequence number become visible together.  An item is the image index
-// << ITEM_BITS | the work tile's index within its image.  The tail and the
+// << ITEM_BITS | the work tile's index within its image, with bit 31 set on
+// the tile's first visit (queued by k_wl_init).  The tail and the
 // count of queued-or-running tiles (pending) share one 64-bit word, so a push
 // moves both with one atomic.  A consumer holding a ticket waits until its
 // item arrives or until no tile is queued or running any more.
 
 constexpr int ITEM_BITS = 18;  // work tiles per image <= (16384 / 32)^2 = 2^18
 constexpr unsigned ITEM_MASK = (1u << ITEM_BITS) - 1;
+constexpr unsigned ITEM_FIRST = 1u << 31;
+constexpr unsigned ITEM_IMAGE_MASK = (1u << (31 - ITEM_BITS)) - 1;  // up to 8192 images
 
 __device__ __forceinline__ unsigned long long ld_vol64(const unsigned long long* p) {
     return *(const volatile unsigned long long*)p;
@@ -130,7 +133,8 @@ __global__ void k_wl_init(Launch L) {
     int before = ((ty + 1) / 2) * ((rx + 1) / 2) + (ty / 2) * (rx / 2);  // evens in rows < ty
     before += (ty & 1) ? tx / 2 : (tx + 1) / 2;                       // evens in row ty, x < tx
     int pos = T.rt_base + (((tx + ty) & 1) ? evens + (k - before) : before);
-    L.wl_slots[pos] = ((unsigned long long)(unsigned)(pos + 1) << 32) | (((unsigned)ti << ITEM_BITS) | (unsigned)k);
+    L.wl_slots[pos] = ((unsigned long long)(unsigned)(pos + 1) << 32) |
+                      (ITEM_FIRST | ((unsigned)ti << ITEM_BITS) | (unsigned)k);
     L.wl_state[i] = WL_QUEUED;
 }
 
@@ -322,6 +326,21 @@ __device__ __forceinline__ bool can_raise(WarpTile& S, int lane) {
     return __any_sync(FULL, v);
 }
 
+// Whether a halo pixel can raise one of the tile's border pixels.  When the
+// interior was at a fixed point before the halo grew, only border pixels
+// can have become raisable, so this is the exact test in that case.
+__device__ __forceinline__ bool border_can_raise(WarpTile& S, int lane) {
+    const int ht = __vimax3_s32(SR(-1, lane - 1), SR(-1, lane), SR(-1, lane + 1));
+    const int hb = __vimax3_s32(SR(RT, lane - 1), SR(RT, lane), SR(RT, lane + 1));
+    const int hl = __vimax3_s32(SR(lane - 1, -1), SR(lane, -1), SR(lane + 1, -1));
+    const int hr = __vimax3_s32(SR(lane - 1, RT), SR(lane, RT), SR(lane + 1, RT));
+    const bool v = min(ht, (int)SM(0, lane)) > (int)SR(0, lane) ||
+                   min(hb, (int)SM(RT - 1, lane)) > (int)SR(RT - 1, lane) ||
+                   min(hl, (int)SM(lane, 0)) > (int)SR(lane, 0) ||
+                   min(hr, (int)SM(lane, RT - 1)) > (int)SR(lane, RT - 1);
+    return __any_sync(FULL, v);
+}
+
 // Whether a changed border line of this tile can raise the facing halo line.
 __device__ __forceinline__ bool line_need(int own, bool changed, int halo_r, int halo_m, int lane) {
     int cv = changed ? own : 0;
@@ -342,7 +361,11 @@ __global__ void __launch_bounds__(RT_WARPS * 32, RECON_MIN_BLOCKS) k_recon(Launc
         ok = __shfl_sync(FULL, ok, 0);
         if (!ok) break;
         item = __shfl_sync(FULL, item, 0);
-        const int ti = (int)(item >> ITEM_BITS), k = (int)(item & ITEM_MASK);
+        const int ti = (int)((item >> ITEM_BITS) & ITEM_IMAGE_MASK), k = (int)(item & ITEM_MASK);
+        // a tile released by a visit was at a fixed point, so on later visits
+        // only its border can have become raisable; its first visit starts
+        // from the marker and sweeps at once
+        bool sweep_now = (item & ITEM_FIRST) != 0, full_check = false;
         const TileDev& T = L.tiles[ti];
         const int W = T.W, H = T.H, rx = T.rtx, ry = T.rty, base = T.rt_base;
         uint8_t* const Rg = T.R;
@@ -363,11 +386,15 @@ __global__ void __launch_bounds__(RT_WARPS * 32, RECON_MIN_BLOCKS) k_recon(Launc
         for (;;) {
             int nr = 0;
             bool more = false;
-            while (can_raise(S, lane)) {
+            bool go = sweep_now || (full_check ? can_raise(S, lane) : border_can_raise(S, lane));
+            sweep_now = false;
+            while (go) {
                 if (nr >= MAX_ROUNDS) { more = true; break; }
                 sweep_round(S, lane);
                 nr++;
+                go = can_raise(S, lane);
             }
+            full_check = more;  // otherwise the interior is at a fixed point now
             bool grew = false;
             if (nr > 0) {
                 // the halo read only decides which neighbours to queue; it is
