@@ -106,8 +106,6 @@ struct Profiler {
 };
 
 void upload_deconv_tables(const int32_t* lut256, const int32_t* wq3);
-// fills the feature pass's constant tables on `device` (current) once; 0 on success
-int features_tables_ready(int device);
 void launch_deconv(const Launch& L, cudaStream_t s, Profiler* pf);
 int recon_grid(int device);
 void launch_recon(const Launch& L, int grid_cap, cudaStream_t s, Profiler* pf);

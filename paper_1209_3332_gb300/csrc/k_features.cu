@@ -12,9 +12,12 @@
 // (warp-aggregated atomics over a single pass of the label plane, or
 // produced directly by the relabel pass in the batched form) lets one CTA
 // own one object and walk only its box.  Pixel sums are integers (exact,
-// order-free); the gradient sums are FP64 in a fixed thread order; the
-// co-occurrence counts are shared-memory histograms.  The FP64 finishing
-// math runs once per object, never per pixel.
+// order-free); the co-occurrence counts are shared-memory histograms.  FP64
+// throughput is scarce on this part (about 2 FMA per cycle per SM), so the
+// finishing math is FP32 arranged so that no step cancels: every
+// co-occurrence statistic is a ratio of exact integers, entropy is a sum of
+// non-negative terms, and the gradient variance is taken on shifted values
+// e = g - c computed as (m2 - c^2) / (g + c) from the exact integer m2.
 #include <cmath>
 #include <mutex>
 
@@ -23,15 +26,6 @@
 namespace nucseg {
 
 constexpr unsigned FULLF = 0xffffffffu;
-
-// c * ln(c) for c < CLNC_N in FP64: a static device table (no allocation),
-// copied from the host once per device by features_tables_ready()
-constexpr int CLNC_N = 4096;
-static __device__ double g_clnc[CLNC_N];
-
-__device__ __forceinline__ double clnc(int c) {
-    return c < CLNC_N ? g_clnc[c] : (double)c * log((double)c);
-}
 
 __global__ void k_fbbox_init(int4* bbox, int K) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -114,15 +108,14 @@ __device__ __forceinline__ T warp_sum(T v) {
     return v;
 }
 
-// |Sobel| as a double: sqrtf (correctly rounded) refined by one Newton step
-// in FP64, s + (m2 - s^2) / (2 s), whose residual m2 - s^2 is exact in FP64;
-// relative error ~1e-14, at two FP64 operations per pixel.
-__device__ __forceinline__ double grad_mag(int m2) {
-    if (m2 == 0) return 0.0;
-    float sf = sqrtf((float)m2);
-    double sd = (double)sf;
-    double r = fma(-sd, sd, (double)m2);
-    return sd + (double)((float)r * (0.5f / sf));
+// g - c for the gradient magnitude g = sqrt(m2) and a shift c close to the
+// object's mean magnitude, with c^2 = c2h + c2l exactly: the numerator
+// m2 - c^2 is formed from exact terms, so the result carries a few ulps of
+// its own size however close g is to c.
+__device__ __forceinline__ float shifted_mag(int m2, float c, float c2h, float c2l) {
+    const float g = sqrtf((float)m2);
+    if (c == 0.f) return g;
+    return __fdiv_rn(__fsub_rn(__fsub_rn((float)m2, c2h), c2l), __fadd_rn(g, c));
 }
 
 constexpr int STAGE_PX = 5120;  // staged region (box + 1-px margin) capacity per warp
@@ -179,7 +172,7 @@ __device__ __forceinline__ void object_features_impl(const ObjJob& J, int obj, i
     };
     int cnt = 0, per = 0, mn = 255, mx = 0, gmn = 0x7fffffff, gmx = 0;
     long long S = 0, Q = 0;
-    double gs = 0.0;
+    float gs = 0.f;
     const int odx[4] = {1, 0, 1, 1}, ody[4] = {0, 1, 1, -1};
     // lane walks the box row-major with stride 32, advancing (y, x) without divisions
     int y = box.y + lane / bw, x = box.x + lane % bw;
@@ -199,7 +192,7 @@ __device__ __forceinline__ void object_features_impl(const ObjJob& J, int obj, i
         per += (cx == 0 || !IN(cy, cx - 1));
         per += (cx == W - 1 || !IN(cy, cx + 1));
         const int m2 = SOBEL(cy, cx);
-        gs += grad_mag(m2);
+        gs = __fadd_rn(gs, sqrtf((float)m2));
         gmn = min(gmn, m2);
         gmx = max(gmx, m2);
 #pragma unroll
@@ -215,14 +208,18 @@ __device__ __forceinline__ void object_features_impl(const ObjJob& J, int obj, i
     const long long Per = warp_sum<long long>(per);
     const int Mn = __reduce_min_sync(FULLF, mn), Mx = __reduce_max_sync(FULLF, mx);
     const int Gmn = __reduce_min_sync(FULLF, gmn), Gmx = __reduce_max_sync(FULLF, gmx);
-    const double Gs = warp_sum<double>(gs);
+    const float Gs = warp_sum<float>(gs);
     if (N == 0) {
         if (lane < NFEAT) out[lane] = 0.f;
         __syncwarp();
         return;
     }
-    const double gmean = Gs / (double)N;
-    double gss = 0.0;
+    // second pass: the magnitudes shifted by their approximate mean c; the mean
+    // is c + E[e] and the variance E[e^2] - E[e]^2, where E[e] is tiny, so
+    // nothing cancels
+    const float c = __fdiv_rn(Gs, (float)N);
+    const float c2h = c * c, c2l = fmaf(c, c, -c2h);
+    float se = 0.f, see = 0.f;
     y = box.y + lane / bw;
     x = box.x + lane % bw;
     for (long long idx = lane; idx < npx; idx += 32) {
@@ -230,26 +227,31 @@ __device__ __forceinline__ void object_features_impl(const ObjJob& J, int obj, i
         x += 32;
         while (x > box.z) { x -= bw; y++; }
         if (!IN(cy, cx)) continue;
-        const double d = grad_mag(SOBEL(cy, cx)) - gmean;
-        gss += d * d;
+        const float e = shifted_mag(SOBEL(cy, cx), c, c2h, c2l);
+        se = __fadd_rn(se, e);
+        see = fmaf(e, e, see);
     }
-    const double Gss = warp_sum<double>(gss);
+    const double Se = warp_sum<double>((double)se), See = warp_sum<double>((double)see);
     __syncwarp();
     // co-occurrence statistics per offset: lanes hold bins lane and lane+32.
     // With counts C_ij and T = sum C_ij: contrast = sum (i-j)^2 C / T, energy =
     // sum C^2 / T^2, homogeneity = sum C/(1+(i-j)^2) / T (integer numerator over
-    // the common multiple 408850 of the denominators 1+(i-j)^2), entropy =
-    // ln T - sum C ln C / T, correlation from integer moments.  Only a few
-    // FP64 operations per offset remain (the GPU's FP64 rate is low).
-    double acc[5] = {0, 0, 0, 0, 0};
+    // the common multiple 408850 of the denominators 1+(i-j)^2), correlation
+    // from exact integer moments, each one FP32 division of exact integers;
+    // entropy = sum (C/T) ln(T/C) with ln(T/C) = log1p((T-C)/C), a sum of
+    // non-negative terms, equal to ln T - sum C ln C / T.
+    float acc[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
     int used = 0;
     const int i0 = lane >> 3, j0 = lane & 7, i1 = i0 + 4, j1 = j0;
     const int d0 = (i0 - j0) * (i0 - j0), d1 = (i1 - j1) * (i1 - j1);
     const long long HL = 408850;  // lcm of 1+d^2 for d = 0..7
+    auto ent = [](long long C, long long T) -> float {
+        return C > 0 ? __fmul_rn(__fdiv_rn((float)C, (float)T), log1pf(__fdiv_rn((float)(T - C), (float)C))) : 0.f;
+    };
 #pragma unroll
     for (int o = 0; o < 4; o++) {
-        const int* c = glcm + o * 64;
-        const long long v0 = c[lane], v1 = c[lane + 32];
+        const int* cc = glcm + o * 64;
+        const long long v0 = cc[lane], v1 = cc[lane + 32];
         const long long T = warp_sum<long long>(v0 + v1);
         if (T == 0) continue;
         used++;
@@ -261,14 +263,15 @@ __device__ __forceinline__ void object_features_impl(const ObjJob& J, int obj, i
         const long long scon = warp_sum<long long>(d0 * v0 + d1 * v1);
         const long long sene = warp_sum<long long>(v0 * v0 + v1 * v1);
         const long long shom = warp_sum<long long>((HL / (1 + d0)) * v0 + (HL / (1 + d1)) * v1);
-        const double sent = warp_sum<double>(clnc((int)v0) + clnc((int)v1));
-        const double Td = (double)T;
+        const float sent = warp_sum<float>(__fadd_rn(ent(v0, T), ent(v1, T)));
+        const float Tf = (float)T;
         const long long vi = T * sii - si * si, vj = T * sjj - sj * sj, cv = T * sij - si * sj;
-        acc[0] += (double)scon / Td;
-        acc[1] += (double)sene / (Td * Td);
-        acc[2] += (double)shom / ((double)HL * Td);
-        acc[3] += log(Td) - sent / Td;
-        acc[4] += (vi == 0 || vj == 0) ? 0.0 : (double)cv / sqrt((double)vi * (double)vj);
+        acc[0] = __fadd_rn(acc[0], __fdiv_rn((float)scon, Tf));
+        acc[1] = __fadd_rn(acc[1], __fdiv_rn((float)sene, __fmul_rn(Tf, Tf)));
+        acc[2] = __fadd_rn(acc[2], __fdiv_rn((float)shom, __fmul_rn((float)HL, Tf)));
+        acc[3] = __fadd_rn(acc[3], sent);
+        acc[4] = __fadd_rn(acc[4], (vi == 0 || vj == 0) ? 0.f
+                                   : __fdiv_rn((float)cv, sqrtf(__fmul_rn((float)vi, (float)vj))));
     }
     if (lane == 0) {
         const double n = (double)N;
@@ -280,11 +283,12 @@ __device__ __forceinline__ void object_features_impl(const ObjJob& J, int obj, i
         f[3] = sqrt((double)var_num) / n;
         f[4] = Mn;
         f[5] = Mx;
-        f[6] = gmean;
-        f[7] = sqrt(Gss / n);
+        const double me = __ddiv_rn(Se, n);
+        f[6] = __dadd_rn((double)c, me);
+        f[7] = sqrt(fmax(__dsub_rn(__ddiv_rn(See, n), __dmul_rn(me, me)), 0.0));
         f[8] = sqrt((double)Gmn);
         f[9] = sqrt((double)Gmx);
-        for (int k = 0; k < 5; k++) f[10 + k] = used ? acc[k] / used : 0.0;
+        for (int k = 0; k < 5; k++) f[10 + k] = used ? __fdiv_rn(acc[k], (float)used) : 0.f;
         for (int k = 0; k < NFEAT; k++) out[k] = (float)f[k];
     }
     __syncwarp();
@@ -351,19 +355,6 @@ __global__ void __launch_bounds__(FW * 32) k_fobj_batched(Launch L) {
         ObjJob J{T.hem8, T.labels, T.W, T.H, T.bbox, T.feats};
         object_features(J, item - T.obj_base, S.glcm, S.mask, S.hem);
     }
-}
-
-int features_tables_ready(int device) {
-    static std::mutex mu;
-    static bool done[64] = {false};
-    if (device < 0 || device >= 64) return 1;
-    std::lock_guard<std::mutex> lk(mu);
-    if (done[device]) return 0;
-    static double tab[CLNC_N];
-    for (int c = 0; c < CLNC_N; c++) tab[c] = c > 0 ? (double)c * std::log((double)c) : 0.0;
-    if (cudaMemcpyToSymbol(g_clnc, tab, sizeof(tab)) != cudaSuccess) return 1;
-    done[device] = true;
-    return 0;
 }
 
 void launch_features_plain(const uint8_t* hem8, const int32_t* labels, int W, int H, int K, float* feats,

@@ -35,7 +35,6 @@ int setup(int dev, int4** addr, int* sms) {
         if (cudaGetSymbolAddress(&p, g_noalloc_bbox) != cudaSuccess || !p) return PIPE_ECUDA;
         int n = 0;
         if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return PIPE_ECUDA;
-        if (features_tables_ready(dev) != 0) return PIPE_ECUDA;
         g_sms[dev] = n;
         g_addr[dev] = static_cast<int4*>(p);
     }

@@ -642,10 +642,6 @@ int pipe_create(const pipe_params* params, int device, pipe_t* out) {
     int32_t lut[256], wq[3];
     deconv_tables(lut, wq);
     upload_deconv_tables(lut, wq);
-    if (features_tables_ready(device) != 0) {
-        delete p;
-        return PIPE_ECUDA;
-    }
     p->recon_cap = std::max(1, recon_grid(device));
     if (prm.autotune_cache) {
         p->tune_file = prm.autotune_cache;

@@ -110,3 +110,12 @@ def assert_matches_digest(got, ref, rgb=None, what=""):
                 assert_planes_equal(got, oracle_all(rgb), planes=(k,))
             raise AssertionError("%s: plane %s differs from the oracle" % (what, k))
     assert_feats_close(got["feats"], ref["feats"])
+
+
+def assert_same_feats(a, b, what=""):
+    """Bit-identical feature rows (two forms of the CUDA path)."""
+    assert a.shape == b.shape, (what, a.shape, b.shape)
+    if not np.array_equal(a, b):
+        bad = np.argwhere(a != b)
+        i, j = bad[0]
+        raise AssertionError("%s feature [%d][%d]: %r vs %r (%d differ)" % (what, i, j, a[i, j], b[i, j], len(bad)))

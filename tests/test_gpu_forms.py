@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 import synth
-from tests.gpu_util import assert_feats_close, assert_planes_equal, oracle_all, run_gpu
+from tests.gpu_util import assert_feats_close, assert_planes_equal, assert_same_feats, oracle_all, run_gpu
 
 pytestmark = pytest.mark.gpu
 
@@ -62,7 +62,7 @@ def test_batched_equals_plain_and_oracle(pipe):
     for t, g in zip(tiles, got):
         alone = run_gpu(pipe, t, want_planes=False)
         assert_planes_equal(g, alone, planes=("hem8", "labels", "edt"))
-        assert np.array_equal(g["feats"], alone["feats"])
+        assert_same_feats(g["feats"], alone["feats"], "batched vs plain")
         r = oracle_all(t)
         assert_planes_equal(g, r, planes=("hem8", "labels", "edt"))
         assert_feats_close(g["feats"], r["feats"])
@@ -75,7 +75,7 @@ def test_batched_graph_replay_and_shape_change(pipe):
     c = run_batched(pipe, tiles[::-1])    # another shape -> another graph
     for x, y in zip(a, b):
         assert_planes_equal(x, y, planes=("hem8", "labels", "edt"))
-        assert np.array_equal(x["feats"], y["feats"])
+        assert_same_feats(x["feats"], y["feats"], "graph replay")
     for x, y in zip(a, c[::-1]):
         assert_planes_equal(x, y, planes=("hem8", "labels", "edt"))
 
@@ -120,7 +120,7 @@ def test_served_alone_and_in_the_mix(pipe):
         for k in ("hem8", "labels", "edt"):
             assert np.array_equal(a[k], m[k]), k
         assert a["n_objects"] == m["n_objects"]
-        assert np.array_equal(a["feats"], m["feats"])
+        assert_same_feats(a["feats"], m["feats"], "served alone vs mix")
         r = oracle_all(t)
         assert a["n_objects"] == r["K"]
         for k in ("hem8", "labels", "edt"):
