@@ -15,7 +15,10 @@
 //    kernel unions facing edge pixels in P with atomicMin links, so global
 //    roots are again component-first pixels;
 //  * later kernels recompute the local labelling from the 2 MB bitmaps
-//    instead of storing a full plane of provisional labels.
+//    instead of storing a full plane of provisional labels;
+//  * a warp's only large shared array is its 1024-entry union-find table
+//    (4 KB), whose root entries also carry a component's payload in bits
+//    16 and up, so that 14 CTAs of 4 warps fit on an SM.
 // Fill holes labels the background with 4-connectivity (dual of the 8-conn
 // foreground) and marks components that touch the image border; every
 // background pixel of an unmarked component is a hole.  Labelling then
@@ -162,9 +165,27 @@ __device__ __forceinline__ uint32_t run_mask(uint32_t w, int s) {
 struct WarpGeo {
     int ti, bx, by, x0, y0, bw, bh, lb;
 };
-__device__ __forceinline__ WarpGeo warp_geo(const Launch& L, int gb) {
+
+// Each CTA copies the first labelling-block index of up to TILE_TAB tiles
+// into shared memory once, so the per-warp tile search reads shared memory.
+constexpr int TILE_TAB = 64;
+__device__ __forceinline__ void load_tile_tab(const Launch& L, int* tab) {
+    for (int i = threadIdx.x; i < min(L.ntiles, TILE_TAB); i += blockDim.x) tab[i] = L.tiles[i].cb_base;
+    __syncthreads();
+}
+__device__ __forceinline__ int tile_of_block(const Launch& L, const int* tab, int gb) {
+    if (L.ntiles > TILE_TAB) return find_tile(L.tiles, L.ntiles, gb, &TileDev::cb_base);
+    int lo = 0, hi = L.ntiles - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (tab[mid] <= gb) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ WarpGeo warp_geo(const Launch& L, const int* tab, int gb) {
     WarpGeo g;
-    g.ti = find_tile(L.tiles, L.ntiles, gb, &TileDev::cb_base);
+    g.ti = tile_of_block(L, tab, gb);
     const TileDev& T = L.tiles[g.ti];
     g.lb = gb - T.cb_base;
     g.by = g.lb / T.cbx;
@@ -180,29 +201,35 @@ __device__ __forceinline__ int gidx(const TileDev& T, const WarpGeo& g, int li) 
     return (g.y0 + (li >> 5)) * T.W + g.x0 + (li & 31);
 }
 
+// A union-find entry: the local root index in bits 0..9; a root's own entry
+// may carry its component's payload in bits 16 and up.
+constexpr int PAR_IDX = 0x3ff;
+__device__ __forceinline__ int par_root(const int* par, int i) { return par[i] & PAR_IDX; }
+
 // Edge roots: [0,CB) left column, [CB,2CB) right column (x=31), [2CB,3CB)
 // top row, [3CB,4CB) bottom row (y=31); -1 where the pixel is not in the class.
 __device__ __forceinline__ void publish_edges(const TileDev& T, const WarpGeo& g, uint32_t w, uint32_t st,
                                               const int* par, int lane) {
     int* e = T.border + (size_t)g.lb * 4 * CB;
-    e[lane] = (w & 1u) ? gidx(T, g, par[lane * CB]) : -1;
-    e[CB + lane] = (w >> 31) ? gidx(T, g, par[lane * CB + run_start(st, 31)]) : -1;
+    e[lane] = (w & 1u) ? gidx(T, g, par_root(par, lane * CB)) : -1;
+    e[CB + lane] = (w >> 31) ? gidx(T, g, par_root(par, lane * CB + run_start(st, 31))) : -1;
     uint32_t w0 = __shfl_sync(FULLM, w, 0), s0 = __shfl_sync(FULLM, st, 0);
     uint32_t w31 = __shfl_sync(FULLM, w, 31), s31 = __shfl_sync(FULLM, st, 31);
-    e[2 * CB + lane] = ((w0 >> lane) & 1u) ? gidx(T, g, par[run_start(s0, lane)]) : -1;
-    e[3 * CB + lane] = ((w31 >> lane) & 1u) ? gidx(T, g, par[31 * CB + run_start(s31, lane)]) : -1;
+    e[2 * CB + lane] = ((w0 >> lane) & 1u) ? gidx(T, g, par_root(par, run_start(s0, lane))) : -1;
+    e[3 * CB + lane] = ((w31 >> lane) & 1u) ? gidx(T, g, par_root(par, 31 * CB + run_start(s31, lane))) : -1;
 }
 
 // Record this block's local roots (run starts that are roots) in the block's
 // own slice of the root list (RL_CAP entries: a 32x32 block has at most 512
 // 4-connected and 256 8-connected components) and initialise P/A at their
-// global index with payload pay[root].  No global counter is involved.
+// global index with payload pay(root).  No global counter is involved.
+template <typename Pay>
 __device__ __forceinline__ void register_roots(const TileDev& T, const WarpGeo& g, uint32_t st, const int* par,
-                                               const int* pay, int lane) {
+                                               Pay pay, int lane) {
     uint32_t rs = 0;
     for (uint32_t m = st; m; m &= m - 1) {
         int s = __ffs(m) - 1;
-        if (par[lane * CB + s] == lane * CB + s) rs |= 1u << s;
+        if (par_root(par, lane * CB + s) == lane * CB + s) rs |= 1u << s;
     }
     int n = __popc(rs), incl = n;
 #pragma unroll
@@ -216,25 +243,25 @@ __device__ __forceinline__ void register_roots(const TileDev& T, const WarpGeo& 
         int li = lane * CB + __ffs(m) - 1;
         int gi = gidx(T, g, li);
         T.P[gi] = gi;
-        T.A[gi] = pay[li];
+        T.A[gi] = pay(li);
         list[k++] = gi;
     }
     if (lane == 31) T.blkroots[g.lb] = incl;
 }
 
-struct WarpSmem {
-    int par[CB * CB];
-    int aux[CB * CB];
-};
 
 // ---- K3a: foreground from the h-dome, background local components ---------------
-__global__ void __launch_bounds__(CCL_WARPS * 32) k_fill_local(Launch L) {
-    __shared__ WarpSmem sm[CCL_WARPS];
+__global__ void __launch_bounds__(CCL_WARPS * 32, 14) k_fill_local(Launch L) {
+    __shared__ int par_sm[CCL_WARPS][CB * CB];
+    __shared__ uint32_t touch_sm[CCL_WARPS][32];
+    __shared__ int tab[TILE_TAB];
+    load_tile_tab(L, tab);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int gb = blockIdx.x * CCL_WARPS + warp;
     if (gb >= L.n_cb) return;
-    WarpSmem& S = sm[warp];
-    const WarpGeo g = warp_geo(L, gb);
+    int* par = par_sm[warp];
+    uint32_t* touch = touch_sm[warp];
+    const WarpGeo g = warp_geo(L, tab, gb);
     const TileDev& T = L.tiles[g.ti];
     const uint32_t vm = valid_mask(g.bw);
     uint32_t fg = 0;
@@ -265,21 +292,24 @@ __global__ void __launch_bounds__(CCL_WARPS * 32) k_fill_local(Launch L) {
     }
     const uint32_t bg = lane < g.bh ? (~fg & vm) : 0u;
     const uint32_t st = bg & ~(bg << 1);
-    warp_ccl<4>(bg, st, lane, S.par);
-    for (uint32_t m = st; m; m &= m - 1) S.aux[lane * CB + __ffs(m) - 1] = 0;
+    warp_ccl<4>(bg, st, lane, par);
+    touch[lane] = 0u;
     __syncwarp();
-    // a component touching the image border marks its root
+    // a component touching the image border marks its root (one bit per pixel)
     const int gy = g.y0 + lane;
     for (uint32_t m = st; m; m &= m - 1) {
         int s = __ffs(m) - 1;
         uint32_t rm = run_mask(bg, s);
-        bool touch = gy == 0 || gy == T.H - 1 || (g.x0 == 0 && (rm & 1u)) ||
-                     (T.W - 1 - g.x0 < 32 && ((rm >> (T.W - 1 - g.x0)) & 1u));
-        if (touch) S.aux[S.par[lane * CB + s]] = 1;
+        bool tb = gy == 0 || gy == T.H - 1 || (g.x0 == 0 && (rm & 1u)) ||
+                  (T.W - 1 - g.x0 < 32 && ((rm >> (T.W - 1 - g.x0)) & 1u));
+        if (tb) {
+            const int r = par_root(par, lane * CB + s);
+            atomicOr(&touch[r >> 5], 1u << (r & 31));
+        }
     }
     __syncwarp();
-    register_roots(T, g, st, S.par, S.aux, lane);
-    publish_edges(T, g, bg, st, S.par, lane);
+    register_roots(T, g, st, par, [&](int li) { return (int)((touch[li >> 5] >> (li & 31)) & 1u); }, lane);
+    publish_edges(T, g, bg, st, par, lane);
 }
 
 // ---- merge facing edge pixels of neighbouring blocks ------------------------------
@@ -300,10 +330,12 @@ __device__ __forceinline__ void union_dedup(int* P, int a, int b, int lane) {
 
 template <int CONN>
 __global__ void __launch_bounds__(CCL_WARPS * 32) k_merge(Launch L) {
+    __shared__ int tab[TILE_TAB];
+    load_tile_tab(L, tab);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int gb = blockIdx.x * CCL_WARPS + warp;
     if (gb >= L.n_cb) return;
-    const WarpGeo g = warp_geo(L, gb);
+    const WarpGeo g = warp_geo(L, tab, gb);
     const TileDev& T = L.tiles[g.ti];
     const int* e = T.border + (size_t)g.lb * 4 * CB;
     // right column pixel (lane, 31) against the next block(s) to the right
@@ -342,10 +374,12 @@ __global__ void __launch_bounds__(CCL_WARPS * 32) k_merge(Launch L) {
 // mode 2: add local areas into the global root; compress P
 // mode 3: mark kept global roots in the root bitmap
 __global__ void __launch_bounds__(CCL_WARPS * 32) k_roots(Launch L, int mode) {
+    __shared__ int tab[TILE_TAB];
+    load_tile_tab(L, tab);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int gb = blockIdx.x * CCL_WARPS + warp;
     if (gb >= L.n_cb) return;
-    const int ti = find_tile(L.tiles, L.ntiles, gb, &TileDev::cb_base);
+    const int ti = tile_of_block(L, tab, gb);
     const TileDev& T = L.tiles[ti];
     const int lb = gb - T.cb_base;
     const int n = T.blkroots[lb];
@@ -382,25 +416,27 @@ __global__ void __launch_bounds__(CCL_WARPS * 32) k_roots(Launch L, int mode) {
 }
 
 // ---- K4a: holes -> filled; foreground local components ----------------------------
-__global__ void __launch_bounds__(CCL_WARPS * 32) k_label_local(Launch L) {
-    __shared__ WarpSmem sm[CCL_WARPS];
+__global__ void __launch_bounds__(CCL_WARPS * 32, 14) k_label_local(Launch L) {
+    __shared__ int par_sm[CCL_WARPS][CB * CB];
+    __shared__ int tab[TILE_TAB];
+    load_tile_tab(L, tab);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int gb = blockIdx.x * CCL_WARPS + warp;
     if (gb >= L.n_cb) return;
-    WarpSmem& S = sm[warp];
-    const WarpGeo g = warp_geo(L, gb);
+    int* par = par_sm[warp];
+    const WarpGeo g = warp_geo(L, tab, gb);
     const TileDev& T = L.tiles[g.ti];
     const uint32_t vm = valid_mask(g.bw);
     const size_t wrow = (size_t)(g.y0 + lane) * T.wpr + g.bx;
     const uint32_t fg = lane < g.bh ? T.fgbits[wrow] : 0u;
     const uint32_t bg = lane < g.bh ? (~fg & vm) : 0u;
     uint32_t st = bg & ~(bg << 1);
-    warp_ccl<4>(bg, st, lane, S.par);
+    warp_ccl<4>(bg, st, lane, par);
     // background runs whose component does not reach the border are holes
     uint32_t filled = fg;
     for (uint32_t m = st; m; m &= m - 1) {
         int s = __ffs(m) - 1;
-        int gr = gidx(T, g, S.par[lane * CB + s]);
+        int gr = gidx(T, g, par[lane * CB + s]);
         if (!__ldcg(T.A + gr)) filled |= run_mask(bg, s);
     }
     if (lane < g.bh) {
@@ -409,16 +445,15 @@ __global__ void __launch_bounds__(CCL_WARPS * 32) k_label_local(Launch L) {
     }
     __syncwarp();
     st = filled & ~(filled << 1);
-    warp_ccl<8>(filled, st, lane, S.par);
-    for (uint32_t m = st; m; m &= m - 1) S.aux[lane * CB + __ffs(m) - 1] = 0;
-    __syncwarp();
+    warp_ccl<8>(filled, st, lane, par);
+    // local areas: each run adds its length to its root's entry, bits 16 and up
     for (uint32_t m = st; m; m &= m - 1) {
         int s = __ffs(m) - 1;
-        atomicAdd(&S.aux[S.par[lane * CB + s]], __popc(run_mask(filled, s)));
+        atomicAdd(&par[par_root(par, lane * CB + s)], __popc(run_mask(filled, s)) << 16);
     }
     __syncwarp();
-    register_roots(T, g, st, S.par, S.aux, lane);
-    publish_edges(T, g, filled, st, S.par, lane);
+    register_roots(T, g, st, par, [&](int li) { return par[li] >> 16; }, lane);
+    publish_edges(T, g, filled, st, par, lane);
 }
 
 // ---- K4e: exclusive popcount prefix of the root bitmap ----------------------------
@@ -484,54 +519,60 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(Launch L) {
 }
 
 // ---- K4f: final labels, kept bitmap, EDT column summaries, object boxes ----------
-struct RelabelSmem {
-    int par[CB * CB];
-    int lab[CB * (CB + 1)];
-};
-
-__global__ void __launch_bounds__(CCL_WARPS * 32) k_relabel(Launch L, int want_bbox) {
-    __shared__ RelabelSmem sm[CCL_WARPS];
+// After the local labelling each lane overwrites its own run starts' entries
+// with the run's final label (0 if the component was filtered out), then
+// writes its row of labels from registers, four labels per 16-byte store.
+__global__ void __launch_bounds__(CCL_WARPS * 32, 14) k_relabel(Launch L, int want_bbox) {
+    __shared__ int par_sm[CCL_WARPS][CB * CB];
+    __shared__ int tab[TILE_TAB];
+    load_tile_tab(L, tab);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int gb = blockIdx.x * CCL_WARPS + warp;
     if (gb >= L.n_cb) return;
-    RelabelSmem& S = sm[warp];
-    const WarpGeo g = warp_geo(L, gb);
+    int* par = par_sm[warp];
+    const WarpGeo g = warp_geo(L, tab, gb);
     const TileDev& T = L.tiles[g.ti];
     const size_t wrow = (size_t)(g.y0 + lane) * T.wpr + g.bx;
     const uint32_t filled = lane < g.bh ? T.filledbits[wrow] : 0u;
     const uint32_t st = filled & ~(filled << 1);
-    warp_ccl<8>(filled, st, lane, S.par);
-    int* labrow = S.lab + lane * (CB + 1);
-    for (int x = 0; x < CB; x++) labrow[x] = 0;
+    warp_ccl<8>(filled, st, lane, par);
     uint32_t kept = 0;
     const int gy = g.y0 + lane;
     for (uint32_t m = st; m; m &= m - 1) {
         const int s = __ffs(m) - 1;
         const uint32_t rm = run_mask(filled, s);
-        const int gl = gidx(T, g, S.par[lane * CB + s]);
+        const int gl = gidx(T, g, par[lane * CB + s]);
         const int gr = __ldcg(T.P + gl);
         const int yy = gr / T.W, xx = gr - yy * T.W;
         const size_t w = (size_t)yy * T.wpr + (xx >> 5);
         const uint32_t bits = T.rootbits[w];
-        if (!((bits >> (xx & 31)) & 1u)) continue;
-        const int lab = T.wordprefix[w] + __popc(bits & ((1u << (xx & 31)) - 1u)) + 1;
-        kept |= rm;
-        const int e = 31 - __clz(rm);
-        for (int x = s; x <= e; x++) labrow[x] = lab;
-        if (want_bbox && lab <= T.feats_cap) {
-            int4* b = T.bbox + (lab - 1);
-            atomicMin(&b->x, g.x0 + s);
-            atomicMax(&b->z, g.x0 + e);
-            atomicMin(&b->y, gy);
-            atomicMax(&b->w, gy);
+        int lab = 0;
+        if ((bits >> (xx & 31)) & 1u) {
+            lab = T.wordprefix[w] + __popc(bits & ((1u << (xx & 31)) - 1u)) + 1;
+            kept |= rm;
+            if (want_bbox && lab <= T.feats_cap) {
+                const int e = 31 - __clz(rm);
+                int4* b = T.bbox + (lab - 1);
+                atomicMin(&b->x, g.x0 + s);
+                atomicMax(&b->z, g.x0 + e);
+                atomicMin(&b->y, gy);
+                atomicMax(&b->w, gy);
+            }
         }
+        par[lane * CB + s] = lab;  // only this lane reads its run starts from here on
     }
     if (lane < g.bh) T.keptbits[wrow] = kept;
-    __syncwarp();
-    // coalesced label rows: lane = column
-    if (lane < g.bw) {
-        int32_t* dst = T.labels + (size_t)g.y0 * T.W + g.x0 + lane;
-        for (int y = 0; y < g.bh; y++) dst[(size_t)y * T.W] = S.lab[y * (CB + 1) + lane];
+    auto lab_at = [&](int x) -> int { return ((kept >> x) & 1u) ? par[lane * CB + run_start(st, x)] : 0; };
+    if (lane < g.bh) {
+        int32_t* dst = T.labels + (size_t)gy * T.W + g.x0;
+        if (g.bw == CB && (T.W & 3) == 0) {
+#pragma unroll
+            for (int q = 0; q < CB / 4; q++)
+                reinterpret_cast<int4*>(dst)[q] = make_int4(lab_at(4 * q), lab_at(4 * q + 1), lab_at(4 * q + 2),
+                                                             lab_at(4 * q + 3));
+        } else {
+            for (int x = 0; x < g.bw; x++) dst[x] = lab_at(x);
+        }
     }
     // EDT input: this chunk's 32 kept bits of each column, as one word per column
     if (T.edt) {
