@@ -59,6 +59,7 @@ struct TileDev {
 };
 
 constexpr int SCAN_CHUNK = 1024;  // bitmap words per scan chunk
+constexpr int LAUNCH_TAB = 64;    // tiles whose block bases travel in the launch parameters
 
 // Shared state of one launch sequence (device memory).
 struct Shared {
@@ -80,6 +81,9 @@ struct Launch {
     int n_rt, n_cb, n_chunks, n_cols, n_rows, n_px;
     long long wait_budget;
     int h, thr, amin, amax;
+    // first labelling block of each of the first LAUNCH_TAB tiles (kernel
+    // parameters live in the constant bank, so a search over them is cheap)
+    int cb_first[LAUNCH_TAB];
 };
 
 // ---- small device helpers ----------------------------------------------------

@@ -166,27 +166,23 @@ struct WarpGeo {
     int ti, bx, by, x0, y0, bw, bh, lb;
 };
 
-// Each CTA copies the first labelling-block index of up to TILE_TAB tiles
-// into shared memory once, so the per-warp tile search reads shared memory.
-constexpr int TILE_TAB = 64;
-__device__ __forceinline__ void load_tile_tab(const Launch& L, int* tab) {
-    for (int i = threadIdx.x; i < min(L.ntiles, TILE_TAB); i += blockDim.x) tab[i] = L.tiles[i].cb_base;
-    __syncthreads();
-}
-__device__ __forceinline__ int tile_of_block(const Launch& L, const int* tab, int gb) {
-    if (L.ntiles > TILE_TAB) return find_tile(L.tiles, L.ntiles, gb, &TileDev::cb_base);
+// The tile of a labelling block: a search over the first-block indices that
+// travel in the launch parameters (up to LAUNCH_TAB tiles), else over the
+// descriptors in global memory.
+__device__ __forceinline__ int tile_of_block(const Launch& L, int gb) {
+    if (L.ntiles > LAUNCH_TAB) return find_tile(L.tiles, L.ntiles, gb, &TileDev::cb_base);
     int lo = 0, hi = L.ntiles - 1;
     while (lo < hi) {
         int mid = (lo + hi + 1) >> 1;
-        if (tab[mid] <= gb) lo = mid; else hi = mid - 1;
+        if (L.cb_first[mid] <= gb) lo = mid; else hi = mid - 1;
     }
     return lo;
 }
 
-__device__ __forceinline__ WarpGeo warp_geo(const Launch& L, const int* tab, int gb) {
+__device__ __forceinline__ WarpGeo warp_geo(const Launch& L, int gb) {
     WarpGeo g;
-    g.ti = tile_of_block(L, tab, gb);
-    const TileDev& T = L.tiles[g.ti];
+    g.ti = tile_of_block(L, gb);
+    const TileDev T = L.tiles[g.ti];  // by value: stores below cannot force reloads
     g.lb = gb - T.cb_base;
     g.by = g.lb / T.cbx;
     g.bx = g.lb - g.by * T.cbx;
@@ -251,18 +247,16 @@ __device__ __forceinline__ void register_roots(const TileDev& T, const WarpGeo& 
 
 
 // ---- K3a: foreground from the h-dome, background local components ---------------
-__global__ void __launch_bounds__(CCL_WARPS * 32, 14) k_fill_local(Launch L) {
+__global__ void __launch_bounds__(CCL_WARPS * 32, 12) k_fill_local(Launch L) {
     __shared__ int par_sm[CCL_WARPS][CB * CB];
     __shared__ uint32_t touch_sm[CCL_WARPS][32];
-    __shared__ int tab[TILE_TAB];
-    load_tile_tab(L, tab);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int gb = blockIdx.x * CCL_WARPS + warp;
     if (gb >= L.n_cb) return;
     int* par = par_sm[warp];
     uint32_t* touch = touch_sm[warp];
-    const WarpGeo g = warp_geo(L, tab, gb);
-    const TileDev& T = L.tiles[g.ti];
+    const WarpGeo g = warp_geo(L, gb);
+    const TileDev T = L.tiles[g.ti];  // by value: stores below cannot force reloads
     const uint32_t vm = valid_mask(g.bw);
     uint32_t fg = 0;
     if (lane < g.bh) {
@@ -330,13 +324,11 @@ __device__ __forceinline__ void union_dedup(int* P, int a, int b, int lane) {
 
 template <int CONN>
 __global__ void __launch_bounds__(CCL_WARPS * 32) k_merge(Launch L) {
-    __shared__ int tab[TILE_TAB];
-    load_tile_tab(L, tab);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int gb = blockIdx.x * CCL_WARPS + warp;
     if (gb >= L.n_cb) return;
-    const WarpGeo g = warp_geo(L, tab, gb);
-    const TileDev& T = L.tiles[g.ti];
+    const WarpGeo g = warp_geo(L, gb);
+    const TileDev T = L.tiles[g.ti];  // by value: stores below cannot force reloads
     const int* e = T.border + (size_t)g.lb * 4 * CB;
     // right column pixel (lane, 31) against the next block(s) to the right
     {
@@ -374,13 +366,11 @@ __global__ void __launch_bounds__(CCL_WARPS * 32) k_merge(Launch L) {
 // mode 2: add local areas into the global root; compress P
 // mode 3: mark kept global roots in the root bitmap
 __global__ void __launch_bounds__(CCL_WARPS * 32) k_roots(Launch L, int mode) {
-    __shared__ int tab[TILE_TAB];
-    load_tile_tab(L, tab);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int gb = blockIdx.x * CCL_WARPS + warp;
     if (gb >= L.n_cb) return;
-    const int ti = tile_of_block(L, tab, gb);
-    const TileDev& T = L.tiles[ti];
+    const int ti = tile_of_block(L, gb);
+    const TileDev T = L.tiles[ti];
     const int lb = gb - T.cb_base;
     const int n = T.blkroots[lb];
     const int* list = T.rootlist + (size_t)lb * RL_CAP;
@@ -416,16 +406,14 @@ __global__ void __launch_bounds__(CCL_WARPS * 32) k_roots(Launch L, int mode) {
 }
 
 // ---- K4a: holes -> filled; foreground local components ----------------------------
-__global__ void __launch_bounds__(CCL_WARPS * 32, 14) k_label_local(Launch L) {
+__global__ void __launch_bounds__(CCL_WARPS * 32, 12) k_label_local(Launch L) {
     __shared__ int par_sm[CCL_WARPS][CB * CB];
-    __shared__ int tab[TILE_TAB];
-    load_tile_tab(L, tab);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int gb = blockIdx.x * CCL_WARPS + warp;
     if (gb >= L.n_cb) return;
     int* par = par_sm[warp];
-    const WarpGeo g = warp_geo(L, tab, gb);
-    const TileDev& T = L.tiles[g.ti];
+    const WarpGeo g = warp_geo(L, gb);
+    const TileDev T = L.tiles[g.ti];  // by value: stores below cannot force reloads
     const uint32_t vm = valid_mask(g.bw);
     const size_t wrow = (size_t)(g.y0 + lane) * T.wpr + g.bx;
     const uint32_t fg = lane < g.bh ? T.fgbits[wrow] : 0u;
@@ -519,36 +507,61 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(Launch L) {
 }
 
 // ---- K4f: final labels, kept bitmap, EDT column summaries, object boxes ----------
-// After the local labelling each lane overwrites its own run starts' entries
-// with the run's final label (0 if the component was filtered out), then
+// The final label is looked up once per local root (global root, root
+// bitmap word, word prefix), and stored in the root's own entry with bit 31
+// set; every run then takes its root's label from shared memory.  Each lane
 // writes its row of labels from registers, four labels per 16-byte store.
-__global__ void __launch_bounds__(CCL_WARPS * 32, 14) k_relabel(Launch L, int want_bbox) {
+constexpr int LAB_FLAG = (int)0x80000000u;
+__global__ void __launch_bounds__(CCL_WARPS * 32, 12) k_relabel(Launch L, int want_bbox) {
     __shared__ int par_sm[CCL_WARPS][CB * CB];
-    __shared__ int tab[TILE_TAB];
-    load_tile_tab(L, tab);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int gb = blockIdx.x * CCL_WARPS + warp;
     if (gb >= L.n_cb) return;
     int* par = par_sm[warp];
-    const WarpGeo g = warp_geo(L, tab, gb);
-    const TileDev& T = L.tiles[g.ti];
+    const WarpGeo g = warp_geo(L, gb);
+    const TileDev T = L.tiles[g.ti];  // by value: stores below cannot force reloads
     const size_t wrow = (size_t)(g.y0 + lane) * T.wpr + g.bx;
     const uint32_t filled = lane < g.bh ? T.filledbits[wrow] : 0u;
     const uint32_t st = filled & ~(filled << 1);
     warp_ccl<8>(filled, st, lane, par);
+    // roots of this lane's row: label (0 if filtered out) into the root's entry
+    uint32_t rs = 0;
+    for (uint32_t m = st; m; m &= m - 1) {
+        const int i = lane * CB + __ffs(m) - 1;
+        if (par[i] == i) rs |= 1u << (i & 31);
+    }
+    uint32_t todo = rs;
+    while (todo) {
+        // up to four roots at a time, so that their lookups overlap
+        int idx[4], gr[4];
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            idx[k] = todo ? lane * CB + __ffs(todo) - 1 : -1;
+            todo &= todo - 1;
+        }
+#pragma unroll
+        for (int k = 0; k < 4; k++) gr[k] = idx[k] >= 0 ? __ldcg(T.P + gidx(T, g, idx[k])) : 0;
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            if (idx[k] < 0) continue;
+            const int yy = gr[k] / T.W, xx = gr[k] - yy * T.W;
+            const size_t w = (size_t)yy * T.wpr + (xx >> 5);
+            const uint32_t bits = T.rootbits[w];
+            const int wp = T.wordprefix[w];  // read unconditionally: both loads overlap
+            const int lab = ((bits >> (xx & 31)) & 1u) ? wp + __popc(bits & ((1u << (xx & 31)) - 1u)) + 1 : 0;
+            par[idx[k]] = lab | LAB_FLAG;
+        }
+    }
+    __syncwarp();
+    // runs: label from the root's entry; kept bits and object boxes
     uint32_t kept = 0;
     const int gy = g.y0 + lane;
     for (uint32_t m = st; m; m &= m - 1) {
         const int s = __ffs(m) - 1;
-        const uint32_t rm = run_mask(filled, s);
-        const int gl = gidx(T, g, par[lane * CB + s]);
-        const int gr = __ldcg(T.P + gl);
-        const int yy = gr / T.W, xx = gr - yy * T.W;
-        const size_t w = (size_t)yy * T.wpr + (xx >> 5);
-        const uint32_t bits = T.rootbits[w];
-        int lab = 0;
-        if ((bits >> (xx & 31)) & 1u) {
-            lab = T.wordprefix[w] + __popc(bits & ((1u << (xx & 31)) - 1u)) + 1;
+        const int v = par[lane * CB + s];
+        const int lab = (v & LAB_FLAG) ? (v & ~LAB_FLAG) : (par[v] & ~LAB_FLAG);
+        if (lab) {
+            const uint32_t rm = run_mask(filled, s);
             kept |= rm;
             if (want_bbox && lab <= T.feats_cap) {
                 const int e = 31 - __clz(rm);
@@ -559,25 +572,40 @@ __global__ void __launch_bounds__(CCL_WARPS * 32, 14) k_relabel(Launch L, int wa
                 atomicMax(&b->w, gy);
             }
         }
-        par[lane * CB + s] = lab;  // only this lane reads its run starts from here on
     }
     if (lane < g.bh) T.keptbits[wrow] = kept;
-    auto lab_at = [&](int x) -> int { return ((kept >> x) & 1u) ? par[lane * CB + run_start(st, x)] : 0; };
+    // label of the run starting at column s of this row
+    auto run_label = [&](int s) -> int {
+        const int v = par[lane * CB + s];
+        return (v & LAB_FLAG) ? (v & ~LAB_FLAG) : (par[v] & ~LAB_FLAG);
+    };
     if (lane < g.bh) {
         int32_t* dst = T.labels + (size_t)gy * T.W + g.x0;
         if (g.bw == CB && (T.W & 3) == 0) {
+            // walk the row once, taking a new label at each run start
+            int cur = 0;
+            int v[4];
 #pragma unroll
-            for (int q = 0; q < CB / 4; q++)
-                reinterpret_cast<int4*>(dst)[q] = make_int4(lab_at(4 * q), lab_at(4 * q + 1), lab_at(4 * q + 2),
-                                                             lab_at(4 * q + 3));
+            for (int x = 0; x < CB; x++) {
+                if ((kept >> x) & (st >> x) & 1u) cur = run_label(x);
+                v[x & 3] = ((kept >> x) & 1u) ? cur : 0;
+                if ((x & 3) == 3) reinterpret_cast<int4*>(dst)[x >> 2] = make_int4(v[0], v[1], v[2], v[3]);
+            }
         } else {
-            for (int x = 0; x < g.bw; x++) dst[x] = lab_at(x);
+            for (int x = 0; x < g.bw; x++) dst[x] = ((kept >> x) & 1u) ? run_label(run_start(st, x)) : 0;
         }
     }
-    // EDT input: this chunk's 32 kept bits of each column, as one word per column
+    // EDT input: this chunk's 32 kept bits of each column, as one word per
+    // column: a 32x32 bit transpose across the lanes in five exchange stages
     if (T.edt) {
-        uint32_t col = 0;
-        for (int y = 0; y < CB; y++) col |= ((__shfl_sync(FULLM, kept, y) >> lane) & 1u) << y;
+        uint32_t col = kept;
+        const uint32_t msk[5] = {0x0000ffffu, 0x00ff00ffu, 0x0f0f0f0fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+        for (int k = 0; k < 5; k++) {
+            const int j = 16 >> k;
+            const uint32_t y = __shfl_xor_sync(FULLM, col, j);
+            col = (lane & j) ? ((col & ~msk[k]) | ((y & ~msk[k]) >> j)) : ((col & msk[k]) | ((y & msk[k]) << j));
+        }
         if (lane < g.bw) T.colbits[(size_t)g.by * T.W + g.x0 + lane] = col;
     }
 }

@@ -362,6 +362,7 @@ Launch make_launch(pipe_t p, LaunchCtx& c, std::vector<TileDev>& td, int n_rt_to
         row += (t.H + RB - 1) / RB;
         px += t.H * ((t.W + 15) / 16);
     }
+    for (int i = 0; i < (int)td.size() && i < LAUNCH_TAB; i++) L.cb_first[i] = td[i].cb_base;
     L.n_rt = rt;
     L.n_cb = cb;
     L.n_chunks = ch;
