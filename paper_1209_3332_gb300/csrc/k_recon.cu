@@ -255,58 +255,34 @@ __device__ __forceinline__ bool merge_halo(WarpTile& S, const uint8_t hr[5], int
     return __any_sync(FULL, grew);
 }
 
-// One round of the four sweeps.  A sweep step updates one line of the tile
-// (a row, lanes = columns; or a column, lanes = rows) from the three pixels
-// of the line before it, which the previous step stored: each lane reads its
-// two diagonal neighbours from shared memory, where the edge lanes find the
-// halo, so no lane needs a special case.  With R <= M everywhere,
-// max(R, min(m, M)) = min(max(R, m), M).  __syncwarp orders each step's
-// stores before the next step's loads.
+// One sweep: RT steps, each updating one line of the tile (a row, lanes =
+// columns; or a column, lanes = rows) from the three pixels of the line
+// before it, which the previous step stored.  A lane's pixel at step i sits
+// at byte offset o + i*ds of the staged planes; its two diagonal neighbours
+// on the previous line are at offset +/- dl from the previous pixel, where
+// the edge lanes find the halo, so no lane needs a special case.  With
+// R <= M everywhere, max(R, min(m, M)) = min(max(R, m), M).  __syncwarp
+// orders each step's stores before the next step's loads.  One body serves
+// the four directions, which keeps the unrolled code small.
+__device__ __forceinline__ void sweep(uint8_t* R, const uint8_t* M, int o, int ds, int dl) {
+    int prev = R[o - ds];
+#pragma unroll 8
+    for (int i = 0; i < RT; i++, o += ds) {
+        const int a = R[o - ds - dl], b = R[o - ds + dl];
+        const int nv = min(max((int)R[o], __vimax3_s32(prev, a, b)), (int)M[o]);
+        R[o] = (uint8_t)nv;
+        prev = nv;
+        __syncwarp();
+    }
+}
+
+// One round of the four sweeps: down, up, right, left.
 __device__ __forceinline__ void sweep_round(WarpTile& S, int lane) {
-    {   // down: row y takes the 3 pixels above it
-        int prev = SR(-1, lane);
-#pragma unroll
-        for (int y = 0; y < RT; y++) {
-            const int a = SR(y - 1, lane - 1), b = SR(y - 1, lane + 1);
-            const int nv = min(max((int)SR(y, lane), __vimax3_s32(prev, a, b)), (int)SM(y, lane));
-            SR(y, lane) = (uint8_t)nv;
-            prev = nv;
-            __syncwarp();
-        }
-    }
-    {   // up: row y takes the 3 pixels below it
-        int prev = SR(RT, lane);
-#pragma unroll
-        for (int y = RT - 1; y >= 0; y--) {
-            const int a = SR(y + 1, lane - 1), b = SR(y + 1, lane + 1);
-            const int nv = min(max((int)SR(y, lane), __vimax3_s32(prev, a, b)), (int)SM(y, lane));
-            SR(y, lane) = (uint8_t)nv;
-            prev = nv;
-            __syncwarp();
-        }
-    }
-    {   // right: column x takes the 3 pixels left of it (lane = row)
-        int prev = SR(lane, -1);
-#pragma unroll
-        for (int x = 0; x < RT; x++) {
-            const int a = SR(lane - 1, x - 1), b = SR(lane + 1, x - 1);
-            const int nv = min(max((int)SR(lane, x), __vimax3_s32(prev, a, b)), (int)SM(lane, x));
-            SR(lane, x) = (uint8_t)nv;
-            prev = nv;
-            __syncwarp();
-        }
-    }
-    {   // left: column x takes the 3 pixels right of it
-        int prev = SR(lane, RT);
-#pragma unroll
-        for (int x = RT - 1; x >= 0; x--) {
-            const int a = SR(lane - 1, x + 1), b = SR(lane + 1, x + 1);
-            const int nv = min(max((int)SR(lane, x), __vimax3_s32(prev, a, b)), (int)SM(lane, x));
-            SR(lane, x) = (uint8_t)nv;
-            prev = nv;
-            __syncwarp();
-        }
-    }
+    const int c = lane + 4, r = (lane + 1) * HS;  // this lane's column / row offset
+    sweep(S.R, S.M, HS + c, HS, 1);               // down: rows 0..31
+    sweep(S.R, S.M, RT * HS + c, -HS, 1);         // up: rows 31..0
+    sweep(S.R, S.M, r + 4, 1, HS);                // right: columns 0..31
+    sweep(S.R, S.M, r + RT + 3, -1, HS);          // left: columns 31..0
 }
 
 // Whether some pixel of the tile can still be raised by one of its 8
@@ -445,7 +421,9 @@ __global__ void __launch_bounds__(RT_WARPS * 32, RECON_MIN_BLOCKS) k_recon(Launc
             if (grew) continue;  // the fresher halo may raise pixels: check again
             int again = 0;
             if (lane == 0) {
-                __threadfence();
+                // no fence needed here: every write-back above was followed by
+                // one, and the requests' pending counts precede this update in
+                // the counter's order through the __syncwarp
                 int st = atomicCAS(&L.wl_state[t], WL_RUNNING, WL_IDLE);
                 if (st == WL_RUNNING) {
                     atomicAdd(&L.sh->tp, ~0ull);  // pending - 1
