@@ -23,18 +23,21 @@
 
 namespace nucseg {
 
-constexpr int HS = 44;            // shared row stride: 11 words (odd: column sweeps are conflict-free)
+constexpr int HS = 46;            // shared row stride in pixels: 23 words (odd: column sweeps are conflict-free)
 constexpr int MAX_ROUNDS = 256;   // sweep rounds before a tile re-queues itself
 constexpr unsigned FULL = 0xffffffffu;
 
+// One warp's staged tile: pixel (y, x), y and x in [-1, RT], is the 16-bit
+// word P[pidx(y, x)] holding R in its low byte and M (hem8) in its high byte,
+// so that one load yields both.  The interior column 0 sits on a 4-byte
+// boundary.
 struct WarpTile {
-    uint8_t R[(RT + 2) * HS];
-    uint8_t M[(RT + 2) * HS];
+    uint16_t P[(RT + 2) * HS];
 };
+__device__ __forceinline__ int pidx(int y, int x) { return (y + 1) * HS + x + 4; }
 
-// pixel (y, x), y and x in [-1, RT]; interior column 0 sits on a 4-byte boundary
-#define SR(y, x) S.R[((y) + 1) * HS + (x) + 4]
-#define SM(y, x) S.M[((y) + 1) * HS + (x) + 4]
+#define SR(y, x) reinterpret_cast<uint8_t*>(S.P)[2 * pidx(y, x)]
+#define SM(y, x) reinterpret_cast<uint8_t*>(S.P)[2 * pidx(y, x) + 1]
 
 __device__ __forceinline__ int ld_vol(const int* p) { return *(const volatile int*)p; }
 
@@ -149,8 +152,8 @@ __device__ __forceinline__ void halo_coord(int q, int lane, int x0, int y0, int&
     else { gy = (lane & 1) ? y0 + RT : y0 - 1; gx = x0 + RT - 1 + ((lane >> 1) & 1); }
 }
 __device__ __forceinline__ uint8_t& halo_ref(WarpTile& S, int q, int lane, bool mask) {
-    uint8_t* A = mask ? S.M : S.R;
-#define AX(y, x) A[((y) + 1) * HS + (x) + 4]
+    uint8_t* A = reinterpret_cast<uint8_t*>(S.P) + (mask ? 1 : 0);
+#define AX(y, x) A[2 * pidx(y, x)]
     if (q == 0) return AX(-1, lane - 1);
     if (q == 1) return AX(RT, lane - 1);
     if (q == 2) return AX(lane, -1);
@@ -197,9 +200,10 @@ __device__ __forceinline__ void load_tile(WarpTile& S, const uint8_t* Rg, const 
         }
 #pragma unroll
         for (int j = 0; j < RT / 4; j++) {
-            int yy = j * 4 + r4;
-            *reinterpret_cast<uint32_t*>(&SR(yy, c4)) = rv[j];
-            *reinterpret_cast<uint32_t*>(&SM(yy, c4)) = mv[j];
+            // four pixels: (R0 M0 R1 M1) and (R2 M2 R3 M3)
+            uint32_t* d = reinterpret_cast<uint32_t*>(&S.P[pidx(j * 4 + r4, c4)]);
+            d[0] = __byte_perm(rv[j], mv[j], 0x5140);
+            d[1] = __byte_perm(rv[j], mv[j], 0x7362);
         }
     } else {
         for (int yy = 0; yy < RT; yy++) {
@@ -226,9 +230,10 @@ __device__ __forceinline__ void store_tile(WarpTile& S, uint8_t* Rg, int W, int 
 #pragma unroll
         for (int j = 0; j < RT / 4; j++) {
             int yy = j * 4 + r4, gy = y0 + yy;
-            if (gy < H)
-                __stcg(reinterpret_cast<unsigned int*>(Rg + (size_t)gy * W + x0 + c4),
-                       *reinterpret_cast<const uint32_t*>(&SR(yy, c4)));
+            if (gy < H) {
+                const uint32_t* d = reinterpret_cast<const uint32_t*>(&S.P[pidx(yy, c4)]);
+                __stcg(reinterpret_cast<unsigned int*>(Rg + (size_t)gy * W + x0 + c4), __byte_perm(d[0], d[1], 0x6420));
+            }
         }
     } else {
         const int gx = x0 + lane;
@@ -264,13 +269,15 @@ __device__ __forceinline__ bool merge_halo(WarpTile& S, const uint8_t hr[5], int
 // R <= M everywhere, max(R, min(m, M)) = min(max(R, m), M).  __syncwarp
 // orders each step's stores before the next step's loads.  One body serves
 // the four directions, which keeps the unrolled code small.
-__device__ __forceinline__ void sweep(uint8_t* R, const uint8_t* M, int o, int ds, int dl) {
-    int prev = R[o - ds];
+__device__ __forceinline__ void sweep(uint16_t* P, int o, int ds, int dl) {
+    uint8_t* R = reinterpret_cast<uint8_t*>(P);  // R of pixel i is byte 2 i
+    int prev = R[2 * (o - ds)];
 #pragma unroll 8
     for (int i = 0; i < RT; i++, o += ds) {
-        const int a = R[o - ds - dl], b = R[o - ds + dl];
-        const int nv = min(max((int)R[o], __vimax3_s32(prev, a, b)), (int)M[o]);
-        R[o] = (uint8_t)nv;
+        const int a = R[2 * (o - ds - dl)], b = R[2 * (o - ds + dl)];
+        const uint32_t rm = P[o];
+        const int nv = min(max((int)(rm & 0xffu), __vimax3_s32(prev, a, b)), (int)(rm >> 8));
+        R[2 * o] = (uint8_t)nv;
         prev = nv;
         __syncwarp();
     }
@@ -279,10 +286,10 @@ __device__ __forceinline__ void sweep(uint8_t* R, const uint8_t* M, int o, int d
 // One round of the four sweeps: down, up, right, left.
 __device__ __forceinline__ void sweep_round(WarpTile& S, int lane) {
     const int c = lane + 4, r = (lane + 1) * HS;  // this lane's column / row offset
-    sweep(S.R, S.M, HS + c, HS, 1);               // down: rows 0..31
-    sweep(S.R, S.M, RT * HS + c, -HS, 1);         // up: rows 31..0
-    sweep(S.R, S.M, r + 4, 1, HS);                // right: columns 0..31
-    sweep(S.R, S.M, r + RT + 3, -1, HS);          // left: columns 31..0
+    sweep(S.P, HS + c, HS, 1);               // down: rows 0..31
+    sweep(S.P, RT * HS + c, -HS, 1);         // up: rows 31..0
+    sweep(S.P, r + 4, 1, HS);                // right: columns 0..31
+    sweep(S.P, r + RT + 3, -1, HS);          // left: columns 31..0
 }
 
 // Whether some pixel of the tile can still be raised by one of its 8
@@ -295,7 +302,8 @@ __device__ __forceinline__ bool can_raise(WarpTile& S, int lane) {
 #pragma unroll 4
     for (int y = 0; y < RT; y++) {
         int c = __vimax3_s32(SR(y + 1, lane - 1), SR(y + 1, lane), SR(y + 1, lane + 1));
-        v |= min(__vimax3_s32(a, b, c), (int)SM(y, lane)) > (int)SR(y, lane);
+        const uint32_t rm = S.P[pidx(y, lane)];
+        v |= min(__vimax3_s32(a, b, c), (int)(rm >> 8)) > (int)(rm & 0xffu);
         a = b;
         b = c;
     }
