@@ -317,6 +317,8 @@ struct pipe_s {
     cudaStream_t serve_compute = nullptr;  // all groups compute in submission order
     cudaEvent_t serve_ref = nullptr;       // recorded at serve_ref_ms (host clock)
     double serve_ref_ms = 0;
+    size_t peak_io = 0, peak_ws = 0;       // largest served group so far
+    int peak_rt = 0, peak_n = 0;
     // launch shapes per batch shape: tuned by the batched form on first sight
     // of a shape, or read from the autotune cache file
     std::map<std::string, Tune> tuned;
@@ -908,13 +910,18 @@ int batch_submit(pipe_t p, const tile_desc* tiles, int n, uint64_t* ticket) {
     std::vector<int> caps(n);
     size_t ws = 0, io = 0, hin = 0, hout = 0;
     int n_rt = 0;
+    std::vector<char> pinned(n);
     for (int i = 0; i < n; i++) {
         size_t N = (size_t)tiles[i].W * tiles[i].H;
         caps[i] = (int)std::min<size_t>(N / 20 + 1, 65536);
         geos[i] = geometry(tiles[i].W, tiles[i].H, caps[i]);
         ws += geos[i].ws_bytes;
         io += al256(3 * N) + al256(N) + 2 * al256(4 * N) + al256(16) + al256((size_t)caps[i] * NFEAT * 4);
-        hin += al256(3 * N);
+        // pinned inputs are copied directly; pageable ones through a pinned staging buffer
+        cudaPointerAttributes pa;
+        pinned[i] = cudaPointerGetAttributes(&pa, tiles[i].rgb_host) == cudaSuccess && pa.type == cudaMemoryTypeHost;
+        cudaGetLastError();
+        if (!pinned[i]) hin += al256(3 * N);
         hout += al256(16) + al256((size_t)caps[i] * NFEAT * 4) +
                 (tiles[i].want_planes ? al256(N) + 2 * al256(4 * N) : 0);
         n_rt += geos[i].rtx * geos[i].rty;
@@ -944,15 +951,26 @@ int batch_submit(pipe_t p, const tile_desc* tiles, int n, uint64_t* ticket) {
         CK(cudaEventCreate(&c.done));  // timed: its GPU timestamp gives the completion time
     }
     Ctx& c = *p->ctxs[ci];
-    size_t have = c.bytes;
-    size_t grow_to = std::max(have, need);
+    // A context that has to grow grows to the largest group seen so far (when
+    // the budget allows), so that contexts converge to one size instead of
+    // each growing -- a synchronising allocation -- as group sizes vary.
+    p->peak_io = std::max(p->peak_io, io);
+    p->peak_ws = std::max(p->peak_ws, ws);
+    p->peak_rt = std::max(p->peak_rt, n_rt);
+    p->peak_n = std::max(p->peak_n, n);
+    const size_t peak_need = p->peak_io + p->peak_ws + sizeof(TileDev) * p->peak_n + sizeof(int) * 3 * p->peak_rt;
+    const bool to_peak = p->hbm_in_use + std::max(c.bytes, peak_need) <= p->prm.hbm_budget_bytes;
+    size_t grow_to = std::max(c.bytes, to_peak ? peak_need : need);
     if (p->hbm_in_use + grow_to > p->prm.hbm_budget_bytes) return PIPE_EBUSY;
+    const size_t g_io = to_peak ? p->peak_io : io, g_ws = to_peak ? p->peak_ws : ws;
+    const int g_rt = to_peak ? p->peak_rt : n_rt, g_n = to_peak ? p->peak_n : n;
     int rc;
     if (c.dev.n < io || c.lc.arena.n < ws || c.lc.wl.n < sizeof(int) * 3 * (size_t)n_rt ||
-        c.lc.tiles.n < sizeof(TileDev) * n || c.lc.shared.n < sizeof(Shared) + sizeof(int) * (2 + n))
+        c.lc.tiles.n < sizeof(TileDev) * n || c.lc.shared.n < sizeof(Shared) + sizeof(int) * (2 + n)) {
         clear_graphs(c.graphs);
-    if ((rc = c.dev.ensure(io))) return rc;
-    if ((rc = ensure_ctx(c.lc, n, n_rt, ws))) return rc;
+        if ((rc = c.dev.ensure(g_io))) return rc;
+        if ((rc = ensure_ctx(c.lc, g_n, g_rt, g_ws))) return rc;
+    }
     c.bytes = c.dev.n + c.lc.arena.n + c.lc.tiles.n + c.lc.wl.n + c.lc.shared.n;
     if (c.h_in_n < hin) {
         if (c.h_in) cudaFreeHost(c.h_in);
@@ -993,17 +1011,14 @@ int batch_submit(pipe_t p, const tile_desc* tiles, int n, uint64_t* ticket) {
         x.rgb = rgb;
         x.pitch = (size_t)t.W * 3;
         // upload: pinned source directly, pageable through the staging buffer
-        cudaPointerAttributes pa;
-        bool pinned = cudaPointerGetAttributes(&pa, t.rgb_host) == cudaSuccess && pa.type == cudaMemoryTypeHost;
-        cudaGetLastError();
         const void* src = t.rgb_host;
         size_t spitch = t.pitch;
-        if (!pinned) {
+        if (!pinned[i]) {
             for (int y = 0; y < t.H; y++) std::memcpy(hi + (size_t)y * t.W * 3, t.rgb_host + (size_t)y * t.pitch, (size_t)t.W * 3);
             src = hi;
             spitch = (size_t)t.W * 3;
+            hi += al256(3 * N);
         }
-        hi += al256(3 * N);
         if (spitch == (size_t)t.W * 3)  // dense rows: one contiguous copy, not H row copies
             CK(cudaMemcpyAsync(rgb, src, (size_t)t.W * 3 * t.H, cudaMemcpyHostToDevice, c.stream));
         else
