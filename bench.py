@@ -454,28 +454,39 @@ def run_ours(args, world, rank, local):
     pinned = [torch.from_numpy(h).pin_memory() for h in host]
     h2d = B * H * W * 3
 
-    def e2e_step(limit_s=60.0):
+    def e2e_run(steps, inflight=2, limit_s=120.0):
+        """`steps` steps through the served API with up to `inflight` in
+        flight: every step uploads its B tiles from pinned host memory and
+        reads back counts and feature rows, in order.  Returns the seconds
+        taken and the D2H bytes of one step."""
         t0 = time.monotonic()
-        tk = None
-        while tk is None:
-            tk = pipe.submit(pinned)
-            if time.monotonic() - t0 > limit_s:
-                raise RuntimeError("e2e submit not admitted within %.0f s" % limit_s)
-        while True:
-            res = pipe.poll(tk)
-            if res is not None:
-                return sum(4 * 3 + r["n_objects"] * 15 * 4 for r in res)
-            if time.monotonic() - t0 > limit_s:
-                raise RuntimeError("e2e batch not done within %.0f s" % limit_s)
-    d2h = e2e_step()
+        q, n, done, d2h = [], 0, 0, 0
+        while done < steps:
+            while len(q) < inflight and n < steps:
+                tk = pipe.submit(pinned)
+                if tk is None:
+                    break
+                q.append(tk)
+                n += 1
+            res = pipe.poll(q[0]) if q else None
+            if res is None:
+                if time.monotonic() - t0 > limit_s:
+                    raise RuntimeError("e2e steps not done within %.0f s" % limit_s)
+                continue
+            q.pop(0)
+            done += 1
+            d2h = sum(4 * 3 + r["n_objects"] * 15 * 4 for r in res)
+        return time.monotonic() - t0, d2h
+    e2e_run(2)
+    lat_s, _ = e2e_run(1, inflight=1)
     barrier(world)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        d2h = e2e_step()
-    e2e_s = max_over_ranks(world, time.perf_counter() - t0)
+    e2e_s, d2h = e2e_run(args.steps)
+    e2e_s = max_over_ranks(world, e2e_s)
     line["e2e"] = {"value": world * B * args.steps / e2e_s, "unit": "tiles/s", "h2d_bytes_per_step": h2d,
                    "d2h_bytes_per_step": d2h,
-                   "path": "batch_submit (pinned host RGB) -> batch_poll (count + feature rows)"}
+                   "path": "batch_submit (pinned host RGB) -> batch_poll (count + feature rows), "
+                           "two steps in flight",
+                   "single_step_latency_ms": 1000.0 * lat_s}
 
     # ---- served form: Poisson arrivals at 80% of the batched rate ----------
     rate = 0.8 * value / world
