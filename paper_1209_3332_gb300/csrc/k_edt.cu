@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(256) k_edt_rows(Launch L, int RB, int Wmax) {
     __shared__ int rowslow[32];
     const int gbnd = blockIdx.x;
     const int ti = find_tile(L.tiles, L.ntiles, gbnd, &TileDev::row_base);
-    const TileDev& T = L.tiles[ti];
+    const TileDev T = L.tiles[ti];
     if (!T.edt) return;
     const int W = T.W, H = T.H;
     const int y0 = (gbnd - T.row_base) * RB;
@@ -86,19 +86,32 @@ __global__ void __launch_bounds__(256) k_edt_rows(Launch L, int RB, int Wmax) {
         return k >= 32 ? FULLE : ((1u << k) - 1u);
     };
     const uint32_t rv = rows_valid(c);
-    // g for the band, one column per thread
-    for (int x = threadIdx.x; x < W; x += blockDim.x) {
-        const uint32_t bg = ~T.colbits[(size_t)c * W + x] & rv;
+    const uint32_t* const colbits = T.colbits;
+    // g for the band, one column per thread; the column words of four columns
+    // are loaded before any is used, so their latencies overlap
+    constexpr int CU = 4;
+    for (int xb = threadIdx.x; xb < W; xb += CU * blockDim.x) {
+    uint32_t wv[CU];
+#pragma unroll
+    for (int u = 0; u < CU; u++) {
+        const int x = xb + u * blockDim.x;
+        wv[u] = x < W ? __ldg(colbits + (size_t)c * W + x) : 0u;
+    }
+#pragma unroll
+    for (int u = 0; u < CU; u++) {
+        const int x = xb + u * blockDim.x;
+        if (x >= W) break;
+        const uint32_t bg = ~wv[u] & rv;
         int above = -1, below = -1;  // nearest background row above / below this chunk
         const int k0 = y0 - r0, k1 = y0 + nrow - 1 - r0;
         if (!(bg & below_or_at(k0)))
             for (int cc = c - 1; cc >= 0; cc--) {
-                uint32_t b2 = ~T.colbits[(size_t)cc * W + x] & rows_valid(cc);
+                uint32_t b2 = ~colbits[(size_t)cc * W + x] & rows_valid(cc);
                 if (b2) { above = cc * CB + 31 - __clz(b2); break; }
             }
         if (!(bg & ~((1u << k1) - 1u)))
             for (int cc = c + 1; cc < nchunk; cc++) {
-                uint32_t b2 = ~T.colbits[(size_t)cc * W + x] & rows_valid(cc);
+                uint32_t b2 = ~colbits[(size_t)cc * W + x] & rows_valid(cc);
                 if (b2) { below = cc * CB + __ffs(b2) - 1; break; }
             }
         for (int j = 0; j < nrow; j++) {
@@ -111,6 +124,7 @@ __global__ void __launch_bounds__(256) k_edt_rows(Launch L, int RB, int Wmax) {
             gs[(size_t)j * Wmax + x] = (uint16_t)gv;
             if (gv > WMAX) rowslow[j] = 1;
         }
+    }
     }
     __syncthreads();
     for (int j = 0; j < nrow; j++) {

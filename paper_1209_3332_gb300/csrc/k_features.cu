@@ -147,12 +147,27 @@ __device__ __forceinline__ void object_features_impl(const ObjJob& J, int obj, i
     constexpr bool staged = STAGED;
     for (int i = lane; i < 4 * 64; i += 32) glcm[i] = 0;
     if (staged) {
-        for (int yy = 0; yy < rh; yy++) {
-            const size_t row = (size_t)(ry0 + yy) * W + rx0;
-            for (int xx = lane; xx < rw; xx += 32) {
-                smask[yy * rw + xx] = J.labels[row + xx] == l;
-                shem[yy * rw + xx] = J.hem8[row + xx];
+        // the region as one index space, four pixels per lane per step with
+        // all their loads issued before the stores, so their latencies overlap
+        const int nreg = rh * rw;
+        int sy = lane / rw, sx = lane - sy * rw;
+        for (int base = lane; base < nreg; base += 4 * 32) {
+            int lab[4], hv[4], at[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                at[u] = base + 32 * u < nreg ? sy * rw + sx : -1;
+                const size_t g = (size_t)(ry0 + sy) * W + rx0 + sx;
+                lab[u] = at[u] >= 0 ? J.labels[g] : 0;
+                hv[u] = at[u] >= 0 ? J.hem8[g] : 0;
+                sx += 32;
+                while (sx >= rw) { sx -= rw; sy++; }
             }
+#pragma unroll
+            for (int u = 0; u < 4; u++)
+                if (at[u] >= 0) {
+                    smask[at[u]] = lab[u] == l;
+                    shem[at[u]] = (uint8_t)hv[u];
+                }
         }
     }
     __syncwarp();

@@ -338,6 +338,7 @@ __global__ void __launch_bounds__(RT_WARPS * 32, RECON_MIN_BLOCKS) k_recon(Launc
     extern __shared__ __align__(16) unsigned char smraw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     WarpTile& S = reinterpret_cast<WarpTile*>(smraw)[warp];
+    int visits = 0;  // tile processings of this warp (diagnostic), added once at exit
     for (;;) {
         unsigned item = 0;
         int ok = 0;
@@ -356,10 +357,8 @@ __global__ void __launch_bounds__(RT_WARPS * 32, RECON_MIN_BLOCKS) k_recon(Launc
         const uint8_t* const Mg = T.hem8;
         const int t = base + k, ty = k / rx, tx = k - ty * rx;
         const int x0 = tx * RT, y0 = ty * RT;
-        if (lane == 0) {
-            atomicExch(&L.wl_state[t], WL_RUNNING);
-            atomicAdd(&L.sh->processed, 1);
-        }
+        if (lane == 0) atomicExch(&L.wl_state[t], WL_RUNNING);
+        visits++;
         __threadfence();
         __syncwarp();
         load_tile(S, Rg, Mg, W, H, x0, y0, lane);
@@ -438,12 +437,12 @@ __global__ void __launch_bounds__(RT_WARPS * 32, RECON_MIN_BLOCKS) k_recon(Launc
                 } else {
                     // a neighbour raised the halo meanwhile: take the tile again
                     atomicExch(&L.wl_state[t], WL_RUNNING);
-                    atomicAdd(&L.sh->processed, 1);
                     again = 1;
                 }
             }
             again = __shfl_sync(FULL, again, 0);
             if (!again) break;
+            visits++;
             __threadfence();
             if (ld_vol(&L.sh->err)) break;
             // only the halo can have changed: the interior belongs to this worker
@@ -452,6 +451,7 @@ __global__ void __launch_bounds__(RT_WARPS * 32, RECON_MIN_BLOCKS) k_recon(Launc
             merge_halo(S, hr, lane);
         }
     }
+    if (lane == 0 && visits) atomicAdd(&L.sh->processed, visits);
 }
 
 // resident CTAs of the reconstruction kernel
