@@ -379,6 +379,7 @@ __global__ void __launch_bounds__(RT_WARPS * 32, RECON_MIN_BLOCKS) k_recon(Launc
             }
             full_check = more;  // otherwise the interior is at a fixed point now
             bool grew = false;
+            int rel = -1;  // lane 31: the state the release found
             if (nr > 0) {
                 // the halo read only decides which neighbours to queue; it is
                 // issued before the write-back so that the two overlap (a stale
@@ -388,6 +389,9 @@ __global__ void __launch_bounds__(RT_WARPS * 32, RECON_MIN_BLOCKS) k_recon(Launc
                 store_tile(S, Rg, W, H, x0, y0, lane);
                 __threadfence();  // this tile's pixels before any request
                 grew = merge_halo(S, hr, lane);
+                // the release overlaps the requests below; only the pending
+                // decrement has to wait for them
+                if (!grew && lane == 31) rel = atomicCAS(&L.wl_state[t], WL_RUNNING, WL_IDLE);
                 const int top = SR(0, lane), bot = SR(RT - 1, lane);
                 const int lef = SR(lane, 0), rig = SR(lane, RT - 1);
                 const bool nU = line_need(top, top != top0, SR(-1, lane), SM(-1, lane), lane);
@@ -426,13 +430,13 @@ __global__ void __launch_bounds__(RT_WARPS * 32, RECON_MIN_BLOCKS) k_recon(Launc
             // before this tile stops counting as running
             __syncwarp();
             if (grew) continue;  // the fresher halo may raise pixels: check again
+            // No fence is needed before releasing: every write-back above was
+            // followed by one, and the requests' pending counts precede the
+            // decrement in the counter's order through the __syncwarp.
+            if (nr == 0 && lane == 31) rel = atomicCAS(&L.wl_state[t], WL_RUNNING, WL_IDLE);
             int again = 0;
-            if (lane == 0) {
-                // no fence needed here: every write-back above was followed by
-                // one, and the requests' pending counts precede this update in
-                // the counter's order through the __syncwarp
-                int st = atomicCAS(&L.wl_state[t], WL_RUNNING, WL_IDLE);
-                if (st == WL_RUNNING) {
+            if (lane == 31) {
+                if (rel == WL_RUNNING) {
                     atomicAdd(&L.sh->tp, ~0ull);  // pending - 1
                 } else {
                     // a neighbour raised the halo meanwhile: take the tile again
@@ -440,7 +444,7 @@ __global__ void __launch_bounds__(RT_WARPS * 32, RECON_MIN_BLOCKS) k_recon(Launc
                     again = 1;
                 }
             }
-            again = __shfl_sync(FULL, again, 0);
+            again = __shfl_sync(FULL, again, 31);
             if (!again) break;
             visits++;
             __threadfence();
