@@ -448,7 +448,7 @@ def run_ours(args, world, rank, local):
                      "form": "seg_tile + features_tile per tile (host reads K between them)"}
     plain_tile(bufs[0])
     line["plain"]["recon_tile_visits_per_work_tile"] = pipe.recon_visits() / float(
-        ((W + 31) // 32) * ((H + 31) // 32))
+        ((W + 63) // 64) * ((H + 63) // 64))
 
     # ---- end to end through the served API with host buffers ----------------
     pinned = [torch.from_numpy(h).pin_memory() for h in host]

@@ -213,7 +213,7 @@ int pipe_autotune_info(pipe_t p, int* recon_workers, int* edt_rows, int* feat_bl
 /* Number of kernels the pipe has launched since creation. */
 long long pipe_launch_count(pipe_t p);
 
-/* Synchronises the device and returns how many 32x32 work tiles the
+/* Synchronises the device and returns how many 64x64 work tiles the
  * reconstruction of the most recent seg_tile call processed (a tile that is
  * re-queued counts again), or -1 before any call.  Diagnostic only. */
 long long pipe_recon_visits(pipe_t p);
