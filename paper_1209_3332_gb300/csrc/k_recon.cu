@@ -312,6 +312,20 @@ __device__ __forceinline__ bool can_raise(CtaTile& S, int qy, int qx, int lane) 
     return __any_sync(FULL, v);
 }
 
+// Whether a pixel of a neighbouring quadrant can raise one of this
+// quadrant's pixels on the two lines it shares with them.  When this
+// quadrant was at a fixed point and has not changed since, only those lines
+// can have become raisable, so this is the exact test in that case.
+__device__ __forceinline__ bool seam_can_raise(CtaTile& S, int qy, int qx, int lane) {
+    const int ex = qx == 0 ? QT - 1 : QT, nx = qx == 0 ? QT : QT - 1;  // own / neighbouring column
+    const int ey = qy == 0 ? QT - 1 : QT, ny = qy == 0 ? QT : QT - 1;  // own / neighbouring row
+    const int x = qx + lane, y = qy + lane;
+    const int mv = __vimax3_s32(SR(y - 1, nx), SR(y, nx), SR(y + 1, nx));
+    const int mh = __vimax3_s32(SR(ny, x - 1), SR(ny, x), SR(ny, x + 1));
+    const bool v = min(mv, (int)SM(y, ex)) > (int)SR(y, ex) || min(mh, (int)SM(ey, x)) > (int)SR(ey, x);
+    return __any_sync(FULL, v);
+}
+
 // Whether a halo pixel can raise a pixel of this quadrant's part of the tile
 // border.  When the tile's interior was at a fixed point before the halo
 // grew, only border pixels can have become raisable, so this is the exact
@@ -420,7 +434,9 @@ __global__ void __launch_bounds__(RT_WARPS * 32, RECON_MIN_BLOCKS) k_recon(Launc
                 if (qgo) sweep_round(S, qy, qx, lane);
                 __syncthreads();
                 nr++;
-                qgo = can_raise(S, qy, qx, lane);
+                // a quadrant that did not sweep was at a fixed point and is
+                // unchanged: only its seams with the others can have moved
+                qgo = qgo ? can_raise(S, qy, qx, lane) : seam_can_raise(S, qy, qx, lane);
                 go = __syncthreads_or(qgo);
             }
             full_check = more;  // otherwise the interior is at a fixed point now
