@@ -425,10 +425,14 @@ __global__ void __launch_bounds__(RT_WARPS * 32, RECON_MIN_BLOCKS) k_recon(Launc
         for (;;) {
             int nr = 0;
             bool more = false;
-            bool go = sweep_now || __syncthreads_or(full_check ? can_raise(S, qy, qx, lane)
-                                                               : border_can_raise(S, qy, qx, lane));
+            // this quadrant may still change: all of them on a first visit; on a
+            // later one, those whose part of the tile border (or, after a round
+            // limit, any pixel) a halo pixel can raise -- the others start at
+            // a fixed point, and the seam tests wake them if needed
+            bool qgo = true;
+            if (!sweep_now) qgo = full_check ? can_raise(S, qy, qx, lane) : border_can_raise(S, qy, qx, lane);
+            bool go = sweep_now || __syncthreads_or(qgo);
             sweep_now = false;
-            bool qgo = true;  // this quadrant may still change
             while (go) {
                 if (nr >= MAX_ROUNDS) { more = true; break; }
                 if (qgo) sweep_round(S, qy, qx, lane);
