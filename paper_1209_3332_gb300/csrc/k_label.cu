@@ -579,21 +579,33 @@ __global__ void __launch_bounds__(CCL_WARPS * 32, 12) k_relabel(Launch L, int wa
         const int v = par[lane * CB + s];
         return (v & LAB_FLAG) ? (v & ~LAB_FLAG) : (par[v] & ~LAB_FLAG);
     };
-    if (lane < g.bh) {
-        int32_t* dst = T.labels + (size_t)gy * T.W + g.x0;
-        if (g.bw == CB && (T.W & 3) == 0) {
-            // walk the row once, taking a new label at each run start
-            int cur = 0;
-            int v[4];
+    if (g.bw == CB && (T.W & 3) == 0) {
+        // lanes 8r..8r+7 write row 4q+r, four labels each: every store covers
+        // four whole 128-byte rows of the block
+        const int c4 = (lane & 7) * 4;
+#pragma unroll 2
+        for (int q = 0; q < CB / 4; q++) {
+            const int y = 4 * q + (lane >> 3);
+            const uint32_t sty = __shfl_sync(FULLM, st, y), kpy = __shfl_sync(FULLM, kept, y);
+            if (y < g.bh) {
+                int v[4];
 #pragma unroll
-            for (int x = 0; x < CB; x++) {
-                if ((kept >> x) & (st >> x) & 1u) cur = run_label(x);
-                v[x & 3] = ((kept >> x) & 1u) ? cur : 0;
-                if ((x & 3) == 3) reinterpret_cast<int4*>(dst)[x >> 2] = make_int4(v[0], v[1], v[2], v[3]);
+                for (int u = 0; u < 4; u++) {
+                    const int x = c4 + u;
+                    int lab = 0;
+                    if ((kpy >> x) & 1u) {
+                        const int e = par[y * CB + run_start(sty, x)];
+                        lab = (e & LAB_FLAG) ? (e & ~LAB_FLAG) : (par[e] & ~LAB_FLAG);
+                    }
+                    v[u] = lab;
+                }
+                reinterpret_cast<int4*>(T.labels + (size_t)(g.y0 + y) * T.W + g.x0)[lane & 7] =
+                    make_int4(v[0], v[1], v[2], v[3]);
             }
-        } else {
-            for (int x = 0; x < g.bw; x++) dst[x] = ((kept >> x) & 1u) ? run_label(run_start(st, x)) : 0;
         }
+    } else if (lane < g.bh) {
+        int32_t* dst = T.labels + (size_t)gy * T.W + g.x0;
+        for (int x = 0; x < g.bw; x++) dst[x] = ((kept >> x) & 1u) ? run_label(run_start(st, x)) : 0;
     }
     // EDT input: this chunk's 32 kept bits of each column, as one word per
     // column: a 32x32 bit transpose across the lanes in five exchange stages
