@@ -259,31 +259,41 @@ __global__ void __launch_bounds__(CCL_WARPS * 32, 12) k_fill_local(Launch L) {
     const TileDev T = L.tiles[g.ti];  // by value: stores below cannot force reloads
     const uint32_t vm = valid_mask(g.bw);
     uint32_t fg = 0;
-    if (lane < g.bh) {
-        const size_t o = (size_t)(g.y0 + lane) * T.W + g.x0;
-        const uint8_t* hp = T.hem8 + o;
-        const uint8_t* rp = T.R + o;
-        const uint32_t thr4 = (uint32_t)L.thr * 0x01010101u;
-        if (g.bw == 32 && ((reinterpret_cast<uintptr_t>(hp) | reinterpret_cast<uintptr_t>(rp)) & 15) == 0) {
+    const uint32_t thr4 = (uint32_t)L.thr * 0x01010101u;
+    if (g.bw == 32 && (T.W & 15) == 0 &&
+        ((reinterpret_cast<uintptr_t>(T.hem8) | reinterpret_cast<uintptr_t>(T.R)) & 15) == 0) {
+        // lanes 2r and 2r+1 read the two 16-byte halves of row r (then of row
+        // r+16), so every load covers 16 whole sectors; each half yields 16
+        // foreground bits, and two shuffles assemble row y's word in lane y
+        uint32_t half[2];
 #pragma unroll
-            for (int q = 0; q < 2; q++) {
-                uint4 hv = __ldg(reinterpret_cast<const uint4*>(hp) + q);
-                uint4 rv = __ldcg(reinterpret_cast<const uint4*>(rp) + q);
-                uint32_t hw[4] = {hv.x, hv.y, hv.z, hv.w}, rw[4] = {rv.x, rv.y, rv.z, rv.w};
+        for (int i = 0; i < 2; i++) {
+            const int row = (lane >> 1) + 16 * i;
+            half[i] = 0;
+            if (row < g.bh) {
+                const size_t o = (size_t)(g.y0 + row) * T.W + g.x0 + (lane & 1) * 16;
+                const uint4 hv = __ldg(reinterpret_cast<const uint4*>(T.hem8 + o));
+                const uint4 rv = __ldcg(reinterpret_cast<const uint4*>(T.R + o));
+                const uint32_t hw[4] = {hv.x, hv.y, hv.z, hv.w}, rw[4] = {rv.x, rv.y, rv.z, rv.w};
 #pragma unroll
                 for (int k = 0; k < 4; k++) {
                     // R <= hem8 bytewise, so the bytewise difference does not wrap
-                    uint32_t ge = __vcmpgeu4(__vsub4(hw[k], rw[k]), thr4);
-                    uint32_t bits = (ge & 1u) | ((ge >> 7) & 2u) | ((ge >> 14) & 4u) | ((ge >> 21) & 8u);
-                    fg |= bits << (q * 16 + k * 4);
+                    const uint32_t ge = __vcmpgeu4(__vsub4(hw[k], rw[k]), thr4);
+                    half[i] |= ((ge & 1u) | ((ge >> 7) & 2u) | ((ge >> 14) & 4u) | ((ge >> 21) & 8u)) << (k * 4);
                 }
             }
-        } else {
-            for (int x = 0; x < g.bw; x++)
-                if ((int)hp[x] - (int)__ldcg(rp + x) >= L.thr) fg |= 1u << x;
         }
-        T.fgbits[(size_t)(g.y0 + lane) * T.wpr + g.bx] = fg;
+        const int src = 2 * (lane & 15);
+        const uint32_t lo0 = __shfl_sync(FULLM, half[0], src), hi0 = __shfl_sync(FULLM, half[0], src + 1);
+        const uint32_t lo1 = __shfl_sync(FULLM, half[1], src), hi1 = __shfl_sync(FULLM, half[1], src + 1);
+        fg = lane < 16 ? (lo0 | (hi0 << 16)) : (lo1 | (hi1 << 16));
+        if (lane >= g.bh) fg = 0;
+    } else if (lane < g.bh) {
+        const size_t o = (size_t)(g.y0 + lane) * T.W + g.x0;
+        for (int x = 0; x < g.bw; x++)
+            if ((int)T.hem8[o + x] - (int)__ldcg(T.R + o + x) >= L.thr) fg |= 1u << x;
     }
+    if (lane < g.bh) T.fgbits[(size_t)(g.y0 + lane) * T.wpr + g.bx] = fg;
     const uint32_t bg = lane < g.bh ? (~fg & vm) : 0u;
     const uint32_t st = bg & ~(bg << 1);
     warp_ccl<4>(bg, st, lane, par);
