@@ -35,10 +35,9 @@ struct TileDev {
     int32_t* n_objects;           // [1]
     float* feats;                 // [feats_cap][15] (batched form)
     int feats_cap;
-    uint32_t* fgbits;             // bitmaps, H rows of wpr words
+    uint32_t* fgbits;             // bitmaps, block-major: CB words (rows) per labelling block
     uint32_t* filledbits;
-    uint32_t* keptbits;           // pixels with label != 0
-    uint32_t* rootbits;           // kept component roots
+    uint32_t* rootbits;           // kept component roots, row-major: H rows of wpr words
     int32_t* wordprefix;          // exclusive popcount prefix of rootbits words
     int32_t* chunksum;            // per scan chunk
     int32_t* P;                   // union-find parents (sparse, H*W)
@@ -119,7 +118,7 @@ void launch_edt(const Launch& L, int RB, int Wmax, cudaStream_t s, Profiler* pf)
 void launch_features_plain(const uint8_t* hem8, const int32_t* labels, int W, int H, int K, float* feats,
                            int4* bbox, int sms, cudaStream_t s, Profiler* pf);
 void launch_features_batched(const Launch& L, int grid, cudaStream_t s, Profiler* pf);
-void launch_unpack_bits(const uint32_t* bits, int W, int H, int wpr, uint8_t* out, cudaStream_t s,
+void launch_unpack_bits(const uint32_t* bits, int W, int H, int cbx, uint8_t* out, cudaStream_t s,
                         Profiler* pf);
 
 }  // namespace nucseg

@@ -193,6 +193,10 @@ __device__ __forceinline__ WarpGeo warp_geo(const Launch& L, int gb) {
     return g;
 }
 __device__ __forceinline__ uint32_t valid_mask(int bw) { return bw >= 32 ? FULLM : ((1u << bw) - 1u); }
+// word of row r of the block in a block-major bitmap
+__device__ __forceinline__ size_t block_word(const TileDev& T, const WarpGeo& g, int r) {
+    return ((size_t)g.by * T.cbx + g.bx) * CB + r;
+}
 __device__ __forceinline__ int gidx(const TileDev& T, const WarpGeo& g, int li) {
     return (g.y0 + (li >> 5)) * T.W + g.x0 + (li & 31);
 }
@@ -293,7 +297,7 @@ __global__ void __launch_bounds__(CCL_WARPS * 32, 12) k_fill_local(Launch L) {
         for (int x = 0; x < g.bw; x++)
             if ((int)T.hem8[o + x] - (int)__ldcg(T.R + o + x) >= L.thr) fg |= 1u << x;
     }
-    if (lane < g.bh) T.fgbits[(size_t)(g.y0 + lane) * T.wpr + g.bx] = fg;
+    if (lane < g.bh) T.fgbits[block_word(T, g, lane)] = fg;
     const uint32_t bg = lane < g.bh ? (~fg & vm) : 0u;
     const uint32_t st = bg & ~(bg << 1);
     warp_ccl<4>(bg, st, lane, par);
@@ -425,8 +429,9 @@ __global__ void __launch_bounds__(CCL_WARPS * 32, 12) k_label_local(Launch L) {
     const WarpGeo g = warp_geo(L, gb);
     const TileDev T = L.tiles[g.ti];  // by value: stores below cannot force reloads
     const uint32_t vm = valid_mask(g.bw);
-    const size_t wrow = (size_t)(g.y0 + lane) * T.wpr + g.bx;
-    const uint32_t fg = lane < g.bh ? T.fgbits[wrow] : 0u;
+    const size_t wrow = (size_t)(g.y0 + lane) * T.wpr + g.bx;  // row-major (root bitmap)
+    const size_t wblk = block_word(T, g, lane);                // block-major (fg, filled)
+    const uint32_t fg = lane < g.bh ? T.fgbits[wblk] : 0u;
     const uint32_t bg = lane < g.bh ? (~fg & vm) : 0u;
     uint32_t st = bg & ~(bg << 1);
     warp_ccl<4>(bg, st, lane, par);
@@ -438,7 +443,7 @@ __global__ void __launch_bounds__(CCL_WARPS * 32, 12) k_label_local(Launch L) {
         if (!__ldcg(T.A + gr)) filled |= run_mask(bg, s);
     }
     if (lane < g.bh) {
-        T.filledbits[wrow] = filled;
+        T.filledbits[wblk] = filled;
         T.rootbits[wrow] = 0u;
     }
     __syncwarp();
@@ -530,8 +535,7 @@ __global__ void __launch_bounds__(CCL_WARPS * 32, 12) k_relabel(Launch L, int wa
     int* par = par_sm[warp];
     const WarpGeo g = warp_geo(L, gb);
     const TileDev T = L.tiles[g.ti];  // by value: stores below cannot force reloads
-    const size_t wrow = (size_t)(g.y0 + lane) * T.wpr + g.bx;
-    const uint32_t filled = lane < g.bh ? T.filledbits[wrow] : 0u;
+    const uint32_t filled = lane < g.bh ? T.filledbits[block_word(T, g, lane)] : 0u;
     const uint32_t st = filled & ~(filled << 1);
     warp_ccl<8>(filled, st, lane, par);
     // roots of this lane's row: label (0 if filtered out) into the root's entry
@@ -583,7 +587,6 @@ __global__ void __launch_bounds__(CCL_WARPS * 32, 12) k_relabel(Launch L, int wa
             }
         }
     }
-    if (lane < g.bh) T.keptbits[wrow] = kept;
     // label of the run starting at column s of this row
     auto run_label = [&](int s) -> int {
         const int v = par[lane * CB + s];
@@ -647,19 +650,21 @@ __global__ void k_counters_reset(Launch L) {
     for (int i = threadIdx.x; i < L.ntiles; i += blockDim.x) L.tile_status[i] = 0;
 }
 
-__global__ void k_unpack_bits(const uint32_t* bits, int W, int H, int wpr, uint8_t* out) {
+// a block-major bitmap (CB words per labelling block) as one byte per pixel
+__global__ void k_unpack_bits(const uint32_t* bits, int W, int H, int cbx, uint8_t* out) {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (long long)W * H) return;
     int y = (int)(i / W), x = (int)(i - (long long)y * W);
-    out[i] = (uint8_t)((bits[(size_t)y * wpr + (x >> 5)] >> (x & 31)) & 1u);
+    const size_t w = ((size_t)(y / CB) * cbx + x / CB) * CB + (y % CB);
+    out[i] = (uint8_t)((bits[w] >> (x & 31)) & 1u);
 }
 
-void launch_unpack_bits(const uint32_t* bits, int W, int H, int wpr, uint8_t* out, cudaStream_t s,
+void launch_unpack_bits(const uint32_t* bits, int W, int H, int cbx, uint8_t* out, cudaStream_t s,
                         Profiler* pf) {
     long long n = (long long)W * H;
     if (n == 0) return;
     pf->begin("unpack_bits", s);
-    k_unpack_bits<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(bits, W, H, wpr, out);
+    k_unpack_bits<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(bits, W, H, cbx, out);
     pf->end("unpack_bits", s);
 }
 

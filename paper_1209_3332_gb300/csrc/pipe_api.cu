@@ -197,7 +197,9 @@ Geo geometry(int W, int H, int feats_cap) {
     b += 2 * al256(g.N * 4);                      // P, A
     b += al256((size_t)g.cbx * g.cby * RL_CAP * 4);  // per-block root lists
     b += al256((size_t)g.cbx * g.cby * 4);        // per-block root counts
-    b += 4 * al256(words * 4);                    // fg, filled, kept, root bitmaps
+    const size_t bwords = (size_t)g.cbx * g.cby * CB;  // block-major bitmaps: CB words per block
+    b += 2 * al256(bwords * 4);                   // fg, filled bitmaps (block-major)
+    b += al256(words * 4);                        // root bitmap (row-major)
     b += al256(words * 4);                        // word prefix
     b += al256((size_t)g.nchunks * 4);            // chunk sums
     b += al256((size_t)g.cbx * g.cby * 4 * CB * 4);  // block edges
@@ -217,9 +219,9 @@ void carve(TileDev& t, const Geo& g, char* base) {
     t.A = (int32_t*)take(g.N * 4);
     t.rootlist = (int32_t*)take((size_t)g.cbx * g.cby * RL_CAP * 4);
     t.blkroots = (int32_t*)take((size_t)g.cbx * g.cby * 4);
-    t.fgbits = (uint32_t*)take(words * 4);
-    t.filledbits = (uint32_t*)take(words * 4);
-    t.keptbits = (uint32_t*)take(words * 4);
+    const size_t bwords = (size_t)g.cbx * g.cby * CB;
+    t.fgbits = (uint32_t*)take(bwords * 4);
+    t.filledbits = (uint32_t*)take(bwords * 4);
     t.rootbits = (uint32_t*)take(words * 4);
     t.wordprefix = (int32_t*)take(words * 4);
     t.chunksum = (int32_t*)take((size_t)g.nchunks * 4);
@@ -843,7 +845,7 @@ int pipe_debug_plane(pipe_t p, int which, void* dst_dev, pipe_stream_t stream) {
     if (which == 0) {
         CK(cudaMemcpyAsync(dst_dev, t.R, (size_t)t.W * t.H, cudaMemcpyDeviceToDevice, s));
     } else {
-        launch_unpack_bits(which == 1 ? t.fgbits : t.filledbits, t.W, t.H, t.wpr, (uint8_t*)dst_dev, s, &p->prof);
+        launch_unpack_bits(which == 1 ? t.fgbits : t.filledbits, t.W, t.H, t.cbx, (uint8_t*)dst_dev, s, &p->prof);
         CK(cudaGetLastError());
     }
     return PIPE_OK;
