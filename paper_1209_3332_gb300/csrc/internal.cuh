@@ -8,9 +8,8 @@
 namespace nucseg {
 
 // ---- geometry ---------------------------------------------------------------
-constexpr int RT = 64;            // reconstruction work tile: RT x RT pixels, one CTA
-constexpr int RT_WARPS = 4;       // warps per reconstruction CTA: one per 32x32 quadrant
-constexpr int RECON_MIN_BLOCKS = 8;   // resident reconstruction CTAs per SM the register budget must allow
+constexpr int RT = 64;            // reconstruction work tile: RT x RT pixels, one warp
+constexpr int RECON_MIN_BLOCKS = 16;  // resident reconstruction workers (one-warp CTAs) per SM the register budget must allow
 constexpr int CB = 32;            // labelling block: CB x CB pixels (one bitmap word per row)
 constexpr int CB_THREADS = 256;
 constexpr int CCL_WARPS = 4;      // labelling blocks (one per warp) per CTA

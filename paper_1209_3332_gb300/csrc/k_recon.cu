@@ -3,50 +3,114 @@
 // queue-based wave propagation, Sec. V-A).  R = lim R_k with
 // R_{k+1} = min(dilate8(R_k), hem8), R_0 = max(hem8 - h, 0) (written by K1).
 //
-// Design (GB300): a persistent kernel whose CTAs are independent workers.
+// Design (GB300): a persistent kernel whose warps are independent workers.
 // The image is cut into 64x64 work tiles; a device-wide queue holds the
-// tiles that may still change.  A CTA pops a tile and stages R and hem8 of
-// the tile plus a one-pixel halo in shared memory, interleaved as one 16-bit
-// word per pixel.  Each of its four warps owns a 32x32 quadrant and runs four
-// directional sweeps over it (down, up, right, left) -- each an exact
-// sequential sweep along one axis with the 32 lanes moving in lockstep along
-// the other -- reading its neighbour quadrants' edge pixels straight from
-// shared memory; after each round an exact, chain-free test per quadrant
-// decides, through the CTA barrier, whether another round is needed.  The CTA
-// then writes the tile back and queues each neighbouring tile that one of the
-// changed border pixels can still raise.  A visit thus pays the queue's
-// round trips (pop, state change, load, write-back, requests, release) once
-// per 4096 pixels.  Values only grow and are bounded by hem8, so any order of
-// tile processings reaches the same unique fixed point; a per-tile state
-// machine (idle / queued / running / running+dirty) makes sure a tile is
-// never processed by two workers at once and never misses a raise of its
-// halo.  Every spin wait is bounded by the pipe's cycle budget, after which
-// the worker records ST_TIMEOUT and returns.
+// tiles that may still change.  A warp pops a tile, stages R and hem8 (M) of
+// the tile and a one-pixel halo in its own shared memory, and runs rounds of
+// four directional sweeps over the whole tile (down, up, right, left), each
+// an exact sequential sweep along one axis:
+//  * the tile is stored as 2x2-pixel blocks, one 32-bit word of R and one of
+//    M per block, so that two pixels of a row and two pixels of a column are
+//    equally one byte permute away from a pair of 16-bit lanes;
+//  * a row sweep gives each lane two adjacent columns, a column sweep two
+//    adjacent rows; the pair is updated with 16x2-bit SIMD max/min
+//    (new = min(max(R, max of the three pixels of the line before), M)),
+//    the two outer neighbours come from the adjacent lanes by shuffle, and
+//    the halo reaches the edge lanes as a third operand of the max (the
+//    other lanes read zeros there), so no lane needs a branch or a select;
+//  * a sweep reads each block once per two lines and never reads what
+//    another lane stored during it.
+// After each round an exact, chain-free test decides whether another is
+// needed.  The warp then writes the tile back and queues each neighbouring
+// tile that one of the changed border pixels can still raise.  Values only
+// grow and are bounded by hem8, so any order of tile processings reaches the
+// same unique fixed point; a per-tile state machine (idle / queued / running
+// / running+dirty) makes sure a tile is never processed by two workers at
+// once and never misses a raise of its halo.  Every spin wait is bounded by
+// the pipe's cycle budget, after which the worker records ST_TIMEOUT and
+// returns.
 #include "internal.cuh"
 
 namespace nucseg {
 
-constexpr int QT = 32;            // quadrant side: one warp per quadrant
-static_assert(RT == 2 * QT && RT_WARPS == 4, "a work tile is four 32x32 quadrants, one warp each");
-constexpr int HS = 70;            // staged row stride in pixels: 35 words (odd: column sweeps are conflict-free)
+constexpr int NB = RT / 2;        // blocks per tile side
+constexpr int BS = NB + 1;        // block row stride: 33 8-byte blocks (odd: column sweeps are conflict-free)
+constexpr int HL = RT + 2;        // halo line length: index = coordinate + 1, coordinates -1..RT
 constexpr int MAX_ROUNDS = 256;   // sweep rounds before a tile re-queues itself
 constexpr unsigned FULL = 0xffffffffu;
 
-// The CTA's staged tile: pixel (y, x), y and x in [-1, RT], is the 16-bit
-// word P[pidx(y, x)] holding R in its low byte and M (hem8) in its high byte,
-// so one load yields both.  Interior columns 0 and 32 sit on 4-byte
-// boundaries.  B0 keeps the four border lines as they were when neighbours
-// were last queued for them (top, bottom, left, right).
-struct CtaTile {
-    uint16_t P[(RT + 2) * HS];
+// A worker's staged tile.  Block (j, i) covers pixels (2j + a, 2i + b),
+// a, b in {0, 1}: B[j * BS + i].x holds their R bytes and .y their M bytes,
+// byte 2a + b.  The halo lines keep R as one 32-bit word per pixel: the
+// first line of each pair (row -1, column -1) in bits 0-7, the second
+// (row RT, column RT) in bits 16-23, which is where a pixel pair of the
+// neighbouring edge lane needs it; the corners appear in a row and in a
+// column line.  Z is a line of zeros, the halo operand of the inner lanes.
+// B0 keeps the four border lines as they were when neighbours were last
+// queued for them (top, bottom, left, right).
+struct WarpTile {
+    uint2 B[NB * BS];
+    uint32_t HRow[2][HL];
+    uint32_t HC[2][HL];
+    uint32_t Z[HL];
+    uint8_t HMr[2][HL + 2];  // M of the halo rows
+    uint8_t HMc[2][HL + 2];  // M of the halo columns
     uint8_t B0[4][RT];
-    int flags[9];      // neighbours to queue: up, down, left, right, UL, UR, DL, DR, self
-    unsigned item;
-    int ok, again;
+    int flags[9];            // neighbours to queue: up, down, left, right, UL, UR, DL, DR, self
 };
-__device__ __forceinline__ int pidx(int y, int x) { return (y + 1) * HS + x + 4; }
-#define SR(y, x) reinterpret_cast<uint8_t*>(S.P)[2 * pidx(y, x)]
-#define SM(y, x) reinterpret_cast<uint8_t*>(S.P)[2 * pidx(y, x) + 1]
+
+// R / M byte of interior pixel (y, x)
+__device__ __forceinline__ uint8_t& rpx(WarpTile& S, int y, int x) {
+    return reinterpret_cast<uint8_t*>(&S.B[(y >> 1) * BS + (x >> 1)].x)[((y & 1) << 1) | (x & 1)];
+}
+__device__ __forceinline__ uint8_t mpx(const WarpTile& S, int y, int x) {
+    return reinterpret_cast<const uint8_t*>(&S.B[(y >> 1) * BS + (x >> 1)].y)[((y & 1) << 1) | (x & 1)];
+}
+// R and M of halo pixel (hy, hx)
+__device__ __forceinline__ int halo_r(const WarpTile& S, int hy, int hx) {
+    if (hy == -1) return (int)(S.HRow[0][hx + 1] & 0xffu);
+    if (hy == RT) return (int)(S.HRow[1][hx + 1] >> 16);
+    if (hx == -1) return (int)(S.HC[0][hy + 1] & 0xffu);
+    return (int)(S.HC[1][hy + 1] >> 16);
+}
+__device__ __forceinline__ int halo_m(const WarpTile& S, int hy, int hx) {
+    if (hy == -1) return S.HMr[0][hx + 1];
+    if (hy == RT) return S.HMr[1][hx + 1];
+    if (hx == -1) return S.HMc[0][hy + 1];
+    return S.HMc[1][hy + 1];
+}
+__device__ __forceinline__ void set_halo_r(WarpTile& S, int hy, int hx, uint32_t r) {
+    if (hy == -1) S.HRow[0][hx + 1] = r;
+    if (hy == RT) S.HRow[1][hx + 1] = r << 16;
+    if (hx == -1) S.HC[0][hy + 1] = r;
+    if (hx == RT) S.HC[1][hy + 1] = r << 16;
+}
+__device__ __forceinline__ void set_halo_m(WarpTile& S, int hy, int hx, uint8_t m) {
+    if (hy == -1) S.HMr[0][hx + 1] = m;
+    if (hy == RT) S.HMr[1][hx + 1] = m;
+    if (hx == -1) S.HMc[0][hy + 1] = m;
+    if (hx == RT) S.HMc[1][hy + 1] = m;
+}
+
+// 16x2-bit SIMD helpers (values are bytes zero-extended to 16-bit lanes)
+__device__ __forceinline__ uint32_t max2(uint32_t a, uint32_t b) {
+    uint32_t d;
+    asm("max.u16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+__device__ __forceinline__ uint32_t min2(uint32_t a, uint32_t b) {
+    uint32_t d;
+    asm("min.u16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+// byte permutes: a block word -> the pixel pair of row a (ROW0/ROW1) or of
+// column b (COL0/COL1) as two 16-bit lanes; two row or column pairs -> a block word
+constexpr uint32_t ROW0 = 0x4140, ROW1 = 0x4342, COL0 = 0x4240, COL1 = 0x4341;
+constexpr uint32_t PACK_ROWS = 0x6420, PACK_COLS = 0x6240;
+// (left neighbour's high lane, own low lane) and (own high lane, right neighbour's low lane)
+constexpr uint32_t FROM_LEFT = 0x1076, FROM_RIGHT = 0x5432;
+// two halo-line words -> a pixel pair (first line: bits 0-7; second line: bits 16-23)
+constexpr uint32_t LINE0_PAIR = 0x5410, LINE1_PAIR = 0x7632;
 
 __device__ __forceinline__ int ld_vol(const int* p) { return *(const volatile int*)p; }
 
@@ -150,110 +214,130 @@ __global__ void k_wl_init(Launch L) {
     L.wl_state[i] = WL_QUEUED;
 }
 
-// ---- staging ----------------------------------------------------------------------
-// A warp's part of the tile halo: line A is the halo row next to its quadrant
-// (row -1 for the top quadrants, row RT for the bottom ones) over its 32
-// columns, line B the halo column (-1 or RT) over its 32 rows, and lane 0
-// adds the corner between them.  The four warps together cover the halo.
-__device__ __forceinline__ void halo_coord(int q, int lane, int qy, int qx, int& hy, int& hx) {
-    const int ay = qy == 0 ? -1 : RT, bx = qx == 0 ? -1 : RT;
-    if (q == 0) { hy = ay; hx = qx + lane; }
-    else if (q == 1) { hy = qy + lane; hx = bx; }
-    else { hy = ay; hx = bx; }
-}
 
-// R (and M) of this warp's halo pixels, 0 outside the image
-__device__ __forceinline__ void load_halo(uint8_t hr[3], uint8_t* hm, const uint8_t* Rg, const uint8_t* Mg, int W,
-                                          int H, int x0, int y0, int qy, int qx, int lane) {
+// ---- staging ----------------------------------------------------------------------
+// Halo pixel q (0..8) of a lane: q 0-1 top row (-1, 2l + q), q 2-3 bottom row
+// (RT, 2l + q - 2), q 4-5 left column (2l + q - 4, -1), q 6-7 right column
+// (2l + q - 6, RT), q 8 the corners, one each on lanes 0-3.
+__device__ __forceinline__ void halo_coord(int q, int lane, int& hy, int& hx) {
+    if (q < 2) { hy = -1; hx = 2 * lane + q; }
+    else if (q < 4) { hy = RT; hx = 2 * lane + q - 2; }
+    else if (q < 6) { hy = 2 * lane + q - 4; hx = -1; }
+    else if (q < 8) { hy = 2 * lane + q - 6; hx = RT; }
+    else { hy = (lane & 2) ? RT : -1; hx = (lane & 1) ? RT : -1; }
+}
+__device__ __forceinline__ bool halo_lane(int q, int lane) { return q < 8 || lane < 4; }
+
+// R (and M) of this lane's halo pixels, 0 outside the image
+__device__ __forceinline__ void load_halo(uint8_t hr[9], uint8_t* hm, const uint8_t* Rg, const uint8_t* Mg, int W,
+                                          int H, int x0, int y0, int lane) {
 #pragma unroll
-    for (int q = 0; q < 3; q++) {
+    for (int q = 0; q < 9; q++) {
         int hy, hx;
-        halo_coord(q, lane, qy, qx, hy, hx);
+        halo_coord(q, lane, hy, hx);
         const int gy = y0 + hy, gx = x0 + hx;
-        const bool in = gy >= 0 && gy < H && gx >= 0 && gx < W && (q < 2 || lane == 0);
+        const bool in = gy >= 0 && gy < H && gx >= 0 && gx < W && halo_lane(q, lane);
         const size_t o = (size_t)gy * W + gx;
         hr[q] = in ? __ldcg(Rg + o) : (uint8_t)0;
         if (hm) hm[q] = in ? __ldg(Mg + o) : (uint8_t)0;
     }
 }
 
-__device__ __forceinline__ void load_quadrant(CtaTile& S, const uint8_t* Rg, const uint8_t* Mg, int W, int H,
-                                              int x0, int y0, int qy, int qx, int lane) {
-    uint8_t hr[3], hm[3];
-    load_halo(hr, hm, Rg, Mg, W, H, x0, y0, qy, qx, lane);
-    const int gx0 = x0 + qx, gy0 = y0 + qy;
-    if ((W & 3) == 0 && gx0 + QT <= W) {
-        // 8 lanes x 4 bytes per row, 4 rows per step, all loads issued first
-        const int r4 = lane >> 3, c4 = (lane & 7) * 4;
-        uint32_t rv[QT / 4], mv[QT / 4];
-#pragma unroll
-        for (int j = 0; j < QT / 4; j++) {
-            const int gy = gy0 + j * 4 + r4;
-            const bool in = gy < H;
-            const size_t o = (size_t)gy * W + gx0 + c4;
-            rv[j] = in ? __ldcg(reinterpret_cast<const unsigned int*>(Rg + o)) : 0u;
-            mv[j] = in ? __ldg(reinterpret_cast<const unsigned int*>(Mg + o)) : 0u;
-        }
-#pragma unroll
-        for (int j = 0; j < QT / 4; j++) {
-            // four pixels: (R0 M0 R1 M1) and (R2 M2 R3 M3)
-            uint32_t* d = reinterpret_cast<uint32_t*>(&S.P[pidx(qy + j * 4 + r4, qx + c4)]);
-            d[0] = __byte_perm(rv[j], mv[j], 0x5140);
-            d[1] = __byte_perm(rv[j], mv[j], 0x7362);
-        }
-    } else {
-        const int gx = gx0 + lane;
-        for (int y = 0; y < QT; y++) {
-            const int gy = gy0 + y;
-            const bool in = gy < H && gx < W;
-            const size_t o = (size_t)gy * W + gx;
-            S.P[pidx(qy + y, qx + lane)] =
-                (uint16_t)((in ? __ldcg(Rg + o) : 0) | ((in ? __ldg(Mg + o) : 0) << 8));
-        }
-    }
-#pragma unroll
-    for (int q = 0; q < 3; q++) {
-        if (q == 2 && lane != 0) continue;
-        int hy, hx;
-        halo_coord(q, lane, qy, qx, hy, hx);
-        S.P[pidx(hy, hx)] = (uint16_t)(hr[q] | (hm[q] << 8));
-    }
+__device__ __forceinline__ bool fast_rows(const uint8_t* p, const uint8_t* q, int W, int x0) {
+    return (W & 15) == 0 && x0 + RT <= W && ((reinterpret_cast<uintptr_t>(p) | reinterpret_cast<uintptr_t>(q)) & 15) == 0;
 }
 
-// Writes this warp's quadrant of R back: 4-byte stores where rows are word aligned.
-__device__ __forceinline__ void store_quadrant(CtaTile& S, uint8_t* Rg, int W, int H, int x0, int y0, int qy,
-                                               int qx, int lane) {
-    const int gx0 = x0 + qx, gy0 = y0 + qy;
-    if ((W & 3) == 0 && gx0 + QT <= W) {
-        const int r4 = lane >> 3, c4 = (lane & 7) * 4;
+__device__ __forceinline__ void load_tile(WarpTile& S, const uint8_t* Rg, const uint8_t* Mg, int W, int H, int x0,
+                                          int y0, int lane) {
+    uint8_t hr[9], hm[9];
+    load_halo(hr, hm, Rg, Mg, W, H, x0, y0, lane);
+    if (fast_rows(Rg, Mg, W, x0)) {
+        // lane: block row jj of a group of 8, 16-pixel segment seg; rows 2j and
+        // 2j + 1 of R and M with 16-byte loads, eight blocks built from them
+        const int jj = lane >> 2, seg = lane & 3;
+#pragma unroll 1
+        for (int g = 0; g < NB / 8; g++) {
+            const int j = g * 8 + jj, gy = y0 + 2 * j;
+            const size_t o = (size_t)gy * W + x0 + seg * 16;
+            const uint4 z = make_uint4(0, 0, 0, 0);
+            const uint4 rt = gy < H ? __ldcg(reinterpret_cast<const uint4*>(Rg + o)) : z;
+            const uint4 rb = gy + 1 < H ? __ldcg(reinterpret_cast<const uint4*>(Rg + o + W)) : z;
+            const uint4 mt = gy < H ? __ldg(reinterpret_cast<const uint4*>(Mg + o)) : z;
+            const uint4 mb = gy + 1 < H ? __ldg(reinterpret_cast<const uint4*>(Mg + o + W)) : z;
+            const uint32_t rtw[4] = {rt.x, rt.y, rt.z, rt.w}, rbw[4] = {rb.x, rb.y, rb.z, rb.w};
+            const uint32_t mtw[4] = {mt.x, mt.y, mt.z, mt.w}, mbw[4] = {mb.x, mb.y, mb.z, mb.w};
 #pragma unroll
-        for (int j = 0; j < QT / 4; j++) {
-            const int yy = j * 4 + r4, gy = gy0 + yy;
-            if (gy < H) {
-                const uint32_t* d = reinterpret_cast<const uint32_t*>(&S.P[pidx(qy + yy, qx + c4)]);
-                __stcg(reinterpret_cast<unsigned int*>(Rg + (size_t)gy * W + gx0 + c4), __byte_perm(d[0], d[1], 0x6420));
+            for (int u = 0; u < 4; u++) {
+                uint2* d = &S.B[j * BS + seg * 8 + 2 * u];
+                d[0] = make_uint2(__byte_perm(rtw[u], rbw[u], 0x5410), __byte_perm(mtw[u], mbw[u], 0x5410));
+                d[1] = make_uint2(__byte_perm(rtw[u], rbw[u], 0x7632), __byte_perm(mtw[u], mbw[u], 0x7632));
             }
         }
     } else {
-        const int gx = gx0 + lane;
-        for (int y = 0; y < QT; y++) {
-            const int gy = gy0 + y;
-            if (gy < H && gx < W) __stcg(Rg + (size_t)gy * W + gx, SR(qy + y, qx + lane));
+        for (int j = 0; j < NB; j++) {
+            uint32_t rw = 0, mw = 0;
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const int gy = y0 + 2 * j + (q >> 1), gx = x0 + 2 * lane + (q & 1);
+                const bool in = gy < H && gx < W;
+                const size_t o = (size_t)gy * W + gx;
+                rw |= (in ? (uint32_t)__ldcg(Rg + o) : 0u) << (8 * q);
+                mw |= (in ? (uint32_t)__ldg(Mg + o) : 0u) << (8 * q);
+            }
+            S.B[j * BS + lane] = make_uint2(rw, mw);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 9; q++) {
+        if (!halo_lane(q, lane)) continue;
+        int hy, hx;
+        halo_coord(q, lane, hy, hx);
+        set_halo_r(S, hy, hx, hr[q]);
+        set_halo_m(S, hy, hx, hm[q]);
+    }
+}
+
+// Writes the tile's R back: 16-byte stores where rows are 16-byte aligned.
+__device__ __forceinline__ void store_tile(WarpTile& S, uint8_t* Rg, int W, int H, int x0, int y0, int lane) {
+    if (fast_rows(Rg, Rg, W, x0)) {
+        const int jj = lane >> 2, seg = lane & 3;
+#pragma unroll 1
+        for (int g = 0; g < NB / 8; g++) {
+            const int j = g * 8 + jj, gy = y0 + 2 * j;
+            uint32_t top[4], bot[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const uint2* s = &S.B[j * BS + seg * 8 + 2 * u];
+                const uint32_t a = s[0].x, b = s[1].x;
+                top[u] = __byte_perm(a, b, 0x5410);
+                bot[u] = __byte_perm(a, b, 0x7632);
+            }
+            const size_t o = (size_t)gy * W + x0 + seg * 16;
+            if (gy < H) __stcg(reinterpret_cast<uint4*>(Rg + o), make_uint4(top[0], top[1], top[2], top[3]));
+            if (gy + 1 < H) __stcg(reinterpret_cast<uint4*>(Rg + o + W), make_uint4(bot[0], bot[1], bot[2], bot[3]));
+        }
+    } else {
+        for (int j = 0; j < NB; j++) {
+            const uint32_t rw = S.B[j * BS + lane].x;
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const int gy = y0 + 2 * j + (q >> 1), gx = x0 + 2 * lane + (q & 1);
+                if (gy < H && gx < W) __stcg(Rg + (size_t)gy * W + gx, (uint8_t)(rw >> (8 * q)));
+            }
         }
     }
 }
 
-// Raises this warp's staged halo pixels to the values just read; true if any grew.
-__device__ __forceinline__ bool merge_halo(CtaTile& S, const uint8_t hr[3], int qy, int qx, int lane) {
+// Raises the staged halo pixels to the values just read; true if any grew.
+__device__ __forceinline__ bool merge_halo(WarpTile& S, const uint8_t hr[9], int lane) {
     bool grew = false;
 #pragma unroll
-    for (int q = 0; q < 3; q++) {
-        if (q == 2 && lane != 0) continue;
+    for (int q = 0; q < 9; q++) {
+        if (!halo_lane(q, lane)) continue;
         int hy, hx;
-        halo_coord(q, lane, qy, qx, hy, hx);
-        uint8_t& h = SR(hy, hx);
-        if (hr[q] > h) {
-            h = hr[q];
+        halo_coord(q, lane, hy, hx);
+        if (hr[q] > halo_r(S, hy, hx)) {
+            set_halo_r(S, hy, hx, hr[q]);
             grew = true;
         }
     }
@@ -261,146 +345,218 @@ __device__ __forceinline__ bool merge_halo(CtaTile& S, const uint8_t hr[3], int 
 }
 
 // ---- sweeps -------------------------------------------------------------------------
-// One sweep: QT steps, each updating one line of a quadrant (a row, lanes =
-// columns; or a column, lanes = rows) from the three pixels of the line
-// before it, which the previous step stored.  A lane's pixel at step i sits
-// at index o + i*ds of P; its two diagonal neighbours on the previous line
-// are at +/- dl from the previous pixel, where the edge lanes find the halo
-// or the neighbouring quadrant, so no lane needs a special case.  With
-// R <= M everywhere, max(R, min(m, M)) = min(max(R, m), M).  __syncwarp
-// orders each step's stores before the next step's loads; a neighbouring
-// quadrant's edge may be read while its warp updates it, which only ever
-// yields a value that is still a lower bound of R.
-__device__ __forceinline__ void sweep(uint16_t* P, int o, int ds, int dl) {
-    uint8_t* R = reinterpret_cast<uint8_t*>(P);  // R of pixel i is byte 2 i
-    int prev = R[2 * (o - ds)];
-#pragma unroll 8
-    for (int i = 0; i < QT; i++, o += ds) {
-        const int a = R[2 * (o - ds - dl)], b = R[2 * (o - ds + dl)];
-        const uint32_t rm = P[o];
-        const int nv = min(max((int)(rm & 0xffu), __vimax3_s32(prev, a, b)), (int)(rm >> 8));
-        R[2 * o] = (uint8_t)nv;
-        prev = nv;
-        __syncwarp();
+// With R <= M everywhere, max(R, min(m, M)) = min(max(R, m), M).
+
+// Down (DIR = 1) or up (DIR = -1) over all RT rows.  P is the pixel pair of
+// the row before (columns 2l, 2l + 1); its outer neighbours come from lanes
+// l - 1 and l + 1 (the edge lanes get their own pair back, harmlessly, and
+// the halo column through E).
+template <int DIR>
+__device__ __forceinline__ void row_sweep(WarpTile& S, int lane) {
+    const uint32_t* E = lane == 0 ? S.HC[0] : lane == 31 ? S.HC[1] : S.Z;
+    uint32_t P = DIR > 0 ? __byte_perm(S.HRow[0][2 * lane + 1], S.HRow[0][2 * lane + 2], LINE0_PAIR)
+                         : __byte_perm(S.HRow[1][2 * lane + 1], S.HRow[1][2 * lane + 2], LINE1_PAIR);
+    auto block_row = [&](uint2 b, int j) {
+        uint32_t n[2];
+#pragma unroll
+        for (int t = 0; t < 2; t++) {
+            const int a = DIR > 0 ? t : 1 - t, y = 2 * j + a;
+            const uint32_t R = __byte_perm(b.x, 0u, a ? ROW1 : ROW0), M = __byte_perm(b.y, 0u, a ? ROW1 : ROW0);
+            const uint32_t L = __shfl_up_sync(FULL, P, 1), Rt = __shfl_down_sync(FULL, P, 1);
+            const uint32_t w = __vimax3_u16x2(__byte_perm(P, L, FROM_LEFT), P, __byte_perm(P, Rt, FROM_RIGHT));
+            P = min2(__vimax3_u16x2(R, w, E[y - DIR + 1]), M);
+            n[a] = P;
+        }
+        S.B[j * BS + lane].x = __byte_perm(n[0], n[1], PACK_ROWS);
+    };
+    const int j0 = DIR > 0 ? 0 : NB - 1;
+    uint2 b = S.B[j0 * BS + lane];
+#pragma unroll 2
+    for (int k = 0; k < NB - 1; k++) {
+        const int j = j0 + DIR * k;
+        const uint2 nb = S.B[(j + DIR) * BS + lane];  // loaded one block row ahead
+        block_row(b, j);
+        b = nb;
     }
+    block_row(b, j0 + DIR * (NB - 1));
 }
 
-// One round of the four sweeps over quadrant (qy, qx): down, up, right, left.
-__device__ __forceinline__ void sweep_round(CtaTile& S, int qy, int qx, int lane) {
-    sweep(S.P, pidx(qy, qx + lane), HS, 1);
-    sweep(S.P, pidx(qy + QT - 1, qx + lane), -HS, 1);
-    sweep(S.P, pidx(qy + lane, qx), 1, HS);
-    sweep(S.P, pidx(qy + lane, qx + QT - 1), -1, HS);
+// Right (DIR = 1) or left (DIR = -1) over all RT columns; the same with
+// lanes holding rows 2l, 2l + 1 and the halo rows through E.
+template <int DIR>
+__device__ __forceinline__ void col_sweep(WarpTile& S, int lane) {
+    const uint32_t* E = lane == 0 ? S.HRow[0] : lane == 31 ? S.HRow[1] : S.Z;
+    uint32_t C = DIR > 0 ? __byte_perm(S.HC[0][2 * lane + 1], S.HC[0][2 * lane + 2], LINE0_PAIR)
+                         : __byte_perm(S.HC[1][2 * lane + 1], S.HC[1][2 * lane + 2], LINE1_PAIR);
+    auto block_col = [&](uint2 b, int i) {
+        uint32_t n[2];
+#pragma unroll
+        for (int t = 0; t < 2; t++) {
+            const int c = DIR > 0 ? t : 1 - t, x = 2 * i + c;
+            const uint32_t R = __byte_perm(b.x, 0u, c ? COL1 : COL0), M = __byte_perm(b.y, 0u, c ? COL1 : COL0);
+            const uint32_t U = __shfl_up_sync(FULL, C, 1), D = __shfl_down_sync(FULL, C, 1);
+            const uint32_t w = __vimax3_u16x2(__byte_perm(C, U, FROM_LEFT), C, __byte_perm(C, D, FROM_RIGHT));
+            C = min2(__vimax3_u16x2(R, w, E[x - DIR + 1]), M);
+            n[c] = C;
+        }
+        S.B[lane * BS + i].x = __byte_perm(n[0], n[1], PACK_COLS);
+    };
+    const int i0 = DIR > 0 ? 0 : NB - 1;
+    uint2 b = S.B[lane * BS + i0];
+#pragma unroll 2
+    for (int k = 0; k < NB - 1; k++) {
+        const int i = i0 + DIR * k;
+        const uint2 nb = S.B[lane * BS + i + DIR];
+        block_col(b, i);
+        b = nb;
+    }
+    block_col(b, i0 + DIR * (NB - 1));
 }
 
-// Whether some pixel of the quadrant can still be raised by one of its 8
-// neighbours: the exact convergence test, for all pixels in parallel (lane
-// = column), so it has no dependent chain.
-__device__ __forceinline__ bool can_raise(CtaTile& S, int qy, int qx, int lane) {
-    const int x = qx + lane;
-    int a = __vimax3_s32(SR(qy - 1, x - 1), SR(qy - 1, x), SR(qy - 1, x + 1));
-    int b = __vimax3_s32(SR(qy, x - 1), SR(qy, x), SR(qy, x + 1));
+// One round of the four sweeps over the tile: down, up, right, left.
+// __syncwarp orders each sweep's stores before the next sweep's loads.
+__device__ __forceinline__ void sweep_round(WarpTile& S, int lane) {
+    row_sweep<1>(S, lane);
+    __syncwarp();
+    row_sweep<-1>(S, lane);
+    __syncwarp();
+    col_sweep<1>(S, lane);
+    __syncwarp();
+    col_sweep<-1>(S, lane);
+    __syncwarp();
+}
+
+// Whether some pixel of the tile can still be raised by one of its 8
+// neighbours: the exact convergence test, two pixels per lane and row, with
+// no dependent chain; it stops at the first 16-row group that has one.
+__device__ __forceinline__ bool can_raise(const WarpTile& S, int lane) {
+    const uint32_t* E = lane == 0 ? S.HC[0] : lane == 31 ? S.HC[1] : S.Z;
+    // maximum of R over the three columns around each pixel of a pair in row y
+    auto hmax = [&](uint32_t R, int y) -> uint32_t {
+        const uint32_t L = __shfl_up_sync(FULL, R, 1), Rt = __shfl_down_sync(FULL, R, 1);
+        return __vimax3_u16x2(__byte_perm(R, L, FROM_LEFT), __byte_perm(R, Rt, FROM_RIGHT), max2(R, E[y + 1]));
+    };
+    uint32_t hp = hmax(__byte_perm(S.HRow[0][2 * lane + 1], S.HRow[0][2 * lane + 2], LINE0_PAIR), -1);
+    uint2 b = S.B[lane];
+    uint32_t R0 = __byte_perm(b.x, 0u, ROW0), M0 = __byte_perm(b.y, 0u, ROW0);
+    uint32_t h0 = hmax(R0, 0);
     bool v = false;
-#pragma unroll 4
-    for (int y = 0; y < QT; y++) {
-        const int c = __vimax3_s32(SR(qy + y + 1, x - 1), SR(qy + y + 1, x), SR(qy + y + 1, x + 1));
-        const uint32_t rm = S.P[pidx(qy + y, x)];
-        v |= min(__vimax3_s32(a, b, c), (int)(rm >> 8)) > (int)(rm & 0xffu);
-        a = b;
-        b = c;
+    // block row j: rows 2j (R0, M0, h0) and 2j + 1; R2 is row 2j + 2
+    auto block_row = [&](uint32_t R2, uint32_t M2, int j) {
+        const uint32_t R1 = __byte_perm(b.x, 0u, ROW1), M1 = __byte_perm(b.y, 0u, ROW1);
+        const uint32_t h1 = hmax(R1, 2 * j + 1), h2 = hmax(R2, 2 * j + 2);
+        v |= min2(__vimax3_u16x2(hp, h0, h1), M0) != R0;
+        v |= min2(__vimax3_u16x2(h0, h1, h2), M1) != R1;
+        hp = h1;
+        h0 = h2;
+        R0 = R2;
+        M0 = M2;
+    };
+#pragma unroll 1
+    for (int g = 0; g < NB / 8; g++) {
+#pragma unroll
+        for (int jj = 0; jj < 8; jj++) {
+            const int j = g * 8 + jj;
+            if (j + 1 < NB) {
+                const uint2 nb = S.B[(j + 1) * BS + lane];
+                block_row(__byte_perm(nb.x, 0u, ROW0), __byte_perm(nb.y, 0u, ROW0), j);
+                b = nb;
+            } else {
+                block_row(__byte_perm(S.HRow[1][2 * lane + 1], S.HRow[1][2 * lane + 2], LINE1_PAIR), 0u, j);
+            }
+        }
+        if (__any_sync(FULL, v)) return true;
     }
-    return __any_sync(FULL, v);
+    return false;
 }
 
-// Whether a pixel of a neighbouring quadrant can raise one of this
-// quadrant's pixels on the two lines it shares with them.  When this
-// quadrant was at a fixed point and has not changed since, only those lines
-// can have become raisable, so this is the exact test in that case.
-__device__ __forceinline__ bool seam_can_raise(CtaTile& S, int qy, int qx, int lane) {
-    const int ex = qx == 0 ? QT - 1 : QT, nx = qx == 0 ? QT : QT - 1;  // own / neighbouring column
-    const int ey = qy == 0 ? QT - 1 : QT, ny = qy == 0 ? QT : QT - 1;  // own / neighbouring row
-    const int x = qx + lane, y = qy + lane;
-    const int mv = __vimax3_s32(SR(y - 1, nx), SR(y, nx), SR(y + 1, nx));
-    const int mh = __vimax3_s32(SR(ny, x - 1), SR(ny, x), SR(ny, x + 1));
-    const bool v = min(mv, (int)SM(y, ex)) > (int)SR(y, ex) || min(mh, (int)SM(ey, x)) > (int)SR(ey, x);
-    return __any_sync(FULL, v);
-}
-
-// Whether a halo pixel can raise a pixel of this quadrant's part of the tile
-// border.  When the tile's interior was at a fixed point before the halo
-// grew, only border pixels can have become raisable, so this is the exact
-// test in that case.
-__device__ __forceinline__ bool border_can_raise(CtaTile& S, int qy, int qx, int lane) {
-    const int by = qy == 0 ? 0 : RT - 1, hy = qy == 0 ? -1 : RT;
-    const int bx = qx == 0 ? 0 : RT - 1, hx = qx == 0 ? -1 : RT;
-    const int x = qx + lane, y = qy + lane;
-    const int mh = __vimax3_s32(SR(hy, x - 1), SR(hy, x), SR(hy, x + 1));
-    const int mv = __vimax3_s32(SR(y - 1, hx), SR(y, hx), SR(y + 1, hx));
-    const bool v = min(mh, (int)SM(by, x)) > (int)SR(by, x) || min(mv, (int)SM(y, bx)) > (int)SR(y, bx);
+// Whether a halo pixel can raise a pixel of the tile border.  When the
+// tile's interior was at a fixed point before the halo grew, only border
+// pixels can have become raisable, so this is the exact test in that case.
+__device__ __forceinline__ bool border_can_raise(WarpTile& S, int lane) {
+    bool v = false;
+#pragma unroll
+    for (int k = 0; k < 2; k++) {
+        const int p = 2 * lane + k;
+#pragma unroll
+        for (int s = 0; s < 2; s++) {
+            const int hy = s ? RT : -1, by = s ? RT - 1 : 0;
+            const int mh = __vimax3_s32(halo_r(S, hy, p - 1), halo_r(S, hy, p), halo_r(S, hy, p + 1));
+            v |= min(mh, (int)mpx(S, by, p)) > (int)rpx(S, by, p);
+            const int hx = s ? RT : -1, bx = s ? RT - 1 : 0;
+            const int mv = __vimax3_s32(halo_r(S, p - 1, hx), halo_r(S, p, hx), halo_r(S, p + 1, hx));
+            v |= min(mv, (int)mpx(S, p, bx)) > (int)rpx(S, p, bx);
+        }
+    }
     return __any_sync(FULL, v);
 }
 
 // ---- neighbour requests ---------------------------------------------------------------
-// Side s (0 top, 1 bottom, 2 left, 3 right) of the tile, evaluated by warp s
-// after the tile is at a fixed point: halo pixel h of the side (h = -1..RT
-// along it) needs its tile queued when a border pixel changed since the last
-// requests and next to h can raise it.  h = -1 and h = RT are the halo
-// corners, which belong to the diagonal neighbours.  The side's border then
-// becomes the reference for the next requests.
-__device__ __forceinline__ int side_border(int s, int p) {
-    return s == 0 ? pidx(0, p) : s == 1 ? pidx(RT - 1, p) : s == 2 ? pidx(p, 0) : pidx(p, RT - 1);
+// Side s (0 top, 1 bottom, 2 left, 3 right) of the tile, after the tile is at
+// a fixed point: halo pixel h of the side (h = -1..RT along it) needs its
+// tile queued when a border pixel changed since the last requests and next
+// to h can raise it.  h = -1 and h = RT are the halo corners, which belong
+// to the diagonal neighbours.  The side's border then becomes the reference
+// for the next requests.
+__device__ __forceinline__ int border_r(WarpTile& S, int s, int p) {
+    return s == 0 ? rpx(S, 0, p) : s == 1 ? rpx(S, RT - 1, p) : s == 2 ? rpx(S, p, 0) : rpx(S, p, RT - 1);
 }
-__device__ __forceinline__ int side_halo(int s, int h) {
-    return s == 0 ? pidx(-1, h) : s == 1 ? pidx(RT, h) : s == 2 ? pidx(h, -1) : pidx(h, RT);
+__device__ __forceinline__ void side_coord(int s, int h, int& hy, int& hx) {
+    hy = s == 0 ? -1 : s == 1 ? RT : h;
+    hx = s == 2 ? -1 : s == 3 ? RT : h;
 }
-__device__ __forceinline__ void side_requests(CtaTile& S, int s, int lane) {
-    const uint8_t* R8 = reinterpret_cast<const uint8_t*>(S.P);
-    auto cv = [&](int p) -> int {  // border value at p if it changed since the last requests, else 0
-        if (p < 0 || p >= RT) return 0;
-        const int v = R8[2 * side_border(s, p)];
-        return v != S.B0[s][p] ? v : 0;
-    };
-    auto raises = [&](int m, int h) -> bool {
-        const uint32_t hv = S.P[side_halo(s, h)];
-        return min(m, (int)(hv >> 8)) > (int)(hv & 0xffu);
-    };
-    bool line = false;
+__device__ __forceinline__ void side_requests(WarpTile& S, int lane) {
+#pragma unroll 1
+    for (int s = 0; s < 4; s++) {
+        auto cv = [&](int p) -> int {  // border value at p if it changed since the last requests, else 0
+            if (p < 0 || p >= RT) return 0;
+            const int v = border_r(S, s, p);
+            return v != S.B0[s][p] ? v : 0;
+        };
+        auto raises = [&](int m, int h) -> bool {
+            int hy, hx;
+            side_coord(s, h, hy, hx);
+            return min(m, halo_m(S, hy, hx)) > halo_r(S, hy, hx);
+        };
+        bool line = false;
 #pragma unroll
-    for (int u = 0; u < RT / 32; u++) {
-        const int h = lane * (RT / 32) + u;
-        line |= raises(max(max(cv(h - 1), cv(h)), cv(h + 1)), h);
-    }
-    const bool lo = lane == 0 && raises(cv(0), -1);
-    const bool hi = lane == 31 && raises(cv(RT - 1), RT);
-    const bool anyl = __any_sync(FULL, line), anylo = __any_sync(FULL, lo), anyhi = __any_sync(FULL, hi);
-    if (lane == 0) {
-        // corners: top -> UL, UR; bottom -> DL, DR; left -> UL, DL; right -> UR, DR
-        const int cl = s == 0 ? 4 : s == 1 ? 6 : s == 2 ? 4 : 5;
-        const int ch = s == 0 ? 5 : s == 1 ? 7 : s == 2 ? 6 : 7;
-        if (anyl) S.flags[s] = 1;
-        if (anylo) S.flags[cl] = 1;
-        if (anyhi) S.flags[ch] = 1;
+        for (int u = 0; u < RT / 32; u++) {
+            const int h = lane * (RT / 32) + u;
+            line |= raises(max(max(cv(h - 1), cv(h)), cv(h + 1)), h);
+        }
+        const bool lo = lane == 0 && raises(cv(0), -1);
+        const bool hi = lane == 31 && raises(cv(RT - 1), RT);
+        const bool anyl = __any_sync(FULL, line), anylo = __any_sync(FULL, lo), anyhi = __any_sync(FULL, hi);
+        if (lane == 0) {
+            // corners: top -> UL, UR; bottom -> DL, DR; left -> UL, DL; right -> UR, DR
+            const int cl = s == 0 ? 4 : s == 1 ? 6 : s == 2 ? 4 : 5;
+            const int ch = s == 0 ? 5 : s == 1 ? 7 : s == 2 ? 6 : 7;
+            if (anyl) S.flags[s] = 1;
+            if (anylo) S.flags[cl] = 1;
+            if (anyhi) S.flags[ch] = 1;
+        }
     }
     __syncwarp();
-    for (int p = lane; p < RT; p += 32) S.B0[s][p] = R8[2 * side_border(s, p)];
+#pragma unroll 1
+    for (int s = 0; s < 4; s++)
+        for (int p = lane; p < RT; p += 32) S.B0[s][p] = (uint8_t)border_r(S, s, p);
 }
 
-__global__ void __launch_bounds__(RT_WARPS * 32, RECON_MIN_BLOCKS) k_recon(Launch L) {
+__global__ void __launch_bounds__(32, RECON_MIN_BLOCKS) k_recon(Launch L) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    CtaTile& S = *reinterpret_cast<CtaTile*>(smraw);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int qy = (warp >> 1) * QT, qx = (warp & 1) * QT;  // this warp's quadrant
-    int visits = 0;  // tile processings of this CTA (diagnostic), added once at exit
-    if (threadIdx.x < 9) S.flags[threadIdx.x] = 0;
+    WarpTile& S = *reinterpret_cast<WarpTile*>(smraw);
+    const int lane = threadIdx.x;
+    int visits = 0;  // tile processings of this worker (diagnostic), added once at exit
+    if (lane < 9) S.flags[lane] = 0;
+    for (int i = lane; i < HL; i += 32) S.Z[i] = 0u;
+    __syncwarp();
     for (;;) {
-        if (threadIdx.x == 0) {
-            unsigned it = 0;
-            S.ok = wl_pop(L, &it) ? 1 : 0;
-            S.item = it;
-        }
-        __syncthreads();
-        if (!S.ok) break;
-        const unsigned item = S.item;
+        unsigned item = 0;
+        int ok = 0;
+        if (lane == 0) ok = wl_pop(L, &item) ? 1 : 0;
+        ok = __shfl_sync(FULL, ok, 0);
+        if (!ok) break;
+        item = __shfl_sync(FULL, item, 0);
         const int ti = (int)((item >> ITEM_BITS) & ITEM_IMAGE_MASK), k = (int)(item & ITEM_MASK);
         // a tile released by a visit was at a fixed point, so on later visits
         // only its border can have become raisable; its first visit starts
@@ -412,36 +568,27 @@ __global__ void __launch_bounds__(RT_WARPS * 32, RECON_MIN_BLOCKS) k_recon(Launc
         const uint8_t* const Mg = T.hem8;
         const int t = base + k, ty = k / rx, tx = k - ty * rx;
         const int x0 = tx * RT, y0 = ty * RT;
-        if (threadIdx.x == 0) atomicExch(&L.wl_state[t], WL_RUNNING);
+        if (lane == 0) atomicExch(&L.wl_state[t], WL_RUNNING);
         visits++;
         __threadfence();
-        __syncthreads();
-        load_quadrant(S, Rg, Mg, W, H, x0, y0, qy, qx, lane);
-        __syncthreads();
-        // the border as loaded is the reference for the first requests; it is
-        // taken before any warp sweeps
-        for (int p = lane; p < RT; p += 32) S.B0[warp][p] = reinterpret_cast<const uint8_t*>(S.P)[2 * side_border(warp, p)];
-        __syncthreads();
+        __syncwarp();
+        load_tile(S, Rg, Mg, W, H, x0, y0, lane);
+        __syncwarp();
+        // the border as loaded is the reference for the first requests
+#pragma unroll 1
+        for (int s = 0; s < 4; s++)
+            for (int p = lane; p < RT; p += 32) S.B0[s][p] = (uint8_t)border_r(S, s, p);
+        __syncwarp();
         for (;;) {
             int nr = 0;
             bool more = false;
-            // this quadrant may still change: all of them on a first visit; on a
-            // later one, those whose part of the tile border (or, after a round
-            // limit, any pixel) a halo pixel can raise -- the others start at
-            // a fixed point, and the seam tests wake them if needed
-            bool qgo = true;
-            if (!sweep_now) qgo = full_check ? can_raise(S, qy, qx, lane) : border_can_raise(S, qy, qx, lane);
-            bool go = sweep_now || __syncthreads_or(qgo);
+            bool go = sweep_now || (full_check ? can_raise(S, lane) : border_can_raise(S, lane));
             sweep_now = false;
             while (go) {
                 if (nr >= MAX_ROUNDS) { more = true; break; }
-                if (qgo) sweep_round(S, qy, qx, lane);
-                __syncthreads();
+                sweep_round(S, lane);
                 nr++;
-                // a quadrant that did not sweep was at a fixed point and is
-                // unchanged: only its seams with the others can have moved
-                qgo = qgo ? can_raise(S, qy, qx, lane) : seam_can_raise(S, qy, qx, lane);
-                go = __syncthreads_or(qgo);
+                go = can_raise(S, lane);
             }
             full_check = more;  // otherwise the interior is at a fixed point now
             bool grew = false;
@@ -449,17 +596,19 @@ __global__ void __launch_bounds__(RT_WARPS * 32, RECON_MIN_BLOCKS) k_recon(Launc
                 // the halo read only decides which neighbours to queue; it is
                 // issued before the write-back so that the two overlap (a stale
                 // value can only cause a needless request)
-                uint8_t hr[3];
-                load_halo(hr, nullptr, Rg, Mg, W, H, x0, y0, qy, qx, lane);
-                store_quadrant(S, Rg, W, H, x0, y0, qy, qx, lane);
+                uint8_t hr[9];
+                load_halo(hr, nullptr, Rg, Mg, W, H, x0, y0, lane);
+                store_tile(S, Rg, W, H, x0, y0, lane);
                 __threadfence();  // this tile's pixels before any request
-                grew = __syncthreads_or(merge_halo(S, hr, qy, qx, lane));
-                side_requests(S, warp, lane);
-                if (more && threadIdx.x == 0) S.flags[8] = 1;  // not converged within MAX_ROUNDS: run again
-                __syncthreads();
-                if (threadIdx.x < 9 && S.flags[threadIdx.x]) {
+                __syncwarp();
+                grew = __any_sync(FULL, merge_halo(S, hr, lane));
+                __syncwarp();
+                side_requests(S, lane);
+                if (more && lane == 0) S.flags[8] = 1;  // not converged within MAX_ROUNDS: run again
+                __syncwarp();
+                if (lane < 9 && S.flags[lane]) {
                     int target = -1;
-                    switch (threadIdx.x) {
+                    switch (lane) {
                         case 0: if (ty > 0) target = k - rx; break;
                         case 1: if (ty + 1 < ry) target = k + rx; break;
                         case 2: if (tx > 0) target = k - 1; break;
@@ -470,52 +619,50 @@ __global__ void __launch_bounds__(RT_WARPS * 32, RECON_MIN_BLOCKS) k_recon(Launc
                         case 7: if (ty + 1 < ry && tx + 1 < rx) target = k + rx + 1; break;
                         default: target = k; break;
                     }
-                    S.flags[threadIdx.x] = 0;
+                    S.flags[lane] = 0;
                     if (target >= 0) wl_request(L, ti, base, target);
                 }
             }
             // every request (and the pending count it adds) comes before this
             // tile stops counting as running
-            __syncthreads();
+            __syncwarp();
             if (grew) continue;  // the fresher halo may raise pixels: check again
-            if (threadIdx.x == 0) {
+            int again = 0;
+            if (lane == 0) {
                 // no fence needed here: every write-back above was followed by
                 // one, and the requests' pending counts precede this update in
-                // the counter's order through the CTA barrier
+                // the counter's order through the warp barrier
                 const int st = atomicCAS(&L.wl_state[t], WL_RUNNING, WL_IDLE);
                 if (st == WL_RUNNING) {
                     atomicAdd(&L.sh->tp, ~0ull);  // pending - 1
-                    S.again = 0;
                 } else {
                     // a neighbour raised the halo meanwhile: take the tile again
                     atomicExch(&L.wl_state[t], WL_RUNNING);
-                    S.again = 1;
+                    again = 1;
                 }
             }
-            __syncthreads();
-            if (!S.again) break;
+            if (!__shfl_sync(FULL, again, 0)) break;
             visits++;
             __threadfence();
-            // every thread of the CTA must take the same branch around the barriers
-            if (__syncthreads_or(ld_vol(&L.sh->err) != 0)) break;
+            if (__any_sync(FULL, ld_vol(&L.sh->err) != 0)) break;
             // only the halo can have changed: the interior belongs to this worker
-            uint8_t hr[3];
-            load_halo(hr, nullptr, Rg, Mg, W, H, x0, y0, qy, qx, lane);
-            merge_halo(S, hr, qy, qx, lane);
-            __syncthreads();
+            uint8_t hr[9];
+            load_halo(hr, nullptr, Rg, Mg, W, H, x0, y0, lane);
+            merge_halo(S, hr, lane);
+            __syncwarp();
         }
-        __syncthreads();  // the next pop rewrites S.ok and S.item
+        __syncwarp();
     }
-    if (threadIdx.x == 0 && visits) atomicAdd(&L.sh->processed, visits);
+    if (lane == 0 && visits) atomicAdd(&L.sh->processed, visits);
 }
 
-// resident CTAs of the reconstruction kernel
+// resident workers (one warp each) of the reconstruction kernel
 int recon_grid(int device) {
     int sms = 0, per = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
-    const size_t smem = sizeof(CtaTile);
+    const size_t smem = sizeof(WarpTile);
     cudaFuncSetAttribute(k_recon, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_recon, RT_WARPS * 32, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_recon, 32, smem);
     return sms * (per < 1 ? 1 : per);
 }
 
@@ -524,9 +671,9 @@ void launch_recon(const Launch& L, int grid_cap, cudaStream_t s, Profiler* pf) {
     pf->begin("recon_init", s);
     k_wl_init<<<(L.n_rt + 255) / 256, 256, 0, s>>>(L);
     pf->end("recon_init", s);
-    const int grid = L.n_rt < grid_cap ? L.n_rt : grid_cap;  // one work tile per CTA at a time
+    const int grid = L.n_rt < grid_cap ? L.n_rt : grid_cap;  // one work tile per worker at a time
     pf->begin("recon", s);
-    k_recon<<<grid, RT_WARPS * 32, sizeof(CtaTile), s>>>(L);
+    k_recon<<<grid, 32, sizeof(WarpTile), s>>>(L);
     pf->end("recon", s);
 }
 
