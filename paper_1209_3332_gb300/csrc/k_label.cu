@@ -32,12 +32,20 @@ namespace nucseg {
 constexpr unsigned FULLM = 0xffffffffu;
 
 // ---- shared-memory union-find ---------------------------------------------------
-__device__ __forceinline__ int s_find(const int* par, int a) {
+// A warp's table holds one entry per pixel of its 32x32 block, local index
+// i = 32 y + x.  Entry i lives in slot 32 y + ((x + y) mod 32): the lanes of a
+// warp (rows) then reach the entries of one column in 32 different banks.
+struct UF {
+    int* p;
+    __device__ __forceinline__ int& operator[](int i) const { return p[(i & ~31) | ((i + (i >> 5)) & 31)]; }
+};
+
+__device__ __forceinline__ int s_find(UF par, int a) {
     int p = par[a];
     while (p != a) { a = p; p = par[a]; }
     return a;
 }
-__device__ __forceinline__ void s_union(int* par, int a, int b) {
+__device__ __forceinline__ void s_union(UF par, int a, int b) {
     bool done;
     do {
         a = s_find(par, a);
@@ -104,7 +112,7 @@ __device__ __forceinline__ uint32_t below_or_at(int x) { return (2u << x) - 1u; 
 __device__ __forceinline__ int run_start(uint32_t st, int x) { return 31 - __clz(st & below_or_at(x)); }
 
 template <int CONN>
-__device__ __forceinline__ void warp_ccl(uint32_t w, uint32_t st, int lane, int* par) {
+__device__ __forceinline__ void warp_ccl(uint32_t w, uint32_t st, int lane, UF par) {
     // Uniform fast path: every class row is one run, the class rows are
     // contiguous and each overlaps (CONN-adjacency) the row above -- the whole
     // block is one component whose root is its first pixel.  Typical for the
@@ -204,12 +212,12 @@ __device__ __forceinline__ int gidx(const TileDev& T, const WarpGeo& g, int li) 
 // A union-find entry: the local root index in bits 0..9; a root's own entry
 // may carry its component's payload in bits 16 and up.
 constexpr int PAR_IDX = 0x3ff;
-__device__ __forceinline__ int par_root(const int* par, int i) { return par[i] & PAR_IDX; }
+__device__ __forceinline__ int par_root(UF par, int i) { return par[i] & PAR_IDX; }
 
 // Edge roots: [0,CB) left column, [CB,2CB) right column (x=31), [2CB,3CB)
 // top row, [3CB,4CB) bottom row (y=31); -1 where the pixel is not in the class.
 __device__ __forceinline__ void publish_edges(const TileDev& T, const WarpGeo& g, uint32_t w, uint32_t st,
-                                              const int* par, int lane) {
+                                              UF par, int lane) {
     int* e = T.border + (size_t)g.lb * 4 * CB;
     e[lane] = (w & 1u) ? gidx(T, g, par_root(par, lane * CB)) : -1;
     e[CB + lane] = (w >> 31) ? gidx(T, g, par_root(par, lane * CB + run_start(st, 31))) : -1;
@@ -224,7 +232,7 @@ __device__ __forceinline__ void publish_edges(const TileDev& T, const WarpGeo& g
 // 4-connected and 256 8-connected components) and initialise P/A at their
 // global index with payload pay(root).  No global counter is involved.
 template <typename Pay>
-__device__ __forceinline__ void register_roots(const TileDev& T, const WarpGeo& g, uint32_t st, const int* par,
+__device__ __forceinline__ void register_roots(const TileDev& T, const WarpGeo& g, uint32_t st, UF par,
                                                Pay pay, int lane) {
     uint32_t rs = 0;
     for (uint32_t m = st; m; m &= m - 1) {
@@ -257,7 +265,7 @@ __global__ void __launch_bounds__(CCL_WARPS * 32, 12) k_fill_local(Launch L) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int gb = blockIdx.x * CCL_WARPS + warp;
     if (gb >= L.n_cb) return;
-    int* par = par_sm[warp];
+    const UF par{par_sm[warp]};
     uint32_t* touch = touch_sm[warp];
     const WarpGeo g = warp_geo(L, gb);
     const TileDev T = L.tiles[g.ti];  // by value: stores below cannot force reloads
@@ -425,7 +433,7 @@ __global__ void __launch_bounds__(CCL_WARPS * 32, 12) k_label_local(Launch L) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int gb = blockIdx.x * CCL_WARPS + warp;
     if (gb >= L.n_cb) return;
-    int* par = par_sm[warp];
+    const UF par{par_sm[warp]};
     const WarpGeo g = warp_geo(L, gb);
     const TileDev T = L.tiles[g.ti];  // by value: stores below cannot force reloads
     const uint32_t vm = valid_mask(g.bw);
@@ -532,7 +540,7 @@ __global__ void __launch_bounds__(CCL_WARPS * 32, 12) k_relabel(Launch L, int wa
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int gb = blockIdx.x * CCL_WARPS + warp;
     if (gb >= L.n_cb) return;
-    int* par = par_sm[warp];
+    const UF par{par_sm[warp]};
     const WarpGeo g = warp_geo(L, gb);
     const TileDev T = L.tiles[g.ti];  // by value: stores below cannot force reloads
     const uint32_t filled = lane < g.bh ? T.filledbits[block_word(T, g, lane)] : 0u;
