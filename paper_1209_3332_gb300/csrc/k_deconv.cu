@@ -5,12 +5,14 @@
 //
 // hem8 = clamp((sum_c wq_c * od_lut[rgb_c] + 2^18) >> 19, 0, 255) with the
 // integer tables built on the host at pipe creation.  The 256-entry od_lut
-// (u16) is replicated once per lane in shared memory, entry v of lane l at
-// v*32 + l, so 32 data-dependent lookups hit at most two lanes per bank.
-// One thread converts 16 consecutive pixels of a row: three 16-byte loads of
-// interleaved RGB, one 16-byte store to each output plane, when the row is
-// 16-byte aligned; byte accesses otherwise.  HBM-bound: 3 B read + 2 B
-// written per pixel.
+// is replicated once per lane in shared memory as 32-bit words, entry v of
+// lane l at v*32 + l, so 32 data-dependent lookups always hit 32 different
+// banks.  One thread converts 16 consecutive pixels of a row: three 16-byte
+// loads of interleaved RGB, one 16-byte store to each output plane, when the
+// row is 16-byte aligned; byte accesses otherwise.  Clamping and the marker
+// are one DPX instruction each and the output bytes are packed with integer
+// multiply-adds, which keeps the integer ALU pipe below the memory bound.
+// HBM-bound: 3 B read + 2 B written per pixel.
 #include "internal.cuh"
 
 namespace nucseg {
@@ -24,12 +26,14 @@ void upload_deconv_tables(const int32_t* lut256, const int32_t* wq3) {
 }
 
 struct DeconvLut {
-    const uint16_t* t;  // t[v * 32 + lane]
-    int lane, w0, w1, w2;
+    const int32_t* t;  // this lane's column: entry v at t[v * 32]
+    int w0, w1, w2;
+    // clamp((acc + 2^18) >> 19, 0, 255) for acc >= 0 and 0 for acc < 0: the
+    // shifted value is <= 0 exactly when acc < 2^18, so one min-with-relu
+    // covers both ends
     __device__ __forceinline__ uint32_t hem(uint32_t r, uint32_t g, uint32_t b) const {
-        int32_t acc = w0 * (int32_t)t[r * 32 + lane] + w1 * (int32_t)t[g * 32 + lane] + w2 * (int32_t)t[b * 32 + lane];
-        int32_t v = acc < 0 ? 0 : (acc + (1 << 18)) >> 19;
-        return (uint32_t)(v > 255 ? 255 : v);
+        const int32_t acc = w0 * t[r * 32] + (w1 * t[g * 32] + (w2 * t[b * 32] + (1 << 18)));
+        return (uint32_t)__vimin_s32_relu(acc >> 19, 255);
     }
 };
 
@@ -38,10 +42,10 @@ __device__ __forceinline__ void deconv_item(const TileDev* __restrict__ tiles, i
 
 __global__ void __launch_bounds__(256) k_deconv(const TileDev* __restrict__ tiles, int ntiles,
                                                 int n_items, int h) {
-    __shared__ uint16_t T[256 * 32];
-    for (int i = threadIdx.x; i < 256 * 32; i += blockDim.x) T[i] = (uint16_t)c_lut[i >> 5];
+    __shared__ int32_t T[256 * 32];
+    for (int i = threadIdx.x; i < 256 * 32; i += blockDim.x) T[i] = c_lut[i >> 5];
     __syncthreads();
-    const DeconvLut lut{T, (int)(threadIdx.x & 31), c_wq[0], c_wq[1], c_wq[2]};
+    const DeconvLut lut{T + (threadIdx.x & 31), c_wq[0], c_wq[1], c_wq[2]};
     for (int gid = blockIdx.x * blockDim.x + threadIdx.x; gid < n_items; gid += gridDim.x * blockDim.x)
         deconv_item(tiles, ntiles, gid, h, lut);
 }
@@ -64,16 +68,14 @@ __device__ __forceinline__ void deconv_item(const TileDev* __restrict__ tiles, i
         uint4 c = __ldcs(reinterpret_cast<const uint4*>(src) + 2);
         uint32_t w[12] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z, c.w};
         uint32_t hv[4] = {0, 0, 0, 0}, rv[4] = {0, 0, 0, 0};
+        // byte k of the 48 loaded bytes, zero-extended
+        auto byte_at = [&](int k) -> uint32_t { return __byte_perm(w[k >> 2], 0u, 0x4440 | (k & 3)); };
 #pragma unroll
-        for (int p = 0; p < 16; p++) {
-            int o = p * 3;
-            uint32_t r = (w[o >> 2] >> ((o & 3) * 8)) & 255;
-            uint32_t g = (w[(o + 1) >> 2] >> (((o + 1) & 3) * 8)) & 255;
-            uint32_t bb = (w[(o + 2) >> 2] >> (((o + 2) & 3) * 8)) & 255;
-            uint32_t hm = lut.hem(r, g, bb);
-            uint32_t mk = hm > (uint32_t)h ? hm - h : 0;
-            hv[p >> 2] |= hm << ((p & 3) * 8);
-            rv[p >> 2] |= mk << ((p & 3) * 8);
+        for (int p = 15; p >= 0; p--) {  // high pixel first: each word is built by multiply-adds
+            const uint32_t hm = lut.hem(byte_at(3 * p), byte_at(3 * p + 1), byte_at(3 * p + 2));
+            const uint32_t mk = (uint32_t)__viaddmax_s32((int)hm, -h, 0);
+            hv[p >> 2] = hv[p >> 2] * 256u + hm;
+            rv[p >> 2] = rv[p >> 2] * 256u + mk;
         }
         if ((reinterpret_cast<uintptr_t>(dh) & 15) == 0 && (reinterpret_cast<uintptr_t>(dr) & 15) == 0) {
             *reinterpret_cast<uint4*>(dh) = make_uint4(hv[0], hv[1], hv[2], hv[3]);
@@ -88,9 +90,9 @@ __device__ __forceinline__ void deconv_item(const TileDev* __restrict__ tiles, i
     } else {
         int n = min(16, t.W - x0);
         for (int p = 0; p < n; p++) {
-            uint32_t hm = lut.hem(src[3 * p], src[3 * p + 1], src[3 * p + 2]);
+            const uint32_t hm = lut.hem(src[3 * p], src[3 * p + 1], src[3 * p + 2]);
             dh[p] = (uint8_t)hm;
-            dr[p] = (uint8_t)(hm > (uint32_t)h ? hm - h : 0);
+            dr[p] = (uint8_t)__viaddmax_s32((int)hm, -h, 0);
         }
     }
 }

@@ -16,8 +16,9 @@
 // within WMAX use an exact windowed search (a candidate at distance r costs
 // at least r^2, so the search stops once r^2 >= the best value); other rows
 // run Meijster's lower-envelope scan on one thread.  Shared memory holds
-// only the band (4 rows of u16 for a 4096-wide tile), so several CTAs fit on
-// an SM.
+// only the band (4 rows of u16 for a 4096-wide tile, each padded with WMAX
+// "no background" entries on both sides so that the search needs no bounds
+// test), so several CTAs fit on an SM.
 #include "internal.cuh"
 
 namespace nucseg {
@@ -68,7 +69,8 @@ __device__ void meijster_row(const uint16_t* g, int W, int32_t* out) {
 
 __global__ void __launch_bounds__(256) k_edt_rows(Launch L, int RB, int Wmax) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    uint16_t* gs = reinterpret_cast<uint16_t*>(smraw);  // [RB][Wmax]
+    uint16_t* gs = reinterpret_cast<uint16_t*>(smraw);  // [RB][WMAX + Wmax + WMAX]
+    const int Wp = Wmax + 2 * WMAX;
     __shared__ int rowslow[32];
     const int gbnd = blockIdx.x;
     const int ti = find_tile(L.tiles, L.ntiles, gbnd, &TileDev::row_base);
@@ -80,6 +82,10 @@ __global__ void __launch_bounds__(256) k_edt_rows(Launch L, int RB, int Wmax) {
     const int nrow = min(RB, H - y0);
     const int nchunk = T.cby;
     if (threadIdx.x < 32) rowslow[threadIdx.x] = 0;
+    for (int i = threadIdx.x; i < nrow * 2 * WMAX; i += blockDim.x) {
+        const int j = i / (2 * WMAX), k = i - j * 2 * WMAX;
+        gs[(size_t)j * Wp + (k < WMAX ? k : W + k)] = (uint16_t)INFG;
+    }
     __syncthreads();
     auto rows_valid = [&](int cc) -> uint32_t {
         int k = min(CB, H - cc * CB);
@@ -121,23 +127,24 @@ __global__ void __launch_bounds__(256) k_edt_rows(Launch L, int RB, int Wmax) {
             const uint32_t md = bg & ~((1u << k) - 1u);
             const int dd = md ? (__ffs(md) - 1) - k : (below >= 0 ? below - y : INFG);
             const int gv = min(min(du, dd), INFG);
-            gs[(size_t)j * Wmax + x] = (uint16_t)gv;
+            gs[(size_t)j * Wp + WMAX + x] = (uint16_t)gv;
             if (gv > WMAX) rowslow[j] = 1;
         }
     }
     }
     __syncthreads();
     for (int j = 0; j < nrow; j++) {
-        const uint16_t* g = gs + (size_t)j * Wmax;
+        const uint16_t* g = gs + (size_t)j * Wp + WMAX;
         int32_t* out = T.edt + (size_t)(y0 + j) * W;
         if (!rowslow[j]) {
+            // g <= WMAX on this row, so r < WMAX stays within the padding,
+            // whose entries cost INFG^2 and never win
             for (int x = threadIdx.x; x < W; x += blockDim.x) {
-                int g0 = g[x];
+                const int g0 = g[x];
                 int D = sq(g0);
-                for (int r = 1; r * r < D; r++) {
-                    int rr = r * r;
-                    if (x - r >= 0) D = min(D, rr + sq(g[x - r]));
-                    if (x + r < W) D = min(D, rr + sq(g[x + r]));
+                for (int r = 1, rr = 1; rr < D; rr += 2 * r + 1, r++) {
+                    D = __viaddmin_s32(sq(g[x - r]), rr, D);
+                    D = __viaddmin_s32(sq(g[x + r]), rr, D);
                 }
                 out[x] = D;
             }
@@ -147,7 +154,7 @@ __global__ void __launch_bounds__(256) k_edt_rows(Launch L, int RB, int Wmax) {
     }
 }
 
-size_t edt_rows_smem(int RB, int Wmax) { return (size_t)RB * Wmax * 2; }
+size_t edt_rows_smem(int RB, int Wmax) { return (size_t)RB * (Wmax + 2 * WMAX) * 2; }
 
 void launch_edt(const Launch& L, int RB, int Wmax, cudaStream_t s, Profiler* pf) {
     if (L.n_rows == 0) return;
