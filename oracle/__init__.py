@@ -58,6 +58,9 @@ def _load():
         L.oracle_features.argtypes = [vp, vp, ci, ci, ci, vp]
         L.oracle_seg.argtypes = [vp, ci, ci, sz, ci, ci, ci, ci, vp, vp, vp, vp, vp, vp]
         L.oracle_seg.restype = ci
+        L.oracle_morph_disk.argtypes = [vp, ci, ci, ci, ci, vp]
+        L.oracle_morph_open.argtypes = [vp, ci, ci, ci, vp]
+        L.oracle_morph_open.restype = ci
         _lib = L
     return _lib
 
@@ -177,4 +180,32 @@ def seg(rgb, h=20, thr=10, amin=20, amax=1500, planes=False):
     out = dict(hem8=hem8, labels=labels, edt=ed, K=K)
     if planes:
         out.update(R=R, fg=fg, filled=fl)
+    return out
+
+
+def morph_erode(src, r=9):
+    """Grayscale erosion by the disk dx^2 + dy^2 <= r^2 over in-image pixels."""
+    src, p = _c(src, np.uint8)
+    H, W = src.shape
+    out = np.empty((H, W), np.uint8)
+    _load().oracle_morph_disk(p, W, H, r, 0, out.ctypes.data)
+    return out
+
+
+def morph_dilate(src, r=9):
+    """Grayscale dilation by the same disk."""
+    src, p = _c(src, np.uint8)
+    H, W = src.shape
+    out = np.empty((H, W), np.uint8)
+    _load().oracle_morph_disk(p, W, H, r, 1, out.ctypes.data)
+    return out
+
+
+def morph_open(src, r=9):
+    """Opening by the disk (Table I "Morph. Open"; r = 9 is the 19 x 19 disk)."""
+    src, p = _c(src, np.uint8)
+    H, W = src.shape
+    out = np.empty((H, W), np.uint8)
+    if _load().oracle_morph_open(p, W, H, r, out.ctypes.data) != 0:
+        raise ValueError("bad arguments")
     return out

@@ -530,6 +530,38 @@ void oracle_features(const uint8_t* hem8, const int32_t* labels, int W, int H, i
     free(gs); free(gss); free(gmn); free(gmx); free(C);
 }
 
+/* ---- morphological opening by a disk (Table I "Morph. Open") ---------------
+ * Reading: the paper names the operation and its 19 x 19 disk only.  The disk
+ * of radius r is {(dx, dy) : dx^2 + dy^2 <= r^2}; pixels outside the image
+ * take no part (erosion and dilation range over in-image pixels only). */
+void oracle_morph_disk(const uint8_t* src, int W, int H, int r, int is_max, uint8_t* out) {
+    for (int y = 0; y < H; y++)
+        for (int x = 0; x < W; x++) {
+            int v = is_max ? 0 : 255;
+            for (int dy = -r; dy <= r; dy++) {
+                const int yy = y + dy;
+                if (yy < 0 || yy >= H) continue;
+                for (int dx = -r; dx <= r; dx++) {
+                    const int xx = x + dx;
+                    if (xx < 0 || xx >= W || dx * dx + dy * dy > r * r) continue;
+                    const int s = src[(size_t)yy * W + xx];
+                    v = is_max ? (s > v ? s : v) : (s < v ? s : v);
+                }
+            }
+            out[(size_t)y * W + x] = (uint8_t)v;
+        }
+}
+
+int oracle_morph_open(const uint8_t* src, int W, int H, int r, uint8_t* out) {
+    if (W <= 0 || H <= 0 || r < 0 || !src || !out) return -1;
+    uint8_t* e = (uint8_t*)malloc((size_t)W * H);
+    if (!e) return -1;
+    oracle_morph_disk(src, W, H, r, 0, e);
+    oracle_morph_disk(e, W, H, r, 1, out);
+    free(e);
+    return 0;
+}
+
 int oracle_seg(const uint8_t* rgb, int W, int H, size_t pitch, int h, int thr, int amin, int amax,
                uint8_t* hem8, uint8_t* R, uint8_t* fg, uint8_t* filled, int32_t* labels,
                int32_t* edt) {

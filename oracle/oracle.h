@@ -90,6 +90,16 @@ void oracle_edt(const int32_t* labels, int W, int H, int32_t* edt);
 void oracle_features(const uint8_t* hem8, const int32_t* labels, int W, int H, int K,
                      double* feats);
 
+/* Grayscale erosion (is_max = 0) or dilation (is_max = 1) by a disk of
+ * radius r: out(p) = min (max) of src over the in-image pixels q with
+ * |q - p|^2 <= r^2 (the disk is the set of integer offsets (dx, dy) with
+ * dx^2 + dy^2 <= r^2; r = 9 spans 19 x 19).  Plain definition, O(W H r^2). */
+void oracle_morph_disk(const uint8_t* src, int W, int H, int r, int is_max, uint8_t* out);
+
+/* Morphological opening by that disk (Table I "Morph. Open", 19 x 19 disk):
+ * the dilation of the erosion.  Returns -1 on bad arguments. */
+int oracle_morph_open(const uint8_t* src, int W, int H, int r, uint8_t* out);
+
 /* Whole segmentation: deconv -> h-dome -> fill holes -> label -> EDT.
  * Any of R, fg, filled may be NULL.  Returns K, or -1 on bad arguments. */
 int oracle_seg(const uint8_t* rgb, int W, int H, size_t pitch, int h, int thr, int amin, int amax,
