@@ -292,6 +292,62 @@ def timed(torch, stream, fn, steps):
     return e0.elapsed_time(e1)
 
 
+# ALU pipe of the GB300: 152 SMs x 4 sub-partitions x 16 integer lanes per clock
+ALU_LANES_PER_CLK = 152 * 4 * 16
+MORPH_R = 9                      # the 19x19 disk of Table I "Morph. Open"
+# SIMD ops per pixel: R 3-input and 2R + 1 2-input ops per pixel pair and pass, two passes
+MORPH_OPS_PER_PX = MORPH_R + 2 * MORPH_R + 1
+
+
+def morph_open_run(torch, pipe, stream, planes, steps, hbm_peak, want_cpu):
+    """The opening by the 19x19 disk (Table I "Morph. Open") of every hem8
+    plane of the batch through morph_open_tile, timed with CUDA events on the
+    launching stream (planes larger than L2 in all).  The roofline is the ALU
+    pipe: the nested chords take R 3-input and 2R + 1 2-input 16x2-bit SIMD
+    ops per pixel pair and pass."""
+    outs = [torch.empty_like(p) for p in planes]
+
+    def step():
+        for a, b in zip(planes, outs):
+            pipe.morph_open(a, b, MORPH_R, stream=stream)
+    for _ in range(3):
+        step()
+    ms = timed(torch, stream, step, steps) / steps
+    n = len(planes)
+    px = n * planes[0].numel()
+    mhz = peaks_clock()
+    alu_peak = ALU_LANES_PER_CLK * mhz * 1e6 / 1e9          # G lane-ops/s
+    alu = MORPH_OPS_PER_PX * px / (ms / 1000.0) / 1e9
+    gbs = 2.0 * px / (ms / 1000.0) / 1e9                       # read once, write once
+    out = {"radius": MORPH_R, "planes_per_step": n, "plane": list(planes[0].shape), "ms_per_step": ms,
+           "planes_per_s": n * 1000.0 / ms,
+           "roofline": {"bound": "alu", "achieved": alu, "peak": alu_peak, "unit": "G lane-op/s",
+                        "frac": alu / alu_peak, "ops_per_px": MORPH_OPS_PER_PX,
+                        "peak_source": "derived: 152 SMs x 4 x 16 ALU lanes x %.0f MHz" % mhz},
+           "hbm": {"achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+                   "alg_bytes_per_px": 2},
+           "parity": "bit-exact with the oracle (tests/test_gpu_morph.py)"}
+    if want_cpu:
+        import time
+        import oracle
+        a = planes[0][:128 + 4 * MORPH_R].cpu().numpy()     # a band of 128 output rows plus its halo
+        t = time.perf_counter()
+        oracle.morph_open(a, MORPH_R)
+        s = time.perf_counter() - t
+        out["cpu_oracle"] = {"planes_per_s": (a.shape[0] * a.shape[1]) / planes[0].numel() / s, "cores": 1,
+                             "sample": "the oracle on one band of %d x %d pixels of plane 0, %.2f s, scaled"
+                                       % (a.shape[0], a.shape[1], s)}
+    return out
+
+
+def peaks_clock():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f).get("sm_max_mhz", 2070.0))
+    except (OSError, ValueError):
+        return 2070.0
+
+
 def h2d_gbs(torch, dev, nbytes=256 << 20, reps=4):
     """Pinned host-to-device copy bandwidth (best of reps), GB/s."""
     src = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
@@ -519,6 +575,9 @@ def run_ours(args, world, rank, local):
                              "e2e_bound_tiles_per_s": bound, "e2e_frac": line["e2e"]["value"] / world / bound}
     line["kernels_ms"] = {k: round(v[1] / max(v[0], 1), 4)
                           for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
+    # ---- the step before the path: opening by the 19x19 disk ------------------
+    line["morph_open"] = morph_open_run(torch, pipe, stream, [b["hem8"] for b in bufs], max(3, args.steps // 2),
+                                        peak, rank == 0 and world == 1 and not args.no_cpu)
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(host[0])
     if rank == 0:

@@ -155,6 +155,19 @@ typedef struct {
  * defaults otherwise; it never tunes. */
 int seg_features_batch(pipe_t p, const tile_dev* tiles, int n, pipe_stream_t stream);
 
+/* Grayscale opening by a disk (Table I "Morph. Open", which uses a 19x19
+ * disk: radius = 9).  The disk of radius r is the set of integer offsets
+ * (dx, dy) with dx^2 + dy^2 <= r^2.  dst = the dilation of the erosion of
+ * src, each the maximum / minimum over the disk around a pixel, taken over
+ * in-image pixels only.
+ *  src_dev, dst_dev: W x H uint8 planes, row pitch W, caller-owned device
+ *    memory; they must not overlap.
+ *  0 <= radius <= 15; W, H as for seg_tile.
+ * Returns PIPE_EINVAL on a bad argument (nothing is launched); otherwise
+ * the work is asynchronous on `stream`. */
+int morph_open_tile(pipe_t p, const uint8_t* src_dev, int W, int H, int radius, uint8_t* dst_dev,
+                    pipe_stream_t stream);
+
 /* Served form (Sec. IV-D prefetching and asynchronous copy): tiles in host
  * memory are admitted as slots and HBM budget allow, uploaded on copy
  * streams overlapped with compute, processed, and their results downloaded.

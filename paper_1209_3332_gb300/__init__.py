@@ -20,7 +20,7 @@ STATUS_NAMES = ["PIPE_OK", "PIPE_EINVAL", "PIPE_ENOMEM", "PIPE_EBUSY", "PIPE_EAG
 EXPORTS = ["pipe_default_params", "pipe_create", "pipe_destroy", "seg_tile", "features_tile",
            "seg_features_batch", "batch_submit", "batch_poll", "pipe_status_read", "pipe_debug_plane",
            "pipe_profile_enable", "pipe_profile_read", "pipe_launch_count", "pipe_recon_visits",
-           "features_tile_noalloc", "pipe_autotune_info"]
+           "features_tile_noalloc", "pipe_autotune_info", "morph_open_tile"]
 NOALLOC_MAX_OBJECTS = 65536
 
 
@@ -78,6 +78,7 @@ def lib():
     L.seg_tile.argtypes = [vp, vp, ci, ci, sz, vp, vp, vp, vp, vp]
     L.features_tile.argtypes = [vp, vp, vp, ci, ci, ci, vp, vp]
     L.seg_features_batch.argtypes = [vp, ctypes.POINTER(TileDevC), ci, vp]
+    L.morph_open_tile.argtypes = [vp, vp, ci, ci, ci, vp, vp]
     L.batch_submit.argtypes = [vp, ctypes.POINTER(TileDesc), ci, ctypes.POINTER(u64)]
     L.batch_poll.argtypes = [vp, u64, ctypes.POINTER(ci), ctypes.POINTER(TileResult)]
     L.pipe_status_read.argtypes = [vp]
@@ -169,6 +170,15 @@ class Pipe:
         rc = lib().features_tile(self.h, hem8.data_ptr(), labels.data_ptr(), W, H, int(n_objects),
                                  feats.data_ptr() if feats is not None else None, _stream_ptr(stream))
         _check(rc, "features_tile")
+
+    def morph_open(self, src, dst, radius=9, stream=None):
+        """Opening of a (H, W) uint8 device tensor by the disk of the given
+        radius (Table I "Morph. Open": 19x19 disk, radius 9) into dst."""
+        H, W = src.shape
+        if tuple(dst.shape) != (H, W) or not src.is_contiguous() or not dst.is_contiguous():
+            raise ValueError("src and dst must be contiguous (H, W) uint8 planes")
+        rc = lib().morph_open_tile(self.h, src.data_ptr(), W, H, int(radius), dst.data_ptr(), _stream_ptr(stream))
+        _check(rc, "morph_open_tile")
 
     # ---- batched form ---------------------------------------------------
     def seg_features_batch(self, tiles, stream=None):

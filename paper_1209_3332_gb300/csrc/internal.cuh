@@ -15,6 +15,7 @@ constexpr int CB_THREADS = 256;
 constexpr int CCL_WARPS = 4;      // labelling blocks (one per warp) per CTA
 constexpr int RL_CAP = 512;       // root-list slots per labelling block
 constexpr int NFEAT = 15;
+constexpr int MORPH_RMAX = 15;   // largest disk radius of the opening (chords of up to 31 pixels)
 
 // worklist tile states
 constexpr int WL_IDLE = 0, WL_QUEUED = 1, WL_RUNNING = 2, WL_DIRTY = 3;
@@ -114,6 +115,10 @@ void launch_recon(const Launch& L, int grid_cap, cudaStream_t s, Profiler* pf);
 void launch_label(const Launch& L, int want_bbox, int max_objects, int sms, cudaStream_t s, Profiler* pf);
 size_t edt_rows_smem(int RB, int Wmax);
 void launch_edt(const Launch& L, int RB, int Wmax, cudaStream_t s, Profiler* pf);
+size_t morph_open_smem(int r);
+// tmp: a W x H scratch plane (the radius-9 form runs two passes through it); may be null
+void launch_morph_open(const uint8_t* src, uint8_t* dst, uint8_t* tmp, int W, int H, int r, cudaStream_t s,
+                       Profiler* pf);
 void launch_features_plain(const uint8_t* hem8, const int32_t* labels, int W, int H, int K, float* feats,
                            int4* bbox, int sms, cudaStream_t s, Profiler* pf);
 void launch_features_batched(const Launch& L, int grid, cudaStream_t s, Profiler* pf);

@@ -304,6 +304,7 @@ struct pipe_s {
     TileDev last_plain{};
     bool have_last = false;
     DevBuf fbbox;
+    DevBuf morph_tmp;  // scratch plane of morph_open_tile
     // batched form
     LaunchCtx batch;
     GraphCache graphs;
@@ -669,6 +670,7 @@ void pipe_destroy(pipe_t p) {
     rel(p->plain);
     rel(p->batch);
     p->fbbox.release();
+    p->morph_tmp.release();
     for (auto& c : p->ctxs) {
         rel(c->lc);
         c->dev.release();
@@ -732,6 +734,24 @@ int features_tile(pipe_t p, const uint8_t* hem8_dev, const int32_t* labels_dev, 
     }
     launch_features_plain(hem8_dev, labels_dev, W, H, n_objects, feats_dev, (int4*)p->fbbox.p, p->sms, s,
                           &p->prof);
+    CK(cudaGetLastError());
+    return PIPE_OK;
+}
+
+int morph_open_tile(pipe_t p, const uint8_t* src_dev, int W, int H, int radius, uint8_t* dst_dev,
+                    pipe_stream_t stream) {
+    if (!p || !src_dev || !dst_dev || radius < 0 || radius > MORPH_RMAX) return PIPE_EINVAL;
+    if (!valid_size(W, H)) return PIPE_EINVAL;
+    const size_t N = (size_t)W * H;
+    if (src_dev < dst_dev + N && dst_dev < src_dev + N) return PIPE_EINVAL;  // the planes overlap
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaSetDevice(p->device));
+    if (p->morph_tmp.n < N) {  // the scratch plane of the two-pass form grows to the largest plane seen
+        CK(cudaStreamSynchronize(s));
+        const int rc = p->morph_tmp.ensure(N);
+        if (rc) return rc;
+    }
+    launch_morph_open(src_dev, dst_dev, (uint8_t*)p->morph_tmp.p, W, H, radius, s, &p->prof);
     CK(cudaGetLastError());
     return PIPE_OK;
 }
