@@ -113,7 +113,7 @@ __global__ void __launch_bounds__(256) k_morph_open(const uint8_t* __restrict__ 
 //    accumulator of row t - dy by C_{w(dy)} for every dy, and the
 //    accumulator of row t - R is then complete.  The step loop is unrolled
 //    2R + 1 times so that every accumulator index is a constant, and input
-//    rows are fetched one loop trip ahead.
+//    rows are fetched two loop trips ahead.
 // Pixels outside the image take no part: they enter as 255 for a min and 0
 // for a max.
 constexpr int MS_WARPS = 4, MS_SW = 64, MS_SEG = 128;
@@ -163,12 +163,13 @@ __global__ void __launch_bounds__(MS_WARPS * 32) k_morph_stream(const uint8_t* _
                    ? __ldg(reinterpret_cast<const unsigned int*>(src + (size_t)t * W + cw))
                    : NEUTRAL_WORD;
     };
-    // slot u of the unrolled step loop holds the row that step u consumes:
-    // a row is fetched one loop trip (2R + 1 rows) ahead, and no register
-    // whose load may still be in flight is ever copied
-    uint32_t pf[K];
+    // slot u of the unrolled step loop holds the row that step u consumes
+    // (pf) and the one after it (pf2): a row is fetched two loop trips
+    // (4R + 2 rows) ahead and moves from pf2 to pf after one trip, when its
+    // load has long completed (one trip ahead left loads exposed)
+    uint32_t pf[K], pf2[K];
 #pragma unroll
-    for (int q = 0; q < K; q++) pf[q] = fetch(t0 + q);
+    for (int q = 0; q < K; q++) { pf[q] = fetch(t0 + q); pf2[q] = fetch(t0 + K + q); }
     uint32_t acc[K];
 #pragma unroll
     for (int k = 0; k < K; k++) acc[k] = NEUTRAL;
@@ -178,7 +179,8 @@ __global__ void __launch_bounds__(MS_WARPS * 32) k_morph_stream(const uint8_t* _
             const int t = tb + u;
             if (t >= t1) break;
             const uint32_t w = pf[u];
-            pf[u] = fetch(t + K);
+            pf[u] = pf2[u];
+            pf2[u] = fetch(t + 2 * K);
             // the row's 16-bit pixels: ev[j] = column xs - A + j, od[j] = ev[j + 1]
             const uint32_t e0 = __byte_perm(w, 0u, 0x4140), e1 = __byte_perm(w, 0u, 0x4342);
             const uint32_t ne0 = __shfl_down_sync(0xffffffffu, e0, 1);
