@@ -61,6 +61,8 @@ def _load():
         L.oracle_morph_disk.argtypes = [vp, ci, ci, ci, ci, vp]
         L.oracle_morph_open.argtypes = [vp, ci, ci, ci, vp]
         L.oracle_morph_open.restype = ci
+        L.oracle_watershed.argtypes = [vp, vp, ci, ci, ci, vp]
+        L.oracle_watershed.restype = ci
         _lib = L
     return _lib
 
@@ -209,3 +211,16 @@ def morph_open(src, r=9):
     if _load().oracle_morph_open(p, W, H, r, out.ctypes.data) != 0:
         raise ValueError("bad arguments")
     return out
+
+
+def watershed(labels, edt, h=1):
+    """Watershed split of labelled objects on the distance transform (Table I
+    "Pre-Watershed" + "Watershed"); returns (split labels, number of basins)."""
+    labels, pl = _c(labels, np.int32)
+    edt, pe = _c(edt, np.int32)
+    H, W = labels.shape
+    out = np.empty((H, W), np.int32)
+    n = _load().oracle_watershed(pl, pe, W, H, h, out.ctypes.data)
+    if n < 0:
+        raise ValueError("bad arguments")
+    return out, n

@@ -562,6 +562,147 @@ int oracle_morph_open(const uint8_t* src, int W, int H, int r, uint8_t* out) {
     return 0;
 }
 
+/* ---- watershed split of objects (Table I "Pre-Watershed", "Watershed") -------
+ * Readings: the paper names the operations only.  Markers are the regional
+ * maxima of the h-maxima of the integer distance; flooding is by the squared
+ * distance in synchronous waves with an explicit tie rule, so that the result
+ * is one exact function of the input (see oracle.h). */
+static int isqrt_floor(long long v) {
+    if (v <= 0) return 0;
+    long long r = (long long)sqrt((double)v);
+    while (r * r > v) r--;
+    while ((r + 1) * (r + 1) <= v) r++;
+    return (int)r;
+}
+
+int oracle_watershed(const int32_t* labels, const int32_t* edt, int W, int H, int h, int32_t* out) {
+    if (W <= 0 || H <= 0 || h < 0 || !labels || !edt || !out) return -1;
+    const size_t N = (size_t)W * H;
+    uint8_t* d = (uint8_t*)malloc(N);
+    uint8_t* m = (uint8_t*)malloc(N);
+    uint8_t* R = (uint8_t*)malloc(N);
+    int32_t* name = (int32_t*)malloc(N * sizeof(int32_t));   /* marker / basin name, -1 unset */
+    int32_t* nxt = (int32_t*)malloc(N * sizeof(int32_t));
+    int32_t* stk = (int32_t*)malloc(N * sizeof(int32_t));
+    if (!d || !m || !R || !name || !nxt || !stk) {
+        free(d); free(m); free(R); free(name); free(nxt); free(stk);
+        return -1;
+    }
+    for (size_t i = 0; i < N; i++) {
+        const int v = labels[i] > 0 ? isqrt_floor(edt[i]) : 0;
+        d[i] = (uint8_t)(v > 255 ? 255 : v);
+        m[i] = (uint8_t)(d[i] > h ? d[i] - h : 0);
+        name[i] = -1;
+    }
+    oracle_recon(m, d, W, H, R, NULL);
+    /* markers: flood each plateau of equal R (object pixels, 8-connected) from
+       its first pixel in raster order; it is a marker if no pixel of it has a
+       higher neighbour */
+    int32_t* plateau = nxt;  /* reused as the plateau id of each pixel */
+    for (size_t i = 0; i < N; i++) plateau[i] = -1;
+    for (size_t i0 = 0; i0 < N; i0++) {
+        if (labels[i0] <= 0 || plateau[i0] >= 0) continue;
+        int top = 0, maximal = 1;
+        size_t cnt = 0;
+        stk[top++] = (int32_t)i0;
+        plateau[i0] = (int32_t)i0;
+        while (top) {
+            const int32_t p = stk[--top];
+            cnt++;
+            const int y = p / W, x = p - y * W;
+            for (int dy = -1; dy <= 1; dy++)
+                for (int dx = -1; dx <= 1; dx++) {
+                    if (!dy && !dx) continue;
+                    const int yy = y + dy, xx = x + dx;
+                    if (yy < 0 || yy >= H || xx < 0 || xx >= W) continue;
+                    const size_t q = (size_t)yy * W + xx;
+                    if (labels[q] <= 0) continue;
+                    if (R[q] > R[p]) maximal = 0;
+                    if (R[q] == R[p] && plateau[q] < 0) {
+                        plateau[q] = (int32_t)i0;
+                        stk[top++] = (int32_t)q;
+                    }
+                }
+        }
+        (void)cnt;
+        if (maximal) name[i0] = (int32_t)i0;  /* provisional: spread below */
+    }
+    for (size_t i = 0; i < N; i++)
+        if (labels[i] > 0 && name[plateau[i]] == plateau[i]) name[i] = plateau[i];
+    /* flooding in synchronous waves */
+    for (;;) {
+        long long L = -1;
+        for (size_t i = 0; i < N; i++) {
+            if (labels[i] <= 0 || name[i] >= 0) continue;
+            const int y = (int)(i / W), x = (int)(i - (size_t)y * W);
+            int front = 0;
+            for (int dy = -1; dy <= 1 && !front; dy++)
+                for (int dx = -1; dx <= 1; dx++) {
+                    const int yy = y + dy, xx = x + dx;
+                    if ((!dy && !dx) || yy < 0 || yy >= H || xx < 0 || xx >= W) continue;
+                    if (name[(size_t)yy * W + xx] >= 0) { front = 1; break; }
+                }
+            if (front && edt[i] > L) L = edt[i];
+        }
+        if (L < 0) break;
+        for (;;) {
+            int n = 0;
+            for (size_t i = 0; i < N; i++) {
+                nxt[i] = -1;
+                if (labels[i] <= 0 || name[i] >= 0 || edt[i] < L) continue;
+                const int y = (int)(i / W), x = (int)(i - (size_t)y * W);
+                int best = -1;
+                long long bd = -1;
+                for (int dy = -1; dy <= 1; dy++)
+                    for (int dx = -1; dx <= 1; dx++) {
+                        const int yy = y + dy, xx = x + dx;
+                        if ((!dy && !dx) || yy < 0 || yy >= H || xx < 0 || xx >= W) continue;
+                        const size_t q = (size_t)yy * W + xx;
+                        if (name[q] < 0) continue;
+                        if (edt[q] > bd || (edt[q] == bd && name[q] < best)) {
+                            bd = edt[q];
+                            best = name[q];
+                        }
+                    }
+                if (best >= 0) { nxt[i] = best; n++; }
+            }
+            if (!n) break;
+            for (size_t i = 0; i < N; i++)
+                if (nxt[i] >= 0) name[i] = nxt[i];
+        }
+    }
+    /* numbering: per object (input label order), basins by first pixel */
+    int K = 0;
+    for (size_t i = 0; i < N; i++)
+        if (labels[i] > K) K = labels[i];
+    int* cnt = (int*)calloc((size_t)K + 2, sizeof(int));
+    int32_t* first = stk;  /* first[name] = 1 when pixel name's basin starts at pixel i: via a rank map */
+    for (size_t i = 0; i < N; i++) first[i] = 0;
+    /* rank of a basin inside its object = number of basins of that object
+       whose first pixel precedes it; basins are met in raster order of their
+       first pixels, so a running count per object gives the rank */
+    int32_t* rank = nxt;
+    for (size_t i = 0; i < N; i++) rank[i] = 0;
+    for (size_t i = 0; i < N; i++) {
+        if (labels[i] <= 0) continue;
+        const int32_t b = name[i];
+        if (!first[b]) {
+            first[b] = 1;
+            rank[b] = ++cnt[labels[i]];
+        }
+    }
+    int* off = (int*)calloc((size_t)K + 2, sizeof(int));
+    int total = 0;
+    for (int k = 1; k <= K; k++) {
+        off[k] = total;
+        total += cnt[k];
+    }
+    for (size_t i = 0; i < N; i++) out[i] = labels[i] > 0 ? off[labels[i]] + rank[name[i]] : 0;
+    free(cnt); free(off);
+    free(d); free(m); free(R); free(name); free(nxt); free(stk);
+    return total;
+}
+
 int oracle_seg(const uint8_t* rgb, int W, int H, size_t pitch, int h, int thr, int amin, int amax,
                uint8_t* hem8, uint8_t* R, uint8_t* fg, uint8_t* filled, int32_t* labels,
                int32_t* edt) {

@@ -100,6 +100,24 @@ void oracle_morph_disk(const uint8_t* src, int W, int H, int r, int is_max, uint
  * the dilation of the erosion.  Returns -1 on bad arguments. */
 int oracle_morph_open(const uint8_t* src, int W, int H, int r, uint8_t* out);
 
+/* Watershed split of labelled objects on the distance transform (Table I
+ * "Pre-Watershed" and "Watershed"; the paper names the operations only, and
+ * states that its CPU and GPU versions differ).  Definition:
+ *  d = min(255, floor(sqrt(edt))) on object pixels (labels > 0), 0 elsewhere;
+ *  R = reconstruction by dilation, 8-connected, of max(d - h, 0) under d;
+ *  markers = maximal 8-connected plateaus of equal R among object pixels
+ *    with no 8-neighbour of larger R; a marker is named by the raster index
+ *    of its first pixel;
+ *  flooding in synchronous waves: with F the unlabelled object pixels that
+ *    have a labelled 8-neighbour and L = max of edt over F, every pixel of F
+ *    with edt >= L takes, in one wave, the name of its labelled 8-neighbour
+ *    with the largest edt (then the smallest name); waves repeat at L until
+ *    none qualifies, then L is taken again from the new F;
+ *  out = basins numbered object by object in the order of the input labels,
+ *    within an object in raster order of each basin's first pixel; 0 on
+ *    background.  Returns the number of basins, or -1 on bad arguments. */
+int oracle_watershed(const int32_t* labels, const int32_t* edt, int W, int H, int h, int32_t* out);
+
 /* Whole segmentation: deconv -> h-dome -> fill holes -> label -> EDT.
  * Any of R, fg, filled may be NULL.  Returns K, or -1 on bad arguments. */
 int oracle_seg(const uint8_t* rgb, int W, int H, size_t pitch, int h, int thr, int amin, int amax,
