@@ -564,9 +564,10 @@ int oracle_morph_open(const uint8_t* src, int W, int H, int r, uint8_t* out) {
 
 /* ---- watershed split of objects (Table I "Pre-Watershed", "Watershed") -------
  * Readings: the paper names the operations only.  Markers are the regional
- * maxima of the h-maxima of the integer distance; flooding is by the squared
- * distance in synchronous waves with an explicit tie rule, so that the result
- * is one exact function of the input (see oracle.h). */
+ * maxima of the h-maxima of the integer distance; flooding goes down the
+ * levels of the integer distance in synchronous waves, with ties decided by
+ * the squared distance and then the marker's name, so that the result is one
+ * exact function of the input (see oracle.h). */
 static int isqrt_floor(long long v) {
     if (v <= 0) return 0;
     long long r = (long long)sqrt((double)v);
@@ -642,14 +643,14 @@ int oracle_watershed(const int32_t* labels, const int32_t* edt, int W, int H, in
                     if ((!dy && !dx) || yy < 0 || yy >= H || xx < 0 || xx >= W) continue;
                     if (name[(size_t)yy * W + xx] >= 0) { front = 1; break; }
                 }
-            if (front && edt[i] > L) L = edt[i];
+            if (front && d[i] > L) L = d[i];
         }
         if (L < 0) break;
         for (;;) {
             int n = 0;
             for (size_t i = 0; i < N; i++) {
                 nxt[i] = -1;
-                if (labels[i] <= 0 || name[i] >= 0 || edt[i] < L) continue;
+                if (labels[i] <= 0 || name[i] >= 0 || d[i] < L) continue;
                 const int y = (int)(i / W), x = (int)(i - (size_t)y * W);
                 int best = -1;
                 long long bd = -1;

@@ -109,8 +109,8 @@ int oracle_morph_open(const uint8_t* src, int W, int H, int r, uint8_t* out);
  *    with no 8-neighbour of larger R; a marker is named by the raster index
  *    of its first pixel;
  *  flooding in synchronous waves: with F the unlabelled object pixels that
- *    have a labelled 8-neighbour and L = max of edt over F, every pixel of F
- *    with edt >= L takes, in one wave, the name of its labelled 8-neighbour
+ *    have a labelled 8-neighbour and L = max of d over F, every pixel of F
+ *    with d >= L takes, in one wave, the name of its labelled 8-neighbour
  *    with the largest edt (then the smallest name); waves repeat at L until
  *    none qualifies, then L is taken again from the new F;
  *  out = basins numbered object by object in the order of the input labels,
