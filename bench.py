@@ -340,6 +340,62 @@ def morph_open_run(torch, pipe, stream, planes, steps, hbm_peak, want_cpu):
     return out
 
 
+WS_H = 1                  # marker height of the watershed split (h-maxima of the integer distance)
+WS_BYTES_PER_PX = 12      # minimal pass: labels and EDT read once, the split plane written once
+
+
+def watershed_run(torch, pipe, stream, bufs, steps, hbm_peak, want_cpu):
+    """The watershed split (Table I "Pre-Watershed" + "Watershed") of every
+    tile of the batch through watershed_tile, on the labels and EDT the
+    batched step wrote, timed with CUDA events on the launching stream (the
+    planes of the batch are far larger than L2).  Per-kernel times come from
+    the pipe's own events around each launch."""
+    ks = [int(b["n_objects"].item()) for b in bufs]
+    outs = [torch.empty_like(b["labels"]) for b in bufs]
+    nb = torch.zeros(len(bufs), dtype=torch.int32, device=bufs[0]["labels"].device)
+
+    def step():
+        for i, b in enumerate(bufs):
+            pipe.watershed(b["labels"], b["edt"], ks[i], outs[i], nb[i:i + 1], h=WS_H, stream=stream)
+    for _ in range(3):
+        step()
+    ms = timed(torch, stream, step, steps) / steps
+    before = pipe.profile_read()
+    pipe.profile(True)
+    step()
+    torch.cuda.synchronize()
+    after = pipe.profile_read()
+    pipe.profile(False)
+    kern = {}
+    for k, (c, t) in after.items():
+        c0, t0 = before.get(k, (0, 0.0))
+        if c > c0 and (k.startswith("ws_") or k.startswith("feat_bbox")):
+            kern[k] = round((t - t0) / (c - c0), 4)
+    n = len(bufs)
+    px = sum(b["labels"].numel() for b in bufs)
+    gbs = WS_BYTES_PER_PX * px / (ms / 1000.0) / 1e9
+    out = {"h": WS_H, "tiles_per_step": n, "tile": list(bufs[0]["labels"].shape), "ms_per_step": ms,
+           "tiles_per_s": n * 1000.0 / ms, "objects_per_step": sum(ks),
+           "basins_per_step": int(nb.sum().item()), "kernels_ms": kern,
+           "hbm": {"achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+                   "alg_bytes_per_px": WS_BYTES_PER_PX,
+                   "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"},
+           "parity": "bit-exact with the oracle (tests/test_gpu_watershed.py)"}
+    if want_cpu:
+        import time
+        import oracle
+        rows = 512                                              # a band of the first tile
+        lab = bufs[0]["labels"][:rows].cpu().numpy()
+        edt = bufs[0]["edt"][:rows].cpu().numpy()
+        t = time.perf_counter()
+        oracle.watershed(lab, edt, WS_H)
+        sec = time.perf_counter() - t
+        out["cpu_oracle"] = {"tiles_per_s": lab.size / bufs[0]["labels"].numel() / sec, "cores": 1,
+                             "sample": "the oracle on the first %d rows of tile 0 (%d x %d pixels), %.2f s, scaled"
+                                       % (rows, lab.shape[0], lab.shape[1], sec)}
+    return out
+
+
 def peaks_clock():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -578,6 +634,9 @@ def run_ours(args, world, rank, local):
     # ---- the step before the path: opening by the 19x19 disk ------------------
     line["morph_open"] = morph_open_run(torch, pipe, stream, [b["hem8"] for b in bufs], max(3, args.steps // 2),
                                         peak, rank == 0 and world == 1 and not args.no_cpu)
+    # ---- the step after the path: watershed split of the objects -------------
+    line["watershed"] = watershed_run(torch, pipe, stream, bufs, max(3, args.steps // 2), peak,
+                                      rank == 0 and world == 1 and not args.no_cpu)
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(host[0])
     if rank == 0:

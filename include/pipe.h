@@ -168,6 +168,41 @@ int seg_features_batch(pipe_t p, const tile_dev* tiles, int n, pipe_stream_t str
 int morph_open_tile(pipe_t p, const uint8_t* src_dev, int W, int H, int radius, uint8_t* dst_dev,
                     pipe_stream_t stream);
 
+/* Watershed split of the labelled objects on the distance transform (Table I
+ * "Pre-Watershed": distance transform and markers; "Watershed").  The paper
+ * names the operations only (and notes that its CPU and GPU versions give
+ * different results); the definition computed here, per object k of the
+ * label plane, is:
+ *   d = min(255, floor(sqrt(edt))) on the object, 0 elsewhere;
+ *   R = reconstruction by dilation, 8-connected, of max(d - h, 0) under d
+ *       (the h-maxima of d);
+ *   markers = maximal 8-connected plateaus of equal R with no 8-neighbour of
+ *       larger R, each named by its first pixel in row-major order;
+ *   flooding in synchronous waves: with F the unnamed object pixels having
+ *       a named 8-neighbour and L = max d over F, every pixel of F with
+ *       d >= L takes, in one wave, the name of its named neighbour of largest
+ *       edt (ties: smallest name); waves repeat at L while any pixel is
+ *       named, then L is taken again from the new F;
+ *   out = basins numbered 1..n_basins object by object in label order, and
+ *       within an object by the row-major order of each basin's first pixel;
+ *       0 where labels is 0 or above n_objects.
+ *  labels_dev, edt_dev: W x H int32 planes as written by seg_tile (edt must
+ *    be the exact squared distance transform of labels: > 0 on every object
+ *    pixel); n_objects = K of seg_tile; 0 <= h <= 255 (the marker height).
+ *  out_dev: W x H int32, caller-owned, must not overlap labels or edt;
+ *  n_basins_dev: one int32 receiving the number of basins.
+ *  Objects whose bounding box with a 1-pixel margin exceeds 1024 pixels run
+ *  on a pipe-owned side stream (forked from and joined back to `stream`, so
+ *  the call stays in `stream` order); boxes beyond 7021 pixels are processed
+ *  from image-sized scratch planes the pipe owns (10 bytes per pixel,
+ *  allocated on the first call of a larger size, which synchronises
+ *  `stream`).  A flood that would exceed its wave bound (box pixels + 300)
+ *  leaves that object 0 and sets PIPE_EOVERFLOW in the status word.
+ * Returns PIPE_EINVAL on a bad argument (nothing is launched); otherwise
+ * the work is asynchronous on `stream`. */
+int watershed_tile(pipe_t p, const int32_t* labels_dev, const int32_t* edt_dev, int W, int H, int n_objects,
+                   int h, int32_t* out_dev, int32_t* n_basins_dev, pipe_stream_t stream);
+
 /* Served form (Sec. IV-D prefetching and asynchronous copy): tiles in host
  * memory are admitted as slots and HBM budget allow, uploaded on copy
  * streams overlapped with compute, processed, and their results downloaded.

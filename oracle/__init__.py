@@ -15,6 +15,8 @@ import numpy as np
 _here = os.path.dirname(os.path.abspath(__file__))
 _lib = None
 NFEAT = 15
+CANNY_LOW, CANNY_HIGH = 40, 120   # hysteresis thresholds on the L1 Sobel magnitude of hem8 (our reading)
+EDGE_R = 3                        # radius of the disk dilation the edge counts cover (our reading)
 
 u8p = ctypes.POINTER(ctypes.c_uint8)
 i32p = ctypes.POINTER(ctypes.c_int32)
@@ -63,6 +65,10 @@ def _load():
         L.oracle_morph_open.restype = ci
         L.oracle_watershed.argtypes = [vp, vp, ci, ci, ci, vp]
         L.oracle_watershed.restype = ci
+        L.oracle_canny.argtypes = [vp, ci, ci, ci, ci, vp, vp, vp]
+        L.oracle_canny.restype = ctypes.c_longlong
+        L.oracle_edge_counts.argtypes = [vp, vp, ci, ci, ci, ci, vp]
+        L.oracle_edge_counts.restype = None
         _lib = L
     return _lib
 
@@ -224,3 +230,29 @@ def watershed(labels, edt, h=1):
     if n < 0:
         raise ValueError("bad arguments")
     return out, n
+
+
+def canny(img, low=CANNY_LOW, high=CANNY_HIGH, detail=False):
+    """Canny edge map (Sec. V-A feature-stage transform; Table I "Features
+    comp."): uint8 plane of 0/1.  detail=True also returns the L1 Sobel
+    magnitude and the class plane (0, 1 candidate, 2 strong)."""
+    img, p = _c(img, np.uint8)
+    H, W = img.shape
+    out = np.empty((H, W), np.uint8)
+    mag = np.empty((H, W), np.int32)
+    cls = np.empty((H, W), np.uint8)
+    n = _load().oracle_canny(p, W, H, int(low), int(high), out.ctypes.data, mag.ctypes.data, cls.ctypes.data)
+    if n < 0:
+        raise ValueError("bad arguments")
+    return (out, mag, cls) if detail else out
+
+
+def edge_counts(edges, labels, K, r=EDGE_R):
+    """Edge pixels within each object's disk dilation of radius r (Sec. II
+    "edge" features): int32 [K]."""
+    edges, pe = _c(edges, np.uint8)
+    labels, pl = _c(labels, np.int32)
+    H, W = labels.shape
+    cnt = np.zeros(max(K, 1), np.int32)
+    _load().oracle_edge_counts(pe, pl, W, H, int(K), int(r), cnt.ctypes.data)
+    return cnt[:K]

@@ -704,6 +704,111 @@ int oracle_watershed(const int32_t* labels, const int32_t* edt, int W, int H, in
     return total;
 }
 
+/* ---- Canny edges (Sec. V-A feature-stage transform; Table I "Features
+ * comp.") -- readings in oracle.h ------------------------------------------ */
+
+static void sobel_gxgy(const uint8_t* I, int W, int H, int y, int x, int* gx, int* gy) {
+    int v[3][3];
+    for (int dy = -1; dy <= 1; dy++)
+        for (int dx = -1; dx <= 1; dx++)
+            v[dy + 1][dx + 1] = I[(size_t)clampi(y + dy, 0, H - 1) * W + clampi(x + dx, 0, W - 1)];
+    *gx = (v[0][2] + 2 * v[1][2] + v[2][2]) - (v[0][0] + 2 * v[1][0] + v[2][0]);
+    *gy = (v[2][0] + 2 * v[2][1] + v[2][2]) - (v[0][0] + 2 * v[0][1] + v[0][2]);
+}
+
+long long oracle_canny(const uint8_t* I, int W, int H, int low, int high, uint8_t* out, int32_t* mag,
+                       uint8_t* cls) {
+    if (W < 1 || H < 1 || low < 0 || high < low || !I || !out) return -1;
+    const size_t N = (size_t)W * H;
+    int32_t* m = (int32_t*)malloc(N * sizeof(int32_t));
+    int32_t* gxs = (int32_t*)malloc(N * sizeof(int32_t));
+    int32_t* gys = (int32_t*)malloc(N * sizeof(int32_t));
+    uint8_t* c = (uint8_t*)malloc(N);
+    int32_t* stk = (int32_t*)malloc(N * sizeof(int32_t));
+    if (!m || !gxs || !gys || !c || !stk) {
+        free(m); free(gxs); free(gys); free(c); free(stk);
+        return -1;
+    }
+    for (int y = 0; y < H; y++)
+        for (int x = 0; x < W; x++) {
+            int gx, gy;
+            sobel_gxgy(I, W, H, y, x, &gx, &gy);
+            const size_t i = (size_t)y * W + x;
+            gxs[i] = gx;
+            gys[i] = gy;
+            m[i] = abs(gx) + abs(gy);
+        }
+    for (int y = 0; y < H; y++)
+        for (int x = 0; x < W; x++) {
+            const size_t i = (size_t)y * W + x;
+            const long long ax = abs(gxs[i]), ay = abs(gys[i]);
+            int ay_, ax_, by_, bx_;  /* offsets of a and b */
+            if ((ax + ay) * (ax + ay) < 2 * ax * ax) {
+                ay_ = 0; ax_ = -1; by_ = 0; bx_ = 1;
+            } else if (ay > ax && (ay - ax) * (ay - ax) > 2 * ax * ax) {
+                ay_ = -1; ax_ = 0; by_ = 1; bx_ = 0;
+            } else if ((long long)gxs[i] * gys[i] > 0) {
+                ay_ = -1; ax_ = -1; by_ = 1; bx_ = 1;
+            } else {
+                ay_ = -1; ax_ = 1; by_ = 1; bx_ = -1;
+            }
+            const int ya = y + ay_, xa = x + ax_, yb = y + by_, xb = x + bx_;
+            const int ma = (ya >= 0 && ya < H && xa >= 0 && xa < W) ? m[(size_t)ya * W + xa] : 0;
+            const int mb = (yb >= 0 && yb < H && xb >= 0 && xb < W) ? m[(size_t)yb * W + xb] : 0;
+            const int keep = m[i] > ma && m[i] >= mb;
+            c[i] = (uint8_t)(keep && m[i] > high ? 2 : (keep && m[i] > low ? 1 : 0));
+        }
+    /* hysteresis: flood from every strong pixel through candidates, 8-connected */
+    memset(out, 0, N);
+    long long n = 0;
+    for (size_t i0 = 0; i0 < N; i0++) {
+        if (c[i0] != 2 || out[i0]) continue;
+        int top = 0;
+        stk[top++] = (int32_t)i0;
+        out[i0] = 1;
+        while (top) {
+            const int32_t p = stk[--top];
+            n++;
+            const int y = p / W, x = p - y * W;
+            for (int dy = -1; dy <= 1; dy++)
+                for (int dx = -1; dx <= 1; dx++) {
+                    const int yy = y + dy, xx = x + dx;
+                    if ((!dy && !dx) || yy < 0 || yy >= H || xx < 0 || xx >= W) continue;
+                    const size_t q = (size_t)yy * W + xx;
+                    if (c[q] && !out[q]) {
+                        out[q] = 1;
+                        stk[top++] = (int32_t)q;
+                    }
+                }
+        }
+    }
+    if (mag) memcpy(mag, m, N * sizeof(int32_t));
+    if (cls) memcpy(cls, c, N);
+    free(m); free(gxs); free(gys); free(c); free(stk);
+    return n;
+}
+
+void oracle_edge_counts(const uint8_t* edges, const int32_t* labels, int W, int H, int K, int r, int32_t* cnt) {
+    for (int k = 0; k < K; k++) cnt[k] = 0;
+    for (int y = 0; y < H; y++)
+        for (int x = 0; x < W; x++) {
+            if (!edges[(size_t)y * W + x]) continue;
+            /* the distinct labels within the disk around the pixel, each counted once */
+            int seen[64], ns = 0;
+            for (int dy = -r; dy <= r; dy++)
+                for (int dx = -r; dx <= r; dx++) {
+                    const int yy = y + dy, xx = x + dx;
+                    if (dx * dx + dy * dy > r * r || yy < 0 || yy >= H || xx < 0 || xx >= W) continue;
+                    const int l = labels[(size_t)yy * W + xx];
+                    if (l < 1 || l > K) continue;
+                    int dup = 0;
+                    for (int j = 0; j < ns; j++) dup |= seen[j] == l;
+                    if (!dup && ns < 64) seen[ns++] = l;
+                }
+            for (int j = 0; j < ns; j++) cnt[seen[j] - 1]++;
+        }
+}
+
 int oracle_seg(const uint8_t* rgb, int W, int H, size_t pitch, int h, int thr, int amin, int amax,
                uint8_t* hem8, uint8_t* R, uint8_t* fg, uint8_t* filled, int32_t* labels,
                int32_t* edt) {

@@ -118,6 +118,38 @@ int oracle_morph_open(const uint8_t* src, int W, int H, int r, uint8_t* out);
  *    background.  Returns the number of basins, or -1 on bad arguments. */
 int oracle_watershed(const int32_t* labels, const int32_t* edt, int W, int H, int h, int32_t* out);
 
+/* Canny edge map of a uint8 plane (Sec. V-A lists Canny among the
+ * feature-stage transforms applied to the deconvolved image; Table I
+ * "Features comp." uses OpenCV's Canny; the paper gives no parameter).
+ * Definition:
+ *  gx, gy = 3x3 Sobel with replicated border (the gradient of the features);
+ *  m = |gx| + |gy|;
+ *  sector of the gradient, with ax = |gx|, ay = |gy| (exact integer tests):
+ *    horizontal if ay < ax tan(22.5 deg)  <=>  (ax + ay)^2 < 2 ax^2;
+ *    vertical   if ay > ax tan(67.5 deg)  <=>  ay > ax and (ay - ax)^2 > 2 ax^2;
+ *    otherwise diagonal, along (+x,+y) if gx gy > 0, along (+x,-y) if < 0;
+ *  the two neighbours along the sector: a = (y, x-1), b = (y, x+1) for the
+ *    horizontal sector; a = (y-1, x), b = (y+1, x) for the vertical one;
+ *    a = (y-1, x-1), b = (y+1, x+1) along (+x,+y); a = (y-1, x+1),
+ *    b = (y+1, x-1) along (+x,-y); m outside the image counts as 0;
+ *  non-maximum suppression: p survives iff m(p) > m(a) and m(p) >= m(b);
+ *  candidates: survivors with m > low; strong: survivors with m > high;
+ *  edges: candidates 8-connected through candidates to a strong pixel.
+ * out = 1 on edges, 0 elsewhere.  mag (may be NULL) receives m; cls (may be
+ * NULL) receives 0 / 1 (candidate) / 2 (strong).  Returns -1 on bad
+ * arguments (W, H < 1, low < 0 or high < low), else the number of edge
+ * pixels. */
+long long oracle_canny(const uint8_t* I, int W, int H, int low, int high, uint8_t* out, int32_t* mag,
+                       uint8_t* cls);
+
+/* Edge features of the objects (Sec. II "edge" feature family): cnt[k-1] =
+ * the number of edge pixels (edges == 1) within the disk dilation of object
+ * k, i.e. at an offset (dx, dy) with dx^2 + dy^2 <= r^2 from one of its
+ * pixels, k = 1..K (0 <= r <= 4).  The steepest gradient of a nucleus lies
+ * on its visible border, a few pixels outside the dome-top mask the
+ * segmentation keeps; a pixel near two objects counts for both. */
+void oracle_edge_counts(const uint8_t* edges, const int32_t* labels, int W, int H, int K, int r, int32_t* cnt);
+
 /* Whole segmentation: deconv -> h-dome -> fill holes -> label -> EDT.
  * Any of R, fg, filled may be NULL.  Returns K, or -1 on bad arguments. */
 int oracle_seg(const uint8_t* rgb, int W, int H, size_t pitch, int h, int thr, int amin, int amax,

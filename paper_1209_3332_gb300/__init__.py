@@ -20,7 +20,7 @@ STATUS_NAMES = ["PIPE_OK", "PIPE_EINVAL", "PIPE_ENOMEM", "PIPE_EBUSY", "PIPE_EAG
 EXPORTS = ["pipe_default_params", "pipe_create", "pipe_destroy", "seg_tile", "features_tile",
            "seg_features_batch", "batch_submit", "batch_poll", "pipe_status_read", "pipe_debug_plane",
            "pipe_profile_enable", "pipe_profile_read", "pipe_launch_count", "pipe_recon_visits",
-           "features_tile_noalloc", "pipe_autotune_info", "morph_open_tile"]
+           "features_tile_noalloc", "pipe_autotune_info", "morph_open_tile", "watershed_tile"]
 NOALLOC_MAX_OBJECTS = 65536
 
 
@@ -79,6 +79,7 @@ def lib():
     L.features_tile.argtypes = [vp, vp, vp, ci, ci, ci, vp, vp]
     L.seg_features_batch.argtypes = [vp, ctypes.POINTER(TileDevC), ci, vp]
     L.morph_open_tile.argtypes = [vp, vp, ci, ci, ci, vp, vp]
+    L.watershed_tile.argtypes = [vp, vp, vp, ci, ci, ci, ci, vp, vp, vp]
     L.batch_submit.argtypes = [vp, ctypes.POINTER(TileDesc), ci, ctypes.POINTER(u64)]
     L.batch_poll.argtypes = [vp, u64, ctypes.POINTER(ci), ctypes.POINTER(TileResult)]
     L.pipe_status_read.argtypes = [vp]
@@ -95,7 +96,8 @@ def lib():
     L.pipe_autotune_info.argtypes = [vp, ctypes.POINTER(ci), ctypes.POINTER(ci), ctypes.POINTER(ci),
                                      ctypes.POINTER(ctypes.c_longlong)]
     for n in ("pipe_create", "seg_tile", "features_tile", "seg_features_batch", "batch_submit", "batch_poll",
-              "pipe_status_read", "pipe_debug_plane", "pipe_profile_enable", "pipe_profile_read"):
+              "pipe_status_read", "pipe_debug_plane", "pipe_profile_enable", "pipe_profile_read",
+              "morph_open_tile", "watershed_tile"):
         getattr(L, n).restype = ci
     _lib = L
     return L
@@ -179,6 +181,18 @@ class Pipe:
             raise ValueError("src and dst must be contiguous (H, W) uint8 planes")
         rc = lib().morph_open_tile(self.h, src.data_ptr(), W, H, int(radius), dst.data_ptr(), _stream_ptr(stream))
         _check(rc, "morph_open_tile")
+
+    def watershed(self, labels, edt, n_objects, out, n_basins, h=1, stream=None):
+        """Watershed split of the labelled objects (Table I "Pre-Watershed" +
+        "Watershed"): labels, edt and out are contiguous (H, W) int32 device
+        tensors, n_basins a one-element int32 device tensor."""
+        H, W = labels.shape
+        for t in (labels, edt, out):
+            if tuple(t.shape) != (H, W) or not t.is_contiguous():
+                raise ValueError("labels, edt and out must be contiguous (H, W) int32 planes")
+        rc = lib().watershed_tile(self.h, labels.data_ptr(), edt.data_ptr(), W, H, int(n_objects), int(h),
+                                  out.data_ptr(), n_basins.data_ptr(), _stream_ptr(stream))
+        _check(rc, "watershed_tile")
 
     # ---- batched form ---------------------------------------------------
     def seg_features_batch(self, tiles, stream=None):

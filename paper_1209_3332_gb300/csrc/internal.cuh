@@ -122,6 +122,15 @@ void launch_morph_open(const uint8_t* src, uint8_t* dst, uint8_t* tmp, int W, in
 void launch_features_plain(const uint8_t* hem8, const int32_t* labels, int W, int H, int K, float* feats,
                            int4* bbox, int sms, cudaStream_t s, Profiler* pf);
 void launch_features_batched(const Launch& L, int grid, cudaStream_t s, Profiler* pf);
+// per object 1..K of a label plane: its box (xmin, ymin, xmax, ymax); empty (xmax < xmin) if absent
+void launch_object_boxes(const int32_t* labels, int W, int H, int K, int4* bbox, cudaStream_t s, Profiler* pf);
+// scratch of the watershed's out-of-stage boxes: a 64-bit and a 16-bit word per pixel
+size_t watershed_scratch_bytes(int W, int H);
+// cnt: K ints (per-object basin counts, then their exclusive prefix); status: a device int
+// side: a second stream for the large boxes (fork/join through the two events)
+void launch_watershed(const int32_t* labels, const int32_t* edt, int W, int H, int K, int h, int32_t* out,
+                      int32_t* n_basins, int4* bbox, int* cnt, void* scratch, int* status, int sms,
+                      cudaStream_t s, cudaStream_t side, cudaEvent_t fork, cudaEvent_t join, Profiler* pf);
 void launch_unpack_bits(const uint32_t* bits, int W, int H, int cbx, uint8_t* out, cudaStream_t s,
                         Profiler* pf);
 

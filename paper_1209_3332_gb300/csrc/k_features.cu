@@ -372,9 +372,7 @@ __global__ void __launch_bounds__(FW * 32) k_fobj_batched(Launch L) {
     }
 }
 
-void launch_features_plain(const uint8_t* hem8, const int32_t* labels, int W, int H, int K, float* feats,
-                           int4* bbox, int sms, cudaStream_t s, Profiler* pf) {
-    if (K <= 0) return;
+void launch_object_boxes(const int32_t* labels, int W, int H, int K, int4* bbox, cudaStream_t s, Profiler* pf) {
     pf->begin("feat_bbox_init", s);
     k_fbbox_init<<<(K + 255) / 256, 256, 0, s>>>(bbox, K);
     pf->end("feat_bbox_init", s);
@@ -382,6 +380,12 @@ void launch_features_plain(const uint8_t* hem8, const int32_t* labels, int W, in
     long long warps = (long long)((W + 32 * 4 * FB_STEPS - 1) / (32 * 4 * FB_STEPS)) * H;
     k_fbbox<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, s>>>(labels, W, H, K, bbox);
     pf->end("feat_bbox", s);
+}
+
+void launch_features_plain(const uint8_t* hem8, const int32_t* labels, int W, int H, int K, float* feats,
+                           int4* bbox, int sms, cudaStream_t s, Profiler* pf) {
+    if (K <= 0) return;
+    launch_object_boxes(labels, W, H, K, bbox, s, pf);
     ObjJob J{hem8, labels, W, H, bbox, feats};
     int grid = (K + FW - 1) / FW < sms * 16 ? (K + FW - 1) / FW : sms * 16;
     pf->begin("feat_objects", s);

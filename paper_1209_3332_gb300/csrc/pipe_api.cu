@@ -305,6 +305,11 @@ struct pipe_s {
     bool have_last = false;
     DevBuf fbbox;
     DevBuf morph_tmp;  // scratch plane of morph_open_tile
+    DevBuf ws_obj;      // watershed_tile: per-object boxes and basin counts
+    DevBuf ws_scratch;  // watershed_tile: planes for boxes larger than the shared-memory stage
+    DevBuf ws_status;   // watershed_tile: device status word
+    cudaStream_t ws_side = nullptr;        // watershed_tile: large boxes overlap the small ones here
+    cudaEvent_t ws_fork = nullptr, ws_join = nullptr;
     // batched form
     LaunchCtx batch;
     GraphCache graphs;
@@ -671,6 +676,12 @@ void pipe_destroy(pipe_t p) {
     rel(p->batch);
     p->fbbox.release();
     p->morph_tmp.release();
+    p->ws_obj.release();
+    p->ws_scratch.release();
+    p->ws_status.release();
+    if (p->ws_side) cudaStreamDestroy(p->ws_side);
+    if (p->ws_fork) cudaEventDestroy(p->ws_fork);
+    if (p->ws_join) cudaEventDestroy(p->ws_join);
     for (auto& c : p->ctxs) {
         rel(c->lc);
         c->dev.release();
@@ -752,6 +763,43 @@ int morph_open_tile(pipe_t p, const uint8_t* src_dev, int W, int H, int radius, 
         if (rc) return rc;
     }
     launch_morph_open(src_dev, dst_dev, (uint8_t*)p->morph_tmp.p, W, H, radius, s, &p->prof);
+    CK(cudaGetLastError());
+    return PIPE_OK;
+}
+
+int watershed_tile(pipe_t p, const int32_t* labels_dev, const int32_t* edt_dev, int W, int H, int n_objects,
+                   int h, int32_t* out_dev, int32_t* n_basins_dev, pipe_stream_t stream) {
+    if (!p || !labels_dev || !edt_dev || !out_dev || !n_basins_dev || n_objects < 0 || h < 0 || h > 255)
+        return PIPE_EINVAL;
+    if (!valid_size(W, H)) return PIPE_EINVAL;
+    const size_t N = (size_t)W * H;
+    auto overlap = [N](const void* a, const void* b) {
+        const char *x = (const char*)a, *y = (const char*)b;
+        return x < y + N * 4 && y < x + N * 4;
+    };
+    if (overlap(out_dev, labels_dev) || overlap(out_dev, edt_dev)) return PIPE_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaSetDevice(p->device));
+    const size_t need_obj = (size_t)std::max(n_objects, 1) * (sizeof(int4) + sizeof(int));
+    const size_t need_scr = watershed_scratch_bytes(W, H);
+    if (p->ws_obj.n < need_obj || p->ws_scratch.n < need_scr || !p->ws_status.p) {
+        CK(cudaStreamSynchronize(s));
+        int rc;
+        if ((rc = p->ws_obj.ensure(need_obj)) || (rc = p->ws_scratch.ensure(need_scr))) return rc;
+        if (!p->ws_status.p) {
+            if ((rc = p->ws_status.ensure(sizeof(int)))) return rc;
+            CK(cudaMemset(p->ws_status.p, 0, sizeof(int)));
+        }
+    }
+    if (!p->ws_side) {
+        CK(cudaStreamCreateWithFlags(&p->ws_side, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&p->ws_fork, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&p->ws_join, cudaEventDisableTiming));
+    }
+    int4* bbox = (int4*)p->ws_obj.p;
+    int* cnt = (int*)(bbox + std::max(n_objects, 1));
+    launch_watershed(labels_dev, edt_dev, W, H, n_objects, h, out_dev, n_basins_dev, bbox, cnt, p->ws_scratch.p,
+                     (int*)p->ws_status.p, p->sms, s, p->ws_side, p->ws_fork, p->ws_join, &p->prof);
     CK(cudaGetLastError());
     return PIPE_OK;
 }
@@ -855,6 +903,12 @@ int pipe_status_read(pipe_t p) {
     };
     check(p->plain, 1);
     check(p->batch, p->batch_ntiles);
+    if (p->ws_status.p) {
+        int st = 0;
+        if (cudaMemcpy(&st, p->ws_status.p, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return PIPE_ECUDA;
+        if (st && result == PIPE_OK) result = st;
+        cudaMemset(p->ws_status.p, 0, sizeof(int));
+    }
     return result;
 }
 
