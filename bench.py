@@ -396,6 +396,68 @@ def watershed_run(torch, pipe, stream, bufs, steps, hbm_peak, want_cpu):
     return out
 
 
+CANNY_LOW, CANNY_HIGH, EDGE_R = 40, 120, 3   # thresholds on the L1 Sobel magnitude; disk radius of the counts
+CANNY_BYTES_PER_PX = 2                        # minimal pass: the plane read once, the edge map written once
+
+
+def canny_run(torch, pipe, stream, bufs, steps, hbm_peak, want_cpu):
+    """Canny edges of every hem8 plane of the batch and the edge counts of
+    its objects (Sec. V-A feature-stage transform, Sec. II edge features)
+    through canny_tile, timed with CUDA events on the launching stream (the
+    planes of the batch are far larger than L2)."""
+    ks = [int(b["n_objects"].item()) for b in bufs]
+    edges = [torch.empty_like(b["hem8"]) for b in bufs]
+    counts = [torch.empty(max(k, 1), dtype=torch.int32, device=b["hem8"].device) for k, b in zip(ks, bufs)]
+
+    def step():
+        for i, b in enumerate(bufs):
+            pipe.canny(b["hem8"], edges[i], labels=b["labels"], n_objects=ks[i], counts=counts[i],
+                       low=CANNY_LOW, high=CANNY_HIGH, radius=EDGE_R, stream=stream)
+    for _ in range(3):
+        step()
+    ms = timed(torch, stream, step, steps) / steps
+    before = pipe.profile_read()
+    pipe.profile(True)
+    step()
+    torch.cuda.synchronize()
+    after = pipe.profile_read()
+    pipe.profile(False)
+    kern = {}
+    for k, (c, t) in after.items():
+        c0, t0 = before.get(k, (0, 0.0))
+        if c > c0:
+            kern[k] = round((t - t0) / (c - c0), 4)
+    n = len(bufs)
+    px = sum(b["hem8"].numel() for b in bufs)
+    nms_ms = kern.get("canny_nms", 0.0)
+    out = {"low": CANNY_LOW, "high": CANNY_HIGH, "radius": EDGE_R, "tiles_per_step": n,
+           "tile": list(bufs[0]["hem8"].shape), "ms_per_step": ms, "tiles_per_s": n * 1000.0 / ms,
+           "edge_px_per_step": int(sum(int(e.sum().item()) for e in edges)), "kernels_ms": kern,
+           "hbm": {"achieved": CANNY_BYTES_PER_PX * px / (ms / 1000.0) / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                   "alg_bytes_per_px": CANNY_BYTES_PER_PX,
+                   "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"},
+           "parity": "bit-exact with the oracle (tests/test_gpu_canny.py)"}
+    out["hbm"]["frac"] = out["hbm"]["achieved"] / hbm_peak
+    if nms_ms > 0:  # the stencil pass alone: the plane read once, strong and candidate planes written
+        gbs = 3.0 * bufs[0]["hem8"].numel() / (nms_ms / 1000.0) / 1e9
+        out["nms_kernel"] = {"achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+                             "alg_bytes_per_px": 3}
+    if want_cpu:
+        import time
+        import oracle
+        rows = 1024
+        img = bufs[0]["hem8"][:rows].cpu().numpy()
+        lab = bufs[0]["labels"][:rows].cpu().numpy()
+        t = time.perf_counter()
+        e = oracle.canny(img, CANNY_LOW, CANNY_HIGH)
+        oracle.edge_counts(e, lab, ks[0], EDGE_R)
+        sec = time.perf_counter() - t
+        out["cpu_oracle"] = {"tiles_per_s": img.size / bufs[0]["hem8"].numel() / sec, "cores": 1,
+                             "sample": "the oracle on the first %d rows of tile 0 (%d x %d pixels), %.2f s, scaled"
+                                       % (rows, img.shape[0], img.shape[1], sec)}
+    return out
+
+
 def peaks_clock():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -637,6 +699,9 @@ def run_ours(args, world, rank, local):
     # ---- the step after the path: watershed split of the objects -------------
     line["watershed"] = watershed_run(torch, pipe, stream, bufs, max(3, args.steps // 2), peak,
                                       rank == 0 and world == 1 and not args.no_cpu)
+    # ---- the feature-stage edge transform: Canny and per-object edge counts --
+    line["canny"] = canny_run(torch, pipe, stream, bufs, max(3, args.steps // 2), peak,
+                              rank == 0 and world == 1 and not args.no_cpu)
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(host[0])
     if rank == 0:

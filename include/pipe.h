@@ -203,6 +203,35 @@ int morph_open_tile(pipe_t p, const uint8_t* src_dev, int W, int H, int radius, 
 int watershed_tile(pipe_t p, const int32_t* labels_dev, const int32_t* edt_dev, int W, int H, int n_objects,
                    int h, int32_t* out_dev, int32_t* n_basins_dev, pipe_stream_t stream);
 
+/* Canny edges of a uint8 plane and the per-object edge counts (Sec. V-A
+ * lists Canny among the feature-stage transforms applied to the
+ * deconvolved image; Sec. II names "edge" among the feature families;
+ * Table I "Features comp." uses OpenCV's Canny).  The paper gives no
+ * parameter; the definition computed here:
+ *   gx, gy = 3x3 Sobel with replicated border; m = |gx| + |gy|;
+ *   gradient sector, ax = |gx|, ay = |gy|: horizontal if
+ *     (ax + ay)^2 < 2 ax^2, vertical if ay > ax and (ay - ax)^2 > 2 ax^2,
+ *     else diagonal along (+x,+y) if gx gy > 0, along (+x,-y) otherwise;
+ *   a pixel survives non-maximum suppression iff m > m(a) and m >= m(b),
+ *     a and b its neighbours along the sector (a on the previous row, or
+ *     the left one for the horizontal sector; m off the image is 0);
+ *   candidates: survivors with m > low; strong: survivors with m > high;
+ *   edges_dev = 1 on candidates 8-connected through candidates to a strong
+ *     pixel, 0 elsewhere;
+ *   counts_dev[k-1] = edge pixels within the disk dilation of object k of
+ *     labels_dev (offsets dx^2 + dy^2 <= radius^2 from one of its pixels;
+ *     a pixel near two objects counts for both), k = 1..n_objects.
+ *  img_dev, edges_dev: W x H uint8 planes, caller-owned, not overlapping;
+ *  labels_dev: W x H int32 (may be NULL when n_objects = 0); counts_dev:
+ *  n_objects int32.  0 <= low <= high; 0 <= radius <= 4.  The hysteresis
+ *  runs the segmentation's reconstruction kernel on pipe-owned scratch (a
+ *  W x H candidate plane and a work queue), allocated on the first call of
+ *  a larger size, which synchronises `stream`.
+ * Returns PIPE_EINVAL on a bad argument (nothing is launched); otherwise
+ * the work is asynchronous on `stream`. */
+int canny_tile(pipe_t p, const uint8_t* img_dev, const int32_t* labels_dev, int W, int H, int n_objects, int low,
+               int high, int radius, uint8_t* edges_dev, int32_t* counts_dev, pipe_stream_t stream);
+
 /* Served form (Sec. IV-D prefetching and asynchronous copy): tiles in host
  * memory are admitted as slots and HBM budget allow, uploaded on copy
  * streams overlapped with compute, processed, and their results downloaded.

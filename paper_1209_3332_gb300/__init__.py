@@ -20,7 +20,7 @@ STATUS_NAMES = ["PIPE_OK", "PIPE_EINVAL", "PIPE_ENOMEM", "PIPE_EBUSY", "PIPE_EAG
 EXPORTS = ["pipe_default_params", "pipe_create", "pipe_destroy", "seg_tile", "features_tile",
            "seg_features_batch", "batch_submit", "batch_poll", "pipe_status_read", "pipe_debug_plane",
            "pipe_profile_enable", "pipe_profile_read", "pipe_launch_count", "pipe_recon_visits",
-           "features_tile_noalloc", "pipe_autotune_info", "morph_open_tile", "watershed_tile"]
+           "features_tile_noalloc", "pipe_autotune_info", "morph_open_tile", "watershed_tile", "canny_tile"]
 NOALLOC_MAX_OBJECTS = 65536
 
 
@@ -80,6 +80,7 @@ def lib():
     L.seg_features_batch.argtypes = [vp, ctypes.POINTER(TileDevC), ci, vp]
     L.morph_open_tile.argtypes = [vp, vp, ci, ci, ci, vp, vp]
     L.watershed_tile.argtypes = [vp, vp, vp, ci, ci, ci, ci, vp, vp, vp]
+    L.canny_tile.argtypes = [vp, vp, vp, ci, ci, ci, ci, ci, ci, vp, vp, vp]
     L.batch_submit.argtypes = [vp, ctypes.POINTER(TileDesc), ci, ctypes.POINTER(u64)]
     L.batch_poll.argtypes = [vp, u64, ctypes.POINTER(ci), ctypes.POINTER(TileResult)]
     L.pipe_status_read.argtypes = [vp]
@@ -97,7 +98,7 @@ def lib():
                                      ctypes.POINTER(ctypes.c_longlong)]
     for n in ("pipe_create", "seg_tile", "features_tile", "seg_features_batch", "batch_submit", "batch_poll",
               "pipe_status_read", "pipe_debug_plane", "pipe_profile_enable", "pipe_profile_read",
-              "morph_open_tile", "watershed_tile"):
+              "morph_open_tile", "watershed_tile", "canny_tile"):
         getattr(L, n).restype = ci
     _lib = L
     return L
@@ -193,6 +194,20 @@ class Pipe:
         rc = lib().watershed_tile(self.h, labels.data_ptr(), edt.data_ptr(), W, H, int(n_objects), int(h),
                                   out.data_ptr(), n_basins.data_ptr(), _stream_ptr(stream))
         _check(rc, "watershed_tile")
+
+    def canny(self, img, edges, labels=None, n_objects=0, counts=None, low=40, high=120, radius=3, stream=None):
+        """Canny edges of a (H, W) uint8 device tensor into edges (uint8 0/1),
+        and, with labels (int32) and counts (int32 [n_objects]), the edge
+        pixels within each object's disk dilation of the given radius."""
+        H, W = img.shape
+        if tuple(edges.shape) != (H, W) or not img.is_contiguous() or not edges.is_contiguous():
+            raise ValueError("img and edges must be contiguous (H, W) uint8 planes")
+        if labels is not None and (tuple(labels.shape) != (H, W) or not labels.is_contiguous()):
+            raise ValueError("labels must be a contiguous (H, W) int32 plane")
+        rc = lib().canny_tile(self.h, img.data_ptr(), labels.data_ptr() if labels is not None else None, W, H,
+                              int(n_objects), int(low), int(high), int(radius), edges.data_ptr(),
+                              counts.data_ptr() if counts is not None else None, _stream_ptr(stream))
+        _check(rc, "canny_tile")
 
     # ---- batched form ---------------------------------------------------
     def seg_features_batch(self, tiles, stream=None):

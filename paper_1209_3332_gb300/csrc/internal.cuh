@@ -99,6 +99,50 @@ __device__ __forceinline__ void set_status(int* status, int code) {
     atomicCAS(status, 0, code);
 }
 
+// Object boxes from one row segment of FB_SEG labels, one warp: each lane
+// reads 4 labels at a time; the lanes holding the same label (one
+// __match_any_sync group per label value) combine their column range and
+// one lane updates the box with atomics.  Labels outside 1..K are ignored.
+constexpr int FB_STEPS = 8;
+constexpr int FB_SEG = 32 * 4 * FB_STEPS;
+__device__ __forceinline__ void bbox_segment(const int32_t* __restrict__ row, int W, int K, int y, int xs,
+                                             int4* bbox, int lane) {
+    const unsigned full = 0xffffffffu;
+    const bool vec = (W & 3) == 0;
+    for (int step = 0; step < FB_STEPS; step++) {
+        const int x0 = xs + (step * 32 + lane) * 4;
+        int v[4] = {0, 0, 0, 0};
+        if (vec && x0 + 3 < W) {
+            int4 q = __ldcs(reinterpret_cast<const int4*>(row + x0));
+            v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+        } else {
+            for (int k = 0; k < 4; k++) v[k] = x0 + k < W ? __ldcs(row + x0 + k) : 0;
+        }
+        if (__ballot_sync(full, (v[0] | v[1] | v[2] | v[3]) != 0) == 0) continue;
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            int lab = (v[k] >= 1 && v[k] <= K) ? v[k] : 0;
+            // the other pixels of this lane with the same label join this update
+            int mn = 0x7fffffff, mx = -1;
+            if (lab) {
+                for (int j = k; j < 4; j++)
+                    if (v[j] == lab) { mn = min(mn, x0 + j); mx = max(mx, x0 + j); v[j] = 0; }
+            }
+            unsigned grp = __match_any_sync(full, lab);
+            if (lab) {
+                int gmn = __reduce_min_sync(grp, (unsigned)mn), gmx = __reduce_max_sync(grp, (unsigned)mx);
+                if (lane == __ffs(grp) - 1) {
+                    int4* b = bbox + (lab - 1);
+                    atomicMin(&b->x, gmn);
+                    atomicMax(&b->z, gmx);
+                    atomicMin(&b->y, y);
+                    atomicMax(&b->w, y);
+                }
+            }
+        }
+    }
+}
+
 // ---- launchers (one per translation unit) -----------------------------------
 // Profiler hook: every kernel launch is bracketed by begin/end with its name;
 // the pipe counts launches and, when enabled, records CUDA events.
@@ -124,6 +168,12 @@ void launch_features_plain(const uint8_t* hem8, const int32_t* labels, int W, in
 void launch_features_batched(const Launch& L, int grid, cudaStream_t s, Profiler* pf);
 // per object 1..K of a label plane: its box (xmin, ymin, xmax, ymax); empty (xmax < xmin) if absent
 void launch_object_boxes(const int32_t* labels, int W, int H, int K, int4* bbox, cudaStream_t s, Profiler* pf);
+// Canny: strong pixels (0/1) into strong, candidates (0/1) into cand
+void launch_canny_nms(const uint8_t* img, int W, int H, int low, int high, uint8_t* strong, uint8_t* cand,
+                      cudaStream_t s, Profiler* pf);
+// per object: edge pixels within its disk dilation of radius r (boxes into bbox)
+void launch_canny_counts(const uint8_t* edges, const int32_t* labels, int W, int H, int K, int r, int4* bbox,
+                         int32_t* counts, int sms, cudaStream_t s, Profiler* pf);
 // scratch of the watershed's out-of-stage boxes: a 64-bit and a 16-bit word per pixel
 size_t watershed_scratch_bytes(int W, int H);
 // cnt: K ints (per-object basin counts, then their exclusive prefix); status: a device int

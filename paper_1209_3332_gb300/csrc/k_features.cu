@@ -35,49 +35,14 @@ __global__ void k_fbbox_init(int4* bbox, int K) {
 // One warp per row segment of 32*4*FB_STEPS pixels: each lane reads 4 labels
 // at a time; the lanes holding the same label (one __match_any_sync group per
 // label value) combine their column range and one lane updates the box.
-constexpr int FB_STEPS = 8;
 __global__ void __launch_bounds__(256) k_fbbox(const int32_t* __restrict__ labels, int W, int H, int K,
                                                int4* bbox) {
     const int lane = threadIdx.x & 31;
-    const int seg = 32 * 4 * FB_STEPS;
-    const int spr = (W + seg - 1) / seg;
+    const int spr = (W + FB_SEG - 1) / FB_SEG;
     long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (gw >= (long long)spr * H) return;
-    const int y = (int)(gw / spr), xs = (int)(gw - (long long)y * spr) * seg;
-    const int32_t* row = labels + (size_t)y * W;
-    const bool vec = (W & 3) == 0;
-    for (int step = 0; step < FB_STEPS; step++) {
-        const int x0 = xs + (step * 32 + lane) * 4;
-        int v[4] = {0, 0, 0, 0};
-        if (vec && x0 + 3 < W) {
-            int4 q = __ldcs(reinterpret_cast<const int4*>(row + x0));
-            v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
-        } else {
-            for (int k = 0; k < 4; k++) v[k] = x0 + k < W ? __ldcs(row + x0 + k) : 0;
-        }
-        if (__ballot_sync(FULLF, (v[0] | v[1] | v[2] | v[3]) != 0) == 0) continue;
-#pragma unroll
-        for (int k = 0; k < 4; k++) {
-            int lab = (v[k] >= 1 && v[k] <= K) ? v[k] : 0;
-            // the other pixels of this lane with the same label join this update
-            int mn = 0x7fffffff, mx = -1;
-            if (lab) {
-                for (int j = k; j < 4; j++)
-                    if (v[j] == lab) { mn = min(mn, x0 + j); mx = max(mx, x0 + j); v[j] = 0; }
-            }
-            unsigned grp = __match_any_sync(FULLF, lab);
-            if (lab) {
-                int gmn = __reduce_min_sync(grp, (unsigned)mn), gmx = __reduce_max_sync(grp, (unsigned)mx);
-                if (lane == __ffs(grp) - 1) {
-                    int4* b = bbox + (lab - 1);
-                    atomicMin(&b->x, gmn);
-                    atomicMax(&b->z, gmx);
-                    atomicMin(&b->y, y);
-                    atomicMax(&b->w, y);
-                }
-            }
-        }
-    }
+    const int y = (int)(gw / spr), xs = (int)(gw - (long long)y * spr) * FB_SEG;
+    bbox_segment(labels + (size_t)y * W, W, K, y, xs, bbox, lane);
 }
 
 struct ObjJob {
@@ -377,7 +342,7 @@ void launch_object_boxes(const int32_t* labels, int W, int H, int K, int4* bbox,
     k_fbbox_init<<<(K + 255) / 256, 256, 0, s>>>(bbox, K);
     pf->end("feat_bbox_init", s);
     pf->begin("feat_bbox", s);
-    long long warps = (long long)((W + 32 * 4 * FB_STEPS - 1) / (32 * 4 * FB_STEPS)) * H;
+    long long warps = (long long)((W + FB_SEG - 1) / FB_SEG) * H;
     k_fbbox<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, s>>>(labels, W, H, K, bbox);
     pf->end("feat_bbox", s);
 }

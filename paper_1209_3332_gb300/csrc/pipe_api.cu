@@ -309,6 +309,9 @@ struct pipe_s {
     DevBuf ws_scratch;  // watershed_tile: planes for boxes larger than the shared-memory stage
     DevBuf ws_status;   // watershed_tile: device status word
     cudaStream_t ws_side = nullptr;        // watershed_tile: large boxes overlap the small ones here
+    LaunchCtx canny;    // canny_tile: the hysteresis runs the reconstruction on this context
+    DevBuf canny_cand;  // canny_tile: candidate plane (the reconstruction's mask)
+    DevBuf canny_obj;   // canny_tile: object boxes
     cudaEvent_t ws_fork = nullptr, ws_join = nullptr;
     // batched form
     LaunchCtx batch;
@@ -677,6 +680,9 @@ void pipe_destroy(pipe_t p) {
     p->fbbox.release();
     p->morph_tmp.release();
     p->ws_obj.release();
+    rel(p->canny);
+    p->canny_cand.release();
+    p->canny_obj.release();
     p->ws_scratch.release();
     p->ws_status.release();
     if (p->ws_side) cudaStreamDestroy(p->ws_side);
@@ -804,6 +810,51 @@ int watershed_tile(pipe_t p, const int32_t* labels_dev, const int32_t* edt_dev, 
     return PIPE_OK;
 }
 
+int canny_tile(pipe_t p, const uint8_t* img_dev, const int32_t* labels_dev, int W, int H, int n_objects, int low,
+               int high, int radius, uint8_t* edges_dev, int32_t* counts_dev, pipe_stream_t stream) {
+    if (!p || !img_dev || !edges_dev || n_objects < 0 || low < 0 || high < low || radius < 0 || radius > 4)
+        return PIPE_EINVAL;
+    if (n_objects > 0 && (!labels_dev || !counts_dev)) return PIPE_EINVAL;
+    if (!valid_size(W, H)) return PIPE_EINVAL;
+    const size_t N = (size_t)W * H;
+    if (img_dev < edges_dev + N && edges_dev < img_dev + N) return PIPE_EINVAL;  // the planes overlap
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaSetDevice(p->device));
+    const int rtx = (W + RT - 1) / RT, rty = (H + RT - 1) / RT, n_rt = rtx * rty;
+    const size_t need_obj = (size_t)std::max(n_objects, 1) * sizeof(int4);
+    if (p->canny_cand.n < N || p->canny_obj.n < need_obj || p->canny.wl.n < sizeof(int) * 3 * (size_t)n_rt ||
+        !p->canny.shared.p) {
+        CK(cudaStreamSynchronize(s));
+        const bool fresh = !p->canny.shared.p;
+        int rc;
+        if ((rc = p->canny_cand.ensure(N)) || (rc = p->canny_obj.ensure(need_obj)) ||
+            (rc = ensure_ctx(p->canny, 1, n_rt, 0)))
+            return rc;
+        if (fresh) CK(cudaMemset(p->canny.shared.p, 0, p->canny.shared.n));
+    }
+    uint8_t* cand = (uint8_t*)p->canny_cand.p;
+    // 1. gradient and non-maximum suppression: strong pixels into edges_dev, candidates into cand
+    launch_canny_nms(img_dev, W, H, low, high, edges_dev, cand, s, &p->prof);
+    // 2. hysteresis: reconstruction by dilation of the strong pixels under the candidates
+    std::vector<TileDev> td(1);
+    std::memset(&td[0], 0, sizeof(TileDev));
+    td[0].W = W;
+    td[0].H = H;
+    td[0].R = edges_dev;
+    td[0].hem8 = cand;
+    td[0].rtx = rtx;
+    td[0].rty = rty;
+    Launch L = make_launch(p, p->canny, td, n_rt, 4);
+    int rc;
+    if ((rc = upload_desc(L, td, s))) return rc;
+    launch_recon(L, p->recon_cap, s, &p->prof);
+    // 3. edge pixels within each object's disk dilation
+    launch_canny_counts(edges_dev, labels_dev, W, H, n_objects, radius, (int4*)p->canny_obj.p, counts_dev, p->sms, s,
+                        &p->prof);
+    CK(cudaGetLastError());
+    return PIPE_OK;
+}
+
 int seg_features_batch(pipe_t p, const tile_dev* tiles, int n, pipe_stream_t stream) {
     if (!p || !tiles || n < 1 || n > 4096) return PIPE_EINVAL;
     for (int i = 0; i < n; i++) {
@@ -903,6 +954,7 @@ int pipe_status_read(pipe_t p) {
     };
     check(p->plain, 1);
     check(p->batch, p->batch_ntiles);
+    check(p->canny, 1);
     if (p->ws_status.p) {
         int st = 0;
         if (cudaMemcpy(&st, p->ws_status.p, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return PIPE_ECUDA;
