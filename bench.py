@@ -346,17 +346,26 @@ WS_BYTES_PER_PX = 12      # minimal pass: labels and EDT read once, the split pl
 
 def watershed_run(torch, pipe, stream, bufs, steps, hbm_peak, want_cpu):
     """The watershed split (Table I "Pre-Watershed" + "Watershed") of every
-    tile of the batch through watershed_tile, on the labels and EDT the
-    batched step wrote, timed with CUDA events on the launching stream (the
-    planes of the batch are far larger than L2).  Per-kernel times come from
-    the pipe's own events around each launch."""
+    tile of the batch, on the labels and EDT the batched step wrote: the
+    batched form (watershed_batch) as the figure, one watershed_tile call per
+    tile beside it; timed with CUDA events on the launching stream (the
+    planes of the batch are far larger than L2).  Per-kernel times (batched
+    form) come from the pipe's own events around each launch."""
     ks = [int(b["n_objects"].item()) for b in bufs]
     outs = [torch.empty_like(b["labels"]) for b in bufs]
     nb = torch.zeros(len(bufs), dtype=torch.int32, device=bufs[0]["labels"].device)
 
-    def step():
+    def plain():
         for i, b in enumerate(bufs):
             pipe.watershed(b["labels"], b["edt"], ks[i], outs[i], nb[i:i + 1], h=WS_H, stream=stream)
+    batch = [dict(labels=b["labels"], edt=b["edt"], out=outs[i], n_objects=ks[i], n_basins=nb[i:i + 1])
+             for i, b in enumerate(bufs)]
+
+    def step():
+        pipe.watershed_batch(batch, h=WS_H, stream=stream)
+    for _ in range(3):
+        plain()
+    plain_ms = timed(torch, stream, plain, steps) / steps
     for _ in range(3):
         step()
     ms = timed(torch, stream, step, steps) / steps
@@ -374,8 +383,11 @@ def watershed_run(torch, pipe, stream, bufs, steps, hbm_peak, want_cpu):
     n = len(bufs)
     px = sum(b["labels"].numel() for b in bufs)
     gbs = WS_BYTES_PER_PX * px / (ms / 1000.0) / 1e9
-    out = {"h": WS_H, "tiles_per_step": n, "tile": list(bufs[0]["labels"].shape), "ms_per_step": ms,
-           "tiles_per_s": n * 1000.0 / ms, "objects_per_step": sum(ks),
+    out = {"h": WS_H, "form": "batched (watershed_batch: the objects of all tiles in one launch per pass)",
+           "tiles_per_step": n, "tile": list(bufs[0]["labels"].shape), "ms_per_step": ms,
+           "tiles_per_s": n * 1000.0 / ms,
+           "plain": {"form": "watershed_tile per tile", "ms_per_step": plain_ms, "tiles_per_s": n * 1000.0 / plain_ms},
+           "objects_per_step": sum(ks),
            "basins_per_step": int(nb.sum().item()), "kernels_ms": kern,
            "hbm": {"achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
                    "alg_bytes_per_px": WS_BYTES_PER_PX,
@@ -486,32 +498,56 @@ def h2d_gbs(torch, dev, nbytes=256 << 20, reps=4):
     return best
 
 
-def serve_run(pipe, pinned, n_requests, rate, seed=3999, max_group=16, max_inflight=2, limit_s=120.0):
+def serve_run(pipe, pinned, n_requests, rate, seed=3999, max_group=16, max_inflight=2, limit_s=120.0, costs=None):
     """Poisson arrivals at `rate` tiles/s; each request is one pool tile.
     Continuous batching: whenever fewer than max_inflight groups are on the
-    device, every request that has arrived (up to max_group) is admitted as
-    the next group, so one group uploads while the previous one computes."""
+    device, the requests that have arrived (up to max_group) are admitted as
+    the next group, so one group uploads while the previous one computes.
+    Without `costs` the group takes them in order of arrival; with `costs`
+    (an estimate per pool tile) they wait in the dispatcher's queue
+    (P.Sched) and the group takes the most expensive first."""
+    import paper_1209_3332_gb300 as P
     rng = random.Random(seed)
     arrivals, t = [], 0.0
     for _ in range(n_requests):
         t += rng.expovariate(rate)
         arrivals.append(t)
+    sched = P.Sched(1, max_group * max_inflight) if costs is not None else None
     waiting, inflight, lat, done_t, sizes = [], [], [], [], []
     i = 0
     t0 = time.monotonic()
+
+    def queued():
+        return sched.counts()[0] if sched else len(waiting)
     while len(lat) < n_requests:
         now = time.monotonic() - t0
         while i < n_requests and arrivals[i] <= now:
-            waiting.append(i)
+            if sched:
+                sched.push(i, costs[i % len(pinned)])
+            else:
+                waiting.append(i)
             i += 1
-        while waiting and len(inflight) < max_inflight:
-            group = waiting[:max_group]
+        while queued() and len(inflight) < max_inflight:
+            if sched:
+                group = []
+                while len(group) < max_group:
+                    r = sched.request(0)
+                    if r is None:
+                        break
+                    group.append(r)
+            else:
+                group = waiting[:max_group]
             tk = pipe.submit([pinned[r % len(pinned)] for r in group])
             if tk is None:
+                if sched:                        # not admitted: back to the queue
+                    for r in group:
+                        sched.done(0, r)
+                        sched.push(r, costs[r % len(pinned)])
                 break
             inflight.append((tk, group))
             sizes.append(len(group))
-            waiting = waiting[len(group):]
+            if not sched:
+                waiting = waiting[len(group):]
         if time.monotonic() - t0 > limit_s:
             raise RuntimeError("served leg exceeded %.0f s" % limit_s)
         still = []
@@ -523,11 +559,13 @@ def serve_run(pipe, pinned, n_requests, rate, seed=3999, max_group=16, max_infli
             for r, out in zip(reqs, res):
                 if out["status"] != 0:
                     raise RuntimeError("served tile status %d" % out["status"])
+                if sched:
+                    sched.done(0, r)
                 done_ms = out["t_done_ms"] - t0 * 1000.0
                 lat.append(done_ms - arrivals[r] * 1000.0)
                 done_t.append(done_ms / 1000.0)
         inflight = still
-        if not waiting and not inflight and i < n_requests:
+        if not queued() and not inflight and i < n_requests:
             time.sleep(max(0.0, min(0.0005, arrivals[i] - (time.monotonic() - t0))))
     lat.sort()
     span = max(done_t) - arrivals[0]
@@ -536,8 +574,32 @@ def serve_run(pipe, pinned, n_requests, rate, seed=3999, max_group=16, max_infli
         return lat[min(len(lat) - 1, int(math.ceil(p / 100.0 * len(lat))) - 1)]
     return {"value": n_requests / span, "unit": "tiles/s", "p50_ms": pct(50), "p99_ms": pct(99),
             "requests": n_requests, "arrival_rate": rate, "pool_tiles": len(pinned),
-            "policy": "continuous batching: <= %d groups in flight, <= %d tiles per group" % (max_inflight, max_group),
+            "policy": "continuous batching: <= %d groups in flight, <= %d tiles per group, %s"
+                      % (max_inflight, max_group, "most expensive first (Sched)" if sched else "arrival order"),
             "groups": len(sizes), "mean_group": sum(sizes) / max(1, len(sizes))}
+
+
+def dispatch_compare(torch, pipe, n_requests, batched_rate):
+    """The served form on a pool of 16 tiles of the served workload (sides
+    2048-4096, 0-5000 nuclei per 4096^2), the same Poisson stream fed in
+    arrival order and through the dispatcher's cost-sorted queue (the PATS
+    order of Sec. IV-B reduced to tile cost; window of Sec. III-B).  The
+    arrival rate is the batched 4096^2 rate scaled by the pool's mean area,
+    so that requests queue up."""
+    import paper_1209_3332_gb300 as P
+    import synth
+    host = [synth.cfg3(i) for i in range(16)]
+    pool = [torch.from_numpy(h).pin_memory() for h in host]
+    costs = [P.tile_cost(h) for h in host]
+    mean_px = sum(h.shape[0] * h.shape[1] for h in host) / len(host)
+    rate = batched_rate * 4096.0 * 4096.0 / mean_px
+    serve_run(pipe, pool, 64, rate)                         # warm the contexts for these shapes
+    fifo = serve_run(pipe, pool, n_requests, rate)
+    lpt = serve_run(pipe, pool, n_requests, rate, costs=costs)
+    return {"pool": "16 served-workload tiles (synth.cfg3), sides %d-%d"
+                    % (min(h.shape[0] for h in host), max(h.shape[0] for h in host)),
+            "arrival_rate": rate, "arrival_order": fifo, "most_expensive_first": lpt,
+            "cost": "tile_cost: W*H*(1 + 8 * dark fraction on a 1-in-64 sample)"}
 
 
 def run_ours(args, world, rank, local):
@@ -666,6 +728,10 @@ def run_ours(args, world, rank, local):
     rate = 0.8 * value / world
     serve_run(pipe, pinned, min(32, 4 * B), rate)  # warm the contexts
     line["served"] = serve_run(pipe, pinned, args.requests, rate)
+
+    # ---- dispatch order on a mixed pool: arrival order vs most expensive first
+    if not args.no_extra:
+        line["dispatch"] = dispatch_compare(torch, pipe, args.requests, value / world)
 
     # ---- roofline of the dominant kernel ------------------------------------
     peak, peak_kind = peaks()

@@ -203,6 +203,26 @@ int morph_open_tile(pipe_t p, const uint8_t* src_dev, int W, int H, int radius, 
 int watershed_tile(pipe_t p, const int32_t* labels_dev, const int32_t* edt_dev, int W, int H, int n_objects,
                    int h, int32_t* out_dev, int32_t* n_basins_dev, pipe_stream_t stream);
 
+/* Batched form of watershed_tile: the split of n tiles of any sizes, one
+ * launch per pass over the objects of all tiles (so that many tiles'
+ * objects share the GPU instead of each call waiting for its slowest
+ * object).  Results are identical to watershed_tile on each tile alone.
+ *  tiles[i]: labels, edt, out (W x H int32, out not overlapping the
+ *    inputs), n_objects = K of the tile (host int), n_basins (one device
+ *    int32); 1 <= n <= 4096; 0 <= h <= 255.
+ *  The pipe's scratch covers all tiles at once: boxes and counts (20 bytes
+ *  per object) and the planes for boxes beyond the shared-memory stage
+ *  (10 bytes per pixel of all tiles), allocated on the first call of a
+ *  larger size, which synchronises `stream`.
+ * Returns PIPE_EINVAL on a bad argument (nothing is launched); otherwise
+ * the work is asynchronous on `stream`. */
+typedef struct {
+    const int32_t* labels; const int32_t* edt; int W, H;
+    int n_objects;
+    int32_t* out; int32_t* n_basins;
+} ws_tile;
+int watershed_batch(pipe_t p, const ws_tile* tiles, int n, int h, pipe_stream_t stream);
+
 /* Canny edges of a uint8 plane and the per-object edge counts (Sec. V-A
  * lists Canny among the feature-stage transforms applied to the
  * deconvolved image; Sec. II names "edge" among the feature families;
@@ -294,6 +314,36 @@ long long pipe_launch_count(pipe_t p);
  * reconstruction of the most recent seg_tile call processed (a tile that is
  * re-queued counts again), or -1 before any call.  Diagnostic only. */
 long long pipe_recon_visits(pipe_t p);
+
+/* ---- Demand-driven tile dispatch (host only; no GPU needed) ----------------
+ * The paper's Manager assigns stage instances on demand: a Worker requests
+ * work as it finishes earlier work and holds at most `window` instances at a
+ * time (Sec. III-B); its PATS scheduler keeps queued instances sorted by an
+ * estimate and gives an idle GPU the one at the top of that order (Sec.
+ * IV-B).  With GPU-only workers the estimate is a tile's processing cost:
+ * a requesting worker gets the most expensive pending tile (longest
+ * processing time first); equal costs keep their order of arrival.  All
+ * calls on one sched_t are thread-safe. */
+typedef struct sched_s* sched_t;
+/* n_workers in [1, 4096], window >= 1.  PIPE_EINVAL / PIPE_ENOMEM. */
+int sched_create(int n_workers, int window, sched_t* out);
+void sched_destroy(sched_t s);
+/* Queues task (an id the caller chooses, unique among queued and held
+ * tasks) with its cost (finite, >= 0).  PIPE_EINVAL otherwise. */
+int sched_push(sched_t s, uint64_t task, double cost);
+/* Grants worker the most expensive queued task: PIPE_OK with *task set;
+ * PIPE_EBUSY if the worker already holds `window` tasks; PIPE_EAGAIN if
+ * nothing is queued; PIPE_EINVAL for a bad worker. */
+int sched_request(sched_t s, int worker, uint64_t* task);
+/* The worker finished task (frees one window slot).  PIPE_EINVAL if the
+ * worker does not hold it. */
+int sched_done(sched_t s, int worker, uint64_t task);
+/* Queued, held (all workers) and completed task counts; any may be NULL. */
+int sched_counts(sched_t s, long long* queued, long long* in_flight, long long* completed);
+/* Cost estimate of an RGB tile for the queue: W * H * (1 + 8 f), f the
+ * fraction of dark pixels (R + G + B < 450: nuclei, not background or
+ * stroma) on a 1-in-64 sample grid.  -1 on bad arguments. */
+double tile_cost(const uint8_t* rgb, int W, int H, size_t pitch);
 
 #ifdef __cplusplus
 }

@@ -20,7 +20,9 @@ STATUS_NAMES = ["PIPE_OK", "PIPE_EINVAL", "PIPE_ENOMEM", "PIPE_EBUSY", "PIPE_EAG
 EXPORTS = ["pipe_default_params", "pipe_create", "pipe_destroy", "seg_tile", "features_tile",
            "seg_features_batch", "batch_submit", "batch_poll", "pipe_status_read", "pipe_debug_plane",
            "pipe_profile_enable", "pipe_profile_read", "pipe_launch_count", "pipe_recon_visits",
-           "features_tile_noalloc", "pipe_autotune_info", "morph_open_tile", "watershed_tile", "canny_tile"]
+           "features_tile_noalloc", "pipe_autotune_info", "morph_open_tile", "watershed_tile", "canny_tile",
+           "watershed_batch", "sched_create", "sched_destroy", "sched_push", "sched_request", "sched_done",
+           "sched_counts", "tile_cost"]
 NOALLOC_MAX_OBJECTS = 65536
 
 
@@ -81,6 +83,22 @@ def lib():
     L.morph_open_tile.argtypes = [vp, vp, ci, ci, ci, vp, vp]
     L.watershed_tile.argtypes = [vp, vp, vp, ci, ci, ci, ci, vp, vp, vp]
     L.canny_tile.argtypes = [vp, vp, vp, ci, ci, ci, ci, ci, ci, vp, vp, vp]
+    L.watershed_batch.argtypes = [vp, ctypes.POINTER(WsTileC), ci, ci, vp]
+    L.sched_create.argtypes = [ci, ci, ctypes.POINTER(vp)]
+    L.sched_create.restype = ci
+    L.sched_destroy.argtypes = [vp]
+    L.sched_destroy.restype = None
+    L.sched_push.argtypes = [vp, u64, ctypes.c_double]
+    L.sched_push.restype = ci
+    L.sched_request.argtypes = [vp, ci, ctypes.POINTER(u64)]
+    L.sched_request.restype = ci
+    L.sched_done.argtypes = [vp, ci, u64]
+    L.sched_done.restype = ci
+    L.sched_counts.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
+                               ctypes.POINTER(ctypes.c_longlong)]
+    L.sched_counts.restype = ci
+    L.tile_cost.argtypes = [vp, ci, ci, sz]
+    L.tile_cost.restype = ctypes.c_double
     L.batch_submit.argtypes = [vp, ctypes.POINTER(TileDesc), ci, ctypes.POINTER(u64)]
     L.batch_poll.argtypes = [vp, u64, ctypes.POINTER(ci), ctypes.POINTER(TileResult)]
     L.pipe_status_read.argtypes = [vp]
@@ -98,7 +116,7 @@ def lib():
                                      ctypes.POINTER(ctypes.c_longlong)]
     for n in ("pipe_create", "seg_tile", "features_tile", "seg_features_batch", "batch_submit", "batch_poll",
               "pipe_status_read", "pipe_debug_plane", "pipe_profile_enable", "pipe_profile_read",
-              "morph_open_tile", "watershed_tile", "canny_tile"):
+              "morph_open_tile", "watershed_tile", "canny_tile", "watershed_batch"):
         getattr(L, n).restype = ci
     _lib = L
     return L
@@ -128,6 +146,68 @@ def _stream_ptr(stream):
         import torch
         stream = torch.cuda.current_stream()
     return ctypes.c_void_p(stream.cuda_stream)
+
+
+def tile_cost(rgb):
+    """Cost estimate of a host RGB tile (H, W, 3) uint8 for the dispatch
+    queue: W * H * (1 + 8 * dark fraction on a 1-in-64 sample)."""
+    import numpy as np
+    a = np.asarray(rgb, dtype=np.uint8)
+    if a.ndim != 3 or a.shape[2] != 3 or a.strides[1:] != (3, 1):
+        a = np.ascontiguousarray(a)               # rows of packed RGB; a row pitch is kept as it is
+    H, W = a.shape[:2]
+    c = lib().tile_cost(a.ctypes.data, W, H, a.strides[0])
+    if c < 0:
+        raise ValueError("bad tile")
+    return c
+
+
+class Sched:
+    """Demand-driven dispatch queue (sched_t): workers request tasks, at most
+    `window` held each, most expensive first (the paper's Manager window,
+    Sec. III-B, with the PATS sorted queue, Sec. IV-B)."""
+
+    def __init__(self, n_workers, window):
+        h = ctypes.c_void_p()
+        _check(lib().sched_create(int(n_workers), int(window), ctypes.byref(h)), "sched_create")
+        self.h = h
+
+    def push(self, task, cost):
+        _check(lib().sched_push(self.h, int(task), float(cost)), "sched_push")
+
+    def request(self, worker):
+        """The granted task id, or None when nothing is queued; raises
+        PipeError(PIPE_EBUSY) when the worker's window is full."""
+        t = ctypes.c_uint64()
+        rc = lib().sched_request(self.h, int(worker), ctypes.byref(t))
+        if rc == PIPE_EAGAIN:
+            return None
+        _check(rc, "sched_request")
+        return t.value
+
+    def done(self, worker, task):
+        _check(lib().sched_done(self.h, int(worker), int(task)), "sched_done")
+
+    def counts(self):
+        q, f, c = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_longlong()
+        _check(lib().sched_counts(self.h, ctypes.byref(q), ctypes.byref(f), ctypes.byref(c)), "sched_counts")
+        return q.value, f.value, c.value
+
+    def close(self):
+        if self.h:
+            lib().sched_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class WsTileC(ctypes.Structure):
+    _fields_ = [("labels", ctypes.c_void_p), ("edt", ctypes.c_void_p), ("W", ctypes.c_int), ("H", ctypes.c_int),
+                ("n_objects", ctypes.c_int), ("out", ctypes.c_void_p), ("n_basins", ctypes.c_void_p)]
 
 
 class Pipe:
@@ -194,6 +274,21 @@ class Pipe:
         rc = lib().watershed_tile(self.h, labels.data_ptr(), edt.data_ptr(), W, H, int(n_objects), int(h),
                                   out.data_ptr(), n_basins.data_ptr(), _stream_ptr(stream))
         _check(rc, "watershed_tile")
+
+    def watershed_batch(self, tiles, h=1, stream=None):
+        """tiles: list of dicts with labels, edt, out (contiguous (H, W) int32
+        device tensors), n_objects (int) and n_basins (one-element int32
+        device tensor)."""
+        arr = (WsTileC * len(tiles))()
+        for i, t in enumerate(tiles):
+            H, W = t["labels"].shape
+            for k in ("labels", "edt", "out"):
+                if tuple(t[k].shape) != (H, W) or not t[k].is_contiguous():
+                    raise ValueError("labels, edt and out must be contiguous (H, W) int32 planes")
+            arr[i].labels, arr[i].edt, arr[i].out = t["labels"].data_ptr(), t["edt"].data_ptr(), t["out"].data_ptr()
+            arr[i].W, arr[i].H, arr[i].n_objects = W, H, int(t["n_objects"])
+            arr[i].n_basins = t["n_basins"].data_ptr()
+        _check(lib().watershed_batch(self.h, arr, len(tiles), int(h), _stream_ptr(stream)), "watershed_batch")
 
     def canny(self, img, edges, labels=None, n_objects=0, counts=None, low=40, high=120, radius=3, stream=None):
         """Canny edges of a (H, W) uint8 device tensor into edges (uint8 0/1),

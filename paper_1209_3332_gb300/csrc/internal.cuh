@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stddef.h>
+#include <vector>
 
 namespace nucseg {
 
@@ -174,12 +175,28 @@ void launch_canny_nms(const uint8_t* img, int W, int H, int low, int high, uint8
 // per object: edge pixels within its disk dilation of radius r (boxes into bbox)
 void launch_canny_counts(const uint8_t* edges, const int32_t* labels, int W, int H, int K, int r, int4* bbox,
                          int32_t* counts, int sms, cudaStream_t s, Profiler* pf);
+// One tile of a batched watershed split.
+struct WsDesc {
+    const int32_t* labels;
+    const int32_t* edt;
+    int32_t* out;
+    int32_t* n_basins;
+    long long px_base;    // first pixel of this tile in the scratch planes
+    int W, H, K;
+    int obj_base;         // first object item of this tile
+    int seg_base;         // first box row segment of this tile
+};
+// descs: host copy; d_descs: device array of the same length
+void launch_watershed_batch(const std::vector<WsDesc>& descs, WsDesc* d_descs, int h, int4* bbox, int* cnt,
+                            int* next, void* scratch, size_t scratch_px, int* status, int sms, cudaStream_t s,
+                            cudaStream_t side, cudaEvent_t fork, cudaEvent_t join, Profiler* pf);
 // scratch of the watershed's out-of-stage boxes: a 64-bit and a 16-bit word per pixel
 size_t watershed_scratch_bytes(int W, int H);
-// cnt: K ints (per-object basin counts, then their exclusive prefix); status: a device int
+// cnt: K ints (per-object basin counts, then their exclusive prefix); next: two device ints (work
+// counters of the two object kernels, zeroed by the launcher); status: a device int
 // side: a second stream for the large boxes (fork/join through the two events)
 void launch_watershed(const int32_t* labels, const int32_t* edt, int W, int H, int K, int h, int32_t* out,
-                      int32_t* n_basins, int4* bbox, int* cnt, void* scratch, int* status, int sms,
+                      int32_t* n_basins, int4* bbox, int* cnt, int* next, void* scratch, int* status, int sms,
                       cudaStream_t s, cudaStream_t side, cudaEvent_t fork, cudaEvent_t join, Profiler* pf);
 void launch_unpack_bits(const uint32_t* bits, int W, int H, int cbx, uint8_t* out, cudaStream_t s,
                         Profiler* pf);

@@ -505,17 +505,25 @@ __device__ __forceinline__ int ws_staged(const int32_t* __restrict__ labels, con
 
 __device__ __forceinline__ int ws_box_px(int4 bx) { return (bx.z - bx.x + 3) * (bx.w - bx.y + 3); }
 
+// The next object for this warp from a launch-wide counter (objects go to
+// whichever warp is free, so a warp that drew a slow object takes no more).
+__device__ __forceinline__ int ws_next(int* next, int lane) {
+    int v = 0;
+    if (lane == 0) v = atomicAdd(next, 1);
+    return __shfl_sync(WFULL, v, 0);
+}
+
 // Small boxes: one warp per object, WS_STAGE pixels of stage each.  Writes
 // the basin's rank inside the object to out and the basin count to
 // cnt[object]; objects with larger boxes are left to k_ws_large.
 __global__ void __launch_bounds__(WS_WARPS * 32) k_ws_objects(const int32_t* __restrict__ labels,
                                                                const int32_t* __restrict__ edt, int W, int H,
                                                                int K, int h, const int4* __restrict__ bbox,
-                                                               int32_t* out, int* cnt, int* status) {
+                                                               int32_t* out, int* cnt, int* next, int* status) {
     extern __shared__ __align__(16) char ws_smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     char* stage = ws_smem + (size_t)warp * WS_STAGE * WS_PX_BYTES;
-    for (int obj = blockIdx.x * WS_WARPS + warp; obj < K; obj += gridDim.x * WS_WARPS) {
+    for (int obj = ws_next(next, lane); obj < K; obj = ws_next(next, lane)) {
         const int4 bx = bbox[obj];
         if (bx.z < bx.x) {
             if (lane == 0) cnt[obj] = 0;
@@ -533,10 +541,10 @@ __global__ void __launch_bounds__(WS_WARPS * 32) k_ws_objects(const int32_t* __r
 __global__ void __launch_bounds__(32) k_ws_large(const int32_t* __restrict__ labels, const int32_t* __restrict__ edt,
                                                  int W, int H, int K, int h, const int4* __restrict__ bbox,
                                                  int32_t* out, int* cnt, int cap, uint16_t* gdr,
-                                                 unsigned long long* gw, int* status) {
+                                                 unsigned long long* gw, int* next, int* status) {
     extern __shared__ __align__(16) char ws_smem[];
     const int lane = threadIdx.x;
-    for (int obj = blockIdx.x; obj < K; obj += gridDim.x) {
+    for (int obj = ws_next(next, lane); obj < K; obj = ws_next(next, lane)) {
         const int4 bx = bbox[obj];
         if (bx.z < bx.x || ws_box_px(bx) <= WS_STAGE) continue;
         const int c = ws_box_px(bx) <= cap
@@ -547,8 +555,8 @@ __global__ void __launch_bounds__(32) k_ws_large(const int32_t* __restrict__ lab
     }
 }
 
-// In place: cnt[i] -> exclusive prefix; total -> *n_basins.
-__global__ void __launch_bounds__(1024) k_ws_scan(int* cnt, int K, int32_t* n_basins) {
+// In place: cnt[i] -> exclusive prefix; total -> *n_basins (one CTA of 1024).
+__device__ __forceinline__ void ws_scan_block(int* cnt, int K, int32_t* n_basins) {
     __shared__ int wsum[32];
     __shared__ int carry;
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
@@ -584,6 +592,20 @@ __global__ void __launch_bounds__(1024) k_ws_scan(int* cnt, int K, int32_t* n_ba
     if (t == 0) *n_basins = carry;
 }
 
+__global__ void __launch_bounds__(1024) k_ws_scan(int* cnt, int K, int32_t* n_basins) {
+    ws_scan_block(cnt, K, n_basins);
+}
+
+// out += o on the pixels of object k inside box bx (one warp).
+__device__ __forceinline__ void ws_offset_obj(const int32_t* __restrict__ labels, int W, int k, int4 bx, int o,
+                                              int32_t* out, int lane) {
+    const int bw = bx.z - bx.x + 1, n = bw * (bx.w - bx.y + 1);
+    for (Walk it(lane, bw); it.f < n; it.next()) {
+        const size_t g = (size_t)(bx.y + it.y) * W + (bx.x + it.x);
+        if (labels[g] == k) out[g] += o;
+    }
+}
+
 // out += the object's first basin number - 1 on the object's pixels.
 __global__ void __launch_bounds__(256) k_ws_offset(const int32_t* __restrict__ labels, int W, int K,
                                                    const int4* __restrict__ bbox, const int* __restrict__ off,
@@ -594,11 +616,103 @@ __global__ void __launch_bounds__(256) k_ws_offset(const int32_t* __restrict__ l
         const int o = off[obj];
         const int4 bx = bbox[obj];
         if (o == 0 || bx.z < bx.x) continue;
-        const int bw = bx.z - bx.x + 1, n = bw * (bx.w - bx.y + 1);
-        for (Walk it(lane, bw); it.f < n; it.next()) {
-            const size_t g = (size_t)(bx.y + it.y) * W + (bx.x + it.x);
-            if (labels[g] == obj + 1) out[g] += o;
+        ws_offset_obj(labels, W, obj + 1, bx, o, out, lane);
+    }
+}
+
+// ---- batched form: the objects of many tiles in one launch per pass ----------------
+// Items are objects numbered across the tiles; the tile of an item is the last
+// descriptor whose obj_base is <= the item (seg_base likewise for box segments).
+__device__ __forceinline__ int ws_desc_of(const WsDesc* __restrict__ D, int n, int item, bool by_seg) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if ((by_seg ? D[mid].seg_base : D[mid].obj_base) <= item) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+constexpr int WS_DESC_PACK = 16;
+struct WsDescPack {
+    int first, n;
+    WsDesc d[WS_DESC_PACK];
+};
+
+__global__ void k_ws_set_desc(WsDesc* dst, WsDescPack pk) {
+    if ((int)threadIdx.x < pk.n) dst[pk.first + threadIdx.x] = pk.d[threadIdx.x];
+}
+
+__global__ void k_ws_bbox_init_b(int4* bbox, int total) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < total) bbox[i] = make_int4(0x7fffffff, 0x7fffffff, -1, -1);
+}
+
+__global__ void __launch_bounds__(256) k_ws_bbox_b(const WsDesc* __restrict__ D, int n, int total_segs,
+                                                   int4* bbox) {
+    const int lane = threadIdx.x & 31;
+    const int gw = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (gw >= total_segs) return;
+    const WsDesc& T = D[ws_desc_of(D, n, gw, true)];
+    const int k = gw - T.seg_base, spr = (T.W + FB_SEG - 1) / FB_SEG;
+    const int y = k / spr, xs = (k - y * spr) * FB_SEG;
+    bbox_segment(T.labels + (size_t)y * T.W, T.W, T.K, y, xs, bbox + T.obj_base, lane);
+}
+
+__global__ void __launch_bounds__(WS_WARPS * 32) k_ws_objects_b(const WsDesc* __restrict__ D, int n, int total,
+                                                                 int h, const int4* __restrict__ bbox, int* cnt,
+                                                                 int* next, int* status) {
+    extern __shared__ __align__(16) char ws_smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    char* stage = ws_smem + (size_t)warp * WS_STAGE * WS_PX_BYTES;
+    for (int item = ws_next(next, lane); item < total; item = ws_next(next, lane)) {
+        const int4 bx = bbox[item];
+        if (bx.z < bx.x) {
+            if (lane == 0) cnt[item] = 0;
+            continue;
         }
+        if (ws_box_px(bx) > WS_STAGE) continue;
+        const WsDesc& T = D[ws_desc_of(D, n, item, false)];
+        const int c = ws_staged(T.labels, T.edt, T.W, T.H, item - T.obj_base + 1, bx, h, stage, WS_STAGE, T.out,
+                                status, lane);
+        if (lane == 0) cnt[item] = c;
+        __syncwarp();
+    }
+}
+
+__global__ void __launch_bounds__(32) k_ws_large_b(const WsDesc* __restrict__ D, int n, int total, int h,
+                                                   const int4* __restrict__ bbox, int* cnt, int cap, uint16_t* gdr,
+                                                   unsigned long long* gw, int* next, int* status) {
+    extern __shared__ __align__(16) char ws_smem[];
+    const int lane = threadIdx.x;
+    for (int item = ws_next(next, lane); item < total; item = ws_next(next, lane)) {
+        const int4 bx = bbox[item];
+        if (bx.z < bx.x || ws_box_px(bx) <= WS_STAGE) continue;
+        const WsDesc& T = D[ws_desc_of(D, n, item, false)];
+        const int k = item - T.obj_base + 1;
+        const int c = ws_box_px(bx) <= cap
+                          ? ws_staged(T.labels, T.edt, T.W, T.H, k, bx, h, ws_smem, cap, T.out, status, lane)
+                          : ws_object_global(T.labels, T.edt, T.W, k, bx, h, gdr + T.px_base, gw + T.px_base,
+                                             T.out, status, lane);
+        if (lane == 0) cnt[item] = c;
+        __syncwarp();
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_ws_scan_b(const WsDesc* __restrict__ D, int* cnt) {
+    const WsDesc& T = D[blockIdx.x];
+    ws_scan_block(cnt + T.obj_base, T.K, T.n_basins);
+}
+
+__global__ void __launch_bounds__(256) k_ws_offset_b(const WsDesc* __restrict__ D, int n, int total,
+                                                     const int4* __restrict__ bbox, const int* __restrict__ off) {
+    const int lane = threadIdx.x & 31;
+    const int nw = gridDim.x * (blockDim.x >> 5);
+    for (int item = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); item < total; item += nw) {
+        const int o = off[item];
+        const int4 bx = bbox[item];
+        if (o == 0 || bx.z < bx.x) continue;
+        const WsDesc& T = D[ws_desc_of(D, n, item, false)];
+        ws_offset_obj(T.labels, T.W, item - T.obj_base + 1, bx, o, T.out, lane);
     }
 }
 
@@ -607,7 +721,7 @@ size_t watershed_scratch_bytes(int W, int H) {
 }
 
 void launch_watershed(const int32_t* labels, const int32_t* edt, int W, int H, int K, int h, int32_t* out,
-                      int32_t* n_basins, int4* bbox, int* cnt, void* scratch, int* status, int sms,
+                      int32_t* n_basins, int4* bbox, int* cnt, int* next, void* scratch, int* status, int sms,
                       cudaStream_t s, cudaStream_t side, cudaEvent_t fork, cudaEvent_t join, Profiler* pf) {
     static bool attrs[64] = {};  // opt-in shared memory above 48 KB, once per device
     const int small_smem = WS_WARPS * WS_STAGE * WS_PX_BYTES;
@@ -627,18 +741,20 @@ void launch_watershed(const int32_t* labels, const int32_t* edt, int W, int H, i
     launch_object_boxes(labels, W, H, K, bbox, s, pf);
     unsigned long long* gw = (unsigned long long*)scratch;
     uint16_t* gdr = (uint16_t*)(gw + N);
+    cudaMemsetAsync(next, 0, 2 * sizeof(int), s);
     // the large boxes on the side stream, overlapping the small ones
     cudaEventRecord(fork, s);
     cudaStreamWaitEvent(side, fork, 0);
     pf->begin("ws_large", side);
     k_ws_large<<<K < sms * 2 ? K : sms * 2, 32, WS_LARGE_SMEM, side>>>(labels, edt, W, H, K, h, bbox, out, cnt,
-                                                                   WS_LARGE_SMEM / WS_PX_BYTES, gdr, gw, status);
+                                                                   WS_LARGE_SMEM / WS_PX_BYTES, gdr, gw, next + 1,
+                                                                   status);
     pf->end("ws_large", side);
     cudaEventRecord(join, side);
     const int ctas = (K + WS_WARPS - 1) / WS_WARPS;
     pf->begin("ws_objects", s);
     k_ws_objects<<<ctas < sms * 4 ? ctas : sms * 4, WS_WARPS * 32, small_smem, s>>>(labels, edt, W, H, K, h, bbox,
-                                                                                 out, cnt, status);
+                                                                                 out, cnt, next, status);
     pf->end("ws_objects", s);
     cudaStreamWaitEvent(s, join, 0);
     pf->begin("ws_scan", s);
@@ -648,6 +764,67 @@ void launch_watershed(const int32_t* labels, const int32_t* edt, int W, int H, i
     pf->begin("ws_offset", s);
     k_ws_offset<<<octas < sms * 8 ? octas : sms * 8, 256, 0, s>>>(labels, W, K, bbox, cnt, out);
     pf->end("ws_offset", s);
+}
+
+void launch_watershed_batch(const std::vector<WsDesc>& descs, WsDesc* d_descs, int h, int4* bbox, int* cnt,
+                            int* next, void* scratch, size_t scratch_px, int* status, int sms, cudaStream_t s,
+                            cudaStream_t side, cudaEvent_t fork, cudaEvent_t join, Profiler* pf) {
+    static bool attrs[64] = {};  // opt-in shared memory above 48 KB, once per device
+    const int small_smem = WS_WARPS * WS_STAGE * WS_PX_BYTES;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64 || !attrs[dev]) {
+        cudaFuncSetAttribute(k_ws_objects_b, cudaFuncAttributeMaxDynamicSharedMemorySize, small_smem);
+        cudaFuncSetAttribute(k_ws_large_b, cudaFuncAttributeMaxDynamicSharedMemorySize, WS_LARGE_SMEM);
+        if (dev >= 0 && dev < 64) attrs[dev] = true;
+    }
+    const int n = (int)descs.size();
+    int total = 0, segs = 0;
+    for (const WsDesc& d : descs) {
+        cudaMemsetAsync(d.out, 0, (size_t)d.W * d.H * sizeof(int32_t), s);
+        total += d.K;
+        segs += (d.W + FB_SEG - 1) / FB_SEG * d.H;
+    }
+    for (int i = 0; i < n; i += WS_DESC_PACK) {
+        WsDescPack pk;
+        pk.first = i;
+        pk.n = n - i < WS_DESC_PACK ? n - i : WS_DESC_PACK;
+        for (int k = 0; k < pk.n; k++) pk.d[k] = descs[i + k];
+        k_ws_set_desc<<<1, WS_DESC_PACK, 0, s>>>(d_descs, pk);
+    }
+    if (total > 0) {
+        unsigned long long* gw = (unsigned long long*)scratch;
+        uint16_t* gdr = (uint16_t*)(gw + scratch_px);
+        pf->begin("ws_bbox_init", s);
+        k_ws_bbox_init_b<<<(total + 255) / 256, 256, 0, s>>>(bbox, total);
+        pf->end("ws_bbox_init", s);
+        pf->begin("ws_bbox", s);
+        k_ws_bbox_b<<<(unsigned)(((long long)segs * 32 + 255) / 256), 256, 0, s>>>(d_descs, n, segs, bbox);
+        pf->end("ws_bbox", s);
+        cudaMemsetAsync(next, 0, 2 * sizeof(int), s);
+        cudaEventRecord(fork, s);
+        cudaStreamWaitEvent(side, fork, 0);
+        pf->begin("ws_large", side);
+        k_ws_large_b<<<total < sms * 2 ? total : sms * 2, 32, WS_LARGE_SMEM, side>>>(
+            d_descs, n, total, h, bbox, cnt, WS_LARGE_SMEM / WS_PX_BYTES, gdr, gw, next + 1, status);
+        pf->end("ws_large", side);
+        cudaEventRecord(join, side);
+        const int ctas = (total + WS_WARPS - 1) / WS_WARPS;
+        pf->begin("ws_objects", s);
+        k_ws_objects_b<<<ctas < sms * 4 ? ctas : sms * 4, WS_WARPS * 32, small_smem, s>>>(d_descs, n, total, h, bbox,
+                                                                                        cnt, next, status);
+        pf->end("ws_objects", s);
+        cudaStreamWaitEvent(s, join, 0);
+    }
+    pf->begin("ws_scan", s);
+    k_ws_scan_b<<<n, 1024, 0, s>>>(d_descs, cnt);
+    pf->end("ws_scan", s);
+    if (total > 0) {
+        const int octas = (total + 7) / 8;
+        pf->begin("ws_offset", s);
+        k_ws_offset_b<<<octas < sms * 8 ? octas : sms * 8, 256, 0, s>>>(d_descs, n, total, bbox, cnt);
+        pf->end("ws_offset", s);
+    }
 }
 
 }  // namespace nucseg

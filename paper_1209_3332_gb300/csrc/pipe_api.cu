@@ -308,6 +308,7 @@ struct pipe_s {
     DevBuf ws_obj;      // watershed_tile: per-object boxes and basin counts
     DevBuf ws_scratch;  // watershed_tile: planes for boxes larger than the shared-memory stage
     DevBuf ws_status;   // watershed_tile: device status word
+    DevBuf ws_desc;     // watershed_batch: tile descriptors
     cudaStream_t ws_side = nullptr;        // watershed_tile: large boxes overlap the small ones here
     LaunchCtx canny;    // canny_tile: the hysteresis runs the reconstruction on this context
     DevBuf canny_cand;  // canny_tile: candidate plane (the reconstruction's mask)
@@ -685,6 +686,7 @@ void pipe_destroy(pipe_t p) {
     p->canny_obj.release();
     p->ws_scratch.release();
     p->ws_status.release();
+    p->ws_desc.release();
     if (p->ws_side) cudaStreamDestroy(p->ws_side);
     if (p->ws_fork) cudaEventDestroy(p->ws_fork);
     if (p->ws_join) cudaEventDestroy(p->ws_join);
@@ -786,7 +788,7 @@ int watershed_tile(pipe_t p, const int32_t* labels_dev, const int32_t* edt_dev, 
     if (overlap(out_dev, labels_dev) || overlap(out_dev, edt_dev)) return PIPE_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     CK(cudaSetDevice(p->device));
-    const size_t need_obj = (size_t)std::max(n_objects, 1) * (sizeof(int4) + sizeof(int));
+    const size_t need_obj = (size_t)std::max(n_objects, 1) * (sizeof(int4) + sizeof(int)) + 2 * sizeof(int);
     const size_t need_scr = watershed_scratch_bytes(W, H);
     if (p->ws_obj.n < need_obj || p->ws_scratch.n < need_scr || !p->ws_status.p) {
         CK(cudaStreamSynchronize(s));
@@ -804,8 +806,70 @@ int watershed_tile(pipe_t p, const int32_t* labels_dev, const int32_t* edt_dev, 
     }
     int4* bbox = (int4*)p->ws_obj.p;
     int* cnt = (int*)(bbox + std::max(n_objects, 1));
-    launch_watershed(labels_dev, edt_dev, W, H, n_objects, h, out_dev, n_basins_dev, bbox, cnt, p->ws_scratch.p,
+    int* next = cnt + std::max(n_objects, 1);
+    launch_watershed(labels_dev, edt_dev, W, H, n_objects, h, out_dev, n_basins_dev, bbox, cnt, next, p->ws_scratch.p,
                      (int*)p->ws_status.p, p->sms, s, p->ws_side, p->ws_fork, p->ws_join, &p->prof);
+    CK(cudaGetLastError());
+    return PIPE_OK;
+}
+
+int watershed_batch(pipe_t p, const ws_tile* tiles, int n, int h, pipe_stream_t stream) {
+    if (!p || !tiles || n < 1 || n > 4096 || h < 0 || h > 255) return PIPE_EINVAL;
+    std::vector<WsDesc> d(n);
+    size_t objs = 0, px = 0;
+    for (int i = 0; i < n; i++) {
+        const ws_tile& t = tiles[i];
+        if (!t.labels || !t.edt || !t.out || !t.n_basins || t.n_objects < 0 || !valid_size(t.W, t.H))
+            return PIPE_EINVAL;
+        const size_t N = (size_t)t.W * t.H;
+        const char *o = (const char*)t.out, *l = (const char*)t.labels, *e = (const char*)t.edt;
+        if ((o < l + N * 4 && l < o + N * 4) || (o < e + N * 4 && e < o + N * 4)) return PIPE_EINVAL;
+        d[i].labels = t.labels;
+        d[i].edt = t.edt;
+        d[i].out = t.out;
+        d[i].n_basins = t.n_basins;
+        d[i].px_base = (long long)px;
+        d[i].W = t.W;
+        d[i].H = t.H;
+        d[i].K = t.n_objects;
+        d[i].obj_base = (int)objs;
+        d[i].seg_base = 0;
+        objs += (size_t)t.n_objects;
+        px += N;
+    }
+    if (objs > (size_t)INT32_MAX / 32) return PIPE_EINVAL;
+    long long segs = 0;
+    for (auto& x : d) {
+        x.seg_base = (int)segs;
+        segs += (long long)(x.W + FB_SEG - 1) / FB_SEG * x.H;
+    }
+    if (segs * 32 > INT32_MAX) return PIPE_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaSetDevice(p->device));
+    const size_t need_obj = std::max(objs, (size_t)1) * (sizeof(int4) + sizeof(int)) + 2 * sizeof(int);
+    const size_t need_scr = px * (sizeof(unsigned long long) + sizeof(uint16_t));
+    const size_t need_desc = sizeof(WsDesc) * (size_t)n;
+    if (p->ws_obj.n < need_obj || p->ws_scratch.n < need_scr || p->ws_desc.n < need_desc || !p->ws_status.p) {
+        CK(cudaStreamSynchronize(s));
+        int rc;
+        if ((rc = p->ws_obj.ensure(need_obj)) || (rc = p->ws_scratch.ensure(need_scr)) ||
+            (rc = p->ws_desc.ensure(need_desc)))
+            return rc;
+        if (!p->ws_status.p) {
+            if ((rc = p->ws_status.ensure(sizeof(int)))) return rc;
+            CK(cudaMemset(p->ws_status.p, 0, sizeof(int)));
+        }
+    }
+    if (!p->ws_side) {
+        CK(cudaStreamCreateWithFlags(&p->ws_side, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&p->ws_fork, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&p->ws_join, cudaEventDisableTiming));
+    }
+    int4* bbox = (int4*)p->ws_obj.p;
+    int* cnt = (int*)(bbox + std::max(objs, (size_t)1));
+    int* next = cnt + std::max(objs, (size_t)1);
+    launch_watershed_batch(d, (WsDesc*)p->ws_desc.p, h, bbox, cnt, next, p->ws_scratch.p, px, (int*)p->ws_status.p, p->sms,
+                           s, p->ws_side, p->ws_fork, p->ws_join, &p->prof);
     CK(cudaGetLastError());
     return PIPE_OK;
 }

@@ -13,7 +13,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def declared():
     src = open(os.path.join(ROOT, "include", "pipe.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(?:int|void|long long)\s+(\w+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(?:int|void|long long|double)\s+(\w+)\s*\(", src)))
 
 
 def test_library_builds_and_exports_every_declared_symbol():

@@ -4,7 +4,9 @@ closed-form shapes (discs, symmetric pairs, chains, necks at several marker
 heights), random unions of discs, objects whose box exceeds the shared-memory
 stage (the global-memory path), image edges, a tile without background,
 labels above n_objects, workload tiles through the whole GPU path up to the
-full 4096^2 benchmark tile, determinism, and the argument checks."""
+full 4096^2 benchmark tile, determinism, the batched form (equal to the
+oracle per tile, and to the plain form on four 4096^2 tiles), and the
+argument checks."""
 import numpy as np
 import pytest
 
@@ -145,6 +147,52 @@ def test_full_4096_benchmark_tile(pipe):
     a, na = gpu_ws(pipe, r["labels"], r["edt"], r["K"], 1)
     b, nb = gpu_ws(pipe, r["labels"], r["edt"], r["K"], 1)
     assert na == nb and np.array_equal(a, b)
+
+
+def _ws_batch(pipe, labs, Ks, h):
+    import torch
+    dev = torch.device("cuda", 0)
+    tiles = []
+    for lab, K in zip(labs, Ks):
+        L = torch.from_numpy(np.ascontiguousarray(lab, np.int32)).to(dev)
+        tiles.append(dict(labels=L, edt=torch.from_numpy(oracle.edt(lab)).to(dev), out=torch.full_like(L, -7),
+                          n_objects=K, n_basins=torch.full((1,), -7, dtype=torch.int32, device=dev)))
+    pipe.watershed_batch(tiles, h=h)
+    torch.cuda.synchronize()
+    return [(t["out"].cpu().numpy(), int(t["n_basins"].item())) for t in tiles]
+
+
+@pytest.mark.parametrize("h", [1, 2])
+def test_batched_form_equals_the_oracle_per_tile(pipe, h):
+    """Tiles of ragged sizes in one batch: workload tiles with clusters (one
+    with labels above n_objects), a chain of discs whose box exceeds the
+    stage, a 1x1 tile, empty tiles."""
+    labs = []
+    for seed, (W, H) in enumerate(((300, 200), (64, 33), (420, 300), (17, 90), (513, 257))):
+        rgb = synth.tile(W, H, 500 + seed, n_nuclei=max(1, W * H // 900), frac_cluster=0.5)
+        labs.append(oracle.seg(rgb, amax=6000)["labels"])
+    labs.append(lab_of(discs(300, 420, [(40, 20 + 22 * i) for i in range(12)], 12)))
+    labs.append(np.ones((1, 1), np.int32))
+    labs.append(np.zeros((5, 7), np.int32))
+    Ks = [int(x.max()) for x in labs]
+    Ks[0] -= 2
+    got = _ws_batch(pipe, labs, Ks, h)
+    for lab, K, (out, n) in zip(labs, Ks, got):
+        want, wn = oracle.watershed(np.where(lab <= K, lab, 0), oracle.edt(lab), h)
+        assert n == wn and np.array_equal(out, want)
+
+
+def test_batched_form_equals_the_plain_form_on_4096_tiles(pipe):
+    import bench
+    labs = []
+    for i in range(4):
+        rgb = synth.tile(4096, 4096, bench.tile_seed(0, i), n_nuclei=3000, frac_cluster=0.2, n_stroma=150)
+        labs.append(oracle.seg(rgb)["labels"])
+    Ks = [int(x.max()) for x in labs]
+    got = _ws_batch(pipe, labs, Ks, 1)
+    for lab, K, (out, n) in zip(labs, Ks, got):
+        plain, pn = gpu_ws(pipe, lab, oracle.edt(lab), K, 1)
+        assert n == pn and np.array_equal(out, plain)
 
 
 def test_argument_checks(pipe):
