@@ -505,7 +505,7 @@ __device__ __forceinline__ int ws_staged(const int32_t* __restrict__ labels, con
 
 __device__ __forceinline__ int ws_box_px(int4 bx) { return (bx.z - bx.x + 3) * (bx.w - bx.y + 3); }
 
-// The next object for this warp from a launch-wide counter (objects go to
+// The next entry for this warp from a launch-wide counter (entries go to
 // whichever warp is free, so a warp that drew a slow object takes no more).
 __device__ __forceinline__ int ws_next(int* next, int lane) {
     int v = 0;
@@ -513,40 +513,50 @@ __device__ __forceinline__ int ws_next(int* next, int lane) {
     return __shfl_sync(WFULL, v, 0);
 }
 
-// Small boxes: one warp per object, WS_STAGE pixels of stage each.  Writes
-// the basin's rank inside the object to out and the basin count to
-// cnt[object]; objects with larger boxes are left to k_ws_large.
+// Sorts the objects before the two object kernels: an absent object
+// (empty box) gets count 0; an object whose box exceeds the small stage is
+// appended to the large list (next[1] entries).
+__global__ void k_ws_classify(const int4* __restrict__ bbox, int total, int* cnt, int* next, int* list) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= total) return;
+    const int4 bx = bbox[i];
+    if (bx.z < bx.x) cnt[i] = 0;
+    else if (ws_box_px(bx) > WS_STAGE) list[atomicAdd(next + 1, 1)] = i;
+}
+
+// Small boxes: one warp per object (the grid covers every object, so CTAs
+// retire as their objects finish and the large-box CTAs find room), with
+// WS_STAGE pixels of stage each.  Writes the basin's rank inside the object
+// to out and the basin count to cnt[object]; objects with larger boxes are
+// left to k_ws_large.
 __global__ void __launch_bounds__(WS_WARPS * 32) k_ws_objects(const int32_t* __restrict__ labels,
                                                                const int32_t* __restrict__ edt, int W, int H,
                                                                int K, int h, const int4* __restrict__ bbox,
-                                                               int32_t* out, int* cnt, int* next, int* status) {
+                                                               int32_t* out, int* cnt, int* status) {
     extern __shared__ __align__(16) char ws_smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     char* stage = ws_smem + (size_t)warp * WS_STAGE * WS_PX_BYTES;
-    for (int obj = ws_next(next, lane); obj < K; obj = ws_next(next, lane)) {
-        const int4 bx = bbox[obj];
-        if (bx.z < bx.x) {
-            if (lane == 0) cnt[obj] = 0;
-            continue;
-        }
-        if (ws_box_px(bx) > WS_STAGE) continue;
-        const int c = ws_staged(labels, edt, W, H, obj + 1, bx, h, stage, WS_STAGE, out, status, lane);
-        if (lane == 0) cnt[obj] = c;
-        __syncwarp();
-    }
+    const int obj = blockIdx.x * WS_WARPS + warp;
+    if (obj >= K) return;
+    const int4 bx = bbox[obj];
+    if (bx.z < bx.x || ws_box_px(bx) > WS_STAGE) return;
+    const int c = ws_staged(labels, edt, W, H, obj + 1, bx, h, stage, WS_STAGE, out, status, lane);
+    if (lane == 0) cnt[obj] = c;
 }
 
-// Large boxes: one warp per CTA with a stage of `cap` pixels; boxes beyond
-// it run on the global scratch planes.
+// Large boxes: one warp per CTA with a stage of `cap` pixels, drawing from
+// the large list (next[0] the draw counter, next[1] its length); boxes
+// beyond the stage run on the global scratch planes.
 __global__ void __launch_bounds__(32) k_ws_large(const int32_t* __restrict__ labels, const int32_t* __restrict__ edt,
-                                                 int W, int H, int K, int h, const int4* __restrict__ bbox,
-                                                 int32_t* out, int* cnt, int cap, uint16_t* gdr,
-                                                 unsigned long long* gw, int* next, int* status) {
+                                                 int W, int H, int h, const int4* __restrict__ bbox, int32_t* out,
+                                                 int* cnt, int cap, uint16_t* gdr, unsigned long long* gw, int* next,
+                                                 const int* __restrict__ list, int* status) {
     extern __shared__ __align__(16) char ws_smem[];
     const int lane = threadIdx.x;
-    for (int obj = ws_next(next, lane); obj < K; obj = ws_next(next, lane)) {
+    const int nl = next[1];
+    for (int i = ws_next(next, lane); i < nl; i = ws_next(next, lane)) {
+        const int obj = list[i];
         const int4 bx = bbox[obj];
-        if (bx.z < bx.x || ws_box_px(bx) <= WS_STAGE) continue;
         const int c = ws_box_px(bx) <= cap
                           ? ws_staged(labels, edt, W, H, obj + 1, bx, h, ws_smem, cap, out, status, lane)
                           : ws_object_global(labels, edt, W, obj + 1, bx, h, gdr, gw, out, status, lane);
@@ -660,33 +670,30 @@ __global__ void __launch_bounds__(256) k_ws_bbox_b(const WsDesc* __restrict__ D,
 
 __global__ void __launch_bounds__(WS_WARPS * 32) k_ws_objects_b(const WsDesc* __restrict__ D, int n, int total,
                                                                  int h, const int4* __restrict__ bbox, int* cnt,
-                                                                 int* next, int* status) {
+                                                                 int* status) {
     extern __shared__ __align__(16) char ws_smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     char* stage = ws_smem + (size_t)warp * WS_STAGE * WS_PX_BYTES;
-    for (int item = ws_next(next, lane); item < total; item = ws_next(next, lane)) {
-        const int4 bx = bbox[item];
-        if (bx.z < bx.x) {
-            if (lane == 0) cnt[item] = 0;
-            continue;
-        }
-        if (ws_box_px(bx) > WS_STAGE) continue;
-        const WsDesc& T = D[ws_desc_of(D, n, item, false)];
-        const int c = ws_staged(T.labels, T.edt, T.W, T.H, item - T.obj_base + 1, bx, h, stage, WS_STAGE, T.out,
-                                status, lane);
-        if (lane == 0) cnt[item] = c;
-        __syncwarp();
-    }
+    const int item = blockIdx.x * WS_WARPS + warp;
+    if (item >= total) return;
+    const int4 bx = bbox[item];
+    if (bx.z < bx.x || ws_box_px(bx) > WS_STAGE) return;
+    const WsDesc& T = D[ws_desc_of(D, n, item, false)];
+    const int c = ws_staged(T.labels, T.edt, T.W, T.H, item - T.obj_base + 1, bx, h, stage, WS_STAGE, T.out, status,
+                            lane);
+    if (lane == 0) cnt[item] = c;
 }
 
-__global__ void __launch_bounds__(32) k_ws_large_b(const WsDesc* __restrict__ D, int n, int total, int h,
+__global__ void __launch_bounds__(32) k_ws_large_b(const WsDesc* __restrict__ D, int n, int h,
                                                    const int4* __restrict__ bbox, int* cnt, int cap, uint16_t* gdr,
-                                                   unsigned long long* gw, int* next, int* status) {
+                                                   unsigned long long* gw, int* next, const int* __restrict__ list,
+                                                   int* status) {
     extern __shared__ __align__(16) char ws_smem[];
     const int lane = threadIdx.x;
-    for (int item = ws_next(next, lane); item < total; item = ws_next(next, lane)) {
+    const int nl = next[1];
+    for (int i = ws_next(next, lane); i < nl; i = ws_next(next, lane)) {
+        const int item = list[i];
         const int4 bx = bbox[item];
-        if (bx.z < bx.x || ws_box_px(bx) <= WS_STAGE) continue;
         const WsDesc& T = D[ws_desc_of(D, n, item, false)];
         const int k = item - T.obj_base + 1;
         const int c = ws_box_px(bx) <= cap
@@ -741,20 +748,23 @@ void launch_watershed(const int32_t* labels, const int32_t* edt, int W, int H, i
     launch_object_boxes(labels, W, H, K, bbox, s, pf);
     unsigned long long* gw = (unsigned long long*)scratch;
     uint16_t* gdr = (uint16_t*)(gw + N);
+    int* list = next + 2;
     cudaMemsetAsync(next, 0, 2 * sizeof(int), s);
-    // the large boxes on the side stream, overlapping the small ones
+    pf->begin("ws_classify", s);
+    k_ws_classify<<<(K + 255) / 256, 256, 0, s>>>(bbox, K, cnt, next, list);
+    pf->end("ws_classify", s);
+    // the large boxes on the (higher-priority) side stream, overlapping the small ones
     cudaEventRecord(fork, s);
     cudaStreamWaitEvent(side, fork, 0);
     pf->begin("ws_large", side);
-    k_ws_large<<<K < sms * 2 ? K : sms * 2, 32, WS_LARGE_SMEM, side>>>(labels, edt, W, H, K, h, bbox, out, cnt,
-                                                                   WS_LARGE_SMEM / WS_PX_BYTES, gdr, gw, next + 1,
-                                                                   status);
+    k_ws_large<<<K < sms ? K : sms, 32, WS_LARGE_SMEM, side>>>(labels, edt, W, H, h, bbox, out, cnt,
+                                                           WS_LARGE_SMEM / WS_PX_BYTES, gdr, gw, next, list,
+                                                           status);
     pf->end("ws_large", side);
     cudaEventRecord(join, side);
     const int ctas = (K + WS_WARPS - 1) / WS_WARPS;
     pf->begin("ws_objects", s);
-    k_ws_objects<<<ctas < sms * 4 ? ctas : sms * 4, WS_WARPS * 32, small_smem, s>>>(labels, edt, W, H, K, h, bbox,
-                                                                                 out, cnt, next, status);
+    k_ws_objects<<<ctas, WS_WARPS * 32, small_smem, s>>>(labels, edt, W, H, K, h, bbox, out, cnt, status);
     pf->end("ws_objects", s);
     cudaStreamWaitEvent(s, join, 0);
     pf->begin("ws_scan", s);
@@ -801,18 +811,21 @@ void launch_watershed_batch(const std::vector<WsDesc>& descs, WsDesc* d_descs, i
         pf->begin("ws_bbox", s);
         k_ws_bbox_b<<<(unsigned)(((long long)segs * 32 + 255) / 256), 256, 0, s>>>(d_descs, n, segs, bbox);
         pf->end("ws_bbox", s);
+        int* list = next + 2;
         cudaMemsetAsync(next, 0, 2 * sizeof(int), s);
+        pf->begin("ws_classify", s);
+        k_ws_classify<<<(total + 255) / 256, 256, 0, s>>>(bbox, total, cnt, next, list);
+        pf->end("ws_classify", s);
         cudaEventRecord(fork, s);
         cudaStreamWaitEvent(side, fork, 0);
         pf->begin("ws_large", side);
-        k_ws_large_b<<<total < sms * 2 ? total : sms * 2, 32, WS_LARGE_SMEM, side>>>(
-            d_descs, n, total, h, bbox, cnt, WS_LARGE_SMEM / WS_PX_BYTES, gdr, gw, next + 1, status);
+        k_ws_large_b<<<total < sms ? total : sms, 32, WS_LARGE_SMEM, side>>>(
+            d_descs, n, h, bbox, cnt, WS_LARGE_SMEM / WS_PX_BYTES, gdr, gw, next, list, status);
         pf->end("ws_large", side);
         cudaEventRecord(join, side);
         const int ctas = (total + WS_WARPS - 1) / WS_WARPS;
         pf->begin("ws_objects", s);
-        k_ws_objects_b<<<ctas < sms * 4 ? ctas : sms * 4, WS_WARPS * 32, small_smem, s>>>(d_descs, n, total, h, bbox,
-                                                                                        cnt, next, status);
+        k_ws_objects_b<<<ctas, WS_WARPS * 32, small_smem, s>>>(d_descs, n, total, h, bbox, cnt, status);
         pf->end("ws_objects", s);
         cudaStreamWaitEvent(s, join, 0);
     }
