@@ -192,9 +192,9 @@ void launch_watershed_batch(const std::vector<WsDesc>& descs, WsDesc* d_descs, i
                             cudaStream_t side, cudaEvent_t fork, cudaEvent_t join, Profiler* pf);
 // scratch of the watershed's out-of-stage boxes: a 64-bit and a 16-bit word per pixel
 size_t watershed_scratch_bytes(int W, int H);
-// cnt: K ints (per-object basin counts, then their exclusive prefix); next: 2 + K device ints (the
-// large-box draw counter and list length, zeroed by the launcher, then the large-box list); status:
-// a device int
+// cnt: K ints (per-object basin counts, then their exclusive prefix); next: 3 + K device ints (the
+// large-box draw counter, the large-box list length and the small-box draw counter, zeroed by the
+// launcher, then the large-box list); status: a device int
 // side: a second stream for the large boxes (fork/join through the two events)
 void launch_watershed(const int32_t* labels, const int32_t* edt, int W, int H, int K, int h, int32_t* out,
                       int32_t* n_basins, int4* bbox, int* cnt, int* next, void* scratch, int* status, int sms,

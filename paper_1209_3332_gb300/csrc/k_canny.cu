@@ -29,41 +29,41 @@ __global__ void __launch_bounds__(CT_THREADS) k_canny_nms(const uint8_t* __restr
                                                           int high, uint8_t* __restrict__ strong,
                                                           uint8_t* __restrict__ cand) {
     __shared__ uint8_t si[CT_S][CT_S + 4];
-    __shared__ int16_t sm[CT_M][CT_M + 2];       // m, 0 off the image
-    __shared__ int32_t sg[CT][CT + 1];            // (gx, gy) of the inner tile, two 16-bit halves
-    const int x0 = blockIdx.x * CT, y0 = blockIdx.y * CT;
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 columns x 8 rows of threads
-    for (int ly = ty; ly < CT_S; ly += 8) {       // replicated border: clamped coordinates
-        const int gy = min(max(y0 - 2 + ly, 0), H - 1);
-        const uint8_t* row = I + (size_t)gy * W;
-        for (int lx = tx; lx < CT_S; lx += 32) si[ly][lx] = row[min(max(x0 - 2 + lx, 0), W - 1)];
+    __shared__ int16_t sm[CT_M][CT_M + 2];
+    const int x0 = blockIdx.x * CT, y0 = blockIdx.y * CT, t = threadIdx.x;
+    for (int i = t; i < CT_S * CT_S; i += CT_THREADS) {  // replicated border: clamped coordinates
+        const int ly = i / CT_S, lx = i - ly * CT_S;
+        const int gy = min(max(y0 - 2 + ly, 0), H - 1), gx = min(max(x0 - 2 + lx, 0), W - 1);
+        si[ly][lx] = I[(size_t)gy * W + gx];
     }
     __syncthreads();
-    for (int ly = ty; ly < CT_M; ly += 8) {       // m at (y0 - 1 + ly, x0 - 1 + lx)
-        const int gy = y0 - 1 + ly;
-        for (int lx = tx; lx < CT_M; lx += 32) {
-            const int gx = x0 - 1 + lx;
+    for (int i = t; i < CT_M * CT_M; i += CT_THREADS) {  // m at (y0 - 1 + ly, x0 - 1 + lx); 0 off the image
+        const int ly = i / CT_M, lx = i - ly * CT_M;
+        const int gy = y0 - 1 + ly, gx = x0 - 1 + lx;
+        int m = 0;
+        if ((unsigned)gy < (unsigned)H && (unsigned)gx < (unsigned)W) {
             const int a = si[ly][lx], b = si[ly][lx + 1], c = si[ly][lx + 2];
             const int d = si[ly + 1][lx], f = si[ly + 1][lx + 2];
             const int g = si[ly + 2][lx], hh = si[ly + 2][lx + 1], k = si[ly + 2][lx + 2];
             const int sx = (c + 2 * f + k) - (a + 2 * d + g);
             const int sy = (g + 2 * hh + k) - (a + 2 * b + c);
-            const bool in = (unsigned)gy < (unsigned)H && (unsigned)gx < (unsigned)W;
-            sm[ly][lx] = (int16_t)(in ? abs(sx) + abs(sy) : 0);
-            if (ly >= 1 && ly <= CT && lx >= 1 && lx <= CT)
-                sg[ly - 1][lx - 1] = (int32_t)((uint32_t)(uint16_t)sx | ((uint32_t)(uint16_t)sy << 16));
+            m = abs(sx) + abs(sy);
         }
+        sm[ly][lx] = (int16_t)m;
     }
     __syncthreads();
-    const int gx = x0 + tx;
-    for (int ly = ty; ly < CT; ly += 8) {
-        const int gy = y0 + ly;
+    for (int i = t; i < CT * CT; i += CT_THREADS) {
+        const int ly = i / CT, lx = i - ly * CT;
+        const int gy = y0 + ly, gx = x0 + lx;
         if (gy >= H || gx >= W) continue;
-        const int32_t v = sg[ly][tx];
-        const int sx = (int16_t)(v & 0xffff), sy = v >> 16;
+        const int a = si[ly + 1][lx + 1], b = si[ly + 1][lx + 2], c = si[ly + 1][lx + 3];
+        const int d = si[ly + 2][lx + 1], f = si[ly + 2][lx + 3];
+        const int g = si[ly + 3][lx + 1], hh = si[ly + 3][lx + 2], k = si[ly + 3][lx + 3];
+        const int sx = (c + 2 * f + k) - (a + 2 * d + g);
+        const int sy = (g + 2 * hh + k) - (a + 2 * b + c);
         const int ax = abs(sx), ay = abs(sy);
         int ady, adx, bdy, bdx;
-        if ((ax + ay) * (ax + ay) < 2 * ax * ax) {           // |gx|, |gy| <= 1020: no overflow
+        if ((ax + ay) * (ax + ay) < 2 * ax * ax) {           // |gx| <= 1020 per term: no overflow
             ady = 0; adx = -1; bdy = 0; bdx = 1;
         } else if (ay > ax && (ay - ax) * (ay - ax) > 2 * ax * ax) {
             ady = -1; adx = 0; bdy = 1; bdx = 0;
@@ -72,22 +72,11 @@ __global__ void __launch_bounds__(CT_THREADS) k_canny_nms(const uint8_t* __restr
         } else {
             ady = -1; adx = 1; bdy = 1; bdx = -1;
         }
-        const int m = sm[ly + 1][tx + 1];
-        const bool keep = m > sm[ly + 1 + ady][tx + 1 + adx] && m >= sm[ly + 1 + bdy][tx + 1 + bdx];
+        const int m = sm[ly + 1][lx + 1];
+        const bool keep = m > sm[ly + 1 + ady][lx + 1 + adx] && m >= sm[ly + 1 + bdy][lx + 1 + bdx];
         const size_t o = (size_t)gy * W + gx;
         strong[o] = (uint8_t)(keep && m > high);
         cand[o] = (uint8_t)(keep && m > low);
-    }
-}
-
-// Advances the row-major position (ly, lx) in a box of width bw by 32
-// pixels (32 = qy * bw + qx).
-__device__ __forceinline__ void step32(int& ly, int& lx, int qy, int qx, int bw) {
-    lx += qx;
-    ly += qy;
-    if (lx >= bw) {
-        lx -= bw;
-        ly++;
     }
 }
 
@@ -105,10 +94,8 @@ __global__ void __launch_bounds__(256) k_canny_counts(const uint8_t* __restrict_
             const int x0 = max(bx.x - r, 0), y0 = max(bx.y - r, 0);
             const int x1 = min(bx.z + r, W - 1), y1 = min(bx.w + r, H - 1);
             const int bw = x1 - x0 + 1, n = bw * (y1 - y0 + 1);
-            int ly = lane / bw, lx = lane - ly * bw;              // position of f, stepped by 32
-            const int qy = 32 / bw, qx = 32 - qy * bw;
-            for (int f = lane; f < n; f += 32, step32(ly, lx, qy, qx, bw)) {
-                const int y = y0 + ly, x = x0 + lx;
+            for (int f = lane; f < n; f += 32) {
+                const int ly = f / bw, y = y0 + ly, x = x0 + (f - ly * bw);
                 if (!edges[(size_t)y * W + x]) continue;
                 bool hit = false;
                 for (int dy = -r; dy <= r && !hit; dy++) {

@@ -524,24 +524,24 @@ __global__ void k_ws_classify(const int4* __restrict__ bbox, int total, int* cnt
     else if (ws_box_px(bx) > WS_STAGE) list[atomicAdd(next + 1, 1)] = i;
 }
 
-// Small boxes: one warp per object (the grid covers every object, so CTAs
-// retire as their objects finish and the large-box CTAs find room), with
-// WS_STAGE pixels of stage each.  Writes the basin's rank inside the object
-// to out and the basin count to cnt[object]; objects with larger boxes are
-// left to k_ws_large.
+// Small boxes: persistent warps drawing objects from a launch-wide counter
+// (next[2]), WS_STAGE pixels of stage each.  Writes the basin's rank inside
+// the object to out and the basin count to cnt[object]; absent objects and
+// larger boxes were sorted out by k_ws_classify.
 __global__ void __launch_bounds__(WS_WARPS * 32) k_ws_objects(const int32_t* __restrict__ labels,
                                                                const int32_t* __restrict__ edt, int W, int H,
                                                                int K, int h, const int4* __restrict__ bbox,
-                                                               int32_t* out, int* cnt, int* status) {
+                                                               int32_t* out, int* cnt, int* next, int* status) {
     extern __shared__ __align__(16) char ws_smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     char* stage = ws_smem + (size_t)warp * WS_STAGE * WS_PX_BYTES;
-    const int obj = blockIdx.x * WS_WARPS + warp;
-    if (obj >= K) return;
-    const int4 bx = bbox[obj];
-    if (bx.z < bx.x || ws_box_px(bx) > WS_STAGE) return;
-    const int c = ws_staged(labels, edt, W, H, obj + 1, bx, h, stage, WS_STAGE, out, status, lane);
-    if (lane == 0) cnt[obj] = c;
+    for (int obj = ws_next(next + 2, lane); obj < K; obj = ws_next(next + 2, lane)) {
+        const int4 bx = bbox[obj];
+        if (bx.z < bx.x || ws_box_px(bx) > WS_STAGE) continue;
+        const int c = ws_staged(labels, edt, W, H, obj + 1, bx, h, stage, WS_STAGE, out, status, lane);
+        if (lane == 0) cnt[obj] = c;
+        __syncwarp();
+    }
 }
 
 // Large boxes: one warp per CTA with a stage of `cap` pixels, drawing from
@@ -670,18 +670,19 @@ __global__ void __launch_bounds__(256) k_ws_bbox_b(const WsDesc* __restrict__ D,
 
 __global__ void __launch_bounds__(WS_WARPS * 32) k_ws_objects_b(const WsDesc* __restrict__ D, int n, int total,
                                                                  int h, const int4* __restrict__ bbox, int* cnt,
-                                                                 int* status) {
+                                                                 int* next, int* status) {
     extern __shared__ __align__(16) char ws_smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     char* stage = ws_smem + (size_t)warp * WS_STAGE * WS_PX_BYTES;
-    const int item = blockIdx.x * WS_WARPS + warp;
-    if (item >= total) return;
-    const int4 bx = bbox[item];
-    if (bx.z < bx.x || ws_box_px(bx) > WS_STAGE) return;
-    const WsDesc& T = D[ws_desc_of(D, n, item, false)];
-    const int c = ws_staged(T.labels, T.edt, T.W, T.H, item - T.obj_base + 1, bx, h, stage, WS_STAGE, T.out, status,
-                            lane);
-    if (lane == 0) cnt[item] = c;
+    for (int item = ws_next(next + 2, lane); item < total; item = ws_next(next + 2, lane)) {
+        const int4 bx = bbox[item];
+        if (bx.z < bx.x || ws_box_px(bx) > WS_STAGE) continue;
+        const WsDesc& T = D[ws_desc_of(D, n, item, false)];
+        const int c = ws_staged(T.labels, T.edt, T.W, T.H, item - T.obj_base + 1, bx, h, stage, WS_STAGE, T.out,
+                                status, lane);
+        if (lane == 0) cnt[item] = c;
+        __syncwarp();
+    }
 }
 
 __global__ void __launch_bounds__(32) k_ws_large_b(const WsDesc* __restrict__ D, int n, int h,
@@ -748,8 +749,8 @@ void launch_watershed(const int32_t* labels, const int32_t* edt, int W, int H, i
     launch_object_boxes(labels, W, H, K, bbox, s, pf);
     unsigned long long* gw = (unsigned long long*)scratch;
     uint16_t* gdr = (uint16_t*)(gw + N);
-    int* list = next + 2;
-    cudaMemsetAsync(next, 0, 2 * sizeof(int), s);
+    int* list = next + 3;
+    cudaMemsetAsync(next, 0, 3 * sizeof(int), s);
     pf->begin("ws_classify", s);
     k_ws_classify<<<(K + 255) / 256, 256, 0, s>>>(bbox, K, cnt, next, list);
     pf->end("ws_classify", s);
@@ -764,7 +765,8 @@ void launch_watershed(const int32_t* labels, const int32_t* edt, int W, int H, i
     cudaEventRecord(join, side);
     const int ctas = (K + WS_WARPS - 1) / WS_WARPS;
     pf->begin("ws_objects", s);
-    k_ws_objects<<<ctas, WS_WARPS * 32, small_smem, s>>>(labels, edt, W, H, K, h, bbox, out, cnt, status);
+    k_ws_objects<<<ctas < sms * 4 ? ctas : sms * 4, WS_WARPS * 32, small_smem, s>>>(labels, edt, W, H, K, h, bbox,
+                                                                                 out, cnt, next, status);
     pf->end("ws_objects", s);
     cudaStreamWaitEvent(s, join, 0);
     pf->begin("ws_scan", s);
@@ -811,8 +813,8 @@ void launch_watershed_batch(const std::vector<WsDesc>& descs, WsDesc* d_descs, i
         pf->begin("ws_bbox", s);
         k_ws_bbox_b<<<(unsigned)(((long long)segs * 32 + 255) / 256), 256, 0, s>>>(d_descs, n, segs, bbox);
         pf->end("ws_bbox", s);
-        int* list = next + 2;
-        cudaMemsetAsync(next, 0, 2 * sizeof(int), s);
+        int* list = next + 3;
+        cudaMemsetAsync(next, 0, 3 * sizeof(int), s);
         pf->begin("ws_classify", s);
         k_ws_classify<<<(total + 255) / 256, 256, 0, s>>>(bbox, total, cnt, next, list);
         pf->end("ws_classify", s);
@@ -825,7 +827,8 @@ void launch_watershed_batch(const std::vector<WsDesc>& descs, WsDesc* d_descs, i
         cudaEventRecord(join, side);
         const int ctas = (total + WS_WARPS - 1) / WS_WARPS;
         pf->begin("ws_objects", s);
-        k_ws_objects_b<<<ctas, WS_WARPS * 32, small_smem, s>>>(d_descs, n, total, h, bbox, cnt, status);
+        k_ws_objects_b<<<ctas < sms * 4 ? ctas : sms * 4, WS_WARPS * 32, small_smem, s>>>(d_descs, n, total, h, bbox,
+                                                                                        cnt, next, status);
         pf->end("ws_objects", s);
         cudaStreamWaitEvent(s, join, 0);
     }

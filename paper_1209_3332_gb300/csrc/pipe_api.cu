@@ -788,7 +788,7 @@ int watershed_tile(pipe_t p, const int32_t* labels_dev, const int32_t* edt_dev, 
     if (overlap(out_dev, labels_dev) || overlap(out_dev, edt_dev)) return PIPE_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     CK(cudaSetDevice(p->device));
-    const size_t need_obj = (size_t)std::max(n_objects, 1) * (sizeof(int4) + 2 * sizeof(int)) + 2 * sizeof(int);
+    const size_t need_obj = (size_t)std::max(n_objects, 1) * (sizeof(int4) + 2 * sizeof(int)) + 3 * sizeof(int);
     const size_t need_scr = watershed_scratch_bytes(W, H);
     if (p->ws_obj.n < need_obj || p->ws_scratch.n < need_scr || !p->ws_status.p) {
         CK(cudaStreamSynchronize(s));
@@ -848,7 +848,7 @@ int watershed_batch(pipe_t p, const ws_tile* tiles, int n, int h, pipe_stream_t 
     if (segs * 32 > INT32_MAX) return PIPE_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     CK(cudaSetDevice(p->device));
-    const size_t need_obj = std::max(objs, (size_t)1) * (sizeof(int4) + 2 * sizeof(int)) + 2 * sizeof(int);
+    const size_t need_obj = std::max(objs, (size_t)1) * (sizeof(int4) + 2 * sizeof(int)) + 3 * sizeof(int);
     const size_t need_scr = px * (sizeof(unsigned long long) + sizeof(uint16_t));
     const size_t need_desc = sizeof(WsDesc) * (size_t)n;
     if (p->ws_obj.n < need_obj || p->ws_scratch.n < need_scr || p->ws_desc.n < need_desc || !p->ws_status.p) {
