@@ -2,7 +2,8 @@
 "Features comp.") and per-object edge counts (Sec. II "edge" features) with
 the oracle, bit for bit: random planes of ragged sizes at several
 thresholds, ideal steps, hem8 and labels of workload tiles at every radius,
-the full 4096^2 benchmark tile, and the argument checks of the C ABI."""
+an object whose box exceeds the count kernel's mask stage, the full 4096^2
+benchmark tile, and the argument checks of the C ABI."""
 import numpy as np
 import pytest
 
@@ -72,6 +73,19 @@ def test_workload_tiles_with_counts(pipe, r):
         assert e.any()
     seg = oracle.seg(synth.tile(333, 517, 9, n_nuclei=90, frac_cluster=0.5))
     check(pipe, seg["hem8"], seg["labels"], seg["K"] - 3, low=20, high=60, r=r)   # labels above n_objects
+
+
+def test_objects_whose_box_exceeds_the_count_stage(pipe):
+    """A ring with a 141 x 141 box (beyond the 4096-pixel mask stage of the
+    count kernel: the label plane is read instead) beside a small disc."""
+    H, W = 200, 260
+    yy, xx = np.mgrid[:H, :W]
+    rr = (yy - 100) ** 2 + (xx - 100) ** 2
+    m = ((rr <= 70 ** 2) & (rr >= 60 ** 2)) | (((yy - 40) ** 2 + (xx - 220) ** 2) <= 100)
+    lab, K = oracle.label(m.astype(np.uint8), 1, 10 ** 9)
+    img = np.where(m, 200, 20).astype(np.uint8)
+    for r in (0, 1, 3, 4):
+        check(pipe, img, lab, K, r=r)
 
 
 def test_full_4096_benchmark_tile(pipe):
