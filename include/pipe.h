@@ -338,6 +338,11 @@ int sched_request(sched_t s, int worker, uint64_t* task);
 /* The worker finished task (frees one window slot).  PIPE_EINVAL if the
  * worker does not hold it. */
 int sched_done(sched_t s, int worker, uint64_t task);
+/* Failure recovery (the Manager re-serves work): every task the worker
+ * holds goes back to the queue with its cost, and its window empties; a
+ * later sched_done from it for those tasks returns PIPE_EINVAL.
+ * *requeued (may be NULL) receives the number of tasks returned. */
+int sched_release(sched_t s, int worker, long long* requeued);
 /* Queued, held (all workers) and completed task counts; any may be NULL. */
 int sched_counts(sched_t s, long long* queued, long long* in_flight, long long* completed);
 /* Cost estimate of an RGB tile for the queue: W * H * (1 + 8 f), f the

@@ -22,7 +22,7 @@ EXPORTS = ["pipe_default_params", "pipe_create", "pipe_destroy", "seg_tile", "fe
            "pipe_profile_enable", "pipe_profile_read", "pipe_launch_count", "pipe_recon_visits",
            "features_tile_noalloc", "pipe_autotune_info", "morph_open_tile", "watershed_tile", "canny_tile",
            "watershed_batch", "sched_create", "sched_destroy", "sched_push", "sched_request", "sched_done",
-           "sched_counts", "tile_cost"]
+           "sched_release", "sched_counts", "tile_cost"]
 NOALLOC_MAX_OBJECTS = 65536
 
 
@@ -94,6 +94,8 @@ def lib():
     L.sched_request.restype = ci
     L.sched_done.argtypes = [vp, ci, u64]
     L.sched_done.restype = ci
+    L.sched_release.argtypes = [vp, ci, ctypes.POINTER(ctypes.c_longlong)]
+    L.sched_release.restype = ci
     L.sched_counts.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
                                ctypes.POINTER(ctypes.c_longlong)]
     L.sched_counts.restype = ci
@@ -187,6 +189,13 @@ class Sched:
 
     def done(self, worker, task):
         _check(lib().sched_done(self.h, int(worker), int(task)), "sched_done")
+
+    def release(self, worker):
+        """Return every task the worker holds to the queue (failure
+        recovery); the number returned."""
+        n = ctypes.c_longlong()
+        _check(lib().sched_release(self.h, int(worker), ctypes.byref(n)), "sched_release")
+        return n.value
 
     def counts(self):
         q, f, c = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_longlong()

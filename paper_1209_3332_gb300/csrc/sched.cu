@@ -27,7 +27,11 @@ struct sched_s {
     int n_workers = 0, window = 0;
     // cost (descending), then arrival order: multimap keeps equal keys in insertion order
     std::multimap<double, uint64_t, std::greater<double>> queue;
-    std::unordered_map<uint64_t, int> state;  // task -> -1 queued, else the worker holding it
+    struct Entry {
+        int holder;   // -1 queued, else the worker holding it
+        double cost;
+    };
+    std::unordered_map<uint64_t, Entry> state;
     std::vector<int> inflight;
     long long granted = 0, completed = 0;
 };
@@ -52,7 +56,7 @@ int sched_push(sched_t s, uint64_t task, double cost) {
     std::lock_guard<std::mutex> g(s->mu);
     if (s->state.count(task)) return PIPE_EINVAL;
     s->queue.emplace(cost, task);
-    s->state[task] = -1;
+    s->state[task] = {-1, cost};
     return PIPE_OK;
 }
 
@@ -64,7 +68,7 @@ int sched_request(sched_t s, int worker, uint64_t* task) {
     auto it = s->queue.begin();
     *task = it->second;
     s->queue.erase(it);
-    s->state[*task] = worker;
+    s->state[*task].holder = worker;
     s->inflight[worker]++;
     s->granted++;
     return PIPE_OK;
@@ -74,10 +78,25 @@ int sched_done(sched_t s, int worker, uint64_t task) {
     if (!s || worker < 0 || worker >= s->n_workers) return PIPE_EINVAL;
     std::lock_guard<std::mutex> g(s->mu);
     auto it = s->state.find(task);
-    if (it == s->state.end() || it->second != worker) return PIPE_EINVAL;
+    if (it == s->state.end() || it->second.holder != worker) return PIPE_EINVAL;
     s->state.erase(it);
     s->inflight[worker]--;
     s->completed++;
+    return PIPE_OK;
+}
+
+int sched_release(sched_t s, int worker, long long* requeued) {
+    if (!s || worker < 0 || worker >= s->n_workers) return PIPE_EINVAL;
+    std::lock_guard<std::mutex> g(s->mu);
+    long long n = 0;
+    for (auto& kv : s->state)
+        if (kv.second.holder == worker) {
+            kv.second.holder = -1;
+            s->queue.emplace(kv.second.cost, kv.first);
+            n++;
+        }
+    s->inflight[worker] = 0;
+    if (requeued) *requeued = n;
     return PIPE_OK;
 }
 

@@ -1,74 +1,152 @@
-"""Manager/Worker tile dispatch across processes (Sec. III-B), over
-torch.distributed point-to-point messages.
+"""Manager/Worker tile dispatch across processes (Sec. III-B), over a
+torch.distributed key-value store (``TCPStore``), with failure detection.
 
-Rank 0 is the Manager: it holds the cost-sorted queue (``Sched``, the native
-dispatcher of libpipe) and answers requests.  Every other rank is a Worker:
-it asks for a tile whenever it holds fewer than ``window`` (the paper's
-window of stage instances per Worker, so that the next assignment and its
-input overlap the processing of the current one), processes the oldest tile
-it holds, and reports it done.  The Manager grants the most expensive queued
-tile (the PATS order of Sec. IV-B, reduced to tile cost for GPU-only
-Workers).  Messages between a pair of ranks arrive in order, so a Worker's
-report of a finished tile always reaches the Manager before its next
-request.  The messages carry only tile ids; tile data stays with the ranks.
+The Manager holds the cost-sorted queue (``Sched``, the native dispatcher of
+libpipe) and answers requests.  A Worker asks for a tile whenever it holds
+fewer than ``window`` (the paper's window of stage instances per Worker, so
+that the next assignment and its input overlap the processing of the
+current one), processes the oldest tile it holds, and reports it done.  The
+Manager grants the most expensive queued tile (the PATS order of Sec. IV-B,
+reduced to tile cost for GPU-only Workers).  Only tile ids travel; tile data
+stays with the ranks.
+
+Messages are store keys, which the Manager polls without blocking, so it can
+keep a deadline: a Worker that holds tiles and has not been heard from for
+``timeout_s`` is declared failed and its tiles go back to the queue for the
+others (the paper's Manager re-serves work on demand).  A failed Worker that
+comes back is told there is no more work, and its late reports are
+ignored.  When every live Worker has been told so and has reported every
+tile it holds, the Manager sets the closed key, which also ends any Worker
+still waiting.
+
+The store must outlive every Worker (the process hosting a ``TCPStore``
+server keeps it): a failed Worker that comes back after it has gone gets a
+connection error instead of the closed key.
+
+Keys (prefix ``dispatch/``): ``req/<w>/<i>`` is Worker w's i-th request;
+``grant/<w>/<i>`` the answer (a tile id, or -1: no more work); ``done/<w>/<j>``
+Worker w's j-th report (a tile id); ``closed`` the end.
 """
 import collections
-
-import torch
-import torch.distributed as dist
+import time
 
 from . import Sched
 
-_REQUEST, _DONE = 0, 1
+_P = "dispatch/"
 
 
-def manager(tasks, costs, window, world_size=None):
-    """Serve the Workers (ranks 1..world_size-1) until every Worker has been
-    told there is no more work and has reported every tile it held.  Returns
-    the grant log: (worker rank, task id) in grant order."""
-    world = world_size or dist.get_world_size()
-    s = Sched(world - 1, window)
+def _has(store, key):
+    return store.check([key])
+
+
+def manager(store, tasks, costs, n_workers, window, timeout_s=None, poll_s=0.0005):
+    """Serve Workers 0..n_workers-1 through `store` until the work is done.
+    Returns a dict: "grants" [(worker, task)] in grant order, "completed"
+    [(worker, task)] in report order (exactly one entry per task), "failed"
+    the Workers declared failed, "requeued" the tiles returned by them.
+
+    A request that finds the queue empty while another live Worker holds
+    tiles is left unanswered until it can be answered (those tiles may still
+    come back); only then is a Worker told there is no more work."""
+    s = Sched(n_workers, window)
     for t, c in zip(tasks, costs):
         s.push(int(t), float(c))
-    msg = torch.zeros(2, dtype=torch.int64)
-    active = set(range(1, world))
-    log = []
-    while active or s.counts()[1] > 0:
-        src = dist.recv(msg)
-        op, task = int(msg[0]), int(msg[1])
-        if op == _DONE:
-            s.done(src - 1, task)
-            continue
-        t = s.request(src - 1)
-        dist.send(torch.tensor([-1 if t is None else t], dtype=torch.int64), src)
-        if t is None:
-            active.discard(src)
-        else:
-            log.append((src, t))
+    nreq = [0] * n_workers
+    ndone = [0] * n_workers
+    held = [set() for _ in range(n_workers)]
+    told = [False] * n_workers
+    failed, requeued = [], []
+    grants, completed = [], []
+    now = time.monotonic()
+    seen = [now] * n_workers
+    noticed = [-1] * n_workers     # the last request index counted as a sign of life
+    while True:
+        busy = False
+        for w in range(n_workers):
+            # a Worker writes each report before its next request, so once a
+            # request is visible every older report is too: look for the
+            # request, then drain the reports, then answer the request
+            asked = not told[w] and _has(store, "%sreq/%d/%d" % (_P, w, nreq[w]))
+            while True:
+                k = "%sdone/%d/%d" % (_P, w, ndone[w])
+                if not _has(store, k):
+                    break
+                busy = True
+                seen[w] = time.monotonic()
+                t = int(store.get(k))
+                ndone[w] += 1
+                if w not in failed and t in held[w]:
+                    s.done(w, t)
+                    held[w].discard(t)
+                    completed.append((w, t))
+            if not asked:
+                continue
+            if noticed[w] != nreq[w]:  # a deferred request is not a new sign of life
+                noticed[w] = nreq[w]
+                seen[w] = time.monotonic()
+            t = None if w in failed else s.request(w)
+            if t is None and w not in failed and any(held[v] for v in range(n_workers) if v != w):
+                continue                                  # wait: tiles held elsewhere may come back
+            busy = True
+            store.set("%sgrant/%d/%d" % (_P, w, nreq[w]), str(-1 if t is None else t))
+            nreq[w] += 1
+            if t is None:
+                told[w] = True
+            else:
+                held[w].add(t)
+                grants.append((w, t))
+        if timeout_s is not None:
+            now = time.monotonic()
+            for w in range(n_workers):
+                if w not in failed and held[w] and now - seen[w] > timeout_s:
+                    failed.append(w)
+                    requeued.extend(sorted(held[w]))
+                    s.release(w)
+                    held[w].clear()
+        if all(told[w] or w in failed for w in range(n_workers)) and not any(held):
+            break
+        if not busy:
+            time.sleep(poll_s)
+    store.set(_P + "closed", "1")
     s.close()
-    return log
+    return {"grants": grants, "completed": completed, "failed": failed, "requeued": requeued}
 
 
-def worker(process, window):
-    """Request, process and report tiles until the Manager has none left;
-    process(task id) does the work.  Returns the task ids processed, in
-    order."""
+def worker(store, w, process, window, poll_s=0.0005):
+    """Worker w: keeps one request outstanding while it holds fewer than
+    `window` tiles, processes the tiles it holds meanwhile (oldest first),
+    and reports each; ends when told there is no more work (or the Manager
+    has closed) and nothing is left.  process(task id) does the work.
+    Returns the task ids processed, in order."""
     held = collections.deque()
     done = []
+    nreq = ndone = 0
     more = True
-    reply = torch.zeros(1, dtype=torch.int64)
+    asking = False
     while True:
-        while more and len(held) < window:
-            dist.send(torch.tensor([_REQUEST, 0], dtype=torch.int64), 0)
-            dist.recv(reply, 0)
-            t = int(reply[0])
-            if t < 0:
-                more = False
-            else:
-                held.append(t)
-        if not held:
+        if more and not asking and len(held) < window:
+            store.set("%sreq/%d/%d" % (_P, w, nreq), "1")
+            asking = True
+        if asking:
+            key = "%sgrant/%d/%d" % (_P, w, nreq)
+            if _has(store, key):
+                t = int(store.get(key))
+                nreq += 1
+                asking = False
+                if t < 0:
+                    more = False
+                else:
+                    held.append(t)
+                continue
+            if _has(store, _P + "closed"):
+                more = asking = False
+        if held:
+            t = held.popleft()
+            process(t)
+            done.append(t)
+            store.set("%sdone/%d/%d" % (_P, w, ndone), str(t))
+            ndone += 1
+            continue
+        if not more and not asking:
             return done
-        t = held.popleft()
-        process(t)
-        done.append(t)
-        dist.send(torch.tensor([_DONE, t], dtype=torch.int64), 0)
+        time.sleep(poll_s)

@@ -1,8 +1,9 @@
 """The demand-driven dispatcher (host only, no GPU): the most expensive queued
 tile first with ties in arrival order (the PATS sorted queue, Sec. IV-B),
-the window of tiles a worker may hold (Sec. III-B), argument checks, many
-threads at once, the tile cost estimate, and the Manager/Worker protocol
-over gloo with three ranks."""
+the window of tiles a worker may hold (Sec. III-B), release of a failed
+worker's tiles, argument checks, many threads at once, the tile cost
+estimate, and the Manager/Worker protocol across processes over a
+TCPStore, with a stalled worker detected and its tiles served again."""
 import os
 import threading
 
@@ -36,6 +37,19 @@ def test_window_limits_the_tiles_a_worker_holds():
     s.done(0, 5)
     assert s.request(0) == 2
     assert s.counts() == (2, 3, 1)
+
+
+def test_release_returns_a_workers_tiles_to_the_queue():
+    s = P.Sched(2, 3)
+    for i, c in enumerate([1.0, 5.0, 3.0, 4.0]):
+        s.push(i, c)
+    assert [s.request(0), s.request(0), s.request(1)] == [1, 3, 2]
+    assert s.release(0) == 2
+    assert s.counts() == (3, 1, 0)
+    with pytest.raises(P.PipeError):
+        s.done(0, 1)                             # released: no longer held by worker 0
+    assert [s.request(1), s.request(1)] == [1, 3]  # back in cost order
+    assert s.release(0) == 0
 
 
 def test_argument_checks():
@@ -103,46 +117,115 @@ def test_tile_cost_follows_area_and_density():
     assert P.tile_cost(big[:, :512]) == P.tile_cost(np.ascontiguousarray(big[:, :512]))
 
 
-def _dispatch_rank(rank, world, port, tasks, costs, window, q):
+def _dispatch_rank(role, port, tasks, costs, window, n_workers, stall, q):
+    import time as _t
+    from datetime import timedelta
     import torch.distributed as dist
-    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
-    dist.init_process_group("gloo", rank=rank, world_size=world)
     from paper_1209_3332_gb300 import dispatch
-    if rank == 0:
-        out = ("log", dispatch.manager(tasks, costs, window))
+    store = dist.TCPStore("127.0.0.1", port, n_workers + 1, role == "manager", timeout=timedelta(seconds=60))
+    if role == "manager":
+        q.put(("manager", dispatch.manager(store, tasks, costs, n_workers, window,
+                                           timeout_s=0.3 if stall is not None else None)))
+        # this process hosts the store: it stays until every Worker has left
+        store.wait(["test/bye/%d" % w for w in range(n_workers)], timedelta(seconds=60))
     else:
-        out = ("done", rank, dispatch.worker(lambda t: None, window))
-    q.put(out)
-    dist.barrier()
-    dist.destroy_process_group()
+        first = [True]
+
+        def process(t):
+            if role == stall and first[0]:          # this worker hangs on its first tile
+                first[0] = False
+                _t.sleep(2.0)
+        q.put(("worker", role, dispatch.worker(store, role, process, window)))
+        store.set("test/bye/%d" % role, "1")
 
 
-def test_manager_worker_over_gloo_three_ranks():
-    """Rank 0 manages, ranks 1 and 2 work with a window of 2: every tile is
-    processed exactly once, tiles are granted most expensive first (all are
-    queued before the first request), and no worker ever holds more than
-    its window (the grant log is consistent with the done reports)."""
+def _run_dispatch(tasks, costs, window, n_workers, stall=None):
     import multiprocessing as mp
     import socket
     with socket.socket() as sk:
         sk.bind(("127.0.0.1", 0))
         port = sk.getsockname()[1]
-    rng = np.random.default_rng(5)
-    tasks = list(range(60))
-    costs = [float(c) for c in rng.integers(0, 1000, len(tasks))]
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
-    ps = [ctx.Process(target=_dispatch_rank, args=(r, 3, port, tasks, costs, 2, q)) for r in range(3)]
+    roles = ["manager"] + list(range(n_workers))
+    ps = [ctx.Process(target=_dispatch_rank, args=(r, port, tasks, costs, window, n_workers, stall, q))
+          for r in roles]
     for p in ps:
         p.start()
-    res = [q.get(timeout=120) for _ in range(3)]
+    res = [q.get(timeout=120) for _ in roles]
     for p in ps:
         p.join(timeout=60)
         assert p.exitcode == 0
-    log = next(r[1] for r in res if r[0] == "log")
-    done = {r[1]: r[2] for r in res if r[0] == "done"}
-    assert sorted(t for v in done.values() for t in v) == tasks
-    granted = [t for _, t in log]
-    assert [costs[t] for t in granted] == sorted(costs, reverse=True)
+    m = next(r[1] for r in res if r[0] == "manager")
+    done = {r[1]: r[2] for r in res if r[0] == "worker"}
+    return m, done
+
+
+def test_manager_worker_three_processes():
+    """A Manager and three Workers (separate processes sharing a TCPStore),
+    window 2: every tile is completed exactly once, tiles are granted most
+    expensive first (all are queued before the first request), and each
+    Worker processes its tiles in grant order."""
+    rng = np.random.default_rng(5)
+    tasks = list(range(60))
+    costs = [float(c) for c in rng.integers(0, 1000, len(tasks))]
+    m, done = _run_dispatch(tasks, costs, 2, 3)
+    assert sorted(t for _, t in m["completed"]) == tasks and not m["failed"]
+    assert [costs[t] for _, t in m["grants"]] == sorted(costs, reverse=True)
     for w, ts in done.items():
-        assert [t for r, t in log if r == w] == ts   # each worker processes its tiles in grant order
+        assert [t for r, t in m["grants"] if r == w] == ts
+
+
+def test_a_stalled_worker_is_detected_and_its_tiles_served_again():
+    """Worker 1 hangs for 2 s on its first tile while holding two (its
+    window): after 0.3 s without a word the Manager declares it failed and
+    returns both tiles to the queue; the other Workers complete every tile
+    exactly once; the stalled Worker's late reports are ignored and it is
+    told there is no more work (or finds the Manager closed)."""
+    tasks = list(range(40))
+    costs = [float(40 - t) for t in tasks]
+    m, done = _run_dispatch(tasks, costs, 2, 3, stall=1)
+    assert m["failed"] == [1]
+    assert len(m["requeued"]) == 2
+    assert sorted(t for _, t in m["completed"]) == tasks
+    assert all(w != 1 for w, _ in m["completed"])
+    assert set(m["requeued"]) <= set(t for w, t in m["completed"])
+    assert set(m["requeued"]) <= set(done[1])           # it did process them, late
+
+
+def test_a_worker_that_stops_for_good_is_detected():
+    """In-process (threads over one TCPStore): Worker 1 takes its window of
+    tiles and then never speaks again; the Manager declares it failed after
+    the deadline and Worker 0 completes every tile."""
+    import socket
+    import threading
+    import time
+    from datetime import timedelta
+    import torch.distributed as dist
+    from paper_1209_3332_gb300 import dispatch
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    master = dist.TCPStore("127.0.0.1", port, 1, True, timeout=timedelta(seconds=30), wait_for_workers=False)
+    res = {}
+
+    def run1():  # Worker 1 by hand: two requests, each awaited, then silence
+        st = dist.TCPStore("127.0.0.1", port, 1, False, timeout=timedelta(seconds=30))
+        for i in range(2):
+            st.set("dispatch/req/1/%d" % i, "1")
+            st.wait(["dispatch/grant/1/%d" % i], timedelta(seconds=30))
+        res[1] = True
+
+    def run0():
+        st = dist.TCPStore("127.0.0.1", port, 1, False, timeout=timedelta(seconds=30))
+        time.sleep(0.05)                          # let Worker 1 take its tiles first
+        res[0] = dispatch.worker(st, 0, lambda t: time.sleep(0.002), 2)
+    ths = [threading.Thread(target=f, daemon=True) for f in (run1, run0)]
+    for t in ths:
+        t.start()
+    m = dispatch.manager(master, list(range(30)), [float(30 - t) for t in range(30)], 2, 2, timeout_s=0.3)
+    for t in ths:
+        t.join(30)
+    assert res.get(1) and m["failed"] == [1] and len(m["requeued"]) == 2
+    assert sorted(t for _, t in m["completed"]) == list(range(30))
+    assert all(w == 0 for w, _ in m["completed"]) and sorted(res[0]) == list(range(30))
