@@ -210,10 +210,11 @@ int watershed_tile(pipe_t p, const int32_t* labels_dev, const int32_t* edt_dev, 
  *  tiles[i]: labels, edt, out (W x H int32, out not overlapping the
  *    inputs), n_objects = K of the tile (host int), n_basins (one device
  *    int32); 1 <= n <= 4096; 0 <= h <= 255.
- *  The pipe's scratch covers all tiles at once: boxes and counts (20 bytes
- *  per object) and the planes for boxes beyond the shared-memory stage
- *  (10 bytes per pixel of all tiles), allocated on the first call of a
- *  larger size, which synchronises `stream`.
+ *  The pipe's scratch covers all tiles at once: boxes, basin counts and the
+ *  list of large boxes (24 bytes per object) and the planes for boxes
+ *  beyond the shared-memory stage (10 bytes per pixel of all tiles),
+ *  allocated on the first call of a larger size, which synchronises
+ *  `stream`.
  * Returns PIPE_EINVAL on a bad argument (nothing is launched); otherwise
  * the work is asynchronous on `stream`. */
 typedef struct {
