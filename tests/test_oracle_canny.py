@@ -131,3 +131,56 @@ def test_edge_counts_are_the_edges_in_each_objects_disk_dilation(r):
     assert oracle.edge_counts(e, lab, K, r).tolist() == want
     if r == 3:
         assert sum(want) > 10 * K
+
+
+def _nms_by_angle(img):
+    """Non-maximum suppression restated with SciPy's Sobel and
+    floating-point angles (atan2) instead of the oracle's exact integer
+    sector tests: horizontal below 22.5 degrees, vertical above 67.5,
+    otherwise the diagonal of the gradient's sign."""
+    f = img.astype(np.int64)
+    gx = ndimage.sobel(f, axis=1, mode="nearest")
+    gy = ndimage.sobel(f, axis=0, mode="nearest")
+    m = np.abs(gx) + np.abs(gy)
+    H, W = img.shape
+    mp = np.zeros((H + 2, W + 2), np.int64)
+    mp[1:-1, 1:-1] = m
+    ang = np.degrees(np.arctan2(np.abs(gy), np.abs(gx)))
+    keep = np.zeros((H, W), bool)
+    for y in range(H):
+        for x in range(W):
+            if ang[y, x] < 22.5:
+                a, b = (0, -1), (0, 1)
+            elif ang[y, x] > 67.5:
+                a, b = (-1, 0), (1, 0)
+            elif gx[y, x] * gy[y, x] > 0:
+                a, b = (-1, -1), (1, 1)
+            else:
+                a, b = (-1, 1), (1, -1)
+            v = m[y, x]
+            keep[y, x] = v > mp[y + 1 + a[0], x + 1 + a[1]] and v >= mp[y + 1 + b[0], x + 1 + b[1]]
+    return m, keep
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_suppression_matches_angles_computed_in_floating_point(seed):
+    """Planes whose gradients fall near the 22.5 and 67.5 degree sector
+    boundaries (linear ramps at slopes around tan 22.5 = 0.414 and
+    tan 67.5 = 2.414, with noise), plus a random plane: with thresholds 0,
+    the candidates are exactly the survivors with m > 0."""
+    rng = np.random.default_rng(seed)
+    H, W = 40, 48
+    yy, xx = np.mgrid[:H, :W]
+    planes = [rng.integers(0, 256, (H, W), dtype=np.uint8)]
+    for slope in (0.38, 0.41, 0.42, 0.45, 2.3, 2.41, 2.42, 2.6):
+        ramp = 3.0 * xx + 3.0 * slope * yy + rng.normal(0, 4, (H, W))
+        ramp = ramp if seed % 2 == 0 else -ramp
+        planes.append(np.clip(ramp - ramp.min(), 0, 255).astype(np.uint8))
+    checked = 0
+    for img in planes:
+        _, m, cls = oracle.canny(img, 0, 0, detail=True)
+        mref, keep = _nms_by_angle(img)
+        assert np.array_equal(m, mref)
+        assert np.array_equal(cls > 0, keep & (mref > 0))
+        checked += int(keep.sum())
+    assert checked > 500
