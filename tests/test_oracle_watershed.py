@@ -99,3 +99,26 @@ def test_invariants_on_a_workload_tile():
         assert kb == 1, b
     # clusters of touching nuclei were split somewhere
     assert n > K
+
+
+def test_basins_are_numbered_by_their_first_pixel_within_each_object():
+    """Within every object the basin numbers increase with the raster
+    position of each basin's first pixel (not of its marker), and objects
+    take consecutive ranges in label order; checked on a tile with many
+    split clusters."""
+    rgb = synth.tile(768, 768, 91, n_nuclei=300, frac_cluster=0.6, frac_overlap=0.3, n_stroma=2)
+    r = oracle.seg(rgb, amax=6000)
+    lab = r["labels"]
+    out, n = oracle.watershed(lab, r["edt"], 1)
+    flat_out, flat_lab = out.ravel(), lab.ravel()
+    first = {}
+    for i in np.flatnonzero(flat_out):
+        first.setdefault(int(flat_out[i]), i)
+    split = 0
+    for k in range(1, int(lab.max()) + 1):
+        basins = sorted(set(np.unique(flat_out[flat_lab == k]).tolist()))
+        assert basins == list(range(basins[0], basins[-1] + 1))
+        assert [first[b] for b in basins] == sorted(first[b] for b in basins)
+        split += len(basins) > 1
+    assert split >= 5
+    assert n == max(first)
