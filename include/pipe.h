@@ -21,6 +21,9 @@
  *    pitch argument says otherwise.
  *  - A pipe_t may be used from one host thread at a time, except
  *    batch_submit / batch_poll, which are safe to call concurrently.
+ *  - The stream-taking calls of one pipe share its scratch buffers: calls
+ *    on different streams must not overlap on the GPU (order the streams
+ *    with events, or use one stream per pipe).
  */
 #ifndef GB300_NUCSEG_PIPE_H
 #define GB300_NUCSEG_PIPE_H
