@@ -39,7 +39,7 @@ def _has(store, key):
     return store.check([key])
 
 
-def manager(store, tasks, costs, n_workers, window, timeout_s=None, poll_s=0.0005):
+def manager(store, tasks, costs, n_workers, window, timeout_s=None, poll_s=0.0005, deadline_s=None):
     """Serve Workers 0..n_workers-1 through `store` until the work is done.
     Returns a dict: "grants" [(worker, task)] in grant order, "completed"
     [(worker, task)] in report order (exactly one entry per task), "failed"
@@ -47,7 +47,9 @@ def manager(store, tasks, costs, n_workers, window, timeout_s=None, poll_s=0.000
 
     A request that finds the queue empty while another live Worker holds
     tiles is left unanswered until it can be answered (those tiles may still
-    come back); only then is a Worker told there is no more work."""
+    come back); only then is a Worker told there is no more work.  With
+    deadline_s, the whole run is bounded: past it the Manager closes and
+    raises TimeoutError."""
     s = Sched(n_workers, window)
     for t, c in zip(tasks, costs):
         s.push(int(t), float(c))
@@ -60,7 +62,12 @@ def manager(store, tasks, costs, n_workers, window, timeout_s=None, poll_s=0.000
     now = time.monotonic()
     seen = [now] * n_workers
     noticed = [-1] * n_workers     # the last request index counted as a sign of life
+    end = None if deadline_s is None else now + deadline_s
     while True:
+        if end is not None and time.monotonic() > end:
+            store.set(_P + "closed", "1")
+            s.close()
+            raise TimeoutError("dispatch did not finish within %.1f s" % deadline_s)
         busy = False
         for w in range(n_workers):
             # a Worker writes each report before its next request, so once a

@@ -39,6 +39,23 @@ def test_window_limits_the_tiles_a_worker_holds():
     assert s.counts() == (2, 3, 1)
 
 
+def test_the_manager_gives_up_at_its_deadline():
+    """No Worker ever asks: with deadline_s the Manager closes and raises."""
+    import socket
+    import time
+    from datetime import timedelta
+    import torch.distributed as dist
+    from paper_1209_3332_gb300 import dispatch
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    st = dist.TCPStore("127.0.0.1", port, 1, True, timeout=timedelta(seconds=10), wait_for_workers=False)
+    t0 = time.monotonic()
+    with pytest.raises(TimeoutError):
+        dispatch.manager(st, [0, 1], [1.0, 2.0], 1, 1, deadline_s=0.2)
+    assert time.monotonic() - t0 < 5 and st.check(["dispatch/closed"])
+
+
 def test_release_returns_a_workers_tiles_to_the_queue():
     s = P.Sched(2, 3)
     for i, c in enumerate([1.0, 5.0, 3.0, 4.0]):
@@ -125,7 +142,7 @@ def _dispatch_rank(role, port, tasks, costs, window, n_workers, stall, q):
     store = dist.TCPStore("127.0.0.1", port, n_workers + 1, role == "manager", timeout=timedelta(seconds=60))
     if role == "manager":
         q.put(("manager", dispatch.manager(store, tasks, costs, n_workers, window,
-                                           timeout_s=0.3 if stall is not None else None)))
+                                           timeout_s=0.3 if stall is not None else None, deadline_s=60)))
         # this process hosts the store: it stays until every Worker has left
         store.wait(["test/bye/%d" % w for w in range(n_workers)], timedelta(seconds=60))
     else:
@@ -223,7 +240,8 @@ def test_a_worker_that_stops_for_good_is_detected():
     ths = [threading.Thread(target=f, daemon=True) for f in (run1, run0)]
     for t in ths:
         t.start()
-    m = dispatch.manager(master, list(range(30)), [float(30 - t) for t in range(30)], 2, 2, timeout_s=0.3)
+    m = dispatch.manager(master, list(range(30)), [float(30 - t) for t in range(30)], 2, 2, timeout_s=0.3,
+                         deadline_s=60)
     for t in ths:
         t.join(30)
     assert res.get(1) and m["failed"] == [1] and len(m["requeued"]) == 2
