@@ -6,6 +6,7 @@ estimate, and the Manager/Worker protocol across processes over a
 TCPStore, with a stalled worker detected and its tiles served again."""
 import os
 import threading
+import time
 
 import numpy as np
 import pytest
@@ -134,7 +135,7 @@ def test_tile_cost_follows_area_and_density():
     assert P.tile_cost(big[:, :512]) == P.tile_cost(np.ascontiguousarray(big[:, :512]))
 
 
-def _dispatch_rank(role, port, tasks, costs, window, n_workers, stall, q):
+def _dispatch_rank(role, port, tasks, costs, window, n_workers, stall, q, heartbeat_s=None):
     import time as _t
     from datetime import timedelta
     import torch.distributed as dist
@@ -152,11 +153,11 @@ def _dispatch_rank(role, port, tasks, costs, window, n_workers, stall, q):
             if role == stall and first[0]:          # this worker hangs on its first tile
                 first[0] = False
                 _t.sleep(2.0)
-        q.put(("worker", role, dispatch.worker(store, role, process, window)))
+        q.put(("worker", role, dispatch.worker(store, role, process, window, heartbeat_s=heartbeat_s)))
         store.set("test/bye/%d" % role, "1")
 
 
-def _run_dispatch(tasks, costs, window, n_workers, stall=None):
+def _run_dispatch(tasks, costs, window, n_workers, stall=None, heartbeat_s=None):
     import multiprocessing as mp
     import socket
     with socket.socket() as sk:
@@ -165,7 +166,7 @@ def _run_dispatch(tasks, costs, window, n_workers, stall=None):
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     roles = ["manager"] + list(range(n_workers))
-    ps = [ctx.Process(target=_dispatch_rank, args=(r, port, tasks, costs, window, n_workers, stall, q))
+    ps = [ctx.Process(target=_dispatch_rank, args=(r, port, tasks, costs, window, n_workers, stall, q, heartbeat_s))
           for r in roles]
     for p in ps:
         p.start()
@@ -247,3 +248,45 @@ def test_a_worker_that_stops_for_good_is_detected():
     assert res.get(1) and m["failed"] == [1] and len(m["requeued"]) == 2
     assert sorted(t for _, t in m["completed"]) == list(range(30))
     assert all(w == 0 for w, _ in m["completed"]) and sorted(res[0]) == list(range(30))
+
+
+def test_a_slow_tile_under_a_heartbeat_is_not_a_failure():
+    """Worker 1 takes 2 s on its first tile, far past the Manager's 0.3 s
+    timeout, but its heartbeat thread keeps beating every 0.05 s: no Worker
+    is declared failed, nothing is served twice, and every tile is completed
+    exactly once."""
+    tasks = list(range(30))
+    costs = [float(30 - t) for t in tasks]
+    m, done = _run_dispatch(tasks, costs, 2, 3, stall=1, heartbeat_s=0.05)
+    assert m["failed"] == [] and m["requeued"] == []
+    assert sorted(t for _, t in m["completed"]) == tasks
+    assert sorted(sum(done.values(), [])) == tasks
+
+
+def test_workers_return_when_the_manager_raises():
+    """The Manager's queue refuses a request (the Worker runs with a larger
+    window than the Manager's, so its second request finds its window full):
+    the Manager raises, but sets the closed key first, so the Worker still
+    returns."""
+    import socket
+    import threading
+    from datetime import timedelta
+    import torch.distributed as dist
+    import paper_1209_3332_gb300 as P
+    from paper_1209_3332_gb300 import dispatch
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    master = dist.TCPStore("127.0.0.1", port, 1, True, timeout=timedelta(seconds=30), wait_for_workers=False)
+    res = {}
+
+    def run0():
+        st = dist.TCPStore("127.0.0.1", port, 1, False, timeout=timedelta(seconds=30))
+        res[0] = dispatch.worker(st, 0, lambda t: time.sleep(0.05), 2)
+    th = threading.Thread(target=run0, daemon=True)
+    th.start()
+    with pytest.raises(P.PipeError):
+        dispatch.manager(master, list(range(10)), [1.0] * 10, 1, 1, deadline_s=30)
+    assert master.check(["dispatch/closed"])
+    th.join(30)
+    assert not th.is_alive() and len(res[0]) >= 1
