@@ -123,7 +123,9 @@ int features_tile(pipe_t p, const uint8_t* hem8_dev, const int32_t* labels_dev, 
  * entries (1 MiB) that every GPU loading this library holds until exit.
  *  - Uses the current CUDA device.  The first call on a device looks up the
  *    array's device address (cudaGetSymbolAddress); make that first call
- *    before any stream capture.
+ *    before any stream capture.  The address is kept for the life of the
+ *    process: after a cudaDeviceReset of that device it is stale, so the
+ *    entry point must not be called on a device this process has reset.
  *  - n_objects > PIPE_NOALLOC_MAX_OBJECTS: PIPE_EINVAL, nothing launched.
  *  - All calls share the one array (each call first resets the entries it
  *    uses): calls that overlap on the GPU -- on different streams, or from
@@ -269,23 +271,34 @@ typedef struct {
 } tile_desc;
 typedef struct {
     int status, n_objects;
-    float* feats;             /* pipe-owned [n_objects][15] */
+    int n_feats;              /* feature rows in feats: min(n_objects, the tile's capacity) */
+    float* feats;             /* pipe-owned [n_feats][15] */
     uint8_t* hem8; int32_t* labels; int32_t* edt; /* pipe-owned, if want_planes */
     double t_arrive_ms, t_done_ms;  /* submit and completion times, ms of CLOCK_MONOTONIC */
 } tile_result;
 /* Admits the n tiles as one group: they are uploaded and processed together
  * as one batched launch on a context of their own, concurrently with the
- * groups already in flight.  PIPE_EBUSY (nothing enqueued) when max_slots
- * contexts are busy or the group would exceed hbm_budget_bytes together with
- * the groups in flight; PIPE_ENOMEM when the group alone exceeds it. */
+ * groups already in flight.  Contexts keep their device buffers between
+ * groups, and hbm_budget_bytes bounds the device memory of all contexts,
+ * busy or idle: to grow a context, or start a new one, idle contexts are
+ * freed first when the total would pass the budget.  PIPE_EBUSY (nothing
+ * enqueued) when max_slots contexts are busy or the group does not fit
+ * beside the busy ones; PIPE_ENOMEM when the group alone exceeds the
+ * budget. */
 int batch_submit(pipe_t p, const tile_desc* tiles, int n, uint64_t* ticket);
 /* PIPE_EAGAIN (n_done = 0) until every tile of the ticket is done; then
- * fills out[0..n) and sets n_done = n.  The pipe-owned result arrays of a
- * completed ticket stay valid until batch_poll is called for a different
- * ticket (which releases them) or the pipe is destroyed.  A tile whose
- * object count exceeds the feature capacity min(W*H/20+1, 65536) reports
- * PIPE_EOVERFLOW with n_objects = K and the first capacity rows. */
+ * fills out[0..n) and sets n_done = n (a done ticket may be polled again).
+ * The pipe-owned result arrays of a completed ticket stay valid until
+ * batch_release is called for that ticket or the pipe is destroyed; polls
+ * of other tickets, from any thread, never touch them.  A tile whose object
+ * count exceeds its feature capacity (min(W*H/20+1, 65536) rows) reports
+ * PIPE_EOVERFLOW with n_objects = K and n_feats = the capacity.
+ * PIPE_EINVAL for an unknown or released ticket. */
 int batch_poll(pipe_t p, uint64_t ticket, int* n_done, tile_result* out);
+/* Frees the results of a completed ticket; the ticket is unknown afterwards.
+ * The caller must not read them (from any thread) after this call.
+ * PIPE_EAGAIN if the ticket is not done yet, PIPE_EINVAL if unknown. */
+int batch_release(pipe_t p, uint64_t ticket);
 
 /* ---- introspection used by tests and the benchmark ---------------------- */
 
@@ -310,6 +323,11 @@ int pipe_profile_read(pipe_t p, const char** names, long long* launches, double*
 /* Launch shapes used by the most recent seg_features_batch call, and the
  * number of timed passes the autotuner has run since creation. */
 int pipe_autotune_info(pipe_t p, int* recon_workers, int* edt_rows, int* feat_blocks, long long* tune_runs);
+
+/* Device memory of the served form: bytes held by all its contexts (never
+ * above hbm_budget_bytes), bytes of the contexts with a group in flight,
+ * and the number of contexts; any pointer may be NULL. */
+int pipe_serve_memory(pipe_t p, size_t* allocated, size_t* in_flight, int* contexts);
 
 /* Number of kernels the pipe has launched since creation. */
 long long pipe_launch_count(pipe_t p);

@@ -18,7 +18,8 @@ STATUS_NAMES = ["PIPE_OK", "PIPE_EINVAL", "PIPE_ENOMEM", "PIPE_EBUSY", "PIPE_EAG
                 "PIPE_EOVERFLOW", "PIPE_ECUDA"]
 
 EXPORTS = ["pipe_default_params", "pipe_create", "pipe_destroy", "seg_tile", "features_tile",
-           "seg_features_batch", "batch_submit", "batch_poll", "pipe_status_read", "pipe_debug_plane",
+           "seg_features_batch", "batch_submit", "batch_poll", "batch_release", "pipe_serve_memory",
+           "pipe_status_read", "pipe_debug_plane",
            "pipe_profile_enable", "pipe_profile_read", "pipe_launch_count", "pipe_recon_visits",
            "features_tile_noalloc", "pipe_autotune_info", "morph_open_tile", "watershed_tile", "canny_tile",
            "watershed_batch", "sched_create", "sched_destroy", "sched_push", "sched_request", "sched_done",
@@ -54,7 +55,7 @@ class TileDesc(ctypes.Structure):
 
 
 class TileResult(ctypes.Structure):
-    _fields_ = [("status", ctypes.c_int), ("n_objects", ctypes.c_int),
+    _fields_ = [("status", ctypes.c_int), ("n_objects", ctypes.c_int), ("n_feats", ctypes.c_int),
                 ("feats", ctypes.POINTER(ctypes.c_float)), ("hem8", ctypes.POINTER(ctypes.c_uint8)),
                 ("labels", ctypes.POINTER(ctypes.c_int32)), ("edt", ctypes.POINTER(ctypes.c_int32)),
                 ("t_arrive_ms", ctypes.c_double), ("t_done_ms", ctypes.c_double)]
@@ -103,6 +104,8 @@ def lib():
     L.tile_cost.restype = ctypes.c_double
     L.batch_submit.argtypes = [vp, ctypes.POINTER(TileDesc), ci, ctypes.POINTER(u64)]
     L.batch_poll.argtypes = [vp, u64, ctypes.POINTER(ci), ctypes.POINTER(TileResult)]
+    L.batch_release.argtypes = [vp, u64]
+    L.pipe_serve_memory.argtypes = [vp, ctypes.POINTER(sz), ctypes.POINTER(sz), ctypes.POINTER(ci)]
     L.pipe_status_read.argtypes = [vp]
     L.pipe_debug_plane.argtypes = [vp, ci, vp, vp]
     L.pipe_profile_enable.argtypes = [vp, ci]
@@ -117,6 +120,7 @@ def lib():
     L.pipe_autotune_info.argtypes = [vp, ctypes.POINTER(ci), ctypes.POINTER(ci), ctypes.POINTER(ci),
                                      ctypes.POINTER(ctypes.c_longlong)]
     for n in ("pipe_create", "seg_tile", "features_tile", "seg_features_batch", "batch_submit", "batch_poll",
+              "batch_release", "pipe_serve_memory",
               "pipe_status_read", "pipe_debug_plane", "pipe_profile_enable", "pipe_profile_read",
               "morph_open_tile", "watershed_tile", "canny_tile", "watershed_batch"):
         getattr(L, n).restype = ci
@@ -353,8 +357,9 @@ class Pipe:
         self._keep[tk.value] = (keep, len(tiles), want_planes)
         return tk.value
 
-    def poll(self, ticket, copy=True):
-        """None while the ticket runs; then a list of per-tile dicts."""
+    def poll(self, ticket):
+        """None while the ticket runs; then a list of per-tile dicts (the
+        results are copied out and the ticket released)."""
         import numpy as np
         keep, n, planes = self._keep[ticket]
         out = (TileResult * n)()
@@ -367,7 +372,7 @@ class Pipe:
         for i in range(n):
             r = out[i]
             H, W = keep[i].shape[0], keep[i].shape[1]
-            rows = min(r.n_objects, max(1, min(W * H // 20 + 1, 65536)))
+            rows = r.n_feats
             d = dict(status=r.status, n_objects=r.n_objects, t_arrive_ms=r.t_arrive_ms, t_done_ms=r.t_done_ms)
             d["feats"] = (np.ctypeslib.as_array(r.feats, (rows, NFEAT)).copy() if rows > 0 and r.feats
                           else np.zeros((0, NFEAT), np.float32))
@@ -376,8 +381,17 @@ class Pipe:
                 d["labels"] = np.ctypeslib.as_array(r.labels, (H, W)).copy()
                 d["edt"] = np.ctypeslib.as_array(r.edt, (H, W)).copy()
             res.append(d)
+        _check(lib().batch_release(self.h, ticket), "batch_release")
         del self._keep[ticket]
         return res
+
+    def serve_memory(self):
+        """Device bytes held by the served form's contexts (all, and those
+        with a group in flight) and the number of contexts."""
+        a, f, c = ctypes.c_size_t(), ctypes.c_size_t(), ctypes.c_int()
+        _check(lib().pipe_serve_memory(self.h, ctypes.byref(a), ctypes.byref(f), ctypes.byref(c)),
+               "pipe_serve_memory")
+        return dict(allocated=a.value, in_flight=f.value, contexts=c.value)
 
     # ---- introspection --------------------------------------------------
     def status(self):

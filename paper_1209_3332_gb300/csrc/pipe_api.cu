@@ -279,6 +279,7 @@ struct Ctx {
 
 struct TicketTile {
     int W, H, want;
+    int cap;                       // feature rows the result buffer holds
     size_t out_off, nobj_off, st_off;
 };
 
@@ -323,8 +324,6 @@ struct pipe_s {
     std::vector<std::unique_ptr<Ctx>> ctxs;
     std::map<uint64_t, std::unique_ptr<Ticket>> tickets;
     uint64_t next_ticket = 1;
-    uint64_t last_polled = 0;      // completed ticket whose results are still held
-    size_t hbm_in_use = 0;
     EventProfiler serve_prof;      // launches of the served form (counted, not timed)
     cudaStream_t serve_compute = nullptr;  // all groups compute in submission order
     cudaEvent_t serve_ref = nullptr;       // recorded at serve_ref_ms (host clock)
@@ -348,6 +347,45 @@ int ensure_ctx(LaunchCtx& c, int ntiles, int n_rt, size_t arena_bytes) {
     if ((rc = c.shared.ensure(sizeof(Shared) + sizeof(int) * (2 + std::max(ntiles, 1))))) return rc;
     if ((rc = c.arena.ensure(std::max(arena_bytes, (size_t)256)))) return rc;
     return PIPE_OK;
+}
+
+// Device bytes of a served context's buffers, and what they become when the
+// context is made ready for a group of n tiles (io: caller-visible buffers,
+// ws: workspace arena, n_rt: reconstruction work tiles).  ensure() only
+// grows a buffer, so each part becomes the larger of the two.
+size_t wl_bytes(int n_rt) { return sizeof(int) * 3 * (size_t)std::max(n_rt, 1); }
+size_t tiles_bytes(int n) { return sizeof(TileDev) * (size_t)std::max(n, 1); }
+size_t shared_bytes(int n) { return sizeof(Shared) + sizeof(int) * (2 + (size_t)std::max(n, 1)); }
+size_t ctx_need(size_t io, size_t ws, int n, int n_rt) {
+    return io + std::max(ws, (size_t)256) + tiles_bytes(n) + wl_bytes(n_rt) + shared_bytes(n);
+}
+bool ctx_fits(const Ctx& c, size_t io, size_t ws, int n, int n_rt) {
+    return c.dev.n >= io && c.lc.arena.n >= ws && c.lc.wl.n >= wl_bytes(n_rt) && c.lc.tiles.n >= tiles_bytes(n) &&
+           c.lc.shared.n >= shared_bytes(n);
+}
+size_t ctx_bytes(const Ctx& c) { return c.dev.n + c.lc.arena.n + c.lc.tiles.n + c.lc.wl.n + c.lc.shared.n; }
+size_t ctx_bytes_after(const Ctx& c, size_t io, size_t ws, int n, int n_rt) {
+    return std::max(c.dev.n, io) + std::max(c.lc.arena.n, std::max(ws, (size_t)256)) +
+           std::max(c.lc.tiles.n, tiles_bytes(n)) + std::max(c.lc.wl.n, wl_bytes(n_rt)) +
+           std::max(c.lc.shared.n, shared_bytes(n));
+}
+// Frees an idle context's device buffers (its graphs refer to them).  Idle
+// means batch_poll has seen its last group complete, so no GPU work still
+// uses them.
+void ctx_release_device(Ctx& c) {
+    clear_graphs(c.graphs);
+    c.dev.release();
+    c.lc.tiles.release();
+    c.lc.wl.release();
+    c.lc.shared.release();
+    c.lc.arena.release();
+    c.bytes = 0;
+}
+// Device bytes held by all served contexts, busy or idle.
+size_t serve_allocated(pipe_t p) {
+    size_t s = 0;
+    for (auto& c : p->ctxs) s += c->bytes;
+    return s;
 }
 
 // Fill launch-wide bases of the descriptors and the Launch totals.
@@ -1122,31 +1160,29 @@ int batch_submit(pipe_t p, const tile_desc* tiles, int n, uint64_t* ticket) {
                 (tiles[i].want_planes ? al256(N) + 2 * al256(4 * N) : 0);
         n_rt += geos[i].rtx * geos[i].rty;
     }
-    // admission: a free context (reused if large enough) within the HBM budget
+    // admission: a free context (reused if large enough) within the HBM budget.
+    // The budget counts the device memory of every context, busy or idle: an
+    // idle context keeps its buffers for the next group, so growing one (or
+    // starting a new one) first frees idle contexts when the total would
+    // pass the budget.
+    const size_t need = ctx_need(io, ws, n, n_rt);
+    if (need > p->prm.hbm_budget_bytes) return PIPE_ENOMEM;  // never admissible as one group
     int ci = -1;
     for (int k = 0; k < (int)p->ctxs.size(); k++) {
         Ctx& c = *p->ctxs[k];
-        if (c.busy) continue;
-        if (c.dev.n >= io && c.lc.arena.n >= ws && c.h_in_n >= hin && c.h_out_n >= hout &&
-            c.lc.wl.n >= sizeof(int) * 3 * (size_t)n_rt && c.lc.tiles.n >= sizeof(TileDev) * n &&
-            c.lc.shared.n >= sizeof(Shared) + sizeof(int) * (2 + n)) {
+        if (!c.busy && ctx_fits(c, io, ws, n, n_rt) && c.h_in_n >= hin && c.h_out_n >= hout) {
             ci = k;
             break;
         }
-        if (ci < 0) ci = k;  // a free context to grow if nothing fits
     }
-    size_t need = io + ws + sizeof(TileDev) * n + sizeof(int) * 3 * n_rt;
-    if (need > p->prm.hbm_budget_bytes) return PIPE_ENOMEM;  // never admissible as one group
-    if (ci < 0) {
-        if ((int)p->ctxs.size() >= p->prm.max_slots) return PIPE_EBUSY;
-        p->ctxs.emplace_back(new Ctx());
-        ci = (int)p->ctxs.size() - 1;
-        Ctx& c = *p->ctxs[ci];
-        CK(cudaStreamCreateWithFlags(&c.stream, cudaStreamNonBlocking));
-        CK(cudaEventCreateWithFlags(&c.uploaded, cudaEventDisableTiming));
-        CK(cudaEventCreate(&c.done));  // timed: its GPU timestamp gives the completion time
+    const bool reuse = ci >= 0;
+    if (!reuse) {
+        for (int k = 0; k < (int)p->ctxs.size() && ci < 0; k++)
+            if (!p->ctxs[k]->busy) ci = k;  // a free context to grow
+        if (ci < 0 && (int)p->ctxs.size() >= p->prm.max_slots) return PIPE_EBUSY;
     }
-    Ctx& c = *p->ctxs[ci];
+    size_t g_io = io, g_ws = ws;
+    int g_rt = n_rt, g_n = n;
     // A context that has to grow grows to the largest group seen so far (when
     // the budget allows), so that contexts converge to one size instead of
     // each growing -- a synchronising allocation -- as group sizes vary.
@@ -1154,20 +1190,58 @@ int batch_submit(pipe_t p, const tile_desc* tiles, int n, uint64_t* ticket) {
     p->peak_ws = std::max(p->peak_ws, ws);
     p->peak_rt = std::max(p->peak_rt, n_rt);
     p->peak_n = std::max(p->peak_n, n);
-    const size_t peak_need = p->peak_io + p->peak_ws + sizeof(TileDev) * p->peak_n + sizeof(int) * 3 * p->peak_rt;
-    const bool to_peak = p->hbm_in_use + std::max(c.bytes, peak_need) <= p->prm.hbm_budget_bytes;
-    size_t grow_to = std::max(c.bytes, to_peak ? peak_need : need);
-    if (p->hbm_in_use + grow_to > p->prm.hbm_budget_bytes) return PIPE_EBUSY;
-    const size_t g_io = to_peak ? p->peak_io : io, g_ws = to_peak ? p->peak_ws : ws;
-    const int g_rt = to_peak ? p->peak_rt : n_rt, g_n = to_peak ? p->peak_n : n;
-    int rc;
-    if (c.dev.n < io || c.lc.arena.n < ws || c.lc.wl.n < sizeof(int) * 3 * (size_t)n_rt ||
-        c.lc.tiles.n < sizeof(TileDev) * n || c.lc.shared.n < sizeof(Shared) + sizeof(int) * (2 + n)) {
-        clear_graphs(c.graphs);
-        if ((rc = c.dev.ensure(g_io))) return rc;
-        if ((rc = ensure_ctx(c.lc, g_n, g_rt, g_ws))) return rc;
+    if (!reuse) {
+        const size_t cur = ci >= 0 ? p->ctxs[ci]->bytes : 0;
+        const size_t others = serve_allocated(p) - cur;
+        size_t idle_others = 0;
+        for (int k = 0; k < (int)p->ctxs.size(); k++)
+            if (k != ci && !p->ctxs[k]->busy) idle_others += p->ctxs[k]->bytes;
+        auto after = [&](size_t a_io, size_t a_ws, int a_n, int a_rt) {
+            return ci >= 0 ? ctx_bytes_after(*p->ctxs[ci], a_io, a_ws, a_n, a_rt) : ctx_need(a_io, a_ws, a_n, a_rt);
+        };
+        const size_t at_peak = after(p->peak_io, p->peak_ws, p->peak_n, p->peak_rt);
+        const size_t at_need = after(io, ws, n, n_rt);
+        const size_t budget = p->prm.hbm_budget_bytes;
+        size_t target;
+        if (others + at_peak <= budget) {
+            target = at_peak;
+            g_io = p->peak_io; g_ws = p->peak_ws; g_n = p->peak_n; g_rt = p->peak_rt;
+        } else if (others + at_need <= budget) {
+            target = at_need;
+        } else if (others - idle_others + at_need <= budget) {
+            target = at_need;  // fits once idle contexts give their memory back
+        } else {
+            return PIPE_EBUSY;
+        }
+        // free idle contexts, largest first, until the grown context fits
+        while (serve_allocated(p) - cur + target > budget) {
+            int big = -1;
+            for (int k = 0; k < (int)p->ctxs.size(); k++)
+                if (k != ci && !p->ctxs[k]->busy && p->ctxs[k]->bytes > 0 &&
+                    (big < 0 || p->ctxs[k]->bytes > p->ctxs[big]->bytes))
+                    big = k;
+            if (big < 0) return PIPE_EBUSY;
+            ctx_release_device(*p->ctxs[big]);
+        }
+        if (ci < 0) {
+            p->ctxs.emplace_back(new Ctx());
+            ci = (int)p->ctxs.size() - 1;
+            Ctx& c = *p->ctxs[ci];
+            CK(cudaStreamCreateWithFlags(&c.stream, cudaStreamNonBlocking));
+            CK(cudaEventCreateWithFlags(&c.uploaded, cudaEventDisableTiming));
+            CK(cudaEventCreate(&c.done));  // timed: its GPU timestamp gives the completion time
+        }
     }
-    c.bytes = c.dev.n + c.lc.arena.n + c.lc.tiles.n + c.lc.wl.n + c.lc.shared.n;
+    Ctx& c = *p->ctxs[ci];
+    int rc;
+    if (!ctx_fits(c, io, ws, n, n_rt)) {
+        clear_graphs(c.graphs);
+        rc = c.dev.ensure(g_io);
+        if (!rc) rc = ensure_ctx(c.lc, g_n, g_rt, g_ws);
+        c.bytes = ctx_bytes(c);
+        if (rc) return rc;
+    }
+    c.bytes = ctx_bytes(c);
     if (c.h_in_n < hin) {
         if (c.h_in) cudaFreeHost(c.h_in);
         c.h_in = nullptr;
@@ -1220,7 +1294,7 @@ int batch_submit(pipe_t p, const tile_desc* tiles, int n, uint64_t* ticket) {
         else
             CK(cudaMemcpy2DAsync(rgb, (size_t)t.W * 3, src, spitch, (size_t)t.W * 3, t.H, cudaMemcpyHostToDevice,
                                  c.stream));
-        TicketTile tt{t.W, t.H, t.want_planes, 0, 0, 0};
+        TicketTile tt{t.W, t.H, t.want_planes, caps[i], 0, 0, 0};
         tt.nobj_off = hoff; hoff += al256(16);
         tt.out_off = hoff; hoff += al256((size_t)caps[i] * NFEAT * 4);
         if (t.want_planes) hoff += al256(N) + 2 * al256(4 * N);
@@ -1286,7 +1360,6 @@ int batch_submit(pipe_t p, const tile_desc* tiles, int n, uint64_t* ticket) {
     // complete, so nothing of this group still reads the context's buffers.
     CK(cudaGetLastError());
     c.busy = true;
-    p->hbm_in_use += c.bytes;
     p->prof.launches += 0;
     uint64_t id = p->next_ticket++;
     p->tickets[id] = std::move(tk);
@@ -1322,13 +1395,12 @@ int batch_poll(pipe_t p, uint64_t ticket, int* n_done, tile_result* out) {
             std::memcpy(vals, ho + tt.nobj_off, sizeof(vals));
             K[i] = vals[0];
             st[i] = vals[1] ? vals[1] : vals[2];
-            int rows = std::min(K[i], (int)((tt.W * (size_t)tt.H) / 20 + 1 < 65536 ? (tt.W * (size_t)tt.H) / 20 + 1 : 65536));
+            const int rows = std::max(0, std::min(K[i], tt.cap));
             const float* f = (const float*)(ho + tt.out_off);
-            tk.feats[i].assign(f, f + (size_t)std::max(rows, 0) * NFEAT);
+            tk.feats[i].assign(f, f + (size_t)rows * NFEAT);
             if (tt.want) {
                 size_t N = (size_t)tt.W * tt.H;
-                size_t cap = std::min<size_t>(N / 20 + 1, 65536);
-                const char* q = ho + tt.out_off + al256(cap * NFEAT * 4);
+                const char* q = ho + tt.out_off + al256((size_t)tt.cap * NFEAT * 4);
                 tk.hem8[i].assign((const uint8_t*)q, (const uint8_t*)q + N);
                 tk.labels[i].assign((const int32_t*)(q + al256(N)), (const int32_t*)(q + al256(N)) + N);
                 tk.edt[i].assign((const int32_t*)(q + al256(N) + al256(4 * N)), (const int32_t*)(q + al256(N) + al256(4 * N)) + N);
@@ -1341,7 +1413,6 @@ int batch_poll(pipe_t p, uint64_t ticket, int* n_done, tile_result* out) {
         double td = now_ms();
         if (cudaEventElapsedTime(&el, p->serve_ref, c.done) == cudaSuccess) td = p->serve_ref_ms + el;
         c.busy = false;
-        p->hbm_in_use -= std::min(p->hbm_in_use, c.bytes);
         for (int i = 0; i < n; i++) tk.tiles[i].out_off = 0;
         tk.t_submit = tk.t_submit;
         tk.ctx = -1;
@@ -1356,7 +1427,8 @@ int batch_poll(pipe_t p, uint64_t ticket, int* n_done, tile_result* out) {
             tile_result& r = out[i];
             r.status = (int)tk.tiles[i].st_off;
             r.n_objects = (int)tk.tiles[i].nobj_off;
-            if (r.status == PIPE_OK && r.n_objects > (int)(tk.feats[i].size() / NFEAT)) r.status = PIPE_EOVERFLOW;
+            r.n_feats = (int)(tk.feats[i].size() / NFEAT);
+            if (r.status == PIPE_OK && r.n_objects > r.n_feats) r.status = PIPE_EOVERFLOW;
             r.feats = tk.feats[i].empty() ? nullptr : tk.feats[i].data();
             r.hem8 = tk.hem8[i].empty() ? nullptr : tk.hem8[i].data();
             r.labels = tk.labels[i].empty() ? nullptr : tk.labels[i].data();
@@ -1366,9 +1438,30 @@ int batch_poll(pipe_t p, uint64_t ticket, int* n_done, tile_result* out) {
         }
     }
     *n_done = n;
-    // results of the previously polled ticket are released now
-    if (p->last_polled && p->last_polled != ticket) p->tickets.erase(p->last_polled);
-    p->last_polled = ticket;
+    return PIPE_OK;
+}
+
+int batch_release(pipe_t p, uint64_t ticket) {
+    if (!p) return PIPE_EINVAL;
+    std::lock_guard<std::mutex> lk(p->mu);
+    auto it = p->tickets.find(ticket);
+    if (it == p->tickets.end()) return PIPE_EINVAL;
+    if (!it->second->done) return PIPE_EAGAIN;  // its group still uses a context
+    p->tickets.erase(it);
+    return PIPE_OK;
+}
+
+int pipe_serve_memory(pipe_t p, size_t* allocated, size_t* in_flight, int* contexts) {
+    if (!p) return PIPE_EINVAL;
+    std::lock_guard<std::mutex> lk(p->mu);
+    size_t a = 0, f = 0;
+    for (auto& c : p->ctxs) {
+        a += c->bytes;
+        if (c->busy) f += c->bytes;
+    }
+    if (allocated) *allocated = a;
+    if (in_flight) *in_flight = f;
+    if (contexts) *contexts = (int)p->ctxs.size();
     return PIPE_OK;
 }
 

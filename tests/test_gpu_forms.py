@@ -173,3 +173,86 @@ def test_autotune_keeps_results_and_cache_file_round_trip(tmp_path):
         for k in ("hem8", "labels", "edt"):
             assert np.array_equal(x[k], y[k]) and np.array_equal(x[k], z[k]), k
         assert np.array_equal(x["feats"], y["feats"]) and np.array_equal(x["feats"], z["feats"])
+
+
+def test_served_budget_counts_idle_contexts():
+    """The HBM budget bounds the device memory of every served context, busy
+    or idle: groups of alternating sizes, up to two in flight, never leave
+    more than hbm_budget_bytes allocated, and every result equals the tile's
+    result alone."""
+    import paper_1209_3332_gb300 as P
+    small = [synth.tile(512, 384, 61, n_nuclei=40)]
+    big = [synth.tile(1024, 1024, 62 + i, n_nuclei=250, frac_cluster=0.2) for i in range(3)]
+    probe = P.Pipe(0, max_slots=3)
+    ref = {}
+    for grp in (small, big):
+        for t, r in zip(grp, wait(probe, probe.submit(grp))):
+            ref[id(t)] = r
+    probe.close()
+    one_big = P.Pipe(0, max_slots=1)
+    wait(one_big, one_big.submit(big))
+    need_big = one_big.serve_memory()["allocated"]
+    one_big.close()
+    budget = int(1.5 * need_big)
+    p = P.Pipe(0, max_slots=3, hbm_budget_bytes=budget)
+    # a context stays busy until its ticket is polled, so a second big group
+    # submitted before any poll cannot fit beside the first
+    tk = p.submit(big)
+    assert tk is not None
+    assert p.submit(big) is None
+    assert p.serve_memory()["allocated"] <= budget
+    seq = [small, big[:2], small, big, big[:1], small + big[:1], big]
+    inflight, k = [(tk, big)], 0
+    t0 = time.time()
+    while k < len(seq) or inflight:
+        if k < len(seq) and len(inflight) < 2:
+            tk = p.submit(seq[k])
+            assert p.serve_memory()["allocated"] <= budget
+            if tk is not None:
+                inflight.append((tk, seq[k]))
+                k += 1
+        still = []
+        for tk, grp in inflight:
+            res = p.poll(tk)
+            if res is None:
+                still.append((tk, grp))
+                continue
+            for t, r in zip(grp, res):
+                assert r["status"] == 0
+                assert r["n_objects"] == ref[id(t)]["n_objects"]
+                assert_same_feats(r["feats"], ref[id(t)]["feats"], "served under a small budget")
+        inflight = still
+        assert p.serve_memory()["allocated"] <= budget
+        assert time.time() - t0 < 120
+    m = p.serve_memory()
+    assert m["in_flight"] == 0 and m["allocated"] <= budget
+    assert p.status() == P.PIPE_OK
+    p.close()
+
+
+def test_served_concurrent_polls_keep_each_tickets_results(pipe):
+    """Two threads poll their own tickets at once: a poll never releases
+    another ticket's results (they stay until that ticket is released)."""
+    import threading
+    tiles = [synth.tile(768, 512, 71 + i, n_nuclei=120, frac_cluster=0.2) for i in range(4)]
+    ref = [wait(pipe, pipe.submit([t]))[0] for t in tiles]
+    tks = [pipe.submit([t]) for t in tiles]
+    assert all(tk is not None for tk in tks)
+    got = [None] * 4
+    errs = []
+
+    def worker(idx):
+        try:
+            for i in idx:
+                got[i] = wait(pipe, tks[i])[0]
+        except Exception as e:  # reported by the main thread
+            errs.append(e)
+    th = [threading.Thread(target=worker, args=(idx,)) for idx in ((0, 2), (1, 3))]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join(120)
+    assert not errs, errs
+    for a, b in zip(got, ref):
+        assert a["n_objects"] == b["n_objects"]
+        assert_same_feats(a["feats"], b["feats"], "concurrent polls")
