@@ -1,7 +1,7 @@
 """Benchmark: 4096x4096 tiles per second through the segmentation + feature path.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--batch B]
-                    [--impl ours|reference] [--no-cpu] [--no-extra]
+                    [--impl ours|reference] [--no-cpu] [--no-extra] [--no-configs]
 
 One step is one pass of the whole path -- colour deconvolution, h-dome
 reconstruction, fill holes, labelling + area filter + relabel, EDT and
@@ -14,13 +14,21 @@ are resident in HBM when the timed region starts; a batch's inputs alone
 
 Reported beside the batched value: the plain form (seg_tile + features_tile,
 one tile per call) on the same tiles; the served form (batch_submit /
-batch_poll under Poisson arrivals at 80% of the batched rate, with p50/p99
-latency); an end-to-end figure (whole batches submitted from pinned host
-memory through the served API and polled to completion); per-kernel CUDA
-event times; the roofline of the dominant kernel; and the CPU oracle.
+batch_poll under Poisson arrivals at 80% and at 125% of the batched rate,
+with p50/p99 latency); an end-to-end figure (whole batches submitted from
+pinned host memory through the served API and polled to completion);
+per-kernel CUDA event times; the roofline of the dominant kernel; the steps
+beside the path (opening, watershed, Canny); the other workloads -- the
+64-tile mixed batch (batched vs plain), the served pool (2000 Poisson
+requests at 80% of the mixed batch's rate under the 40 GiB budget) and the
+stress stream (4096 worst-case tiles from pinned host memory, against the
+batched and plain forms), each result checked bit for bit against the
+batched form; and the CPU oracle.
 
-N>1 (torchrun): every rank is an independent replica on its own tiles (the
-path shards by tile; there is no data exchange), value = all tiles / max time.
+N>1: every rank is an independent replica on its own tiles (the path shards
+by tile; there is no data exchange), value = all tiles / max time.  Under
+torchrun the ranks come from the environment; with --gpus N and no
+WORLD_SIZE, bench.py starts the N ranks itself under torch.distributed.run.
 
 --impl reference times the CPU oracle (the plain C program written from the
 paper's definitions) on this host's cores on full tiles of the same
@@ -498,14 +506,17 @@ def h2d_gbs(torch, dev, nbytes=256 << 20, reps=4):
     return best
 
 
-def serve_run(pipe, pinned, n_requests, rate, seed=3999, max_group=16, max_inflight=2, limit_s=120.0, costs=None):
+def serve_run(pipe, pinned, n_requests, rate, seed=3999, max_group=16, max_inflight=2, limit_s=120.0, costs=None,
+              check=None):
     """Poisson arrivals at `rate` tiles/s; each request is one pool tile.
     Continuous batching: whenever fewer than max_inflight groups are on the
     device, the requests that have arrived (up to max_group) are admitted as
     the next group, so one group uploads while the previous one computes.
     Without `costs` the group takes them in order of arrival; with `costs`
     (an estimate per pool tile) they wait in the dispatcher's queue
-    (P.Sched) and the group takes the most expensive first."""
+    (P.Sched) and the group takes the most expensive first.  check(pool
+    index, result) is called on every result (it raises on a mismatch).
+    Also reports the served contexts' peak device memory."""
     import paper_1209_3332_gb300 as P
     rng = random.Random(seed)
     arrivals, t = [], 0.0
@@ -514,7 +525,7 @@ def serve_run(pipe, pinned, n_requests, rate, seed=3999, max_group=16, max_infli
         arrivals.append(t)
     sched = P.Sched(1, max_group * max_inflight) if costs is not None else None
     waiting, inflight, lat, done_t, sizes = [], [], [], [], []
-    i = 0
+    i, peak_mem = 0, 0
     t0 = time.monotonic()
 
     def queued():
@@ -559,12 +570,15 @@ def serve_run(pipe, pinned, n_requests, rate, seed=3999, max_group=16, max_infli
             for r, out in zip(reqs, res):
                 if out["status"] != 0:
                     raise RuntimeError("served tile status %d" % out["status"])
+                if check is not None:
+                    check(r % len(pinned), out)
                 if sched:
                     sched.done(0, r)
                 done_ms = out["t_done_ms"] - t0 * 1000.0
                 lat.append(done_ms - arrivals[r] * 1000.0)
                 done_t.append(done_ms / 1000.0)
         inflight = still
+        peak_mem = max(peak_mem, pipe.serve_memory()["allocated"])
         if not queued() and not inflight and i < n_requests:
             time.sleep(max(0.0, min(0.0005, arrivals[i] - (time.monotonic() - t0))))
     lat.sort()
@@ -576,7 +590,9 @@ def serve_run(pipe, pinned, n_requests, rate, seed=3999, max_group=16, max_infli
             "requests": n_requests, "arrival_rate": rate, "pool_tiles": len(pinned),
             "policy": "continuous batching: <= %d groups in flight, <= %d tiles per group, %s"
                       % (max_inflight, max_group, "most expensive first (Sched)" if sched else "arrival order"),
-            "groups": len(sizes), "mean_group": sum(sizes) / max(1, len(sizes))}
+            "groups": len(sizes), "mean_group": sum(sizes) / max(1, len(sizes)),
+            "peak_device_bytes": peak_mem, "hbm_budget_bytes": pipe.params.hbm_budget_bytes,
+            "checked": check is not None}
 
 
 def dispatch_compare(torch, pipe, n_requests, batched_rate):
@@ -600,6 +616,189 @@ def dispatch_compare(torch, pipe, n_requests, batched_rate):
                     % (min(h.shape[0] for h in host), max(h.shape[0] for h in host)),
             "arrival_rate": rate, "arrival_order": fifo, "most_expensive_first": lpt,
             "cost": "tile_cost: W*H*(1 + 8 * dark fraction on a 1-in-64 sample)"}
+
+
+def feats_cap_of(W, H):
+    """The served form's feature capacity of a W x H tile."""
+    return max(1, min(W * H // 20 + 1, 65536))
+
+
+def tile_buffers(torch, dev, host):
+    """Device buffers of the batched / plain forms for host tiles of any sizes."""
+    bufs = []
+    for h in host:
+        Ht, Wt = h.shape[:2]
+        bufs.append(dict(rgb=torch.from_numpy(h).to(dev), hem8=torch.empty((Ht, Wt), dtype=torch.uint8, device=dev),
+                         labels=torch.empty((Ht, Wt), dtype=torch.int32, device=dev),
+                         edt=torch.empty((Ht, Wt), dtype=torch.int32, device=dev),
+                         n_objects=torch.zeros(1, dtype=torch.int32, device=dev),
+                         feats=torch.empty((feats_cap_of(Wt, Ht), 15), dtype=torch.float32, device=dev)))
+    return bufs
+
+
+def px4k(host):
+    """Pixels of the tiles in 4096 x 4096 tile equivalents."""
+    return sum(h.shape[0] * h.shape[1] for h in host) / float(H * W)
+
+
+def batched_vs_plain(torch, pipe, stream, bufs, steps):
+    """The batched form over all of `bufs` in one launch per pass, timed
+    with CUDA events, and the plain form (seg_tile + features_tile per
+    tile) on the same tiles; the plain outputs must equal the batched ones
+    bit for bit (labels, K, feature rows).  Returns ms per step of each and
+    the batched results (K and feature rows per tile, on the host)."""
+    def batched():
+        pipe.seg_features_batch(bufs, stream=stream)
+    for _ in range(3):
+        batched()                       # the first call tunes this batch shape
+    stream.synchronize()
+    ms_b = timed(torch, stream, batched, steps) / steps
+    ref = [(int(b["n_objects"].item()), b["labels"].clone(), b["feats"].clone()) for b in bufs]
+
+    def plain():
+        for b in bufs:
+            pipe.seg_tile(b["rgb"], b["hem8"], b["labels"], b["edt"], b["n_objects"], stream=stream)
+            stream.synchronize()        # the plain feature call takes K from the host
+            pipe.features_tile(b["hem8"], b["labels"], int(b["n_objects"].item()), b["feats"], stream=stream)
+    plain()
+    n_plain = max(1, steps // 2)
+    ms_p = timed(torch, stream, plain, n_plain) / n_plain
+    out = []
+    for b, (K, lab, ft) in zip(bufs, ref):
+        k2 = int(b["n_objects"].item())
+        rows = min(K, ft.shape[0])
+        if k2 != K or not torch.equal(lab, b["labels"]) or not torch.equal(ft[:rows], b["feats"][:rows]):
+            raise RuntimeError("plain and batched forms differ on a tile")
+        out.append((K, ft[:rows].cpu().numpy()))
+    st = pipe.status()
+    if st != 0:
+        raise RuntimeError("device status %d" % st)
+    return ms_b, ms_p, out
+
+
+def make_check(ref):
+    """check(pool index, served result): K and every feature row equal the
+    batched form's on that pool tile, bit for bit."""
+    import numpy as np
+
+    def check(i, out):
+        K, ft = ref[i]
+        if out["n_objects"] != K or not np.array_equal(out["feats"], ft):
+            raise RuntimeError("served result of pool tile %d differs from the batched form" % i)
+    return check
+
+
+def cfg2_run(torch, pipe, stream, steps):
+    """The 64-tile mixed batch (sides 1024-4096, 0-5000 nuclei per 4096^2,
+    tile 0 empty, tile 1 at 5000): the batched form in one launch per pass
+    against the plain form on the same tiles."""
+    import synth
+    host = [synth.cfg2(i) for i in range(64)]
+    bufs = tile_buffers(torch, torch.device("cuda", torch.cuda.current_device()), host)
+    ms_b, ms_p, _ = batched_vs_plain(torch, pipe, stream, bufs, steps)
+    eq = px4k(host)
+    n = len(host)
+    out = {"workload": "64 tiles, sides uniform in {1024,2048,3072,4096}, 0-5000 nuclei per 4096^2 "
+                       "(synth.cfg2, seeds 2000+i)", "tiles_per_step": n, "4k_equivalents_per_step": eq,
+           "batched": {"ms_per_step": ms_b, "tiles_per_s": n * 1000.0 / ms_b, "4k_equiv_per_s": eq * 1000.0 / ms_b},
+           "plain": {"ms_per_step": ms_p, "tiles_per_s": n * 1000.0 / ms_p, "4k_equiv_per_s": eq * 1000.0 / ms_p},
+           "parity": "plain == batched bit for bit on every tile in this run; oracle parity in "
+                     "tests/test_gpu_configs.py"}
+    out["batched_over_plain"] = ms_p / ms_b
+    del bufs
+    torch.cuda.empty_cache()
+    return out
+
+
+def cfg3_run(torch, pipe, stream, cfg2_rate, n_requests, steps):
+    """Config 3: Poisson arrivals over the 64-tile served pool (sides
+    2048-4096 in steps of 256, densities as config 2) at 80% of the config-2
+    batched rate, through batch_submit / batch_poll under the pipe's 40 GiB
+    HBM budget; every result is checked against the batched form on its
+    pool tile."""
+    import synth
+    host = [synth.cfg3(i) for i in range(64)]
+    dev = torch.device("cuda", torch.cuda.current_device())
+    bufs = tile_buffers(torch, dev, host)
+    ms_b, _, ref = batched_vs_plain(torch, pipe, stream, bufs, max(2, steps // 4))
+    del bufs
+    torch.cuda.empty_cache()
+    pinned = [torch.from_numpy(h).pin_memory() for h in host]
+    rate = 0.8 * cfg2_rate
+    serve_run(pipe, pinned, 64, rate)                     # warm the contexts for these shapes
+    r = serve_run(pipe, pinned, n_requests, rate, check=make_check(ref))
+    pool_rate = len(host) * 1000.0 / ms_b
+    r.update(workload="%d requests cycling 64 tiles of synth.cfg3 (sides 2048-4096, 0-5000 nuclei per 4096^2), "
+                      "Poisson arrivals at 0.8 x the config-2 batched tiles/s" % n_requests,
+             batched_pool_tiles_per_s=pool_rate, offered_load_vs_batched=rate / pool_rate,
+             parity="every served result equals the batched form on its pool tile, bit for bit")
+    return r
+
+
+def stream_run(pipe, pinned, n_tiles, group=16, inflight=2, limit_s=300.0, check=None):
+    """n_tiles requests cycling the pinned pool, submitted in groups of
+    `group` with up to `inflight` groups on the device (a closed loop that
+    keeps the device busy); returns tiles/s and group latencies."""
+    t0 = time.monotonic()
+    q, sent, done, lat = [], 0, 0, []
+    while done < n_tiles:
+        while len(q) < inflight and sent < n_tiles:
+            idx = [(sent + k) % len(pinned) for k in range(min(group, n_tiles - sent))]
+            tk = pipe.submit([pinned[i] for i in idx])
+            if tk is None:
+                break
+            q.append((tk, idx, time.monotonic()))
+            sent += len(idx)
+        if not q:
+            continue
+        res = pipe.poll(q[0][0])
+        if res is None:
+            if time.monotonic() - t0 > limit_s:
+                raise RuntimeError("stream not done within %.0f s" % limit_s)
+            continue
+        tk, idx, ts = q.pop(0)
+        for i, out in zip(idx, res):
+            if out["status"] != 0:
+                raise RuntimeError("streamed tile status %d" % out["status"])
+            if check is not None:
+                check(i, out)
+        lat.append(1000.0 * (time.monotonic() - ts))
+        done += len(idx)
+    el = time.monotonic() - t0
+    lat.sort()
+    return {"tiles": n_tiles, "seconds": el, "tiles_per_s": n_tiles / el, "group": group, "groups_in_flight": inflight,
+            "group_latency_p50_ms": lat[len(lat) // 2], "group_latency_p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))]}
+
+
+def cfg4_run(torch, pipe, stream, n_tiles, steps, link_gbs):
+    """Config 4, the stress workload: worst-case 4096^2 tiles (8000 nuclei,
+    half in chains, a serpentine ramp corridor) from a pool of 32, streamed
+    from pinned host memory through batch_submit / batch_poll (batched +
+    served), against the batched and plain forms on 16 tiles resident in
+    HBM; every streamed result is checked against the batched form."""
+    import synth
+    host = [synth.cfg4(i) for i in range(32)]
+    dev = torch.device("cuda", torch.cuda.current_device())
+    ref, resident = [], None
+    for half in (host[:16], host[16:]):
+        bufs = tile_buffers(torch, dev, half)
+        ms_b, ms_p, r = batched_vs_plain(torch, pipe, stream, bufs, max(2, steps // 4))
+        ref.extend(r)
+        if resident is None:
+            resident = {"batched": {"tiles_per_s": 16 * 1000.0 / ms_b, "ms_per_step": ms_b},
+                        "plain": {"tiles_per_s": 16 * 1000.0 / ms_p, "ms_per_step": ms_p}}
+        del bufs
+        torch.cuda.empty_cache()
+    pinned = [torch.from_numpy(h).pin_memory() for h in host]
+    stream_run(pipe, pinned, 64)                           # warm
+    r = stream_run(pipe, pinned, n_tiles, check=make_check(ref))
+    link_bound = link_gbs * 1e9 / (3.0 * H * W)
+    return {"workload": "%d worst-case 4096x4096 tiles cycling a pool of 32 (synth.cfg4: 8000 nuclei, half in "
+                        "chains of 10-30, serpentine ramp corridor)" % n_tiles,
+            "streamed": r, "resident": resident,
+            "streamed_over_plain": r["tiles_per_s"] / resident["plain"]["tiles_per_s"],
+            "link_bound_tiles_per_s": link_bound, "streamed_frac_of_link": r["tiles_per_s"] / link_bound,
+            "parity": "every streamed result equals the batched form on its pool tile, bit for bit"}
 
 
 def run_ours(args, world, rank, local):
@@ -724,10 +923,12 @@ def run_ours(args, world, rank, local):
                            "two steps in flight",
                    "single_step_latency_ms": 1000.0 * lat_s}
 
-    # ---- served form: Poisson arrivals at 80% of the batched rate ----------
+    # ---- served form: Poisson arrivals at 80% and 125% of the batched rate ---
     rate = 0.8 * value / world
     serve_run(pipe, pinned, min(32, 4 * B), rate)  # warm the contexts
     line["served"] = serve_run(pipe, pinned, args.requests, rate)
+    line["served_saturated"] = serve_run(pipe, pinned, args.requests, 1.25 * value / world)
+    line["served_saturated"]["offered_load_vs_batched"] = 1.25
 
     # ---- dispatch order on a mixed pool: arrival order vs most expensive first
     if not args.no_extra:
@@ -768,11 +969,29 @@ def run_ours(args, world, rank, local):
     # ---- the feature-stage edge transform: Canny and per-object edge counts --
     line["canny"] = canny_run(torch, pipe, stream, bufs, max(3, args.steps // 2), peak,
                               rank == 0 and world == 1 and not args.no_cpu)
+    # ---- the other workloads: mixed batch, served pool, worst-case stream ----
+    if world == 1 and not args.no_configs:
+        line["cfg2"] = cfg2_run(torch, pipe, stream, max(3, args.steps // 2))
+        line["cfg3"] = cfg3_run(torch, pipe, stream, line["cfg2"]["batched"]["tiles_per_s"], args.cfg3_requests,
+                                args.steps)
+        line["cfg4"] = cfg4_run(torch, pipe, stream, args.cfg4_tiles, args.steps, link)
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(host[0])
     if rank == 0:
         print(json.dumps(line), flush=True)
     pipe.close()
+
+
+def relaunch(n):
+    """Runs this command again under torch.distributed.run with n local
+    ranks (rendezvous on 127.0.0.1); returns its exit code."""
+    import socket
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", str(n),
+           "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.abspath(__file__)] + sys.argv[1:]
+    return subprocess.call(cmd)
 
 
 def main():
@@ -785,8 +1004,16 @@ def main():
     ap.add_argument("--requests", type=int, default=400, help="requests in the served leg")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
     ap.add_argument("--no-extra", action="store_true", help="timed region only")
+    ap.add_argument("--no-configs", action="store_true", help="skip the mixed-batch, served-pool and stress legs")
+    ap.add_argument("--cfg3-requests", type=int, default=2000, help="requests of the served-pool leg")
+    ap.add_argument("--cfg4-tiles", type=int, default=4096, help="tiles streamed in the stress leg")
     args = ap.parse_args()
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        # one process per GPU: start the ranks here rather than run one replica
+        sys.exit(relaunch(args.gpus))
     world, rank, local = dist_setup()
+    if world != args.gpus:
+        sys.exit("bench.py: --gpus %d but WORLD_SIZE is %d" % (args.gpus, world))
     if args.impl == "reference":
         run_reference(args, world, rank)
     else:
