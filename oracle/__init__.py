@@ -17,6 +17,7 @@ _lib = None
 NFEAT = 15
 CANNY_LOW, CANNY_HIGH = 40, 120   # hysteresis thresholds on the L1 Sobel magnitude of hem8 (our reading)
 EDGE_R = 3                        # radius of the disk dilation the edge counts cover (our reading)
+RBC_LO, RBC_HI = 40, 100          # red-dominance thresholds of the RBC mask and markers (our reading)
 
 u8p = ctypes.POINTER(ctypes.c_uint8)
 i32p = ctypes.POINTER(ctypes.c_int32)
@@ -67,6 +68,8 @@ def _load():
         L.oracle_watershed.restype = ci
         L.oracle_canny.argtypes = [vp, ci, ci, ci, ci, vp, vp, vp]
         L.oracle_canny.restype = ctypes.c_longlong
+        L.oracle_rbc.argtypes = [vp, ci, ci, sz, ci, ci, vp, vp]
+        L.oracle_rbc.restype = ctypes.c_longlong
         L.oracle_edge_counts.argtypes = [vp, vp, ci, ci, ci, ci, vp]
         L.oracle_edge_counts.restype = None
         _lib = L
@@ -256,3 +259,21 @@ def edge_counts(edges, labels, K, r=EDGE_R):
     cnt = np.zeros(max(K, 1), np.int32)
     _load().oracle_edge_counts(pe, pl, W, H, int(K), int(r), cnt.ctypes.data)
     return cnt[:K]
+
+
+def rbc(rgb, t_lo=RBC_LO, t_hi=RBC_HI, detail=False):
+    """Red blood cell mask (Table I "RBC detection"): uint8 plane of 0/1,
+    the 8-connected components of {R - max(G, B) >= t_lo} that hold a pixel
+    with R - max(G, B) >= t_hi.  detail=True also returns the int16 red
+    dominance plane."""
+    a = np.asarray(rgb, dtype=np.uint8)
+    if a.ndim != 3 or a.shape[2] != 3 or a.strides[1:] != (3, 1):
+        a = np.ascontiguousarray(a)
+    H, W = a.shape[:2]
+    out = np.empty((H, W), np.uint8)
+    red = np.empty((H, W), np.int16)
+    n = _load().oracle_rbc(a.ctypes.data, W, H, a.strides[0], int(t_lo), int(t_hi), out.ctypes.data,
+                           red.ctypes.data)
+    if n < 0:
+        raise ValueError("bad arguments")
+    return (out, red) if detail else out

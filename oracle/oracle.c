@@ -704,6 +704,42 @@ int oracle_watershed(const int32_t* labels, const int32_t* edt, int W, int H, in
     return total;
 }
 
+/* RBC detection: red dominance, then the mask components that hold a marker
+ * pixel, found by a breadth-first flood from the markers (raster order of
+ * the seeds; the result does not depend on it). */
+long long oracle_rbc(const uint8_t* rgb, int W, int H, size_t pitch, int t_lo, int t_hi, uint8_t* out,
+                     int16_t* red) {
+    if (W < 1 || H < 1 || pitch < (size_t)W * 3 || t_lo < 0 || t_hi < t_lo || t_hi > 255) return -1;
+    const size_t N = (size_t)W * H;
+    int16_t* d = (int16_t*)malloc(N * sizeof(int16_t));
+    int32_t* q = (int32_t*)malloc(N * sizeof(int32_t));
+    if (!d || !q) { free(d); free(q); return -1; }
+    for (int y = 0; y < H; y++)
+        for (int x = 0; x < W; x++) {
+            const uint8_t* p = rgb + (size_t)y * pitch + (size_t)x * 3;
+            const int gb = p[1] > p[2] ? p[1] : p[2];
+            d[(size_t)y * W + x] = (int16_t)(p[0] - gb);
+        }
+    if (red) memcpy(red, d, N * sizeof(int16_t));
+    memset(out, 0, N);
+    size_t head = 0, tail = 0;
+    for (size_t i = 0; i < N; i++)
+        if (d[i] >= t_hi) { out[i] = 1; q[tail++] = (int32_t)i; }
+    while (head < tail) {
+        const int i = q[head++], y = i / W, x = i % W;
+        for (int dy = -1; dy <= 1; dy++)
+            for (int dx = -1; dx <= 1; dx++) {
+                const int yy = y + dy, xx = x + dx;
+                if (yy < 0 || yy >= H || xx < 0 || xx >= W) continue;
+                const size_t j = (size_t)yy * W + xx;
+                if (!out[j] && d[j] >= t_lo) { out[j] = 1; q[tail++] = (int32_t)j; }
+            }
+    }
+    free(d);
+    free(q);
+    return (long long)tail;
+}
+
 /* ---- Canny edges (Sec. V-A feature-stage transform; Table I "Features
  * comp.") -- readings in oracle.h ------------------------------------------ */
 

@@ -150,6 +150,20 @@ long long oracle_canny(const uint8_t* I, int W, int H, int low, int high, uint8_
  * segmentation keeps; a pixel near two objects counts for both. */
 void oracle_edge_counts(const uint8_t* edges, const int32_t* labels, int W, int H, int K, int r, int32_t* cnt);
 
+/* Red blood cell detection (Table I "RBC detection": OpenCV colour
+ * operations and Vincent's MR; the paper gives no definition).  Our reading:
+ *  red dominance d = R - max(G, B) per pixel (an integer in [-255, 255]);
+ *  marker = {d >= t_hi}, mask = {d >= t_lo}, 0 <= t_lo <= t_hi <= 255;
+ *  out = the binary reconstruction by dilation, 8-connected, of the marker
+ *    under the mask: 1 on the 8-connected components of the mask that hold
+ *    a marker pixel, 0 elsewhere.
+ * Plain definition: a breadth-first flood from every marker pixel through
+ * the mask.  rgb: H rows of 3*W bytes at `pitch`; out: H*W; red (may be
+ * NULL) receives d.  Returns the number of RBC pixels, or -1 on bad
+ * arguments. */
+long long oracle_rbc(const uint8_t* rgb, int W, int H, size_t pitch, int t_lo, int t_hi, uint8_t* out,
+                     int16_t* red);
+
 /* Whole segmentation: deconv -> h-dome -> fill holes -> label -> EDT.
  * Any of R, fg, filled may be NULL.  Returns K, or -1 on bad arguments. */
 int oracle_seg(const uint8_t* rgb, int W, int H, size_t pitch, int h, int thr, int amin, int amax,

@@ -35,14 +35,15 @@ class SynthCfg(ctypes.Structure):
                 ("n_nuclei", ctypes.c_int), ("frac_overlap", ctypes.c_double),
                 ("frac_cluster", ctypes.c_double), ("frac_chain", ctypes.c_double),
                 ("n_stroma", ctypes.c_int), ("stroma_rmin", ctypes.c_double),
-                ("stroma_rmax", ctypes.c_double), ("corridor", ctypes.c_int)]
+                ("stroma_rmax", ctypes.c_double), ("corridor", ctypes.c_int), ("n_rbc", ctypes.c_int)]
 
 
 def build(force=False):
     """Compile libsynth.so next to this file (gcc, OpenMP)."""
     so = os.path.join(_here, "libsynth.so")
     src = os.path.join(_here, "synth.c")
-    if force or not os.path.exists(so) or os.path.getmtime(so) < os.path.getmtime(src):
+    hdr = os.path.join(_here, "synth.h")
+    if force or not os.path.exists(so) or os.path.getmtime(so) < max(os.path.getmtime(src), os.path.getmtime(hdr)):
         subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
                                "-o", so, src, "-lm"])
     return so
@@ -58,10 +59,10 @@ def _load():
 
 
 def tile(W, H, seed, n_nuclei=0, frac_overlap=0.0, frac_cluster=0.0, frac_chain=0.0,
-         n_stroma=0, stroma_rmin=40.0, stroma_rmax=120.0, corridor=False):
+         n_stroma=0, stroma_rmin=40.0, stroma_rmax=120.0, corridor=False, n_rbc=0):
     """Return an (H, W, 3) uint8 RGB tile."""
     cfg = SynthCfg(W, H, seed, n_nuclei, frac_overlap, frac_cluster, frac_chain, n_stroma,
-                   stroma_rmin, stroma_rmax, 1 if corridor else 0)
+                   stroma_rmin, stroma_rmax, 1 if corridor else 0, n_rbc)
     out = np.empty((H, W, 3), np.uint8)
     rc = _load().synth_tile(ctypes.byref(cfg), out.ctypes.data, W * 3)
     if rc != 0:

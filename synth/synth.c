@@ -13,8 +13,8 @@
  * bytes are the same on every host architecture; only the ellipse geometry
  * uses libm cos/sin.
  *
- * Paint order: background -> stroma blobs -> nuclei -> serpentine corridor
- * -> per-channel noise (Irwin-Hall sum of 12 uniforms, sd 6) -> separable
+ * Paint order: background -> stroma blobs -> nuclei -> red blood cells ->
+ * serpentine corridor -> per-channel noise (Irwin-Hall sum of 12 uniforms, sd 6) -> separable
  * Gaussian blur sigma 1 (radius 3, mirror border) -> round half to even and
  * clamp to uint8.
  */
@@ -88,6 +88,7 @@ static const int BG[3] = {225, 215, 228};
 static const int NUC[3] = {90, 60, 140};
 static const int STROMA[3] = {200, 150, 190};
 static const int CORR_END[3] = {160, 110, 170};
+static const int RBC[3] = {200, 60, 70};
 
 /* one nucleus: semi-axes uniform in [4,12], angle uniform in [0,pi), colour +-8 jitter */
 typedef struct { double cx, cy, a, b, th; } nuc;
@@ -223,6 +224,29 @@ int synth_tile(const synth_cfg* cfg, uint8_t* out, size_t pitch) {
             placed++;
             prev = m;
             have_prev = 1;
+        }
+    }
+
+    /* red blood cells: discs of radius uniform in [3.5, 5.5] px, colour +-8
+       jitter; 30% of the draws start a touching clump of 2..5 (rouleaux).
+       Their draws come from a stream of their own, so the rest of a tile
+       does not depend on n_rbc. */
+    rstream rbc = {seed, 3, 0};
+    for (int placed_rbc = 0; placed_rbc < cfg->n_rbc;) {
+        int len = rs_unif(&rbc) < 0.3 ? rs_int(&rbc, 2, 5) : 1;
+        double cx = W * rs_unif(&rbc), cy = H * rs_unif(&rbc);
+        double rad = 3.5 + 2.0 * rs_unif(&rbc);
+        double phi = 2 * M_PI * rs_unif(&rbc);
+        for (int k = 0; k < len && placed_rbc < cfg->n_rbc; k++) {
+            int32_t colq[3];
+            for (int c = 0; c < 3; c++) colq[c] = (RBC[c] + rs_int(&rbc, -8, 8)) * Q;
+            fill_disc_q(&cv, cx, cy, rad, colq);
+            placed_rbc++;
+            double r2 = 3.5 + 2.0 * rs_unif(&rbc);
+            phi += 0.6 * (rs_unif(&rbc) - 0.5);
+            cx += 0.9 * (rad + r2) * cos(phi);
+            cy += 0.9 * (rad + r2) * sin(phi);
+            rad = r2;
         }
     }
 

@@ -17,6 +17,7 @@ typedef struct {
     int n_stroma;         /* discs with colour (200,150,190) +-5 */
     double stroma_rmin, stroma_rmax;
     int corridor;         /* 1: paint a serpentine low-contrast ramp band */
+    int n_rbc;            /* red blood cells: discs with colour (200,60,70) +-8 */
 } synth_cfg;
 
 /* Writes H rows of W*3 bytes (R,G,B interleaved) at `out` with row pitch
