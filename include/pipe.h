@@ -229,6 +229,25 @@ typedef struct {
 } ws_tile;
 int watershed_batch(pipe_t p, const ws_tile* tiles, int n, int h, pipe_stream_t stream);
 
+/* Red blood cell detection (Table I "RBC detection", which the paper lists
+ * with its CPU sources, OpenCV and Vincent's morphological reconstruction,
+ * and no definition).  The definition computed here:
+ *   d = R - max(G, B) per pixel (red dominance, an integer in [-255, 255]);
+ *   marker = d >= t_hi; mask = d >= t_lo;
+ *   out_dev = 1 on the 8-connected components of the mask that hold a
+ *     marker pixel (the binary reconstruction by dilation of the marker
+ *     under the mask), 0 elsewhere.
+ *  rgb_dev: H rows of 3*W bytes (R,G,B) at pitch_bytes >= 3*W; out_dev: a
+ *  W x H uint8 plane, caller-owned, not overlapping the input;
+ *  0 <= t_lo <= t_hi <= 255 (the workload uses 40 and 100).  The pipe owns
+ *  the scratch (a W x H mask plane, one seed flag per 64x64 work tile and a
+ *  work queue), allocated on the first call of a larger size, which
+ *  synchronises `stream`.
+ * Returns PIPE_EINVAL on a bad argument (nothing is launched); otherwise
+ * the work is asynchronous on `stream`. */
+int rbc_tile(pipe_t p, const uint8_t* rgb_dev, int W, int H, size_t pitch_bytes, int t_lo, int t_hi,
+             uint8_t* out_dev, pipe_stream_t stream);
+
 /* Canny edges of a uint8 plane and the per-object edge counts (Sec. V-A
  * lists Canny among the feature-stage transforms applied to the
  * deconvolved image; Sec. II names "edge" among the feature families;

@@ -21,7 +21,7 @@ EXPORTS = ["pipe_default_params", "pipe_create", "pipe_destroy", "seg_tile", "fe
            "seg_features_batch", "batch_submit", "batch_poll", "batch_release", "pipe_serve_memory",
            "pipe_status_read", "pipe_debug_plane",
            "pipe_profile_enable", "pipe_profile_read", "pipe_launch_count", "pipe_recon_visits",
-           "features_tile_noalloc", "pipe_autotune_info", "morph_open_tile", "watershed_tile", "canny_tile",
+           "features_tile_noalloc", "pipe_autotune_info", "morph_open_tile", "watershed_tile", "canny_tile", "rbc_tile",
            "watershed_batch", "sched_create", "sched_destroy", "sched_push", "sched_request", "sched_done",
            "sched_release", "sched_counts", "tile_cost"]
 NOALLOC_MAX_OBJECTS = 65536
@@ -84,6 +84,7 @@ def lib():
     L.morph_open_tile.argtypes = [vp, vp, ci, ci, ci, vp, vp]
     L.watershed_tile.argtypes = [vp, vp, vp, ci, ci, ci, ci, vp, vp, vp]
     L.canny_tile.argtypes = [vp, vp, vp, ci, ci, ci, ci, ci, ci, vp, vp, vp]
+    L.rbc_tile.argtypes = [vp, vp, ci, ci, sz, ci, ci, vp, vp]
     L.watershed_batch.argtypes = [vp, ctypes.POINTER(WsTileC), ci, ci, vp]
     L.sched_create.argtypes = [ci, ci, ctypes.POINTER(vp)]
     L.sched_create.restype = ci
@@ -122,7 +123,7 @@ def lib():
     for n in ("pipe_create", "seg_tile", "features_tile", "seg_features_batch", "batch_submit", "batch_poll",
               "batch_release", "pipe_serve_memory",
               "pipe_status_read", "pipe_debug_plane", "pipe_profile_enable", "pipe_profile_read",
-              "morph_open_tile", "watershed_tile", "canny_tile", "watershed_batch"):
+              "morph_open_tile", "watershed_tile", "canny_tile", "watershed_batch", "rbc_tile"):
         getattr(L, n).restype = ci
     _lib = L
     return L
@@ -302,6 +303,19 @@ class Pipe:
             arr[i].W, arr[i].H, arr[i].n_objects = W, H, int(t["n_objects"])
             arr[i].n_basins = t["n_basins"].data_ptr()
         _check(lib().watershed_batch(self.h, arr, len(tiles), int(h), _stream_ptr(stream)), "watershed_batch")
+
+    def rbc(self, rgb, out, t_lo=40, t_hi=100, stream=None, pitch=None):
+        """Red blood cell mask (Table I "RBC detection") of an (H, W, 3) uint8
+        device tensor into out, a contiguous (H, W) uint8 plane (0/1): the
+        8-connected components of R - max(G, B) >= t_lo holding a pixel with
+        R - max(G, B) >= t_hi."""
+        H, W = rgb.shape[0], rgb.shape[1]
+        if tuple(out.shape) != (H, W) or not out.is_contiguous():
+            raise ValueError("out must be a contiguous (H, W) uint8 plane")
+        pitch = pitch if pitch is not None else rgb.stride(0) * rgb.element_size()
+        rc = lib().rbc_tile(self.h, rgb.data_ptr(), W, H, pitch, int(t_lo), int(t_hi), out.data_ptr(),
+                            _stream_ptr(stream))
+        _check(rc, "rbc_tile")
 
     def canny(self, img, edges, labels=None, n_objects=0, counts=None, low=40, high=120, radius=3, stream=None):
         """Canny edges of a (H, W) uint8 device tensor into edges (uint8 0/1),

@@ -67,6 +67,7 @@ struct Shared {
     int head, err;                      // worklist head; first device-side error
     int processed;                      // tile processings (diagnostic)
     int nobj;                           // object items of a batched feature pass
+    int nseed;                          // work tiles of a seeded reconstruction queued at the start
 };
 
 struct Launch {
@@ -157,6 +158,26 @@ void upload_deconv_tables(const int32_t* lut256, const int32_t* wq3);
 void launch_deconv(const Launch& L, cudaStream_t s, Profiler* pf);
 int recon_grid(int device);
 void launch_recon(const Launch& L, int grid_cap, cudaStream_t s, Profiler* pf);
+// The reconstruction started from a sparse marker: only the work tiles whose
+// flag is set (a marker pixel in the tile or its one-pixel halo) are queued
+// at the start; the others are at a fixed point and wait to be requested.
+// flags: one int per work tile of the launch, set by the kernel that wrote the
+// marker and zeroed by the caller before it; L.sh->nseed must be zeroed too.
+void launch_recon_seeded(const Launch& L, const int* flags, int grid_cap, cudaStream_t s, Profiler* pf);
+
+// Sets the seed flags of a 16-pixel chunk at (x0, y) of an image with rtx x
+// rty work tiles (x0 a multiple of 16, so the chunk lies in one work tile):
+// the tile holding it, and the neighbours whose one-pixel halo holds one of
+// its marker pixels (bit p of m: pixel x0 + p is a marker pixel).
+__device__ __forceinline__ void flag_seed_tiles(int* flags, int rtx, int rty, int x0, int y, unsigned m) {
+    if (!m) return;
+    const int tx = x0 / RT, ty = y / RT, yr = y - ty * RT;
+    const int ylo = (yr == 0 && ty > 0) ? ty - 1 : ty, yhi = (yr == RT - 1 && ty + 1 < rty) ? ty + 1 : ty;
+    const int xlo = ((x0 & (RT - 1)) == 0 && (m & 1u) && tx > 0) ? tx - 1 : tx;
+    const int xhi = (((x0 + 15) & (RT - 1)) == RT - 1 && (m & 0x8000u) && tx + 1 < rtx) ? tx + 1 : tx;
+    for (int yy = ylo; yy <= yhi; yy++)
+        for (int xx = xlo; xx <= xhi; xx++) flags[yy * rtx + xx] = 1;
+}
 void launch_label(const Launch& L, int want_bbox, int max_objects, int sms, cudaStream_t s, Profiler* pf);
 size_t edt_rows_smem(int RB, int Wmax);
 void launch_edt(const Launch& L, int RB, int Wmax, cudaStream_t s, Profiler* pf);
@@ -199,6 +220,11 @@ size_t watershed_scratch_bytes(int W, int H);
 void launch_watershed(const int32_t* labels, const int32_t* edt, int W, int H, int K, int h, int32_t* out,
                       int32_t* n_basins, int4* bbox, int* cnt, int* next, void* scratch, int* status, int sms,
                       cudaStream_t s, cudaStream_t side, cudaEvent_t fork, cudaEvent_t join, Profiler* pf);
+// RBC detection planes: d = R - max(G, B); marker (0/1) = d >= t_hi into
+// marker, mask (0/1) = d >= t_lo into mask, and the seed flags of the work
+// tiles (RT x RT) that the marker pixels touch.
+void launch_rbc_planes(const uint8_t* rgb, size_t pitch, int W, int H, int t_lo, int t_hi, uint8_t* marker,
+                       uint8_t* mask, int* flags, cudaStream_t s, Profiler* pf);
 void launch_unpack_bits(const uint32_t* bits, int W, int H, int cbx, uint8_t* out, cudaStream_t s,
                         Profiler* pf);
 

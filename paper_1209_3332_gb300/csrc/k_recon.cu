@@ -656,6 +656,50 @@ __global__ void __launch_bounds__(32, RECON_MIN_BLOCKS) k_recon(Launch L) {
     if (lane == 0 && visits) atomicAdd(&L.sh->processed, visits);
 }
 
+// ---- seeded start: only the flagged work tiles are queued (any order: the
+// fixed point does not depend on it); the others start idle ------------------------
+__global__ void k_wl_seed(Launch L, const int* __restrict__ flags) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= L.n_rt) return;
+    if (flags[i]) {
+        const int ti = find_tile(L.tiles, L.ntiles, i, &TileDev::rt_base);
+        const unsigned pos = (unsigned)atomicAdd(&L.sh->nseed, 1);
+        L.wl_slots[pos] = ((unsigned long long)(pos + 1) << 32) |
+                          (ITEM_FIRST | ((unsigned)ti << ITEM_BITS) | (unsigned)(i - L.tiles[ti].rt_base));
+        L.wl_state[i] = WL_QUEUED;
+    } else {
+        L.wl_state[i] = WL_IDLE;
+    }
+}
+
+// the slots past the seeds are free for their producer index; the queue
+// counters start at the seeds
+__global__ void k_wl_seed_finish(Launch L) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = L.sh->nseed;
+    if (i == 0) {
+        L.sh->head = 0;
+        L.sh->tp = ((unsigned long long)(unsigned)n << 32) | (unsigned)n;
+        L.sh->err = 0;
+        L.sh->processed = 0;
+    }
+    if (i >= n && i < L.n_rt) L.wl_slots[i] = (unsigned long long)(unsigned)i << 32;
+}
+
+void launch_recon_seeded(const Launch& L, const int* flags, int grid_cap, cudaStream_t s, Profiler* pf) {
+    if (L.n_rt == 0) return;
+    pf->begin("recon_seed", s);
+    k_wl_seed<<<(L.n_rt + 255) / 256, 256, 0, s>>>(L, flags);
+    pf->end("recon_seed", s);
+    pf->begin("recon_seed_finish", s);
+    k_wl_seed_finish<<<(L.n_rt + 255) / 256, 256, 0, s>>>(L);
+    pf->end("recon_seed_finish", s);
+    const int grid = L.n_rt < grid_cap ? L.n_rt : grid_cap;
+    pf->begin("recon", s);
+    k_recon<<<grid, 32, sizeof(WarpTile), s>>>(L);
+    pf->end("recon", s);
+}
+
 // resident workers (one warp each) of the reconstruction kernel
 int recon_grid(int device) {
     int sms = 0, per = 0;

@@ -311,6 +311,9 @@ struct pipe_s {
     DevBuf ws_status;   // watershed_tile: device status word
     DevBuf ws_desc;     // watershed_batch: tile descriptors
     cudaStream_t ws_side = nullptr;        // watershed_tile: large boxes overlap the small ones here
+    LaunchCtx rbc;      // rbc_tile: the reconstruction of the RBC markers runs on this context
+    DevBuf rbc_mask;    // rbc_tile: the mask plane
+    DevBuf rbc_flags;   // rbc_tile: seed flags, one int per work tile
     LaunchCtx canny;    // canny_tile: the hysteresis runs the reconstruction on this context
     DevBuf canny_cand;  // canny_tile: candidate plane (the reconstruction's mask)
     DevBuf canny_obj;   // canny_tile: object boxes
@@ -719,6 +722,9 @@ void pipe_destroy(pipe_t p) {
     p->fbbox.release();
     p->morph_tmp.release();
     p->ws_obj.release();
+    rel(p->rbc);
+    p->rbc_mask.release();
+    p->rbc_flags.release();
     rel(p->canny);
     p->canny_cand.release();
     p->canny_obj.release();
@@ -916,6 +922,50 @@ int watershed_batch(pipe_t p, const ws_tile* tiles, int n, int h, pipe_stream_t 
     return PIPE_OK;
 }
 
+int rbc_tile(pipe_t p, const uint8_t* rgb_dev, int W, int H, size_t pitch_bytes, int t_lo, int t_hi, uint8_t* out_dev,
+             pipe_stream_t stream) {
+    if (!p || !rgb_dev || !out_dev || t_lo < 0 || t_hi < t_lo || t_hi > 255) return PIPE_EINVAL;
+    if (!valid_size(W, H) || pitch_bytes < (size_t)W * 3) return PIPE_EINVAL;
+    const size_t N = (size_t)W * H;
+    const uint8_t* rgb_end = rgb_dev + (size_t)(H - 1) * pitch_bytes + (size_t)W * 3;
+    if (rgb_dev < out_dev + N && out_dev < rgb_end) return PIPE_EINVAL;  // the planes overlap
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaSetDevice(p->device));
+    const int rtx = (W + RT - 1) / RT, rty = (H + RT - 1) / RT, n_rt = rtx * rty;
+    if (p->rbc_mask.n < N || p->rbc_flags.n < sizeof(int) * (size_t)n_rt || p->rbc.wl.n < sizeof(int) * 3 * (size_t)n_rt ||
+        !p->rbc.shared.p) {
+        CK(cudaStreamSynchronize(s));
+        const bool fresh = !p->rbc.shared.p;
+        int rc;
+        if ((rc = p->rbc_mask.ensure(N)) || (rc = p->rbc_flags.ensure(sizeof(int) * (size_t)n_rt)) ||
+            (rc = ensure_ctx(p->rbc, 1, n_rt, 0)))
+            return rc;
+        if (fresh) CK(cudaMemset(p->rbc.shared.p, 0, p->rbc.shared.n));
+    }
+    std::vector<TileDev> td(1);
+    std::memset(&td[0], 0, sizeof(TileDev));
+    td[0].W = W;
+    td[0].H = H;
+    td[0].R = out_dev;
+    td[0].hem8 = (uint8_t*)p->rbc_mask.p;
+    td[0].rtx = rtx;
+    td[0].rty = rty;
+    Launch L = make_launch(p, p->rbc, td, n_rt, 4);
+    int* flags = (int*)p->rbc_flags.p;
+    // 1. red dominance: the marker into out_dev, the mask into the pipe's
+    //    plane, and the work tiles the marker touches
+    CK(cudaMemsetAsync(flags, 0, sizeof(int) * (size_t)n_rt, s));
+    CK(cudaMemsetAsync(&L.sh->nseed, 0, sizeof(int), s));
+    launch_rbc_planes(rgb_dev, pitch_bytes, W, H, t_lo, t_hi, out_dev, (uint8_t*)p->rbc_mask.p, flags, s, &p->prof);
+    // 2. reconstruction by dilation of the marker under the mask, started from
+    //    the flagged work tiles only
+    int rc;
+    if ((rc = upload_desc(L, td, s))) return rc;
+    launch_recon_seeded(L, flags, p->recon_cap, s, &p->prof);
+    CK(cudaGetLastError());
+    return PIPE_OK;
+}
+
 int canny_tile(pipe_t p, const uint8_t* img_dev, const int32_t* labels_dev, int W, int H, int n_objects, int low,
                int high, int radius, uint8_t* edges_dev, int32_t* counts_dev, pipe_stream_t stream) {
     if (!p || !img_dev || !edges_dev || n_objects < 0 || low < 0 || high < low || radius < 0 || radius > 4)
@@ -1061,6 +1111,7 @@ int pipe_status_read(pipe_t p) {
     check(p->plain, 1);
     check(p->batch, p->batch_ntiles);
     check(p->canny, 1);
+    check(p->rbc, 1);
     if (p->ws_status.p) {
         int st = 0;
         if (cudaMemcpy(&st, p->ws_status.p, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return PIPE_ECUDA;
