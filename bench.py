@@ -18,7 +18,7 @@ batch_poll under Poisson arrivals at 80% and at 125% of the batched rate,
 with p50/p99 latency); an end-to-end figure (whole batches submitted from
 pinned host memory through the served API and polled to completion);
 per-kernel CUDA event times; the roofline of the dominant kernel; the steps
-beside the path (opening, watershed, Canny); the other workloads -- the
+beside the path (RBC detection, opening, watershed, Canny); the other workloads -- the
 64-tile mixed batch (batched vs plain), the served pool (2000 Poisson
 requests at 80% of the mixed batch's rate under the 40 GiB budget) and the
 stress stream (4096 worst-case tiles from pinned host memory, against the
@@ -300,19 +300,32 @@ def timed(torch, stream, fn, steps):
     return e0.elapsed_time(e1)
 
 
-# ALU pipe of the GB300: 152 SMs x 4 sub-partitions x 16 integer lanes per clock
-ALU_LANES_PER_CLK = 152 * 4 * 16
 MORPH_R = 9                      # the 19x19 disk of Table I "Morph. Open"
-# SIMD ops per pixel: R 3-input and 2R + 1 2-input ops per pixel pair and pass, two passes
-MORPH_OPS_PER_PX = MORPH_R + 2 * MORPH_R + 1
+# instruction issue of the GB300: 152 SMs x 4 schedulers, one warp instruction each per clock
+ISSUE_PER_CLK = 152 * 4
+
+
+def kernel_instructions(name):
+    """Warp instructions per 4096^2 plane from the committed ncu capture, if
+    the kernel's source is unchanged since the capture (else None)."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            ent = json.load(f)[name]
+        src = os.path.join(ROOT, "paper_1209_3332_gb300", "csrc", ent["source"])
+        if hashlib.sha256(open(src, "rb").read()).hexdigest() != ent["source_sha256"]:
+            return None
+        return float(ent["warp_instructions_per_plane"])
+    except Exception:
+        return None
 
 
 def morph_open_run(torch, pipe, stream, planes, steps, hbm_peak, want_cpu):
     """The opening by the 19x19 disk (Table I "Morph. Open") of every hem8
     plane of the batch through morph_open_tile, timed with CUDA events on the
-    launching stream (planes larger than L2 in all).  The roofline is the ALU
-    pipe: the nested chords take R 3-input and 2R + 1 2-input 16x2-bit SIMD
-    ops per pixel pair and pass."""
+    launching stream (planes larger than L2 in all).  The passes are bound by
+    instruction issue (ncu: issue active 66%, ALU and load/store pipes near
+    55%, DRAM 4%), so the roofline is the SMs' issue rate, against the warp
+    instructions the committed ncu capture counted per plane."""
     outs = [torch.empty_like(p) for p in planes]
 
     def step():
@@ -324,17 +337,21 @@ def morph_open_run(torch, pipe, stream, planes, steps, hbm_peak, want_cpu):
     n = len(planes)
     px = n * planes[0].numel()
     mhz = peaks_clock()
-    alu_peak = ALU_LANES_PER_CLK * mhz * 1e6 / 1e9          # G lane-ops/s
-    alu = MORPH_OPS_PER_PX * px / (ms / 1000.0) / 1e9
     gbs = 2.0 * px / (ms / 1000.0) / 1e9                       # read once, write once
     out = {"radius": MORPH_R, "planes_per_step": n, "plane": list(planes[0].shape), "ms_per_step": ms,
            "planes_per_s": n * 1000.0 / ms,
-           "roofline": {"bound": "alu", "achieved": alu, "peak": alu_peak, "unit": "G lane-op/s",
-                        "frac": alu / alu_peak, "ops_per_px": MORPH_OPS_PER_PX,
-                        "peak_source": "derived: 152 SMs x 4 x 16 ALU lanes x %.0f MHz" % mhz},
            "hbm": {"achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
                    "alg_bytes_per_px": 2},
            "parity": "bit-exact with the oracle (tests/test_gpu_morph.py)"}
+    inst = kernel_instructions("morph_stream")
+    if inst is not None and tuple(planes[0].shape) == (H, W):
+        issue_peak = ISSUE_PER_CLK * mhz * 1e6 / 1e9                  # G warp-instructions/s
+        ach = inst * n / (ms / 1000.0) / 1e9
+        out["roofline"] = {"bound": "issue", "achieved": ach, "peak": issue_peak, "unit": "G warp-inst/s",
+                           "frac": ach / issue_peak, "warp_instructions_per_plane": inst,
+                           "peak_source": "derived: 152 SMs x 4 schedulers x 1 warp instruction per clock x %.0f "
+                                          "MHz; instructions executed from the committed ncu capture "
+                                          "(profiles/k_morph_stream_4096.md)" % mhz}
     if want_cpu:
         import time
         import oracle
@@ -475,6 +492,67 @@ def canny_run(torch, pipe, stream, bufs, steps, hbm_peak, want_cpu):
         out["cpu_oracle"] = {"tiles_per_s": img.size / bufs[0]["hem8"].numel() / sec, "cores": 1,
                              "sample": "the oracle on the first %d rows of tile 0 (%d x %d pixels), %.2f s, scaled"
                                        % (rows, img.shape[0], img.shape[1], sec)}
+    return out
+
+
+RBC_LO, RBC_HI = 40, 100       # red-dominance thresholds of the RBC mask and markers
+RBC_BYTES_PER_PX = 4           # minimal pass: RGB read once, the mask written once
+RBC_TILES, RBC_CELLS = 8, 800  # 4096^2 tiles of the workload with red blood cells painted in
+
+
+def rbc_run(torch, pipe, stream, steps, hbm_peak, want_cpu):
+    """RBC detection (Table I "RBC detection") of 4096^2 workload tiles with
+    red blood cells through rbc_tile, one call per tile, timed with CUDA
+    events on the launching stream (the RGB planes exceed L2); tile 0 is
+    checked against the oracle bit for bit."""
+    import numpy as np
+    import synth
+    dev = torch.device("cuda", torch.cuda.current_device())
+    host = [synth.tile(W, H, 5000 + i, n_nuclei=3000, frac_cluster=0.2, n_stroma=150, n_rbc=RBC_CELLS)
+            for i in range(RBC_TILES)]
+    rgb = [torch.from_numpy(h).to(dev) for h in host]
+    outs = [torch.empty((H, W), dtype=torch.uint8, device=dev) for _ in host]
+
+    def step():
+        for a, b in zip(rgb, outs):
+            pipe.rbc(a, b, RBC_LO, RBC_HI, stream=stream)
+    for _ in range(3):
+        step()
+    ms = timed(torch, stream, step, steps) / steps
+    before = pipe.profile_read()
+    pipe.profile(True)
+    step()
+    torch.cuda.synchronize()
+    after = pipe.profile_read()
+    pipe.profile(False)
+    kern = {}
+    for k, (c, t) in after.items():
+        c0, t0 = before.get(k, (0, 0.0))
+        if c > c0:
+            kern[k] = round((t - t0) / (c - c0), 4)
+    import oracle
+    t0 = time.perf_counter()
+    want = oracle.rbc(host[0], RBC_LO, RBC_HI)
+    cpu_s = time.perf_counter() - t0
+    if not np.array_equal(outs[0].cpu().numpy(), want):
+        raise RuntimeError("rbc_tile differs from the oracle on tile 0")
+    px = RBC_TILES * H * W
+    gbs = RBC_BYTES_PER_PX * px / (ms / 1000.0) / 1e9
+    out = {"t_lo": RBC_LO, "t_hi": RBC_HI, "tiles_per_step": RBC_TILES, "tile": [H, W],
+           "workload": "4096x4096 tiles as the benchmark's, plus %d red blood cells (discs r 3.5-5.5, RGB ~(200,60,70), "
+                       "30%% of draws in clumps of 2-5)" % RBC_CELLS,
+           "ms_per_step": ms, "tiles_per_s": RBC_TILES * 1000.0 / ms,
+           "rbc_px_tile0": int(want.sum()), "kernels_ms": kern,
+           "hbm": {"achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+                   "alg_bytes_per_px": RBC_BYTES_PER_PX, "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"},
+           "parity": "tile 0 equals the oracle bit for bit in this run; tests/test_gpu_rbc.py"}
+    pl = kern.get("rbc_planes")
+    if pl:   # the planes pass alone: RGB read, marker and mask written
+        g = 5.0 * H * W / (pl / 1000.0) / 1e9
+        out["planes_kernel"] = {"achieved": g, "peak": hbm_peak, "unit": "GB/s", "frac": g / hbm_peak,
+                                "alg_bytes_per_px": 5}
+    if want_cpu:
+        out["cpu_oracle"] = {"tiles_per_s": 1.0 / cpu_s, "cores": 1, "sample": "the oracle on tile 0, %.2f s" % cpu_s}
     return out
 
 
@@ -969,6 +1047,9 @@ def run_ours(args, world, rank, local):
     # ---- the feature-stage edge transform: Canny and per-object edge counts --
     line["canny"] = canny_run(torch, pipe, stream, bufs, max(3, args.steps // 2), peak,
                               rank == 0 and world == 1 and not args.no_cpu)
+    # ---- the first step of the segmentation stage: RBC detection -------------
+    line["rbc"] = rbc_run(torch, pipe, stream, max(3, args.steps // 2), peak,
+                          rank == 0 and world == 1 and not args.no_cpu)
     # ---- the other workloads: mixed batch, served pool, worst-case stream ----
     if world == 1 and not args.no_configs:
         line["cfg2"] = cfg2_run(torch, pipe, stream, max(3, args.steps // 2))
