@@ -347,82 +347,107 @@ __device__ __forceinline__ bool merge_halo(WarpTile& S, const uint8_t hr[9], int
 // ---- sweeps -------------------------------------------------------------------------
 // With R <= M everywhere, max(R, min(m, M)) = min(max(R, m), M).
 
-// Down (DIR = 1) or up (DIR = -1) over all RT rows.  P is the pixel pair of
-// the row before (columns 2l, 2l + 1); its outer neighbours come from lanes
-// l - 1 and l + 1 (the edge lanes get their own pair back, harmlessly, and
-// the halo column through E).
-template <int DIR>
-__device__ __forceinline__ void row_sweep(WarpTile& S, int lane) {
+// A row sweep pair: the down sweep (rows 0 -> RT-1) and the up sweep
+// (rows RT-1 -> 0) run at once as two independent chains, one block row of
+// each per step, so the warp always has two dependent chains in flight.
+// Lane l owns block column l in both chains, so every store to a block comes
+// from the one thread that also loads it: in the first half of the steps the
+// chains work on disjoint halves of the tile; at the middle each chain loads
+// its next block row only after the other chain has stored it, and in the
+// second half each chain runs over rows the other has already swept.  Each
+// chain is still one full directional sweep (every row after the line
+// before it), so a round of the two pairs propagates as the four sweeps do,
+// and values only grow towards the unique fixed point whatever the order.
+// P is the pixel pair of the line before (columns 2l, 2l + 1); its outer
+// neighbours come from lanes l - 1 and l + 1 (the edge lanes get their own
+// pair back, harmlessly, and the halo column through E).
+__device__ __forceinline__ uint32_t line_step(uint32_t& P, uint32_t R, uint32_t M, uint32_t e) {
+    const uint32_t L = __shfl_up_sync(FULL, P, 1), Rt = __shfl_down_sync(FULL, P, 1);
+    const uint32_t w = __vimax3_u16x2(__byte_perm(P, L, FROM_LEFT), P, __byte_perm(P, Rt, FROM_RIGHT));
+    P = min2(__vimax3_u16x2(R, w, e), M);
+    return P;
+}
+
+__device__ __forceinline__ void row_sweeps(WarpTile& S, int lane) {
     const uint32_t* E = lane == 0 ? S.HC[0] : lane == 31 ? S.HC[1] : S.Z;
-    uint32_t P = DIR > 0 ? __byte_perm(S.HRow[0][2 * lane + 1], S.HRow[0][2 * lane + 2], LINE0_PAIR)
-                         : __byte_perm(S.HRow[1][2 * lane + 1], S.HRow[1][2 * lane + 2], LINE1_PAIR);
-    auto block_row = [&](uint2 b, int j) {
-        uint32_t n[2];
-#pragma unroll
-        for (int t = 0; t < 2; t++) {
-            const int a = DIR > 0 ? t : 1 - t, y = 2 * j + a;
-            const uint32_t R = __byte_perm(b.x, 0u, a ? ROW1 : ROW0), M = __byte_perm(b.y, 0u, a ? ROW1 : ROW0);
-            const uint32_t L = __shfl_up_sync(FULL, P, 1), Rt = __shfl_down_sync(FULL, P, 1);
-            const uint32_t w = __vimax3_u16x2(__byte_perm(P, L, FROM_LEFT), P, __byte_perm(P, Rt, FROM_RIGHT));
-            P = min2(__vimax3_u16x2(R, w, E[y - DIR + 1]), M);
-            n[a] = P;
-        }
-        S.B[j * BS + lane].x = __byte_perm(n[0], n[1], PACK_ROWS);
+    uint32_t Pd = __byte_perm(S.HRow[0][2 * lane + 1], S.HRow[0][2 * lane + 2], LINE0_PAIR);
+    uint32_t Pu = __byte_perm(S.HRow[1][2 * lane + 1], S.HRow[1][2 * lane + 2], LINE1_PAIR);
+    // down: block row k, rows 2k then 2k + 1; up: block row NB-1-k, rows 2(NB-1-k) + 1 then 2(NB-1-k)
+    auto step = [&](uint2 bd, uint2 bu, int k) {
+        const int jd = k, ju = NB - 1 - k;
+        const uint32_t d0 = line_step(Pd, __byte_perm(bd.x, 0u, ROW0), __byte_perm(bd.y, 0u, ROW0), E[2 * jd]);
+        const uint32_t u1 = line_step(Pu, __byte_perm(bu.x, 0u, ROW1), __byte_perm(bu.y, 0u, ROW1), E[2 * ju + 3]);
+        const uint32_t d1 = line_step(Pd, __byte_perm(bd.x, 0u, ROW1), __byte_perm(bd.y, 0u, ROW1), E[2 * jd + 1]);
+        const uint32_t u0 = line_step(Pu, __byte_perm(bu.x, 0u, ROW0), __byte_perm(bu.y, 0u, ROW0), E[2 * ju + 2]);
+        S.B[jd * BS + lane].x = __byte_perm(d0, d1, PACK_ROWS);
+        S.B[ju * BS + lane].x = __byte_perm(u0, u1, PACK_ROWS);
     };
-    const int j0 = DIR > 0 ? 0 : NB - 1;
-    uint2 b = S.B[j0 * BS + lane];
-#pragma unroll 2
-    for (int k = 0; k < NB - 1; k++) {
-        const int j = j0 + DIR * k;
-        const uint2 nb = S.B[(j + DIR) * BS + lane];  // loaded one block row ahead
-        block_row(b, j);
-        b = nb;
+    uint2 bd = S.B[lane], bu = S.B[(NB - 1) * BS + lane];
+#pragma unroll 1
+    for (int k = 0; k < NB / 2 - 1; k++) {  // first half: disjoint rows, next blocks loaded one step ahead
+        const uint2 nd = S.B[(k + 1) * BS + lane], nu = S.B[(NB - 2 - k) * BS + lane];
+        step(bd, bu, k);
+        bd = nd;
+        bu = nu;
     }
-    block_row(b, j0 + DIR * (NB - 1));
+    step(bd, bu, NB / 2 - 1);
+    // the middle: each chain's next block row is the one the other chain just stored
+    bd = S.B[(NB / 2) * BS + lane];
+    bu = S.B[(NB / 2 - 1) * BS + lane];
+#pragma unroll 1
+    for (int k = NB / 2; k < NB - 1; k++) {
+        const uint2 nd = S.B[(k + 1) * BS + lane], nu = S.B[(NB - 2 - k) * BS + lane];
+        step(bd, bu, k);
+        bd = nd;
+        bu = nu;
+    }
+    step(bd, bu, NB - 1);
 }
 
-// Right (DIR = 1) or left (DIR = -1) over all RT columns; the same with
-// lanes holding rows 2l, 2l + 1 and the halo rows through E.
-template <int DIR>
-__device__ __forceinline__ void col_sweep(WarpTile& S, int lane) {
+// The column sweep pair: right (columns 0 -> RT-1) and left (RT-1 -> 0) at
+// once, lane l owning block row l (rows 2l, 2l + 1) in both chains; the halo
+// rows reach the edge lanes through E.
+__device__ __forceinline__ void col_sweeps(WarpTile& S, int lane) {
     const uint32_t* E = lane == 0 ? S.HRow[0] : lane == 31 ? S.HRow[1] : S.Z;
-    uint32_t C = DIR > 0 ? __byte_perm(S.HC[0][2 * lane + 1], S.HC[0][2 * lane + 2], LINE0_PAIR)
-                         : __byte_perm(S.HC[1][2 * lane + 1], S.HC[1][2 * lane + 2], LINE1_PAIR);
-    auto block_col = [&](uint2 b, int i) {
-        uint32_t n[2];
-#pragma unroll
-        for (int t = 0; t < 2; t++) {
-            const int c = DIR > 0 ? t : 1 - t, x = 2 * i + c;
-            const uint32_t R = __byte_perm(b.x, 0u, c ? COL1 : COL0), M = __byte_perm(b.y, 0u, c ? COL1 : COL0);
-            const uint32_t U = __shfl_up_sync(FULL, C, 1), D = __shfl_down_sync(FULL, C, 1);
-            const uint32_t w = __vimax3_u16x2(__byte_perm(C, U, FROM_LEFT), C, __byte_perm(C, D, FROM_RIGHT));
-            C = min2(__vimax3_u16x2(R, w, E[x - DIR + 1]), M);
-            n[c] = C;
-        }
-        S.B[lane * BS + i].x = __byte_perm(n[0], n[1], PACK_COLS);
+    uint32_t Cr = __byte_perm(S.HC[0][2 * lane + 1], S.HC[0][2 * lane + 2], LINE0_PAIR);
+    uint32_t Cl = __byte_perm(S.HC[1][2 * lane + 1], S.HC[1][2 * lane + 2], LINE1_PAIR);
+    auto step = [&](uint2 br, uint2 bl, int k) {
+        const int ir = k, il = NB - 1 - k;
+        const uint32_t r0 = line_step(Cr, __byte_perm(br.x, 0u, COL0), __byte_perm(br.y, 0u, COL0), E[2 * ir]);
+        const uint32_t l1 = line_step(Cl, __byte_perm(bl.x, 0u, COL1), __byte_perm(bl.y, 0u, COL1), E[2 * il + 3]);
+        const uint32_t r1 = line_step(Cr, __byte_perm(br.x, 0u, COL1), __byte_perm(br.y, 0u, COL1), E[2 * ir + 1]);
+        const uint32_t l0 = line_step(Cl, __byte_perm(bl.x, 0u, COL0), __byte_perm(bl.y, 0u, COL0), E[2 * il + 2]);
+        S.B[lane * BS + ir].x = __byte_perm(r0, r1, PACK_COLS);
+        S.B[lane * BS + il].x = __byte_perm(l0, l1, PACK_COLS);
     };
-    const int i0 = DIR > 0 ? 0 : NB - 1;
-    uint2 b = S.B[lane * BS + i0];
-#pragma unroll 2
-    for (int k = 0; k < NB - 1; k++) {
-        const int i = i0 + DIR * k;
-        const uint2 nb = S.B[lane * BS + i + DIR];
-        block_col(b, i);
-        b = nb;
+    uint2 br = S.B[lane * BS], bl = S.B[lane * BS + NB - 1];
+#pragma unroll 1
+    for (int k = 0; k < NB / 2 - 1; k++) {
+        const uint2 nr = S.B[lane * BS + k + 1], nl = S.B[lane * BS + NB - 2 - k];
+        step(br, bl, k);
+        br = nr;
+        bl = nl;
     }
-    block_col(b, i0 + DIR * (NB - 1));
+    step(br, bl, NB / 2 - 1);
+    br = S.B[lane * BS + NB / 2];
+    bl = S.B[lane * BS + NB / 2 - 1];
+#pragma unroll 1
+    for (int k = NB / 2; k < NB - 1; k++) {
+        const uint2 nr = S.B[lane * BS + k + 1], nl = S.B[lane * BS + NB - 2 - k];
+        step(br, bl, k);
+        br = nr;
+        bl = nl;
+    }
+    step(br, bl, NB - 1);
 }
 
-// One round of the four sweeps over the tile: down, up, right, left.
-// __syncwarp orders each sweep's stores before the next sweep's loads.
+// One round: the row sweep pair, then the column sweep pair.  __syncwarp
+// orders each pair's stores before the next pair's loads (the pairs map
+// lanes to blocks differently).
 __device__ __forceinline__ void sweep_round(WarpTile& S, int lane) {
-    row_sweep<1>(S, lane);
+    row_sweeps(S, lane);
     __syncwarp();
-    row_sweep<-1>(S, lane);
-    __syncwarp();
-    col_sweep<1>(S, lane);
-    __syncwarp();
-    col_sweep<-1>(S, lane);
+    col_sweeps(S, lane);
     __syncwarp();
 }
 
