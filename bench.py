@@ -439,20 +439,33 @@ CANNY_BYTES_PER_PX = 2                        # minimal pass: the plane read onc
 
 def canny_run(torch, pipe, stream, bufs, steps, hbm_peak, want_cpu):
     """Canny edges of every hem8 plane of the batch and the edge counts of
-    its objects (Sec. V-A feature-stage transform, Sec. II edge features)
-    through canny_tile, timed with CUDA events on the launching stream (the
-    planes of the batch are far larger than L2)."""
+    its objects (Sec. V-A feature-stage transform, Sec. II edge features):
+    the batched form (canny_batch: one launch per pass over all tiles) as the
+    figure, one canny_tile call per tile beside it; timed with CUDA events on
+    the launching stream (the planes of the batch are far larger than L2)."""
     ks = [int(b["n_objects"].item()) for b in bufs]
     edges = [torch.empty_like(b["hem8"]) for b in bufs]
     counts = [torch.empty(max(k, 1), dtype=torch.int32, device=b["hem8"].device) for k, b in zip(ks, bufs)]
+    jobs = [dict(img=b["hem8"], edges=edges[i], labels=b["labels"], n_objects=ks[i], counts=counts[i])
+            for i, b in enumerate(bufs)]
 
-    def step():
+    def plain():
         for i, b in enumerate(bufs):
             pipe.canny(b["hem8"], edges[i], labels=b["labels"], n_objects=ks[i], counts=counts[i],
                        low=CANNY_LOW, high=CANNY_HIGH, radius=EDGE_R, stream=stream)
+
+    def step():
+        pipe.canny_batch(jobs, low=CANNY_LOW, high=CANNY_HIGH, radius=EDGE_R, stream=stream)
+    for _ in range(3):
+        plain()
+    plain_ms = timed(torch, stream, plain, steps) / steps
+    ref = [(e.clone(), c.clone()) for e, c in zip(edges, counts)]
     for _ in range(3):
         step()
     ms = timed(torch, stream, step, steps) / steps
+    for (e0, c0), e, c in zip(ref, edges, counts):
+        if not torch.equal(e0, e) or not torch.equal(c0, c):
+            raise RuntimeError("canny_batch differs from canny_tile")
     before = pipe.profile_read()
     pipe.profile(True)
     step()
@@ -466,19 +479,26 @@ def canny_run(torch, pipe, stream, bufs, steps, hbm_peak, want_cpu):
             kern[k] = round((t - t0) / (c - c0), 4)
     n = len(bufs)
     px = sum(b["hem8"].numel() for b in bufs)
-    nms_ms = kern.get("canny_nms", 0.0)
     out = {"low": CANNY_LOW, "high": CANNY_HIGH, "radius": EDGE_R, "tiles_per_step": n,
+           "form": "batched (canny_batch: one launch per pass over all tiles)",
            "tile": list(bufs[0]["hem8"].shape), "ms_per_step": ms, "tiles_per_s": n * 1000.0 / ms,
+           "plain": {"form": "canny_tile per tile", "ms_per_step": plain_ms, "tiles_per_s": n * 1000.0 / plain_ms},
            "edge_px_per_step": int(sum(int(e.sum().item()) for e in edges)), "kernels_ms": kern,
            "hbm": {"achieved": CANNY_BYTES_PER_PX * px / (ms / 1000.0) / 1e9, "peak": hbm_peak, "unit": "GB/s",
                    "alg_bytes_per_px": CANNY_BYTES_PER_PX,
                    "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"},
-           "parity": "bit-exact with the oracle (tests/test_gpu_canny.py)"}
+           "parity": "batched == plain bit for bit in this run; bit-exact with the oracle (tests/test_gpu_canny.py)"}
     out["hbm"]["frac"] = out["hbm"]["achieved"] / hbm_peak
-    if nms_ms > 0:  # the stencil pass alone: the plane read once, strong and candidate planes written
-        gbs = 3.0 * bufs[0]["hem8"].numel() / (nms_ms / 1000.0) / 1e9
+    nms_ms = kern.get("canny_nms", 0.0)
+    if nms_ms > 0:  # the stencil pass alone: the planes read once, strong and candidate planes written
+        gbs = 3.0 * px / (nms_ms / 1000.0) / 1e9
         out["nms_kernel"] = {"achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
                              "alg_bytes_per_px": 3}
+    cnt_ms = kern.get("canny_counts", 0.0)
+    if cnt_ms > 0:  # the counts pass alone: edges and labels read once
+        gbs = 5.0 * px / (cnt_ms / 1000.0) / 1e9
+        out["counts_kernel"] = {"achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+                                "alg_bytes_per_px": 5}
     if want_cpu:
         import time
         import oracle

@@ -269,13 +269,35 @@ int rbc_tile(pipe_t p, const uint8_t* rgb_dev, int W, int H, size_t pitch_bytes,
  *  img_dev, edges_dev: W x H uint8 planes, caller-owned, not overlapping;
  *  labels_dev: W x H int32 (may be NULL when n_objects = 0); counts_dev:
  *  n_objects int32.  0 <= low <= high; 0 <= radius <= 4.  The hysteresis
- *  runs the segmentation's reconstruction kernel on pipe-owned scratch (a
- *  W x H candidate plane and a work queue), allocated on the first call of
- *  a larger size, which synchronises `stream`.
+ *  runs the segmentation's reconstruction kernel, started from the 64x64
+ *  work tiles that hold a strong pixel, on pipe-owned scratch (a W x H
+ *  candidate plane, one seed flag per work tile and a work queue), allocated
+ *  on the first call of a larger size, which synchronises `stream`.
  * Returns PIPE_EINVAL on a bad argument (nothing is launched); otherwise
  * the work is asynchronous on `stream`. */
 int canny_tile(pipe_t p, const uint8_t* img_dev, const int32_t* labels_dev, int W, int H, int n_objects, int low,
                int high, int radius, uint8_t* edges_dev, int32_t* counts_dev, pipe_stream_t stream);
+
+/* Batched form of canny_tile: the edges and edge counts of n tiles of any
+ * sizes in one launch per pass (one suppression launch over all tiles, one
+ * reconstruction queue for every tile's hysteresis, one counts launch), so
+ * that many tiles share the GPU.  Results are identical to canny_tile on
+ * each tile alone.
+ *  tiles[i]: img (W x H uint8), edges (W x H uint8, not overlapping img),
+ *    labels (W x H int32; may be NULL when n_objects = 0), n_objects (host
+ *    int), counts (n_objects int32); 1 <= n <= 4096; low, high, radius as
+ *    for canny_tile.  The pipe's scratch covers all tiles at once (a
+ *    candidate byte per pixel, a seed flag per work tile, the queue),
+ *    allocated on the first call of a larger size, which synchronises
+ *    `stream`.
+ * Returns PIPE_EINVAL on a bad argument (nothing is launched); otherwise
+ * the work is asynchronous on `stream`. */
+typedef struct {
+    const uint8_t* img; const int32_t* labels; int W, H;
+    int n_objects;
+    uint8_t* edges; int32_t* counts;
+} edge_tile;
+int canny_batch(pipe_t p, const edge_tile* tiles, int n, int low, int high, int radius, pipe_stream_t stream);
 
 /* Served form (Sec. IV-D prefetching and asynchronous copy): tiles in host
  * memory are admitted as slots and HBM budget allow, uploaded on copy

@@ -22,7 +22,7 @@ EXPORTS = ["pipe_default_params", "pipe_create", "pipe_destroy", "seg_tile", "fe
            "pipe_status_read", "pipe_debug_plane",
            "pipe_profile_enable", "pipe_profile_read", "pipe_launch_count", "pipe_recon_visits",
            "features_tile_noalloc", "pipe_autotune_info", "morph_open_tile", "watershed_tile", "canny_tile", "rbc_tile",
-           "watershed_batch", "sched_create", "sched_destroy", "sched_push", "sched_request", "sched_done",
+           "watershed_batch", "canny_batch", "sched_create", "sched_destroy", "sched_push", "sched_request", "sched_done",
            "sched_release", "sched_counts", "tile_cost"]
 NOALLOC_MAX_OBJECTS = 65536
 
@@ -85,6 +85,7 @@ def lib():
     L.watershed_tile.argtypes = [vp, vp, vp, ci, ci, ci, ci, vp, vp, vp]
     L.canny_tile.argtypes = [vp, vp, vp, ci, ci, ci, ci, ci, ci, vp, vp, vp]
     L.rbc_tile.argtypes = [vp, vp, ci, ci, sz, ci, ci, vp, vp]
+    L.canny_batch.argtypes = [vp, ctypes.POINTER(EdgeTileC), ci, ci, ci, ci, vp]
     L.watershed_batch.argtypes = [vp, ctypes.POINTER(WsTileC), ci, ci, vp]
     L.sched_create.argtypes = [ci, ci, ctypes.POINTER(vp)]
     L.sched_create.restype = ci
@@ -123,7 +124,7 @@ def lib():
     for n in ("pipe_create", "seg_tile", "features_tile", "seg_features_batch", "batch_submit", "batch_poll",
               "batch_release", "pipe_serve_memory",
               "pipe_status_read", "pipe_debug_plane", "pipe_profile_enable", "pipe_profile_read",
-              "morph_open_tile", "watershed_tile", "canny_tile", "watershed_batch", "rbc_tile"):
+              "morph_open_tile", "watershed_tile", "canny_tile", "watershed_batch", "rbc_tile", "canny_batch"):
         getattr(L, n).restype = ci
     _lib = L
     return L
@@ -217,6 +218,11 @@ class Sched:
             self.close()
         except Exception:
             pass
+
+
+class EdgeTileC(ctypes.Structure):
+    _fields_ = [("img", ctypes.c_void_p), ("labels", ctypes.c_void_p), ("W", ctypes.c_int), ("H", ctypes.c_int),
+                ("n_objects", ctypes.c_int), ("edges", ctypes.c_void_p), ("counts", ctypes.c_void_p)]
 
 
 class WsTileC(ctypes.Structure):
@@ -330,6 +336,25 @@ class Pipe:
                               int(n_objects), int(low), int(high), int(radius), edges.data_ptr(),
                               counts.data_ptr() if counts is not None else None, _stream_ptr(stream))
         _check(rc, "canny_tile")
+
+    def canny_batch(self, tiles, low=40, high=120, radius=3, stream=None):
+        """tiles: list of dicts with img and edges (contiguous (H, W) uint8
+        device tensors) and, optionally, labels ((H, W) int32), n_objects
+        (int) and counts (int32 [n_objects])."""
+        arr = (EdgeTileC * len(tiles))()
+        for i, t in enumerate(tiles):
+            H, W = t["img"].shape
+            if tuple(t["edges"].shape) != (H, W) or not t["img"].is_contiguous() or not t["edges"].is_contiguous():
+                raise ValueError("img and edges must be contiguous (H, W) uint8 planes")
+            lab = t.get("labels")
+            if lab is not None and (tuple(lab.shape) != (H, W) or not lab.is_contiguous()):
+                raise ValueError("labels must be a contiguous (H, W) int32 plane")
+            arr[i].img, arr[i].edges = t["img"].data_ptr(), t["edges"].data_ptr()
+            arr[i].labels = lab.data_ptr() if lab is not None else None
+            arr[i].W, arr[i].H, arr[i].n_objects = W, H, int(t.get("n_objects", 0))
+            arr[i].counts = t["counts"].data_ptr() if t.get("counts") is not None else None
+        _check(lib().canny_batch(self.h, arr, len(tiles), int(low), int(high), int(radius), _stream_ptr(stream)),
+               "canny_batch")
 
     # ---- batched form ---------------------------------------------------
     def seg_features_batch(self, tiles, stream=None):

@@ -169,6 +169,19 @@ void launch_recon_seeded(const Launch& L, const int* flags, int grid_cap, cudaSt
 // rty work tiles (x0 a multiple of 16, so the chunk lies in one work tile):
 // the tile holding it, and the neighbours whose one-pixel halo holds one of
 // its marker pixels (bit p of m: pixel x0 + p is a marker pixel).
+// The work tiles (RT x RT, rtx x rty of them) whose tile or one-pixel halo
+// holds pixel (x, y), as bits of a 3 x 3 neighbourhood: bit (dy + 1) * 3 +
+// (dx + 1) for the tile at offset (dx, dy) from the pixel's own.
+__device__ __forceinline__ unsigned seed_bits_px(int rtx, int rty, int x, int y) {
+    const int tx = x / RT, ty = y / RT, xr = x - tx * RT, yr = y - ty * RT;
+    const int dxl = (xr == 0 && tx > 0) ? -1 : 0, dxh = (xr == RT - 1 && tx + 1 < rtx) ? 1 : 0;
+    const int dyl = (yr == 0 && ty > 0) ? -1 : 0, dyh = (yr == RT - 1 && ty + 1 < rty) ? 1 : 0;
+    unsigned m = 0;
+    for (int dy = dyl; dy <= dyh; dy++)
+        for (int dx = dxl; dx <= dxh; dx++) m |= 1u << ((dy + 1) * 3 + dx + 1);
+    return m;
+}
+
 __device__ __forceinline__ void flag_seed_tiles(int* flags, int rtx, int rty, int x0, int y, unsigned m) {
     if (!m) return;
     const int tx = x0 / RT, ty = y / RT, yr = y - ty * RT;
@@ -190,12 +203,31 @@ void launch_features_plain(const uint8_t* hem8, const int32_t* labels, int W, in
 void launch_features_batched(const Launch& L, int grid, cudaStream_t s, Profiler* pf);
 // per object 1..K of a label plane: its box (xmin, ymin, xmax, ymax); empty (xmax < xmin) if absent
 void launch_object_boxes(const int32_t* labels, int W, int H, int K, int4* bbox, cudaStream_t s, Profiler* pf);
-// Canny: strong pixels (0/1) into strong, candidates (0/1) into cand
-void launch_canny_nms(const uint8_t* img, int W, int H, int low, int high, uint8_t* strong, uint8_t* cand,
+// One tile of a Canny launch (plain: one tile; batched: many).
+struct CannyDesc {
+    const uint8_t* img;      // W x H plane
+    const int32_t* labels;   // W x H labels (may be null when K == 0)
+    uint8_t* edges;          // strong pixels (0/1), grown into the edge map by the hysteresis
+    uint8_t* cand;           // candidates (0/1): the hysteresis mask
+    int32_t* counts;         // K edge counts
+    int W, H, K;
+    int bx;                  // 32-pixel blocks per row
+    int blk_base;            // first 32x32 block of this tile in the launch
+    int rt_base;             // first work tile of this tile in the reconstruction launch
+};
+// Blocks of a tile in the Canny launches (32 x 32 pixels each).
+int canny_blocks(int W, int H);
+void upload_canny_descs(CannyDesc* dst, const std::vector<CannyDesc>& v, cudaStream_t s);
+// descs: host copy; d_descs: device array of the same length.  Zeroes the
+// counts, writes strong pixels into edges and candidates into cand, and sets
+// the seed flags (indexed by rt_base + work tile) of the work tiles the
+// strong pixels touch.
+void launch_canny_nms(const std::vector<CannyDesc>& descs, CannyDesc* d_descs, int low, int high, int* flags,
                       cudaStream_t s, Profiler* pf);
-// per object: edge pixels within its disk dilation of radius r (boxes into bbox)
-void launch_canny_counts(const uint8_t* edges, const int32_t* labels, int W, int H, int K, int r, int4* bbox,
-                         int32_t* counts, int sms, cudaStream_t s, Profiler* pf);
+// Edge counts of every tile: each edge pixel adds one to every object 1..K
+// with a pixel within its disk of radius r (the disk dilation of the object).
+void launch_canny_counts(const std::vector<CannyDesc>& descs, CannyDesc* d_descs, int r, cudaStream_t s,
+                         Profiler* pf);
 // One tile of a batched watershed split.
 struct WsDesc {
     const int32_t* labels;

@@ -315,8 +315,9 @@ struct pipe_s {
     DevBuf rbc_mask;    // rbc_tile: the mask plane
     DevBuf rbc_flags;   // rbc_tile: seed flags, one int per work tile
     LaunchCtx canny;    // canny_tile: the hysteresis runs the reconstruction on this context
-    DevBuf canny_cand;  // canny_tile: candidate plane (the reconstruction's mask)
-    DevBuf canny_obj;   // canny_tile: object boxes
+    DevBuf canny_cand;  // canny_tile / canny_batch: candidate planes (the reconstruction's masks)
+    DevBuf canny_flags; // canny_tile / canny_batch: seed flags, one int per work tile
+    DevBuf canny_desc;  // canny_tile / canny_batch: tile descriptors
     cudaEvent_t ws_fork = nullptr, ws_join = nullptr;
     // batched form
     LaunchCtx batch;
@@ -727,7 +728,8 @@ void pipe_destroy(pipe_t p) {
     p->rbc_flags.release();
     rel(p->canny);
     p->canny_cand.release();
-    p->canny_obj.release();
+    p->canny_flags.release();
+    p->canny_desc.release();
     p->ws_scratch.release();
     p->ws_status.release();
     p->ws_desc.release();
@@ -966,49 +968,102 @@ int rbc_tile(pipe_t p, const uint8_t* rgb_dev, int W, int H, size_t pitch_bytes,
     return PIPE_OK;
 }
 
-int canny_tile(pipe_t p, const uint8_t* img_dev, const int32_t* labels_dev, int W, int H, int n_objects, int low,
-               int high, int radius, uint8_t* edges_dev, int32_t* counts_dev, pipe_stream_t stream) {
-    if (!p || !img_dev || !edges_dev || n_objects < 0 || low < 0 || high < low || radius < 0 || radius > 4)
-        return PIPE_EINVAL;
-    if (n_objects > 0 && (!labels_dev || !counts_dev)) return PIPE_EINVAL;
-    if (!valid_size(W, H)) return PIPE_EINVAL;
-    const size_t N = (size_t)W * H;
-    if (img_dev < edges_dev + N && edges_dev < img_dev + N) return PIPE_EINVAL;  // the planes overlap
-    cudaStream_t s = (cudaStream_t)stream;
-    CK(cudaSetDevice(p->device));
-    const int rtx = (W + RT - 1) / RT, rty = (H + RT - 1) / RT, n_rt = rtx * rty;
-    const size_t need_obj = (size_t)std::max(n_objects, 1) * sizeof(int4);
-    if (p->canny_cand.n < N || p->canny_obj.n < need_obj || p->canny.wl.n < sizeof(int) * 3 * (size_t)n_rt ||
+namespace {
+
+// Canny of n tiles: one NMS launch over all of them, one reconstruction
+// queue for every tile's hysteresis (seeded from the work tiles that hold a
+// strong pixel), one counts launch.  Arguments already checked.
+int canny_run(pipe_t p, const edge_tile* tiles, int n, int low, int high, int radius, cudaStream_t s) {
+    size_t cand_bytes = 0;
+    int n_rt = 0;
+    for (int i = 0; i < n; i++) {
+        cand_bytes += al256((size_t)tiles[i].W * tiles[i].H);
+        n_rt += ((tiles[i].W + RT - 1) / RT) * ((tiles[i].H + RT - 1) / RT);
+    }
+    const size_t desc_bytes = sizeof(CannyDesc) * (size_t)n, flag_bytes = sizeof(int) * (size_t)n_rt;
+    if (p->canny_cand.n < cand_bytes || p->canny_flags.n < flag_bytes || p->canny_desc.n < desc_bytes ||
+        p->canny.wl.n < wl_bytes(n_rt) || p->canny.tiles.n < tiles_bytes(n) || p->canny.shared.n < shared_bytes(n) ||
         !p->canny.shared.p) {
         CK(cudaStreamSynchronize(s));
-        const bool fresh = !p->canny.shared.p;
         int rc;
-        if ((rc = p->canny_cand.ensure(N)) || (rc = p->canny_obj.ensure(need_obj)) ||
-            (rc = ensure_ctx(p->canny, 1, n_rt, 0)))
+        if ((rc = p->canny_cand.ensure(cand_bytes)) || (rc = p->canny_flags.ensure(flag_bytes)) ||
+            (rc = p->canny_desc.ensure(desc_bytes)) || (rc = ensure_ctx(p->canny, n, n_rt, 0)))
             return rc;
-        if (fresh) CK(cudaMemset(p->canny.shared.p, 0, p->canny.shared.n));
+        CK(cudaMemset(p->canny.shared.p, 0, p->canny.shared.n));
     }
-    uint8_t* cand = (uint8_t*)p->canny_cand.p;
-    // 1. gradient and non-maximum suppression: strong pixels into edges_dev, candidates into cand
-    launch_canny_nms(img_dev, W, H, low, high, edges_dev, cand, s, &p->prof);
+    std::vector<CannyDesc> cd(n);
+    std::vector<TileDev> td(n);
+    char* cand = (char*)p->canny_cand.p;
+    int blk = 0, rt = 0;
+    for (int i = 0; i < n; i++) {
+        const edge_tile& t = tiles[i];
+        CannyDesc& c = cd[i];
+        c.img = t.img;
+        c.labels = t.labels;
+        c.edges = t.edges;
+        c.cand = (uint8_t*)cand;
+        c.counts = t.counts;
+        c.W = t.W;
+        c.H = t.H;
+        c.K = t.n_objects;
+        c.bx = (t.W + 31) / 32;
+        c.blk_base = blk;
+        c.rt_base = rt;
+        blk += canny_blocks(t.W, t.H);
+        cand += al256((size_t)t.W * t.H);
+        TileDev& d = td[i];
+        std::memset(&d, 0, sizeof(TileDev));
+        d.W = t.W;
+        d.H = t.H;
+        d.R = t.edges;
+        d.hem8 = c.cand;
+        d.rtx = (t.W + RT - 1) / RT;
+        d.rty = (t.H + RT - 1) / RT;
+        rt += d.rtx * d.rty;
+    }
+    CannyDesc* dcd = (CannyDesc*)p->canny_desc.p;
+    int* flags = (int*)p->canny_flags.p;
+    Launch L = make_launch(p, p->canny, td, n_rt, 4);  // rt_base in the same order as above
+    upload_canny_descs(dcd, cd, s);
+    CK(cudaMemsetAsync(flags, 0, flag_bytes, s));
+    CK(cudaMemsetAsync(&L.sh->nseed, 0, sizeof(int), s));
+    // 1. gradient and non-maximum suppression: strong pixels into the edge
+    //    planes, candidates into the pipe's planes, counts zeroed, seed flags
+    launch_canny_nms(cd, dcd, low, high, flags, s, &p->prof);
     // 2. hysteresis: reconstruction by dilation of the strong pixels under the candidates
-    std::vector<TileDev> td(1);
-    std::memset(&td[0], 0, sizeof(TileDev));
-    td[0].W = W;
-    td[0].H = H;
-    td[0].R = edges_dev;
-    td[0].hem8 = cand;
-    td[0].rtx = rtx;
-    td[0].rty = rty;
-    Launch L = make_launch(p, p->canny, td, n_rt, 4);
     int rc;
     if ((rc = upload_desc(L, td, s))) return rc;
-    launch_recon(L, p->recon_cap, s, &p->prof);
+    launch_recon_seeded(L, flags, p->recon_cap, s, &p->prof);
     // 3. edge pixels within each object's disk dilation
-    launch_canny_counts(edges_dev, labels_dev, W, H, n_objects, radius, (int4*)p->canny_obj.p, counts_dev, p->sms, s,
-                        &p->prof);
+    launch_canny_counts(cd, dcd, radius, s, &p->prof);
     CK(cudaGetLastError());
     return PIPE_OK;
+}
+
+bool canny_args_ok(const edge_tile& t) {
+    if (!t.img || !t.edges || t.n_objects < 0 || !valid_size(t.W, t.H)) return false;
+    if (t.n_objects > 0 && (!t.labels || !t.counts)) return false;
+    const size_t N = (size_t)t.W * t.H;
+    return !(t.img < t.edges + N && t.edges < t.img + N);  // the planes must not overlap
+}
+
+}  // namespace
+
+int canny_tile(pipe_t p, const uint8_t* img_dev, const int32_t* labels_dev, int W, int H, int n_objects, int low,
+               int high, int radius, uint8_t* edges_dev, int32_t* counts_dev, pipe_stream_t stream) {
+    if (!p || low < 0 || high < low || radius < 0 || radius > 4) return PIPE_EINVAL;
+    edge_tile t{img_dev, labels_dev, W, H, n_objects, edges_dev, counts_dev};
+    if (!canny_args_ok(t)) return PIPE_EINVAL;
+    CK(cudaSetDevice(p->device));
+    return canny_run(p, &t, 1, low, high, radius, (cudaStream_t)stream);
+}
+
+int canny_batch(pipe_t p, const edge_tile* tiles, int n, int low, int high, int radius, pipe_stream_t stream) {
+    if (!p || !tiles || n < 1 || n > 4096 || low < 0 || high < low || radius < 0 || radius > 4) return PIPE_EINVAL;
+    for (int i = 0; i < n; i++)
+        if (!canny_args_ok(tiles[i])) return PIPE_EINVAL;
+    CK(cudaSetDevice(p->device));
+    return canny_run(p, tiles, n, low, high, radius, (cudaStream_t)stream);
 }
 
 int seg_features_batch(pipe_t p, const tile_dev* tiles, int n, pipe_stream_t stream) {
