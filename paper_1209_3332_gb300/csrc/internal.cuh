@@ -212,11 +212,13 @@ struct CannyDesc {
     int32_t* counts;         // K edge counts
     int W, H, K;
     int bx;                  // 32-pixel blocks per row
-    int blk_base;            // first 32x32 block of this tile in the launch
+    int blk_base;            // first 32x32 block of this tile in the counts launch
+    int nms_base;            // first warp of this tile in the suppression launch
     int rt_base;             // first work tile of this tile in the reconstruction launch
 };
 // Blocks of a tile in the Canny launches (32 x 32 pixels each).
 int canny_blocks(int W, int H);
+int canny_nms_warps(int W, int H);
 void upload_canny_descs(CannyDesc* dst, const std::vector<CannyDesc>& v, cudaStream_t s);
 // descs: host copy; d_descs: device array of the same length.  Zeroes the
 // counts, writes strong pixels into edges and candidates into cand, and sets

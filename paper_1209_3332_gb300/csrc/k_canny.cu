@@ -27,126 +27,242 @@
 
 namespace nucseg {
 
-constexpr int CT = 32;                 // output tile of one CTA: CT x CT pixels
-constexpr int CT_THREADS = 256;
-constexpr int CT_S = CT + 4;           // staged plane, 2-px halo
-constexpr int CT_M = CT + 2;           // magnitudes, 1-px halo
+constexpr int CT = 32;                 // block of the counts pass: CT x CT pixels
 
-__device__ __forceinline__ int find_block_tile(const CannyDesc* __restrict__ D, int n, int b) {
+// the tile of launch item b, by binary search over the tiles' first items
+__device__ __forceinline__ int find_desc(const CannyDesc* __restrict__ D, int n, int b, int CannyDesc::*base) {
     int lo = 0, hi = n - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        if (D[mid].blk_base <= b) lo = mid; else hi = mid - 1;
+        if (D[mid].*base <= b) lo = mid; else hi = mid - 1;
     }
     return lo;
 }
 
-__global__ void __launch_bounds__(CT_THREADS) k_canny_nms(const CannyDesc* __restrict__ D, int n, int low, int high,
-                                                          int* __restrict__ flags) {
-    __shared__ uint8_t si[CT_S][CT_S + 4];
-    __shared__ int16_t sm[CT_M][CT_M + 2];
-    __shared__ unsigned seeds;
-    const int t = threadIdx.x;
-    const CannyDesc& d = D[find_block_tile(D, n, blockIdx.x)];
+// ---- suppression: one warp streams a strip of 128 columns (4 per lane) down
+// a segment of 64 rows (one work-tile row), keeping the last three image rows,
+// the magnitudes of the last three rows and the Sobel pair of the current row
+// in registers ------------------------------------------------------------------
+constexpr int NS_COLS = 128, NS_ROWS = 64;
+constexpr int NS_WARPS = 4;          // warps per CTA
+
+struct Row8 {                        // image row, columns cx0 - 2 .. cx0 + 5 (replicated border)
+    int v[8];
+};
+
+// the global reads of one row for one lane: its own 4 pixels, and on the
+// strip's edge lanes the two pixels beyond the strip
+struct RowFetch {
+    uint32_t w;
+    int e0, e1;
+};
+
+__device__ __forceinline__ RowFetch ns_fetch(const uint8_t* __restrict__ I, int W, int H, int y, int cx0, bool vec,
+                                             int lane) {
+    const uint8_t* row = I + (size_t)min(max(y, 0), H - 1) * W;
+    RowFetch f;
+    if (vec && cx0 < W) {
+        f.w = __ldg(reinterpret_cast<const uint32_t*>(row + cx0));
+    } else {
+        f.w = 0;
+#pragma unroll
+        for (int k = 3; k >= 0; k--) f.w = (f.w << 8) | __ldg(row + min(cx0 + k, W - 1));
+    }
+    f.e0 = f.e1 = 0;
+    if (lane == 0) {
+        f.e0 = __ldg(row + max(cx0 - 2, 0));
+        f.e1 = __ldg(row + max(cx0 - 1, 0));
+    } else if (lane == 31) {
+        f.e0 = __ldg(row + min(cx0 + 4, W - 1));
+        f.e1 = __ldg(row + min(cx0 + 5, W - 1));
+    }
+    return f;
+}
+
+// columns cx0 - 2 .. cx0 + 5 of a fetched row: the neighbours' pixels by shuffle
+__device__ __forceinline__ Row8 ns_row(const RowFetch& f, int lane) {
+    const uint32_t wl = __shfl_up_sync(0xffffffffu, f.w, 1), wr = __shfl_down_sync(0xffffffffu, f.w, 1);
+    Row8 r;
+#pragma unroll
+    for (int k = 0; k < 4; k++) r.v[2 + k] = (int)((f.w >> (8 * k)) & 0xffu);
+    r.v[0] = lane == 0 ? f.e0 : (int)((wl >> 16) & 0xffu);
+    r.v[1] = lane == 0 ? f.e1 : (int)(wl >> 24);
+    r.v[6] = lane == 31 ? f.e0 : (int)(wr & 0xffu);
+    r.v[7] = lane == 31 ? f.e1 : (int)((wr >> 8) & 0xffu);
+    return r;
+}
+
+__device__ __forceinline__ Row8 ns_load_row(const uint8_t* __restrict__ I, int W, int H, int y, int cx0, bool vec,
+                                            int lane) {
+    return ns_row(ns_fetch(I, W, H, y, cx0, vec, lane), lane);
+}
+
+struct Sob6 {                        // columns cx0 - 1 .. cx0 + 4 of one row
+    int sx[6], sy[6], m[6];
+};
+
+// Sobel of the row between A and C (rows r - 1, r, r + 1, replicated); m is 0
+// for columns off the image, or for every column when the row is off it
+__device__ __forceinline__ Sob6 ns_sobel(const Row8& A, const Row8& B, const Row8& C, int cx0, int W, bool row_in) {
+    int vs[8], vd[8];
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+        vs[k] = A.v[k] + 2 * B.v[k] + C.v[k];
+        vd[k] = C.v[k] - A.v[k];
+    }
+    Sob6 o;
+#pragma unroll
+    for (int j = 0; j < 6; j++) {
+        o.sx[j] = vs[j + 2] - vs[j];
+        o.sy[j] = vd[j] + 2 * vd[j + 1] + vd[j + 2];
+        const int x = cx0 - 1 + j;
+        o.m[j] = (row_in && x >= 0 && x < W) ? abs(o.sx[j]) + abs(o.sy[j]) : 0;
+    }
+    return o;
+}
+
+__global__ void __launch_bounds__(32 * NS_WARPS, 4) k_canny_nms(const CannyDesc* __restrict__ D, int n, int n_warps,
+                                                            int low, int high, int* __restrict__ flags) {
+    const int lane = threadIdx.x & 31;
+    const int gw = blockIdx.x * NS_WARPS + (threadIdx.x >> 5);
+    if (gw >= n_warps) return;
+    const CannyDesc& d = D[find_desc(D, n, gw, &CannyDesc::nms_base)];
     const uint8_t* __restrict__ I = d.img;
-    const int W = d.W, H = d.H, bl = blockIdx.x - d.blk_base;
-    const int by = bl / d.bx, x0 = (bl - by * d.bx) * CT, y0 = by * CT;
-    if (t == 0) seeds = 0u;
-    // this block's share of the counts to zero (strided over the tile's blocks)
-    const int nblk = d.bx * ((H + CT - 1) / CT);
-    for (long long i = (long long)bl * CT_THREADS + t; i < d.K; i += (long long)nblk * CT_THREADS) d.counts[i] = 0;
-    for (int i = t; i < CT_S * CT_S; i += CT_THREADS) {  // replicated border: clamped coordinates
-        const int ly = i / CT_S, lx = i - ly * CT_S;
-        const int gy = min(max(y0 - 2 + ly, 0), H - 1), gx = min(max(x0 - 2 + lx, 0), W - 1);
-        si[ly][lx] = I[(size_t)gy * W + gx];
-    }
-    __syncthreads();
-    for (int i = t; i < CT_M * CT_M; i += CT_THREADS) {  // m at (y0 - 1 + ly, x0 - 1 + lx); 0 off the image
-        const int ly = i / CT_M, lx = i - ly * CT_M;
-        const int gy = y0 - 1 + ly, gx = x0 - 1 + lx;
-        int m = 0;
-        if ((unsigned)gy < (unsigned)H && (unsigned)gx < (unsigned)W) {
-            const int a = si[ly][lx], b = si[ly][lx + 1], c = si[ly][lx + 2];
-            const int e = si[ly + 1][lx], f = si[ly + 1][lx + 2];
-            const int g = si[ly + 2][lx], hh = si[ly + 2][lx + 1], k = si[ly + 2][lx + 2];
-            const int sx = (c + 2 * f + k) - (a + 2 * e + g);
-            const int sy = (g + 2 * hh + k) - (a + 2 * b + c);
-            m = abs(sx) + abs(sy);
-        }
-        sm[ly][lx] = (int16_t)m;
-    }
-    __syncthreads();
+    const int W = d.W, H = d.H, wi = gw - d.nms_base;
+    const int strips = (W + NS_COLS - 1) / NS_COLS, nw = strips * ((H + NS_ROWS - 1) / NS_ROWS);
+    const int seg = wi / strips, strip = wi - seg * strips;
+    const int cx0 = strip * NS_COLS + 4 * lane, ya = seg * NS_ROWS, yb = min(ya + NS_ROWS, H);
+    // this warp's share of the counts to zero
+    for (long long i = (long long)wi * 32 + lane; i < d.K; i += (long long)nw * 32) d.counts[i] = 0;
+    const bool vec = (W & 3) == 0 && (reinterpret_cast<uintptr_t>(I) & 3) == 0;
+    const bool out_vec = vec && (reinterpret_cast<uintptr_t>(d.edges) & 3) == 0 &&
+                         (reinterpret_cast<uintptr_t>(d.cand) & 3) == 0;
+    Row8 P = ns_load_row(I, W, H, ya - 1, cx0, vec, lane);
+    Row8 Q = ns_load_row(I, W, H, ya, cx0, vec, lane);
+    Sob6 prev = ns_sobel(ns_load_row(I, W, H, ya - 2, cx0, vec, lane), P, Q, cx0, W, ya - 1 >= 0);
+    Sob6 cur = ns_sobel(P, Q, ns_load_row(I, W, H, ya + 1, cx0, vec, lane), cx0, W, true);
+    P = Q;
+    Q = ns_load_row(I, W, H, ya + 1, cx0, vec, lane);
     const int rtx = (W + RT - 1) / RT, rty = (H + RT - 1) / RT;
     unsigned seed = 0u;
-    for (int i = t; i < CT * CT; i += CT_THREADS) {
-        const int ly = i / CT, lx = i - ly * CT;
-        const int gy = y0 + ly, gx = x0 + lx;
-        if (gy >= H || gx >= W) continue;
-        const int a = si[ly + 1][lx + 1], b = si[ly + 1][lx + 2], c = si[ly + 1][lx + 3];
-        const int e = si[ly + 2][lx + 1], f = si[ly + 2][lx + 3];
-        const int g = si[ly + 3][lx + 1], hh = si[ly + 3][lx + 2], k = si[ly + 3][lx + 3];
-        const int sx = (c + 2 * f + k) - (a + 2 * e + g);
-        const int sy = (g + 2 * hh + k) - (a + 2 * b + c);
-        const int ax = abs(sx), ay = abs(sy);
-        int ady, adx, bdy, bdx;
-        if ((ax + ay) * (ax + ay) < 2 * ax * ax) {           // |gx| <= 1020 per term: no overflow
-            ady = 0; adx = -1; bdy = 0; bdx = 1;
-        } else if (ay > ax && (ay - ax) * (ay - ax) > 2 * ax * ax) {
-            ady = -1; adx = 0; bdy = 1; bdx = 0;
-        } else if ((sx > 0) == (sy > 0)) {                   // sx sy > 0 (both nonzero here)
-            ady = -1; adx = -1; bdy = 1; bdx = 1;
-        } else {
-            ady = -1; adx = 1; bdy = 1; bdx = -1;
+    RowFetch fn = ns_fetch(I, W, H, ya + 2, cx0, vec, lane);  // one row ahead of its use
+#pragma unroll 1
+    for (int y = ya; y < yb; y++) {
+        const Row8 N = ns_row(fn, lane);
+        fn = ns_fetch(I, W, H, y + 3, cx0, vec, lane);
+        const Sob6 next = ns_sobel(P, Q, N, cx0, W, y + 1 < H);
+        uint32_t ws = 0, wc = 0;
+#pragma unroll
+        for (int c = 0; c < 4; c++) {
+            const int j = c + 1;
+            const int sx = cur.sx[j], sy = cur.sy[j], ax = abs(sx), ay = abs(sy), m = cur.m[j];
+            int ma, mb;
+            if ((ax + ay) * (ax + ay) < 2 * ax * ax) {                  // horizontal
+                ma = cur.m[j - 1]; mb = cur.m[j + 1];
+            } else if (ay > ax && (ay - ax) * (ay - ax) > 2 * ax * ax) {  // vertical
+                ma = prev.m[j]; mb = next.m[j];
+            } else if ((sx > 0) == (sy > 0)) {                          // along (+x, +y)
+                ma = prev.m[j - 1]; mb = next.m[j + 1];
+            } else {                                                    // along (+x, -y)
+                ma = prev.m[j + 1]; mb = next.m[j - 1];
+            }
+            const bool keep = m > ma && m >= mb;
+            ws |= (uint32_t)(keep && m > high) << (8 * c);
+            wc |= (uint32_t)(keep && m > low) << (8 * c);
         }
-        const int m = sm[ly + 1][lx + 1];
-        const bool keep = m > sm[ly + 1 + ady][lx + 1 + adx] && m >= sm[ly + 1 + bdy][lx + 1 + bdx];
-        const size_t o = (size_t)gy * W + gx;
-        const bool strong = keep && m > high;
-        d.edges[o] = (uint8_t)strong;
-        d.cand[o] = (uint8_t)(keep && m > low);
-        if (strong) seed |= seed_bits_px(rtx, rty, gx, gy);
+        if (cx0 < W) {
+            const size_t o = (size_t)y * W + cx0;
+            if (out_vec) {
+                *reinterpret_cast<uint32_t*>(d.edges + o) = ws;
+                *reinterpret_cast<uint32_t*>(d.cand + o) = wc;
+            } else {
+                for (int c = 0; c < 4 && cx0 + c < W; c++) {
+                    d.edges[o + c] = (uint8_t)(ws >> (8 * c));
+                    d.cand[o + c] = (uint8_t)(wc >> (8 * c));
+                }
+            }
+            if (ws) {
+#pragma unroll
+                for (int c = 0; c < 4; c++)
+                    if ((ws >> (8 * c)) & 1u) seed |= seed_bits_px(rtx, rty, cx0 + c, y);
+            }
+        }
+        prev = cur;
+        cur = next;
+        P = Q;
+        Q = N;
     }
-    // the block lies in one work tile: one flag store per touched work tile
-    if (seed) atomicOr(&seeds, seed);
-    __syncthreads();
-    if (t < 9 && ((seeds >> t) & 1u)) {
-        const int dy = t / 3 - 1, dx = t % 3 - 1;
-        flags[d.rt_base + (y0 / RT + dy) * rtx + (x0 / RT + dx)] = 1;
+    // lanes 0-15 and 16-31 each lie in one work tile: one flag store per touched work tile
+    const unsigned lo = __reduce_or_sync(0xffffffffu, lane < 16 ? seed : 0u);
+    const unsigned hi = __reduce_or_sync(0xffffffffu, lane >= 16 ? seed : 0u);
+    if ((lane == 0 || lane == 16) && cx0 < W) {
+        const unsigned m9 = lane == 0 ? lo : hi;
+        const int tx = cx0 / RT, ty = ya / RT;
+        for (int b = 0; b < 9; b++)
+            if ((m9 >> b) & 1u) flags[d.rt_base + (ty + b / 3 - 1) * rtx + (tx + b % 3 - 1)] = 1;
     }
 }
 
 constexpr int CR_MAX = 4;                 // largest disk radius of the counts
-constexpr int CC_S = CT + 2 * CR_MAX;     // staged labels: the block and an r-pixel halo
+constexpr int CC_S = CT + 2 * CR_MAX;     // staged labels: the block and a CR_MAX-pixel halo (40 x 40)
 
-// Edge counts, one 32x32 block per CTA: the labels of the block and its
-// r-pixel halo (0 off the image, and for labels outside 1..K) and the edge
-// bytes of the block staged in shared memory; each edge pixel adds one to
-// every distinct object in its disk (the first four remembered in registers,
-// beyond that an object is new iff no earlier disk offset holds it).
+// Edge counts, one 32x32 block per CTA: the edge bytes of the block, then
+// (for a block with an edge pixel) the labels of the block and a 4-pixel
+// halo (0 off the image, and for labels outside 1..K), staged in shared
+// memory with 16-byte loads where the rows allow; each edge pixel adds one
+// to every distinct object in its disk (the first four remembered in
+// registers, beyond that an object is new iff no earlier disk offset holds
+// it).
 __global__ void __launch_bounds__(256) k_canny_counts(const CannyDesc* __restrict__ D, int n, int r) {
-    __shared__ int32_t sl[CC_S][CC_S + 1];
-    __shared__ uint8_t se[CT][CT];
+    __shared__ __align__(16) int32_t sl[CC_S][CC_S];
+    __shared__ __align__(16) uint8_t se[CT][CT];
     const int t = threadIdx.x;
-    const CannyDesc& d = D[find_block_tile(D, n, blockIdx.x)];
+    const CannyDesc& d = D[find_desc(D, n, blockIdx.x, &CannyDesc::blk_base)];
     const int K = d.K;
     if (K <= 0) return;
     const int W = d.W, H = d.H, bl = blockIdx.x - d.blk_base;
     const int by = bl / d.bx, x0 = (bl - by * d.bx) * CT, y0 = by * CT;
-    const int S = CT + 2 * r;
-    for (int i = t; i < CT * CT; i += 256) {
-        const int ly = i / CT, lx = i - ly * CT, gy = y0 + ly, gx = x0 + lx;
-        se[ly][lx] = (gy < H && gx < W) ? d.edges[(size_t)gy * W + gx] : (uint8_t)0;
-    }
-    __syncthreads();
-    // skip the labels of a block without edge pixels
     int any = 0;
-    for (int i = t; i < CT * CT; i += 256) any |= se[i / CT][i % CT];
-    if (!__syncthreads_or(any)) return;
-    for (int i = t; i < S * S; i += 256) {
-        const int ly = i / S, lx = i - ly * S, gy = y0 - r + ly, gx = x0 - r + lx;
-        int v = 0;
-        if ((unsigned)gy < (unsigned)H && (unsigned)gx < (unsigned)W) v = d.labels[(size_t)gy * W + gx];
-        sl[ly][lx] = (v >= 1 && v <= K) ? v : 0;
+    if (t < 64) {  // the block's edge bytes: one 16-byte row half per thread
+        const int ly = t >> 1, lx = (t & 1) * 16, gy = y0 + ly, gx = x0 + lx;
+        uint4 v = make_uint4(0, 0, 0, 0);
+        const uint8_t* src = d.edges + (size_t)gy * W + gx;
+        if (gy < H) {
+            if (gx + 16 <= W && (reinterpret_cast<uintptr_t>(src) & 15) == 0) {
+                v = *reinterpret_cast<const uint4*>(src);
+            } else {
+                uint32_t w[4] = {0, 0, 0, 0};
+#pragma unroll
+                for (int k = 0; k < 16; k++)
+                    if (gx + k < W) w[k >> 2] |= (uint32_t)src[k] << (8 * (k & 3));
+                v = make_uint4(w[0], w[1], w[2], w[3]);
+            }
+        }
+        *reinterpret_cast<uint4*>(&se[ly][lx]) = v;
+        any = (v.x | v.y | v.z | v.w) != 0;
+    }
+    if (!__syncthreads_or(any)) return;       // no edge pixel: no label is needed
+    const bool vec = (W & 3) == 0 && (reinterpret_cast<uintptr_t>(d.labels) & 15) == 0;
+    for (int i = t; i < CC_S * (CC_S / 4); i += 256) {
+        const int ly = i / (CC_S / 4), q = i - ly * (CC_S / 4);
+        const int gy = y0 - CR_MAX + ly, gx = x0 - CR_MAX + 4 * q;
+        int4 v = make_int4(0, 0, 0, 0);
+        if ((unsigned)gy < (unsigned)H) {
+            const int32_t* src = d.labels + (size_t)gy * W + gx;
+            if (vec && gx >= 0 && gx + 4 <= W) {
+                v = __ldg(reinterpret_cast<const int4*>(src));
+            } else {
+                int e[4];
+#pragma unroll
+                for (int k = 0; k < 4; k++) e[k] = (unsigned)(gx + k) < (unsigned)W ? __ldg(src + k) : 0;
+                v = make_int4(e[0], e[1], e[2], e[3]);
+            }
+        }
+        v.x = (v.x >= 1 && v.x <= K) ? v.x : 0;
+        v.y = (v.y >= 1 && v.y <= K) ? v.y : 0;
+        v.z = (v.z >= 1 && v.z <= K) ? v.z : 0;
+        v.w = (v.w >= 1 && v.w <= K) ? v.w : 0;
+        *reinterpret_cast<int4*>(&sl[ly][4 * q]) = v;
     }
     __syncthreads();
     const int r2 = r * r;
@@ -157,14 +273,14 @@ __global__ void __launch_bounds__(256) k_canny_counts(const CannyDesc* __restric
         for (int dy = -r; dy <= r; dy++)
             for (int dx = -r; dx <= r; dx++) {
                 if (dx * dx + dy * dy > r2) continue;
-                const int v = sl[ly + r + dy][lx + r + dx];
+                const int v = sl[ly + CR_MAX + dy][lx + CR_MAX + dx];
                 if (!v || v == seen0 || v == seen1 || v == seen2 || v == seen3) continue;
                 bool fresh = true;
                 if (nseen >= 4) {  // look for v at an earlier disk offset
                     for (int ey = -r; ey <= dy && fresh; ey++)
                         for (int ex = -r; ex <= r; ex++) {
                             if (ey == dy && ex >= dx) break;
-                            if (ex * ex + ey * ey <= r2 && sl[ly + r + ey][lx + r + ex] == v) {
+                            if (ex * ex + ey * ey <= r2 && sl[ly + CR_MAX + ey][lx + CR_MAX + ex] == v) {
                                 fresh = false;
                                 break;
                             }
@@ -201,13 +317,16 @@ void upload_canny_descs(CannyDesc* dst, const std::vector<CannyDesc>& v, cudaStr
     }
 }
 
+int canny_nms_warps(int W, int H) { return ((W + NS_COLS - 1) / NS_COLS) * ((H + NS_ROWS - 1) / NS_ROWS); }
+
 void launch_canny_nms(const std::vector<CannyDesc>& descs, CannyDesc* d_descs, int low, int high, int* flags,
                       cudaStream_t s, Profiler* pf) {
-    int blocks = 0;
-    for (auto& d : descs) blocks += canny_blocks(d.W, d.H);
-    if (!blocks) return;
+    int warps = 0;
+    for (auto& d : descs) warps += canny_nms_warps(d.W, d.H);
+    if (!warps) return;
     pf->begin("canny_nms", s);
-    k_canny_nms<<<blocks, CT_THREADS, 0, s>>>(d_descs, (int)descs.size(), low, high, flags);
+    k_canny_nms<<<(warps + NS_WARPS - 1) / NS_WARPS, 32 * NS_WARPS, 0, s>>>(d_descs, (int)descs.size(), warps, low,
+                                                                          high, flags);
     pf->end("canny_nms", s);
 }
 

@@ -994,7 +994,7 @@ int canny_run(pipe_t p, const edge_tile* tiles, int n, int low, int high, int ra
     std::vector<CannyDesc> cd(n);
     std::vector<TileDev> td(n);
     char* cand = (char*)p->canny_cand.p;
-    int blk = 0, rt = 0;
+    int blk = 0, nw = 0, rt = 0;
     for (int i = 0; i < n; i++) {
         const edge_tile& t = tiles[i];
         CannyDesc& c = cd[i];
@@ -1008,8 +1008,10 @@ int canny_run(pipe_t p, const edge_tile* tiles, int n, int low, int high, int ra
         c.K = t.n_objects;
         c.bx = (t.W + 31) / 32;
         c.blk_base = blk;
+        c.nms_base = nw;
         c.rt_base = rt;
         blk += canny_blocks(t.W, t.H);
+        nw += canny_nms_warps(t.W, t.H);
         cand += al256((size_t)t.W * t.H);
         TileDev& d = td[i];
         std::memset(&d, 0, sizeof(TileDev));
