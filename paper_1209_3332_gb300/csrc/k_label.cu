@@ -271,7 +271,10 @@ __global__ void __launch_bounds__(CCL_WARPS * 32, 12) k_fill_local(Launch L) {
     const TileDev T = L.tiles[g.ti];  // by value: stores below cannot force reloads
     const uint32_t vm = valid_mask(g.bw);
     uint32_t fg = 0;
-    const uint32_t thr4 = (uint32_t)L.thr * 0x01010101u;
+    // hem8 - R >= thr per byte: R <= hem8 bytewise, so the 32-bit difference
+    // has no borrow between bytes; each byte plus 256 - thr (in its own
+    // 16-bit lane) carries into bit 8 of the lane exactly when it is >= thr
+    const uint32_t bias2 = (uint32_t)max(0, 256 - L.thr) * 0x00010001u;
     if (g.bw == 32 && (T.W & 15) == 0 &&
         ((reinterpret_cast<uintptr_t>(T.hem8) | reinterpret_cast<uintptr_t>(T.R)) & 15) == 0) {
         // lanes 2r and 2r+1 read the two 16-byte halves of row r (then of row
@@ -289,9 +292,9 @@ __global__ void __launch_bounds__(CCL_WARPS * 32, 12) k_fill_local(Launch L) {
                 const uint32_t hw[4] = {hv.x, hv.y, hv.z, hv.w}, rw[4] = {rv.x, rv.y, rv.z, rv.w};
 #pragma unroll
                 for (int k = 0; k < 4; k++) {
-                    // R <= hem8 bytewise, so the bytewise difference does not wrap
-                    const uint32_t ge = __vcmpgeu4(__vsub4(hw[k], rw[k]), thr4);
-                    half[i] |= ((ge & 1u) | ((ge >> 7) & 2u) | ((ge >> 14) & 4u) | ((ge >> 21) & 8u)) << (k * 4);
+                    const uint32_t d = hw[k] - rw[k];
+                    const uint32_t e = (d & 0x00ff00ffu) + bias2, o = ((d >> 8) & 0x00ff00ffu) + bias2;
+                    half[i] |= (((e >> 8) & 1u) | ((o >> 7) & 2u) | ((e >> 22) & 4u) | ((o >> 21) & 8u)) << (k * 4);
                 }
             }
         }
