@@ -108,8 +108,13 @@ __global__ void __launch_bounds__(256) k_edt_rows(Launch L, int RB, int Wmax) {
         const int x = xb + u * blockDim.x;
         if (x >= W) break;
         const uint32_t bg = ~wv[u] & rv;
-        int above = -1, below = -1;  // nearest background row above / below this chunk
         const int k0 = y0 - r0, k1 = y0 + nrow - 1 - r0;
+        const uint32_t band = below_or_at(k1) & ~((1u << k0) - 1u);
+        if ((bg & band) == band) {  // background on every row of the band: g = 0
+            for (int j = 0; j < nrow; j++) gs[(size_t)j * Wp + WMAX + x] = 0;
+            continue;
+        }
+        int above = -1, below = -1;  // nearest background row above / below this chunk
         if (!(bg & below_or_at(k0)))
             for (int cc = c - 1; cc >= 0; cc--) {
                 uint32_t b2 = ~colbits[(size_t)cc * W + x] & rows_valid(cc);
@@ -139,14 +144,26 @@ __global__ void __launch_bounds__(256) k_edt_rows(Launch L, int RB, int Wmax) {
         if (!rowslow[j]) {
             // g <= WMAX on this row, so r < WMAX stays within the padding,
             // whose entries cost INFG^2 and never win
-            for (int x = threadIdx.x; x < W; x += blockDim.x) {
-                const int g0 = g[x];
-                int D = sq(g0);
+            auto solve = [&](int x) -> int {
+                int D = sq(g[x]);
                 for (int r = 1, rr = 1; rr < D; rr += 2 * r + 1, r++) {
                     D = __viaddmin_s32(sq(g[x - r]), rr, D);
                     D = __viaddmin_s32(sq(g[x + r]), rr, D);
                 }
-                out[x] = D;
+                return D;
+            };
+            if ((W & 3) == 0 && (Wp & 3) == 0 && (reinterpret_cast<uintptr_t>(out) & 15) == 0) {
+                // four pixels per thread: one 8-byte read of g (8-byte aligned:
+                // WMAX, x and the row stride Wp are multiples of 4), one 16-byte
+                // store; a run of four background pixels needs no search at all
+                for (int x = 4 * threadIdx.x; x < W; x += 4 * blockDim.x) {
+                    const uint2 gq = *reinterpret_cast<const uint2*>(g + x);
+                    int4 D = make_int4(0, 0, 0, 0);
+                    if (gq.x | gq.y) D = make_int4(solve(x), solve(x + 1), solve(x + 2), solve(x + 3));
+                    *reinterpret_cast<int4*>(out + x) = D;
+                }
+            } else {
+                for (int x = threadIdx.x; x < W; x += blockDim.x) out[x] = solve(x);
             }
         } else if (threadIdx.x == 0) {
             meijster_row(g, W, out);
