@@ -46,8 +46,8 @@ __device__ __forceinline__ int find_desc(const CannyDesc* __restrict__ D, int n,
 constexpr int NS_COLS = 128, NS_ROWS = 64;
 constexpr int NS_WARPS = 4;          // warps per CTA
 
-struct Row8 {                        // image row, columns cx0 - 2 .. cx0 + 5 (replicated border)
-    int v[8];
+struct Row8 {                        // image row, columns cx0 - 2 .. cx0 + 5 (replicated border), as
+    uint32_t p[4];                   // four pairs of 16-bit lanes: (-2,-1), (0,1), (2,3), (4,5)
 };
 
 // the global reads of one row for one lane: its own 4 pixels, and on the
@@ -81,14 +81,14 @@ __device__ __forceinline__ RowFetch ns_fetch(const uint8_t* __restrict__ I, int 
 
 // columns cx0 - 2 .. cx0 + 5 of a fetched row: the neighbours' pixels by shuffle
 __device__ __forceinline__ Row8 ns_row(const RowFetch& f, int lane) {
-    const uint32_t wl = __shfl_up_sync(0xffffffffu, f.w, 1), wr = __shfl_down_sync(0xffffffffu, f.w, 1);
+    uint32_t wl = __shfl_up_sync(0xffffffffu, f.w, 1), wr = __shfl_down_sync(0xffffffffu, f.w, 1);
+    if (lane == 0) wl = ((uint32_t)f.e0 << 16) | ((uint32_t)f.e1 << 24);   // bytes 2, 3: columns -2, -1
+    if (lane == 31) wr = (uint32_t)f.e0 | ((uint32_t)f.e1 << 8);            // bytes 0, 1: columns 4, 5
     Row8 r;
-#pragma unroll
-    for (int k = 0; k < 4; k++) r.v[2 + k] = (int)((f.w >> (8 * k)) & 0xffu);
-    r.v[0] = lane == 0 ? f.e0 : (int)((wl >> 16) & 0xffu);
-    r.v[1] = lane == 0 ? f.e1 : (int)(wl >> 24);
-    r.v[6] = lane == 31 ? f.e0 : (int)(wr & 0xffu);
-    r.v[7] = lane == 31 ? f.e1 : (int)((wr >> 8) & 0xffu);
+    r.p[0] = __byte_perm(wl, 0u, 0x4342);
+    r.p[1] = __byte_perm(f.w, 0u, 0x4140);
+    r.p[2] = __byte_perm(f.w, 0u, 0x4342);
+    r.p[3] = __byte_perm(wr, 0u, 0x4140);
     return r;
 }
 
@@ -97,26 +97,61 @@ __device__ __forceinline__ Row8 ns_load_row(const uint8_t* __restrict__ I, int W
     return ns_row(ns_fetch(I, W, H, y, cx0, vec, lane), lane);
 }
 
-struct Sob6 {                        // columns cx0 - 1 .. cx0 + 4 of one row
-    int sx[6], sy[6], m[6];
+struct Sob6 {                        // columns cx0 - 1 .. cx0 + 4 of one row (index j = column - cx0 + 1)
+    int m[6];                        // L1 magnitude, 0 off the image
+    int ax[4], ay[4], same[4];       // |gx|, |gy| and whether gx, gy have one sign, columns cx0 .. cx0 + 3
 };
 
-// Sobel of the row between A and C (rows r - 1, r, r + 1, replicated); m is 0
-// for columns off the image, or for every column when the row is off it
-__device__ __forceinline__ Sob6 ns_sobel(const Row8& A, const Row8& B, const Row8& C, int cx0, int W, bool row_in) {
-    int vs[8], vd[8];
+__device__ __forceinline__ uint32_t max2(uint32_t a, uint32_t b) {
+    uint32_t d;
+    asm("max.u16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+__device__ __forceinline__ uint32_t min2(uint32_t a, uint32_t b) {
+    uint32_t d;
+    asm("min.u16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+
+// Sobel of the row between A and C (rows r - 1, r, r + 1, replicated) in
+// 16x2-bit lanes, for the column pairs (-1, 0), (1, 2), (3, 4): with
+// vs = A + 2B + C and vd = C - A per column, gx(c) = vs(c+1) - vs(c-1) and
+// gy(c) = vd(c-1) + 2 vd(c) + vd(c+1).  Signed values carry a bias (256 on
+// vd, 1024 on gx and gy) so that every lane stays in [0, 2^16) and packed
+// adds never borrow across lanes.  colmask: per pair, 0xffff on the lanes of
+// columns inside the image; m is 0 elsewhere and on a row off the image.
+__device__ __forceinline__ Sob6 ns_sobel(const Row8& A, const Row8& B, const Row8& C, const uint32_t colmask[3],
+                                         bool row_in) {
+    constexpr uint32_t B256 = 0x01000100u, B1024 = 0x04000400u;
+    uint32_t V[4], Dv[4];
 #pragma unroll
-    for (int k = 0; k < 8; k++) {
-        vs[k] = A.v[k] + 2 * B.v[k] + C.v[k];
-        vd[k] = C.v[k] - A.v[k];
+    for (int k = 0; k < 4; k++) {
+        V[k] = A.p[k] + (B.p[k] << 1) + C.p[k];
+        Dv[k] = C.p[k] + B256 - A.p[k];
+    }
+    const uint32_t rm = row_in ? 0xffffffffu : 0u;
+    uint32_t SX[3], SY[3], AX[3], AY[3];
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        SX[k] = V[k + 1] + B1024 - V[k];
+        SY[k] = Dv[k] + (__byte_perm(Dv[k], Dv[k + 1], 0x5432) << 1) + Dv[k + 1];
+        AX[k] = max2(SX[k], B1024) - min2(SX[k], B1024);
+        AY[k] = max2(SY[k], B1024) - min2(SY[k], B1024);
     }
     Sob6 o;
 #pragma unroll
-    for (int j = 0; j < 6; j++) {
-        o.sx[j] = vs[j + 2] - vs[j];
-        o.sy[j] = vd[j] + 2 * vd[j + 1] + vd[j + 2];
-        const int x = cx0 - 1 + j;
-        o.m[j] = (row_in && x >= 0 && x < W) ? abs(o.sx[j]) + abs(o.sy[j]) : 0;
+    for (int k = 0; k < 3; k++) {
+        const uint32_t M = (AX[k] + AY[k]) & colmask[k] & rm;
+        o.m[2 * k] = (int)(M & 0xffffu);
+        o.m[2 * k + 1] = (int)(M >> 16);
+    }
+    // columns 0..3 are the high lane of pair 0, both lanes of pair 1, the low lane of pair 2
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+        const int k = (c + 1) >> 1, sh = (c & 1) ? 0 : 16;
+        o.ax[c] = (int)((AX[k] >> sh) & 0xffffu);
+        o.ay[c] = (int)((AY[k] >> sh) & 0xffffu);
+        o.same[c] = (((SX[k] >> sh) & 0xffffu) > 1024u) == (((SY[k] >> sh) & 0xffffu) > 1024u);
     }
     return o;
 }
@@ -137,10 +172,16 @@ __global__ void __launch_bounds__(32 * NS_WARPS, 4) k_canny_nms(const CannyDesc*
     const bool vec = (W & 3) == 0 && (reinterpret_cast<uintptr_t>(I) & 3) == 0;
     const bool out_vec = vec && (reinterpret_cast<uintptr_t>(d.edges) & 3) == 0 &&
                          (reinterpret_cast<uintptr_t>(d.cand) & 3) == 0;
+    uint32_t colmask[3];  // pair k holds columns cx0 + 2k - 1 and cx0 + 2k
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        const int x = cx0 + 2 * k - 1;
+        colmask[k] = ((x >= 0 && x < W) ? 0xffffu : 0u) | ((x + 1 >= 0 && x + 1 < W) ? 0xffff0000u : 0u);
+    }
     Row8 P = ns_load_row(I, W, H, ya - 1, cx0, vec, lane);
     Row8 Q = ns_load_row(I, W, H, ya, cx0, vec, lane);
-    Sob6 prev = ns_sobel(ns_load_row(I, W, H, ya - 2, cx0, vec, lane), P, Q, cx0, W, ya - 1 >= 0);
-    Sob6 cur = ns_sobel(P, Q, ns_load_row(I, W, H, ya + 1, cx0, vec, lane), cx0, W, true);
+    Sob6 prev = ns_sobel(ns_load_row(I, W, H, ya - 2, cx0, vec, lane), P, Q, colmask, ya - 1 >= 0);
+    Sob6 cur = ns_sobel(P, Q, ns_load_row(I, W, H, ya + 1, cx0, vec, lane), colmask, true);
     P = Q;
     Q = ns_load_row(I, W, H, ya + 1, cx0, vec, lane);
     const int rtx = (W + RT - 1) / RT, rty = (H + RT - 1) / RT;
@@ -150,18 +191,18 @@ __global__ void __launch_bounds__(32 * NS_WARPS, 4) k_canny_nms(const CannyDesc*
     for (int y = ya; y < yb; y++) {
         const Row8 N = ns_row(fn, lane);
         fn = ns_fetch(I, W, H, y + 3, cx0, vec, lane);
-        const Sob6 next = ns_sobel(P, Q, N, cx0, W, y + 1 < H);
+        const Sob6 next = ns_sobel(P, Q, N, colmask, y + 1 < H);
         uint32_t ws = 0, wc = 0;
 #pragma unroll
         for (int c = 0; c < 4; c++) {
             const int j = c + 1;
-            const int sx = cur.sx[j], sy = cur.sy[j], ax = abs(sx), ay = abs(sy), m = cur.m[j];
+            const int ax = cur.ax[c], ay = cur.ay[c], m = cur.m[j];
             int ma, mb;
             if ((ax + ay) * (ax + ay) < 2 * ax * ax) {                  // horizontal
                 ma = cur.m[j - 1]; mb = cur.m[j + 1];
             } else if (ay > ax && (ay - ax) * (ay - ax) > 2 * ax * ax) {  // vertical
                 ma = prev.m[j]; mb = next.m[j];
-            } else if ((sx > 0) == (sy > 0)) {                          // along (+x, +y)
+            } else if (cur.same[c]) {                                   // along (+x, +y)
                 ma = prev.m[j - 1]; mb = next.m[j + 1];
             } else {                                                    // along (+x, -y)
                 ma = prev.m[j + 1]; mb = next.m[j - 1];
@@ -243,26 +284,39 @@ __global__ void __launch_bounds__(256) k_canny_counts(const CannyDesc* __restric
     }
     if (!__syncthreads_or(any)) return;       // no edge pixel: no label is needed
     const bool vec = (W & 3) == 0 && (reinterpret_cast<uintptr_t>(d.labels) & 15) == 0;
-    for (int i = t; i < CC_S * (CC_S / 4); i += 256) {
+    // 400 four-label groups over 256 threads: both of a thread's loads are
+    // issued before either is stored, so their latencies overlap
+    constexpr int NQ = CC_S * (CC_S / 4);
+    int4 v[2];
+#pragma unroll
+    for (int u = 0; u < 2; u++) {
+        const int i = t + 256 * u;
         const int ly = i / (CC_S / 4), q = i - ly * (CC_S / 4);
         const int gy = y0 - CR_MAX + ly, gx = x0 - CR_MAX + 4 * q;
-        int4 v = make_int4(0, 0, 0, 0);
-        if ((unsigned)gy < (unsigned)H) {
+        v[u] = make_int4(0, 0, 0, 0);
+        if (i < NQ && (unsigned)gy < (unsigned)H) {
             const int32_t* src = d.labels + (size_t)gy * W + gx;
             if (vec && gx >= 0 && gx + 4 <= W) {
-                v = __ldg(reinterpret_cast<const int4*>(src));
+                v[u] = __ldg(reinterpret_cast<const int4*>(src));
             } else {
                 int e[4];
 #pragma unroll
                 for (int k = 0; k < 4; k++) e[k] = (unsigned)(gx + k) < (unsigned)W ? __ldg(src + k) : 0;
-                v = make_int4(e[0], e[1], e[2], e[3]);
+                v[u] = make_int4(e[0], e[1], e[2], e[3]);
             }
         }
-        v.x = (v.x >= 1 && v.x <= K) ? v.x : 0;
-        v.y = (v.y >= 1 && v.y <= K) ? v.y : 0;
-        v.z = (v.z >= 1 && v.z <= K) ? v.z : 0;
-        v.w = (v.w >= 1 && v.w <= K) ? v.w : 0;
-        *reinterpret_cast<int4*>(&sl[ly][4 * q]) = v;
+    }
+#pragma unroll
+    for (int u = 0; u < 2; u++) {
+        const int i = t + 256 * u;
+        if (i >= NQ) break;
+        const int ly = i / (CC_S / 4), q = i - ly * (CC_S / 4);
+        int4 w = v[u];
+        w.x = (w.x >= 1 && w.x <= K) ? w.x : 0;
+        w.y = (w.y >= 1 && w.y <= K) ? w.y : 0;
+        w.z = (w.z >= 1 && w.z <= K) ? w.z : 0;
+        w.w = (w.w >= 1 && w.w <= K) ? w.w : 0;
+        *reinterpret_cast<int4*>(&sl[ly][4 * q]) = w;
     }
     __syncthreads();
     const int r2 = r * r;
