@@ -68,6 +68,7 @@ struct Shared {
     int processed;                      // tile processings (diagnostic)
     int nobj;                           // object items of a batched feature pass
     int nseed;                          // work tiles of a seeded reconstruction queued at the start
+    int cls[4], cls_pos[4];             // initial queue: work tiles per order class, and placed so far
 };
 
 struct Launch {
@@ -75,6 +76,7 @@ struct Launch {
     int ntiles;
     unsigned long long* wl_slots;  // [n_rt] queue ring: sequence << 32 | item
     int* wl_state;         // [n_rt] per-tile state
+    int* rt_src;           // [n_rt] work tiles holding a strong marker (queued first)
     Shared* sh;
     int* tile_status;      // [ntiles]
     int* status;           // global status word

@@ -38,20 +38,24 @@ struct DeconvLut {
 };
 
 __device__ __forceinline__ void deconv_item(const TileDev* __restrict__ tiles, int ntiles, int gid, int h,
-                                            const DeconvLut& lut);
+                                            const DeconvLut& lut, int* __restrict__ rt_src);
+
+// marker values from which a work tile counts as holding a source (nuclei
+// reach about 140, stroma 22 and the background about 10)
+constexpr uint32_t SRC_MARKER = 40;
 
 __global__ void __launch_bounds__(256) k_deconv(const TileDev* __restrict__ tiles, int ntiles,
-                                                int n_items, int h) {
+                                                int n_items, int h, int* __restrict__ rt_src) {
     __shared__ int32_t T[256 * 32];
     for (int i = threadIdx.x; i < 256 * 32; i += blockDim.x) T[i] = c_lut[i >> 5];
     __syncthreads();
     const DeconvLut lut{T + (threadIdx.x & 31), c_wq[0], c_wq[1], c_wq[2]};
     for (int gid = blockIdx.x * blockDim.x + threadIdx.x; gid < n_items; gid += gridDim.x * blockDim.x)
-        deconv_item(tiles, ntiles, gid, h, lut);
+        deconv_item(tiles, ntiles, gid, h, lut, rt_src);
 }
 
 __device__ __forceinline__ void deconv_item(const TileDev* __restrict__ tiles, int ntiles, int gid, int h,
-                                            const DeconvLut& lut) {
+                                            const DeconvLut& lut, int* __restrict__ rt_src) {
     int ti = find_tile(tiles, ntiles, gid, &TileDev::px_base);
     const TileDev& t = tiles[ti];
     int item = gid - t.px_base;
@@ -67,7 +71,7 @@ __device__ __forceinline__ void deconv_item(const TileDev* __restrict__ tiles, i
         uint4 b = __ldcs(reinterpret_cast<const uint4*>(src) + 1);
         uint4 c = __ldcs(reinterpret_cast<const uint4*>(src) + 2);
         uint32_t w[12] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z, c.w};
-        uint32_t hv[4] = {0, 0, 0, 0}, rv[4] = {0, 0, 0, 0};
+        uint32_t hv[4] = {0, 0, 0, 0}, rv[4] = {0, 0, 0, 0}, mkmax = 0;
         // byte k of the 48 loaded bytes, zero-extended
         auto byte_at = [&](int k) -> uint32_t { return __byte_perm(w[k >> 2], 0u, 0x4440 | (k & 3)); };
 #pragma unroll
@@ -76,7 +80,9 @@ __device__ __forceinline__ void deconv_item(const TileDev* __restrict__ tiles, i
             const uint32_t mk = (uint32_t)__viaddmax_s32((int)hm, -h, 0);
             hv[p >> 2] = hv[p >> 2] * 256u + hm;
             rv[p >> 2] = rv[p >> 2] * 256u + mk;
+            mkmax = max(mkmax, mk);
         }
+        if (rt_src && mkmax >= SRC_MARKER) rt_src[t.rt_base + (y / RT) * t.rtx + x0 / RT] = 1;
         if ((reinterpret_cast<uintptr_t>(dh) & 15) == 0 && (reinterpret_cast<uintptr_t>(dr) & 15) == 0) {
             *reinterpret_cast<uint4*>(dh) = make_uint4(hv[0], hv[1], hv[2], hv[3]);
             *reinterpret_cast<uint4*>(dr) = make_uint4(rv[0], rv[1], rv[2], rv[3]);
@@ -89,11 +95,15 @@ __device__ __forceinline__ void deconv_item(const TileDev* __restrict__ tiles, i
         }
     } else {
         int n = min(16, t.W - x0);
+        uint32_t mkmax = 0;
         for (int p = 0; p < n; p++) {
             const uint32_t hm = lut.hem(src[3 * p], src[3 * p + 1], src[3 * p + 2]);
             dh[p] = (uint8_t)hm;
-            dr[p] = (uint8_t)__viaddmax_s32((int)hm, -h, 0);
+            const uint32_t mk = (uint32_t)__viaddmax_s32((int)hm, -h, 0);
+            dr[p] = (uint8_t)mk;
+            mkmax = max(mkmax, mk);
         }
+        if (rt_src && mkmax >= SRC_MARKER) rt_src[t.rt_base + (y / RT) * t.rtx + x0 / RT] = 1;
     }
 }
 
@@ -105,7 +115,8 @@ void launch_deconv(const Launch& L, cudaStream_t s, Profiler* pf) {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     int blocks = (L.n_px + 255) / 256;
     if (blocks > sms * 8) blocks = sms * 8;  // the per-block table setup is amortised over a grid-stride loop
-    k_deconv<<<blocks, 256, 0, s>>>(L.tiles, L.ntiles, L.n_px, L.h);
+    cudaMemsetAsync(L.rt_src, 0, sizeof(int) * (size_t)L.n_rt, s);
+    k_deconv<<<blocks, 256, 0, s>>>(L.tiles, L.ntiles, L.n_px, L.h, L.rt_src);
     pf->end("deconv", s);
 }
 

@@ -189,9 +189,29 @@ __device__ bool wl_pop(const Launch& L, unsigned* item) {
     }
 }
 
-// ---- initial queue: per image, checkerboard order (all tiles with even
-// tx+ty first) so that the first wave of workers does not process adjacent
-// tiles at the same time ----------------------------------------------------------
+// ---- initial queue: the work tiles that hold a strong marker first (a
+// nucleus: its first visit raises the background around it, so that the
+// tiles without one start from raised halos), and within each group the
+// checkerboard order (all tiles with even tx+ty first, so that the first wave
+// of workers does not process adjacent tiles at the same time).  Places
+// within a class are taken by atomics: the order inside a class is not fixed,
+// and the result does not depend on it. ---------------------------------------
+__device__ __forceinline__ int order_class(const Launch& L, int i, int* ti_out, int* k_out) {
+    const int ti = find_tile(L.tiles, L.ntiles, i, &TileDev::rt_base);
+    const TileDev& T = L.tiles[ti];
+    const int k = i - T.rt_base, ty = k / T.rtx, tx = k - ty * T.rtx;
+    *ti_out = ti;
+    *k_out = k;
+    return (L.rt_src[i] ? 0 : 2) + ((tx + ty) & 1);
+}
+
+__global__ void k_wl_count(Launch L) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= L.n_rt) return;
+    int ti, k;
+    atomicAdd(&L.sh->cls[order_class(L, i, &ti, &k)], 1);
+}
+
 __global__ void k_wl_init(Launch L) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i == 0) {
@@ -201,14 +221,11 @@ __global__ void k_wl_init(Launch L) {
         L.sh->processed = 0;
     }
     if (i >= L.n_rt) return;
-    int ti = find_tile(L.tiles, L.ntiles, i, &TileDev::rt_base);
-    const TileDev& T = L.tiles[ti];
-    int k = i - T.rt_base, ty = k / T.rtx, tx = k - ty * T.rtx;
-    int rx = T.rtx, ry = T.rty;
-    int evens = ((rx + 1) / 2) * ((ry + 1) / 2) + (rx / 2) * (ry / 2);
-    int before = ((ty + 1) / 2) * ((rx + 1) / 2) + (ty / 2) * (rx / 2);  // evens in rows < ty
-    before += (ty & 1) ? tx / 2 : (tx + 1) / 2;                       // evens in row ty, x < tx
-    int pos = T.rt_base + (((tx + ty) & 1) ? evens + (k - before) : before);
+    int ti, k;
+    const int c = order_class(L, i, &ti, &k);
+    int base = 0;
+    for (int j = 0; j < c; j++) base += L.sh->cls[j];
+    const int pos = base + atomicAdd(&L.sh->cls_pos[c], 1);
     L.wl_slots[pos] = ((unsigned long long)(unsigned)(pos + 1) << 32) |
                       (ITEM_FIRST | ((unsigned)ti << ITEM_BITS) | (unsigned)k);
     L.wl_state[i] = WL_QUEUED;
@@ -738,6 +755,8 @@ int recon_grid(int device) {
 void launch_recon(const Launch& L, int grid_cap, cudaStream_t s, Profiler* pf) {
     if (L.n_rt == 0) return;
     pf->begin("recon_init", s);
+    cudaMemsetAsync(L.sh->cls, 0, sizeof(L.sh->cls) + sizeof(L.sh->cls_pos), s);
+    k_wl_count<<<(L.n_rt + 255) / 256, 256, 0, s>>>(L);
     k_wl_init<<<(L.n_rt + 255) / 256, 256, 0, s>>>(L);
     pf->end("recon_init", s);
     const int grid = L.n_rt < grid_cap ? L.n_rt : grid_cap;  // one work tile per worker at a time

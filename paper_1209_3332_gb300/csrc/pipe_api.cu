@@ -344,10 +344,14 @@ struct pipe_s {
 
 namespace {
 
+// Reconstruction queue per launch: a 64-bit slot, a state word and a source
+// flag per work tile.
+size_t wl_bytes(int n_rt) { return sizeof(int) * 4 * (size_t)std::max(n_rt, 1); }
+
 int ensure_ctx(LaunchCtx& c, int ntiles, int n_rt, size_t arena_bytes) {
     int rc;
     if ((rc = c.tiles.ensure(sizeof(TileDev) * std::max(ntiles, 1)))) return rc;
-    if ((rc = c.wl.ensure(sizeof(int) * 3 * std::max(n_rt, 1)))) return rc;
+    if ((rc = c.wl.ensure(wl_bytes(n_rt)))) return rc;
     if ((rc = c.shared.ensure(sizeof(Shared) + sizeof(int) * (2 + std::max(ntiles, 1))))) return rc;
     if ((rc = c.arena.ensure(std::max(arena_bytes, (size_t)256)))) return rc;
     return PIPE_OK;
@@ -357,7 +361,7 @@ int ensure_ctx(LaunchCtx& c, int ntiles, int n_rt, size_t arena_bytes) {
 // context is made ready for a group of n tiles (io: caller-visible buffers,
 // ws: workspace arena, n_rt: reconstruction work tiles).  ensure() only
 // grows a buffer, so each part becomes the larger of the two.
-size_t wl_bytes(int n_rt) { return sizeof(int) * 3 * (size_t)std::max(n_rt, 1); }
+
 size_t tiles_bytes(int n) { return sizeof(TileDev) * (size_t)std::max(n, 1); }
 size_t shared_bytes(int n) { return sizeof(Shared) + sizeof(int) * (2 + (size_t)std::max(n, 1)); }
 size_t ctx_need(size_t io, size_t ws, int n, int n_rt) {
@@ -399,6 +403,7 @@ Launch make_launch(pipe_t p, LaunchCtx& c, std::vector<TileDev>& td, int n_rt_to
     L.ntiles = (int)td.size();
     L.wl_slots = (unsigned long long*)c.wl.p;
     L.wl_state = (int*)c.wl.p + 2 * std::max(n_rt_total, 1);
+    L.rt_src = L.wl_state + std::max(n_rt_total, 1);
     L.sh = (Shared*)c.shared.p;
     L.status = (int*)((char*)c.shared.p + sizeof(Shared));
     L.tile_status = L.status + 2;
@@ -759,7 +764,7 @@ int seg_tile(pipe_t p, const uint8_t* rgb_dev, int W, int H, size_t pitch_bytes,
     CK(cudaSetDevice(p->device));
     Geo g = geometry(W, H, 1);
     int n_rt = g.rtx * g.rty;
-    if (p->plain.arena.n < g.ws_bytes || p->plain.wl.n < sizeof(int) * 3 * (size_t)n_rt) CK(cudaStreamSynchronize(s));
+    if (p->plain.arena.n < g.ws_bytes || p->plain.wl.n < wl_bytes(n_rt)) CK(cudaStreamSynchronize(s));
     int rc = ensure_ctx(p->plain, 1, n_rt, g.ws_bytes);
     if (rc) return rc;
     std::vector<TileDev> td(1);
@@ -934,7 +939,7 @@ int rbc_tile(pipe_t p, const uint8_t* rgb_dev, int W, int H, size_t pitch_bytes,
     cudaStream_t s = (cudaStream_t)stream;
     CK(cudaSetDevice(p->device));
     const int rtx = (W + RT - 1) / RT, rty = (H + RT - 1) / RT, n_rt = rtx * rty;
-    if (p->rbc_mask.n < N || p->rbc_flags.n < sizeof(int) * (size_t)n_rt || p->rbc.wl.n < sizeof(int) * 3 * (size_t)n_rt ||
+    if (p->rbc_mask.n < N || p->rbc_flags.n < sizeof(int) * (size_t)n_rt || p->rbc.wl.n < wl_bytes(n_rt) ||
         !p->rbc.shared.p) {
         CK(cudaStreamSynchronize(s));
         const bool fresh = !p->rbc.shared.p;
@@ -1093,7 +1098,7 @@ int seg_features_batch(pipe_t p, const tile_dev* tiles, int n, pipe_stream_t str
         key += std::to_string(tiles[i].W) + "x" + std::to_string(tiles[i].H) + "c" +
                std::to_string(tiles[i].feats_cap) + (tiles[i].edt ? "e" : "n") + ";";
     }
-    bool grow = p->batch.arena.n < total || p->batch.wl.n < sizeof(int) * 3 * (size_t)n_rt ||
+    bool grow = p->batch.arena.n < total || p->batch.wl.n < wl_bytes(n_rt) ||
                 p->batch.tiles.n < sizeof(TileDev) * n || p->batch.shared.n < sizeof(Shared) + sizeof(int) * (2 + n);
     if (grow) {
         CK(cudaStreamSynchronize(s));
