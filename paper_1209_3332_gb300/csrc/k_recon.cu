@@ -205,27 +205,45 @@ __device__ __forceinline__ int order_class(const Launch& L, int i, int* ti_out, 
     return (L.rt_src[i] ? 0 : 2) + ((tx + ty) & 1);
 }
 
+// Counts and places are taken once per warp and class (ballot and popcount),
+// so the four counters see one atomic per warp instead of one per work tile.
 __global__ void k_wl_count(Launch L) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= L.n_rt) return;
-    int ti, k;
-    atomicAdd(&L.sh->cls[order_class(L, i, &ti, &k)], 1);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, lane = threadIdx.x & 31;
+    int ti, k, c = -1;
+    if (i < L.n_rt) c = order_class(L, i, &ti, &k);
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+        const unsigned m = __ballot_sync(FULL, c == j);
+        if (m && lane == __ffs(m) - 1) atomicAdd(&L.sh->cls[j], __popc(m));
+    }
 }
 
 __global__ void k_wl_init(Launch L) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, lane = threadIdx.x & 31;
     if (i == 0) {
         L.sh->head = 0;
         L.sh->tp = ((unsigned long long)(unsigned)L.n_rt << 32) | (unsigned)L.n_rt;
         L.sh->err = 0;
         L.sh->processed = 0;
     }
+    int ti = 0, k = 0, c = -1;
+    if (i < L.n_rt) c = order_class(L, i, &ti, &k);
+    int pos = 0;
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+        const unsigned m = __ballot_sync(FULL, c == j);
+        if (!m) continue;
+        const int leader = __ffs(m) - 1;
+        int first = 0;
+        if (lane == leader) {
+            int base = 0;
+            for (int q = 0; q < j; q++) base += L.sh->cls[q];
+            first = base + atomicAdd(&L.sh->cls_pos[j], __popc(m));
+        }
+        first = __shfl_sync(FULL, first, leader);
+        if (c == j) pos = first + __popc(m & ((1u << lane) - 1u));
+    }
     if (i >= L.n_rt) return;
-    int ti, k;
-    const int c = order_class(L, i, &ti, &k);
-    int base = 0;
-    for (int j = 0; j < c; j++) base += L.sh->cls[j];
-    const int pos = base + atomicAdd(&L.sh->cls_pos[c], 1);
     L.wl_slots[pos] = ((unsigned long long)(unsigned)(pos + 1) << 32) |
                       (ITEM_FIRST | ((unsigned)ti << ITEM_BITS) | (unsigned)k);
     L.wl_state[i] = WL_QUEUED;
