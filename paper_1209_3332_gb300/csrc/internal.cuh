@@ -56,6 +56,7 @@ struct TileDev {
     int row_base;                 // EDT rows base
     int px_base;                  // deconvolution work items base
     int obj_base;                 // first object item of this tile (batched features)
+    int cls[4], cls_pos[4];       // reconstruction queue order: work tiles per class, and placed so far
 };
 
 constexpr int SCAN_CHUNK = 1024;  // bitmap words per scan chunk
@@ -68,7 +69,6 @@ struct Shared {
     int processed;                      // tile processings (diagnostic)
     int nobj;                           // object items of a batched feature pass
     int nseed;                          // work tiles of a seeded reconstruction queued at the start
-    int cls[4], cls_pos[4];             // initial queue: work tiles per order class, and placed so far
 };
 
 struct Launch {
