@@ -56,7 +56,7 @@ struct TileDev {
     int row_base;                 // EDT rows base
     int px_base;                  // deconvolution work items base
     int obj_base;                 // first object item of this tile (batched features)
-    int cls[4], cls_pos[4];       // reconstruction queue order: work tiles per class, and placed so far
+    int cls[8], cls_pos[8];       // reconstruction queue order: work tiles per class, and placed so far
 };
 
 constexpr int SCAN_CHUNK = 1024;  // bitmap words per scan chunk
