@@ -68,6 +68,7 @@ struct Shared {
     int head, err;                      // worklist head; first device-side error
     int processed;                      // tile processings (diagnostic)
     int nobj;                           // object items of a batched feature pass
+    int next_obj;                       // the batched feature pass draws its objects from this counter
     int nseed;                          // work tiles of a seeded reconstruction queued at the start
 };
 

@@ -320,6 +320,7 @@ __global__ void k_obj_prefix(Launch L) {
         run += m;
     }
     L.sh->nobj = run;
+    L.sh->next_obj = 0;
 }
 
 // Batched form: the objects of all tiles, item -> (tile, object) through the
@@ -329,7 +330,14 @@ __global__ void __launch_bounds__(FW * 32) k_fobj_batched(Launch L) {
     const int warp = threadIdx.x >> 5;
     ObjSmem& S = sm[warp];
     const int total = L.sh->nobj;
-    for (int item = blockIdx.x * FW + warp; item < total; item += gridDim.x * FW) {
+    const int lane = threadIdx.x & 31;
+    // objects are drawn one at a time from a counter, so a warp that drew
+    // large boxes does not hold back the end of the pass
+    for (;;) {
+        int item = 0;
+        if (lane == 0) item = atomicAdd(&L.sh->next_obj, 1);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= total) break;
         const int t = find_tile(L.tiles, L.ntiles, item, &TileDev::obj_base);
         const TileDev& T = L.tiles[t];
         ObjJob J{T.hem8, T.labels, T.W, T.H, T.bbox, T.feats};
