@@ -388,6 +388,9 @@ __global__ void __launch_bounds__(CCL_WARPS * 32) k_merge(Launch L) {
 // ---- root-list passes (grid-stride over every tile's list) -----------------------
 // mode 0: border flag of a local root -> its global root
 // mode 1: copy the global root's flag back to every local root; compress P
+//         (the labelling pass must read the flag at its own local roots: a
+//         hole's global root can become a foreground root there, whose entry
+//         that pass overwrites while other blocks would still follow links to it)
 // mode 2: add local areas into the global root; compress P
 // mode 3: mark kept global roots in the root bitmap
 __global__ void __launch_bounds__(CCL_WARPS * 32) k_roots(Launch L, int mode) {
