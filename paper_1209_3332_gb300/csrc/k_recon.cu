@@ -304,7 +304,7 @@ __device__ __forceinline__ void load_tile(WarpTile& S, const uint8_t* Rg, const 
         // lane: block row jj of a group of 8, 16-pixel segment seg; rows 2j and
         // 2j + 1 of R and M with 16-byte loads, eight blocks built from them
         const int jj = lane >> 2, seg = lane & 3;
-#pragma unroll 1
+#pragma unroll 2
         for (int g = 0; g < NB / 8; g++) {
             const int j = g * 8 + jj, gy = y0 + 2 * j;
             const size_t o = (size_t)gy * W + x0 + seg * 16;
@@ -673,12 +673,12 @@ __global__ void __launch_bounds__(32, RECON_MIN_BLOCKS) k_recon(Launch L) {
                 uint8_t hr[9];
                 load_halo(hr, nullptr, Rg, Mg, W, H, x0, y0, lane);
                 store_tile(S, Rg, W, H, x0, y0, lane);
-                __threadfence();  // this tile's pixels before any request
-                __syncwarp();
+                // the stores drain while the requests are worked out in shared memory
                 grew = __any_sync(FULL, merge_halo(S, hr, lane));
                 __syncwarp();
                 side_requests(S, lane);
                 if (more && lane == 0) S.flags[8] = 1;  // not converged within MAX_ROUNDS: run again
+                __threadfence();  // this tile's pixels before any request
                 __syncwarp();
                 if (lane < 9 && S.flags[lane]) {
                     int target = -1;
