@@ -59,7 +59,8 @@ struct TileDev {
     int cls[8], cls_pos[8];       // reconstruction queue order: work tiles per class, and placed so far
 };
 
-constexpr int SCAN_CHUNK = 1024;  // bitmap words per scan chunk
+constexpr int SCAN_THREADS = 1024;           // threads of a scan CTA, four bitmap words each
+constexpr int SCAN_CHUNK = 4 * SCAN_THREADS;  // bitmap words per scan chunk
 constexpr int LAUNCH_TAB = 64;    // tiles whose block bases travel in the launch parameters
 
 // Shared state of one launch sequence (device memory).

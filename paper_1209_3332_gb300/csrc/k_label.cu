@@ -393,40 +393,42 @@ __global__ void __launch_bounds__(CCL_WARPS * 32) k_merge(Launch L) {
 //         that pass overwrites while other blocks would still follow links to it)
 // mode 2: add local areas into the global root; compress P
 // mode 3: mark kept global roots in the root bitmap
+// Each warp strides over the labelling blocks (a grid of a warp per block,
+// or of a few CTAs per SM: most blocks have one or two roots).
 __global__ void __launch_bounds__(CCL_WARPS * 32) k_roots(Launch L, int mode) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int gb = blockIdx.x * CCL_WARPS + warp;
-    if (gb >= L.n_cb) return;
-    const int ti = tile_of_block(L, gb);
-    const TileDev T = L.tiles[ti];
-    const int lb = gb - T.cb_base;
-    const int n = T.blkroots[lb];
-    const int* list = T.rootlist + (size_t)lb * RL_CAP;
-    for (int j = lane; j < n; j += 32) {
-        int r = list[j];
-        if (mode == 0) {
-            if (T.A[r]) {
+    for (int gb = blockIdx.x * CCL_WARPS + warp; gb < L.n_cb; gb += gridDim.x * CCL_WARPS) {
+        const int ti = tile_of_block(L, gb);
+        const TileDev T = L.tiles[ti];  // by value: stores below cannot force reloads
+        const int lb = gb - T.cb_base;
+        const int n = T.blkroots[lb];
+        const int* list = T.rootlist + (size_t)lb * RL_CAP;
+        for (int j = lane; j < n; j += 32) {
+            int r = list[j];
+            if (mode == 0) {
+                if (T.A[r]) {
+                    int g = g_find(T.P, r);
+                    if (g != r) T.A[g] = 1;
+                }
+            } else if (mode == 1) {
                 int g = g_find(T.P, r);
-                if (g != r) T.A[g] = 1;
-            }
-        } else if (mode == 1) {
-            int g = g_find(T.P, r);
-            if (g != r) {
-                T.A[r] = __ldcg(T.A + g);
-                T.P[r] = g;
-            }
-        } else if (mode == 2) {
-            int g = g_find(T.P, r);
-            if (g != r) {
-                atomicAdd(T.A + g, T.A[r]);
-                T.P[r] = g;
-            }
-        } else {
-            if (T.P[r] == r) {
-                int a = T.A[r];
-                if (a >= L.amin && a <= L.amax) {
-                    int y = r / T.W, x = r - y * T.W;
-                    atomicOr(T.rootbits + (size_t)y * T.wpr + (x >> 5), 1u << (x & 31));
+                if (g != r) {
+                    T.A[r] = __ldcg(T.A + g);
+                    T.P[r] = g;
+                }
+            } else if (mode == 2) {
+                int g = g_find(T.P, r);
+                if (g != r) {
+                    atomicAdd(T.A + g, T.A[r]);
+                    T.P[r] = g;
+                }
+            } else {
+                if (T.P[r] == r) {
+                    int a = T.A[r];
+                    if (a >= L.amin && a <= L.amax) {
+                        int y = r / T.W, x = r - y * T.W;
+                        atomicOr(T.rootbits + (size_t)y * T.wpr + (x >> 5), 1u << (x & 31));
+                    }
                 }
             }
         }
@@ -500,22 +502,39 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int* tmp /*[32]*/, in
     return excl;
 }
 
-// per chunk of SCAN_CHUNK words: chunk popcount (pass 0) or word prefixes (pass 1)
-__global__ void __launch_bounds__(SCAN_CHUNK) k_scan_chunks(Launch L, int pass) {
+// per chunk of SCAN_CHUNK words: chunk popcount (pass 0) or word prefixes
+// (pass 1); each thread takes four consecutive words (one 16-byte load where
+// the chunk lies inside the bitmap: chunks start at multiples of 16 KB)
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_chunks(Launch L, int pass) {
     __shared__ int tmp[32];
     int gc = blockIdx.x;
     int ti = find_tile(L.tiles, L.ntiles, gc, &TileDev::chunk_base);
     const TileDev& T = L.tiles[ti];
     int c = gc - T.chunk_base;
-    size_t nwords = (size_t)T.H * T.wpr;
-    size_t w = (size_t)c * SCAN_CHUNK + threadIdx.x;
-    int v = w < nwords ? __popc(T.rootbits[w]) : 0;
+    const size_t nwords = (size_t)T.H * T.wpr;
+    const size_t w = (size_t)c * SCAN_CHUNK + 4 * (size_t)threadIdx.x;
+    uint32_t b[4] = {0u, 0u, 0u, 0u};
+    if (w + 4 <= nwords) {
+        const uint4 v = __ldcg(reinterpret_cast<const uint4*>(T.rootbits + w));
+        b[0] = v.x; b[1] = v.y; b[2] = v.z; b[3] = v.w;
+    } else {
+        for (int i = 0; i < 4; i++)
+            if (w + i < nwords) b[i] = T.rootbits[w + i];
+    }
+    const int p0 = __popc(b[0]), p1 = __popc(b[1]), p2 = __popc(b[2]), p3 = __popc(b[3]);
     int total = 0;
-    int excl = block_exclusive_scan(v, tmp, &total);
+    const int excl = block_exclusive_scan(p0 + p1 + p2 + p3, tmp, &total);
     if (pass == 0) {
         if (threadIdx.x == 0) T.chunksum[c] = total;
-    } else if (w < nwords) {
-        T.wordprefix[w] = excl + T.chunksum[c];
+    } else {
+        const int base = excl + T.chunksum[c];
+        const int v[4] = {base, base + p0, base + p0 + p1, base + p0 + p1 + p2};
+        if (w + 4 <= nwords) {
+            *reinterpret_cast<int4*>(T.wordprefix + w) = make_int4(v[0], v[1], v[2], v[3]);
+        } else {
+            for (int i = 0; i < 4; i++)
+                if (w + i < nwords) T.wordprefix[w + i] = v[i];
+        }
     }
 }
 
@@ -697,6 +716,9 @@ void launch_label(const Launch& L, int want_bbox, int max_objects, int sms, cuda
     k_fill_local<<<(L.n_cb + CCL_WARPS - 1) / CCL_WARPS, CCL_WARPS * 32, 0, s>>>(L);
     pf->end("fill_local", s);
     const int wg = (L.n_cb + CCL_WARPS - 1) / CCL_WARPS;
+    // the area and keep passes stride over the blocks with a few CTAs per SM;
+    // the flag passes, whose finds wait on global links, keep a warp per block
+    const int rg = std::min(wg, sms * 16);
     pf->begin("fill_merge", s);
     k_merge<4><<<wg, CCL_WARPS * 32, 0, s>>>(L);
     pf->end("fill_merge", s);
@@ -713,19 +735,19 @@ void launch_label(const Launch& L, int want_bbox, int max_objects, int sms, cuda
     k_merge<8><<<wg, CCL_WARPS * 32, 0, s>>>(L);
     pf->end("label_merge", s);
     pf->begin("label_roots_area", s);
-    k_roots<<<wg, CCL_WARPS * 32, 0, s>>>(L, 2);
+    k_roots<<<rg, CCL_WARPS * 32, 0, s>>>(L, 2);
     pf->end("label_roots_area", s);
     pf->begin("label_roots_keep", s);
-    k_roots<<<wg, CCL_WARPS * 32, 0, s>>>(L, 3);
+    k_roots<<<rg, CCL_WARPS * 32, 0, s>>>(L, 3);
     pf->end("label_roots_keep", s);
     pf->begin("scan_chunks", s);
-    k_scan_chunks<<<L.n_chunks, SCAN_CHUNK, 0, s>>>(L, 0);
+    k_scan_chunks<<<L.n_chunks, SCAN_THREADS, 0, s>>>(L, 0);
     pf->end("scan_chunks", s);
     pf->begin("scan_tiles", s);
     k_scan_tiles<<<L.ntiles, 1024, 0, s>>>(L);
     pf->end("scan_tiles", s);
     pf->begin("scan_words", s);
-    k_scan_chunks<<<L.n_chunks, SCAN_CHUNK, 0, s>>>(L, 1);
+    k_scan_chunks<<<L.n_chunks, SCAN_THREADS, 0, s>>>(L, 1);
     pf->end("scan_words", s);
     pf->begin("relabel", s);
     k_relabel<<<(L.n_cb + CCL_WARPS - 1) / CCL_WARPS, CCL_WARPS * 32, 0, s>>>(L, want_bbox);
