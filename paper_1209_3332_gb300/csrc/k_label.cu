@@ -386,8 +386,10 @@ __global__ void __launch_bounds__(CCL_WARPS * 32) k_merge(Launch L) {
 }
 
 // ---- root-list passes (grid-stride over every tile's list) -----------------------
+constexpr int HOLE_BIT = 1 << 30;  // in a block's root count between the fill and the labelling
 // mode 0: border flag of a local root -> its global root
-// mode 1: copy the global root's flag back to every local root; compress P
+// mode 1: copy the global root's flag back to every local root; compress P;
+//         mark the blocks that hold a hole (HOLE_BIT in their root count)
 //         (the labelling pass must read the flag at its own local roots: a
 //         hole's global root can become a foreground root there, whose entry
 //         that pass overwrites while other blocks would still follow links to it)
@@ -403,6 +405,7 @@ __global__ void __launch_bounds__(CCL_WARPS * 32) k_roots(Launch L, int mode) {
         const int lb = gb - T.cb_base;
         const int n = T.blkroots[lb];
         const int* list = T.rootlist + (size_t)lb * RL_CAP;
+        bool hole = false;  // mode 1: a background component of this block is a hole
         for (int j = lane; j < n; j += 32) {
             int r = list[j];
             if (mode == 0) {
@@ -412,10 +415,13 @@ __global__ void __launch_bounds__(CCL_WARPS * 32) k_roots(Launch L, int mode) {
                 }
             } else if (mode == 1) {
                 int g = g_find(T.P, r);
+                int f = T.A[r];
                 if (g != r) {
-                    T.A[r] = __ldcg(T.A + g);
+                    f = __ldcg(T.A + g);
+                    T.A[r] = f;
                     T.P[r] = g;
                 }
+                hole |= f == 0;
             } else if (mode == 2) {
                 int g = g_find(T.P, r);
                 if (g != r) {
@@ -432,6 +438,7 @@ __global__ void __launch_bounds__(CCL_WARPS * 32) k_roots(Launch L, int mode) {
                 }
             }
         }
+        if (mode == 1 && __any_sync(FULLM, hole) && lane == 0) T.blkroots[lb] = n | HOLE_BIT;
     }
 }
 
@@ -448,22 +455,25 @@ __global__ void __launch_bounds__(CCL_WARPS * 32, 12) k_label_local(Launch L) {
     const size_t wrow = (size_t)(g.y0 + lane) * T.wpr + g.bx;  // row-major (root bitmap)
     const size_t wblk = block_word(T, g, lane);                // block-major (fg, filled)
     const uint32_t fg = lane < g.bh ? T.fgbits[wblk] : 0u;
-    const uint32_t bg = lane < g.bh ? (~fg & vm) : 0u;
-    uint32_t st = bg & ~(bg << 1);
-    warp_ccl<4>(bg, st, lane, par);
-    // background runs whose component does not reach the border are holes
+    // background runs whose component does not reach the border are holes;
+    // only blocks that hold one (most hold none) label their background again
     uint32_t filled = fg;
-    for (uint32_t m = st; m; m &= m - 1) {
-        int s = __ffs(m) - 1;
-        int gr = gidx(T, g, par[lane * CB + s]);
-        if (!__ldcg(T.A + gr)) filled |= run_mask(bg, s);
+    if (__ldcg(T.blkroots + g.lb) & HOLE_BIT) {
+        const uint32_t bg = lane < g.bh ? (~fg & vm) : 0u;
+        const uint32_t sb = bg & ~(bg << 1);
+        warp_ccl<4>(bg, sb, lane, par);
+        for (uint32_t m = sb; m; m &= m - 1) {
+            int s = __ffs(m) - 1;
+            int gr = gidx(T, g, par[lane * CB + s]);
+            if (!__ldcg(T.A + gr)) filled |= run_mask(bg, s);
+        }
     }
     if (lane < g.bh) {
         T.filledbits[wblk] = filled;
         T.rootbits[wrow] = 0u;
     }
     __syncwarp();
-    st = filled & ~(filled << 1);
+    const uint32_t st = filled & ~(filled << 1);
     warp_ccl<8>(filled, st, lane, par);
     // local areas: each run adds its length to its root's entry, bits 16 and up
     for (uint32_t m = st; m; m &= m - 1) {

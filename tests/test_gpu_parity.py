@@ -86,3 +86,27 @@ def test_all_rgb_triples_through_the_whole_path(pipe):
     v = np.arange(1 << 24, dtype=np.uint32)
     rgb = np.stack([(v >> 16) & 255, (v >> 8) & 255, v & 255], -1).astype(np.uint8).reshape(4096, 4096, 3)
     check(pipe, rgb)
+
+
+def ring_tile(W=620, H=530):
+    """White tile with black annuli: each annulus is a flat dome of the
+    hematoxylin plane, so it is foreground and its inside a hole -- holes of
+    2 to 230 pixels across, inside one 32x32 labelling block or spanning
+    many, nested rings, and rings cut by the tile border (their inside
+    touches the border and is no hole)."""
+    yy, xx = np.mgrid[:H, :W]
+    rgb = np.full((H, W, 3), 255, np.uint8)
+    rings = [(40, 40, 2, 4), (31, 95, 5, 3), (100, 63, 9, 4), (160, 160, 14, 5), (300, 120, 30, 4),
+             (300, 120, 12, 3), (420, 330, 115, 6), (420, 330, 60, 5), (420, 330, 20, 3), (5, 300, 25, 4),
+             (600, 500, 40, 5), (250, 480, 33, 4), (96, 400, 31, 2)]
+    for cx, cy, r, t in rings:
+        d2 = (xx - cx) ** 2 + (yy - cy) ** 2
+        rgb[(d2 >= r * r) & (d2 < (r + t) ** 2)] = 0
+    return rgb
+
+
+def test_holes_of_every_size(pipe):
+    rgb = ring_tile()
+    g, r = check(pipe, rgb)
+    holes = int(r["filled"].sum()) - int(r["fg"].sum())
+    assert holes > 20000  # the rings' insides were filled
