@@ -4,6 +4,7 @@ exactly once, groups respect their size and the limit of groups in flight,
 refused admissions are retried, and with a backlog the cost order takes the
 most expensive pool tiles first."""
 import random
+import types
 import time
 
 import numpy as np
@@ -16,6 +17,7 @@ class FakePipe:
     pixels; one submission in ten is refused."""
 
     def __init__(self, seed):
+        self.params = types.SimpleNamespace(hbm_budget_bytes=2 << 20)  # room for the two groups
         self.rng = random.Random(seed)
         self.n = 0
         self.running = {}
@@ -36,6 +38,11 @@ class FakePipe:
             return None
         del self.running[ticket]
         return [{"status": 0, "t_done_ms": time.monotonic() * 1000.0} for _ in range(k)]
+
+    def serve_memory(self):
+        # contexts of the groups in flight, 1 MB each
+        return {"allocated": len(self.running) << 20, "in_flight": len(self.running) << 20,
+                "contexts": len(self.running)}
 
 
 def pool():
