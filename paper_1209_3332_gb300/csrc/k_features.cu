@@ -16,8 +16,9 @@
 // throughput is scarce on this part (about 2 FMA per cycle per SM), so the
 // finishing math is FP32 arranged so that no step cancels: every
 // co-occurrence statistic is a ratio of exact integers, entropy is a sum of
-// non-negative terms, and the gradient variance is taken on shifted values
-// e = g - c computed as (m2 - c^2) / (g + c) from the exact integer m2.
+// non-negative terms, and the gradient mean and variance come from one pass
+// of Welford updates per lane, the lanes combined pairwise (a sum of
+// non-negative terms).
 #include <cmath>
 #include <mutex>
 
@@ -71,16 +72,6 @@ __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULLF, v, o);
     return v;
-}
-
-// g - c for the gradient magnitude g = sqrt(m2) and a shift c close to the
-// object's mean magnitude, with c^2 = c2h + c2l exactly: the numerator
-// m2 - c^2 is formed from exact terms, so the result carries a few ulps of
-// its own size however close g is to c.
-__device__ __forceinline__ float shifted_mag(int m2, float c, float c2h, float c2l) {
-    const float g = sqrtf((float)m2);
-    if (c == 0.f) return g;
-    return __fdiv_rn(__fsub_rn(__fsub_rn((float)m2, c2h), c2l), __fadd_rn(g, c));
 }
 
 constexpr int STAGE_PX = 5120;  // staged region (box + 1-px margin) capacity per warp
@@ -152,7 +143,7 @@ __device__ __forceinline__ void object_features_impl(const ObjJob& J, int obj, i
     };
     int cnt = 0, per = 0, mn = 255, mx = 0, gmn = 0x7fffffff, gmx = 0;
     long long S = 0, Q = 0;
-    float gs = 0.f;
+    float wm = 0.f, wq = 0.f;  // this lane's running mean and sum of squared deviations of |Sobel|
     const int odx[4] = {1, 0, 1, 1}, ody[4] = {0, 1, 1, -1};
     // lane walks the box row-major with stride 32, advancing (y, x) without divisions
     int y = box.y + lane / bw, x = box.x + lane % bw;
@@ -172,7 +163,11 @@ __device__ __forceinline__ void object_features_impl(const ObjJob& J, int obj, i
         per += (cx == 0 || !IN(cy, cx - 1));
         per += (cx == W - 1 || !IN(cy, cx + 1));
         const int m2 = SOBEL(cy, cx);
-        gs = __fadd_rn(gs, sqrtf((float)m2));
+        {  // Welford's update
+            const float gv = sqrtf((float)m2), d = __fsub_rn(gv, wm);
+            wm = __fadd_rn(wm, __fdiv_rn(d, (float)cnt));
+            wq = __fmaf_rn(d, __fsub_rn(gv, wm), wq);
+        }
         gmn = min(gmn, m2);
         gmx = max(gmx, m2);
 #pragma unroll
@@ -188,30 +183,33 @@ __device__ __forceinline__ void object_features_impl(const ObjJob& J, int obj, i
     const long long Per = warp_sum<long long>(per);
     const int Mn = __reduce_min_sync(FULLF, mn), Mx = __reduce_max_sync(FULLF, mx);
     const int Gmn = __reduce_min_sync(FULLF, gmn), Gmx = __reduce_max_sync(FULLF, gmx);
-    const float Gs = warp_sum<float>(gs);
+    // the lanes' (count, mean, squared deviations) combined pairwise (Chan,
+    // Golub, LeVeque): every term of the combined sum is non-negative
+    float gn = (float)cnt, gm = wm, gq = wq;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float nb = __shfl_xor_sync(FULLF, gn, o), mb = __shfl_xor_sync(FULLF, gm, o);
+        const float qb = __shfl_xor_sync(FULLF, gq, o);
+        // both lanes of a pair form the same sum: the lower lane's part first
+        const bool lo = (lane & o) == 0;
+        const float na = lo ? gn : nb, ma = lo ? gm : mb, qa = lo ? gq : qb;
+        const float n2 = lo ? nb : gn, m2v = lo ? mb : gm, q2 = lo ? qb : gq;
+        const float n = __fadd_rn(na, n2);
+        if (n > 0.f) {
+            const float f = __fdiv_rn(n2, n), d = __fsub_rn(m2v, ma);
+            gm = __fmaf_rn(d, f, ma);
+            gq = __fadd_rn(__fadd_rn(qa, q2), __fmul_rn(__fmul_rn(d, d), __fmul_rn(na, f)));
+        } else {
+            gm = 0.f;
+            gq = 0.f;
+        }
+        gn = n;
+    }
     if (N == 0) {
         if (lane < NFEAT) out[lane] = 0.f;
         __syncwarp();
         return;
     }
-    // second pass: the magnitudes shifted by their approximate mean c; the mean
-    // is c + E[e] and the variance E[e^2] - E[e]^2, where E[e] is tiny, so
-    // nothing cancels
-    const float c = __fdiv_rn(Gs, (float)N);
-    const float c2h = c * c, c2l = fmaf(c, c, -c2h);
-    float se = 0.f, see = 0.f;
-    y = box.y + lane / bw;
-    x = box.x + lane % bw;
-    for (long long idx = lane; idx < npx; idx += 32) {
-        const int cy = y, cx = x;
-        x += 32;
-        while (x > box.z) { x -= bw; y++; }
-        if (!IN(cy, cx)) continue;
-        const float e = shifted_mag(SOBEL(cy, cx), c, c2h, c2l);
-        se = __fadd_rn(se, e);
-        see = fmaf(e, e, see);
-    }
-    const double Se = warp_sum<double>((double)se), See = warp_sum<double>((double)see);
     __syncwarp();
     // co-occurrence statistics per offset: lanes hold bins lane and lane+32.
     // With counts C_ij and T = sum C_ij: contrast = sum (i-j)^2 C / T, energy =
@@ -263,9 +261,8 @@ __device__ __forceinline__ void object_features_impl(const ObjJob& J, int obj, i
         f[3] = sqrt((double)var_num) / n;
         f[4] = Mn;
         f[5] = Mx;
-        const double me = __ddiv_rn(Se, n);
-        f[6] = __dadd_rn((double)c, me);
-        f[7] = sqrt(fmax(__dsub_rn(__ddiv_rn(See, n), __dmul_rn(me, me)), 0.0));
+        f[6] = (double)gm;
+        f[7] = sqrt(__ddiv_rn((double)gq, n));
         f[8] = sqrt((double)Gmn);
         f[9] = sqrt((double)Gmx);
         for (int k = 0; k < 5; k++) f[10 + k] = used ? __fdiv_rn(acc[k], (float)used) : 0.f;
