@@ -113,8 +113,14 @@ void launch_deconv(const Launch& L, cudaStream_t s, Profiler* pf) {
     int sms = 0, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    // one wave of resident CTAs (the 32 KB table limits them to about six per
+    // SM); the per-CTA table setup is amortised over a grid-stride loop
+    static int per_sm = 0;
+    if (per_sm == 0 && (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_deconv, 256, 0) != cudaSuccess ||
+                        per_sm < 1))
+        per_sm = 1;
     int blocks = (L.n_px + 255) / 256;
-    if (blocks > sms * 8) blocks = sms * 8;  // the per-block table setup is amortised over a grid-stride loop
+    if (blocks > sms * per_sm) blocks = sms * per_sm;
     cudaMemsetAsync(L.rt_src, 0, sizeof(int) * (size_t)L.n_rt, s);
     k_deconv<<<blocks, 256, 0, s>>>(L.tiles, L.ntiles, L.n_px, L.h, L.rt_src);
     pf->end("deconv", s);
