@@ -610,23 +610,38 @@ __global__ void __launch_bounds__(CCL_WARPS * 32, 12) k_relabel(Launch L, int wa
         }
     }
     __syncwarp();
-    // runs: label from the root's entry; kept bits and object boxes
+    // runs: label from the root's entry; kept bits and object boxes.  The
+    // lanes take their k-th runs together, so the runs of one object in this
+    // block meet their box with one set of atomics from the group's first lane.
     uint32_t kept = 0;
     const int gy = g.y0 + lane;
-    for (uint32_t m = st; m; m &= m - 1) {
-        const int s = __ffs(m) - 1;
-        const int v = par[lane * CB + s];
-        const int lab = (v & LAB_FLAG) ? (v & ~LAB_FLAG) : (par[v] & ~LAB_FLAG);
-        if (lab) {
-            const uint32_t rm = run_mask(filled, s);
-            kept |= rm;
-            if (want_bbox && lab <= T.feats_cap) {
-                const int e = 31 - __clz(rm);
-                int4* b = T.bbox + (lab - 1);
-                atomicMin(&b->x, g.x0 + s);
-                atomicMax(&b->z, g.x0 + e);
-                atomicMin(&b->y, gy);
-                atomicMax(&b->w, gy);
+    for (uint32_t m = st; __any_sync(FULLM, m != 0u);) {
+        int lab = 0, xs = 0, xe = 0;
+        if (m) {
+            const int s = __ffs(m) - 1;
+            m &= m - 1;
+            const int v = par[lane * CB + s];
+            lab = (v & LAB_FLAG) ? (v & ~LAB_FLAG) : (par[v] & ~LAB_FLAG);
+            if (lab) {
+                const uint32_t rm = run_mask(filled, s);
+                kept |= rm;
+                xs = g.x0 + s;
+                xe = g.x0 + 31 - __clz(rm);
+            }
+        }
+        if (want_bbox) {
+            const bool box = lab != 0 && lab <= T.feats_cap;
+            const unsigned grp = __match_any_sync(FULLM, box ? lab : 0);
+            if (box) {
+                const int x_lo = __reduce_min_sync(grp, xs), x_hi = __reduce_max_sync(grp, xe);
+                const int y_lo = __reduce_min_sync(grp, gy), y_hi = __reduce_max_sync(grp, gy);
+                if (lane == __ffs(grp) - 1) {
+                    int4* b = T.bbox + (lab - 1);
+                    atomicMin(&b->x, x_lo);
+                    atomicMax(&b->z, x_hi);
+                    atomicMin(&b->y, y_lo);
+                    atomicMax(&b->w, y_hi);
+                }
             }
         }
     }
