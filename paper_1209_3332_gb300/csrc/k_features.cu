@@ -77,15 +77,14 @@ __device__ __forceinline__ T warp_sum(T v) {
 constexpr int STAGE_PX = 5120;  // staged region (box + 1-px margin) capacity per warp
 
 // Features of object `obj` by one warp; glcm: this warp's 4x64 counters;
-// smask / shem: this warp's staging buffers.  When the object's box plus a
+// spx: this warp's staging buffer.  When the object's box plus a
 // 1-pixel margin (clipped to the image) fits, it is staged once with
 // coalesced row loads as an in-object byte mask and hem8, and every
 // neighbourhood read comes from shared memory; larger boxes read global
 // memory directly.  Sobel neighbours (clamped to the image), 4-neighbours and
 // co-occurrence partners of box pixels all lie inside that region.
 template <bool STAGED>
-__device__ __forceinline__ void object_features_impl(const ObjJob& J, int obj, int* glcm, uint8_t* smask,
-                                                     uint8_t* shem) {
+__device__ __forceinline__ void object_features_impl(const ObjJob& J, int obj, int* glcm, uint16_t* spx) {
     const int lane = threadIdx.x & 31;
     const int l = obj + 1;
     const int4 box = J.bbox[obj];
@@ -120,63 +119,59 @@ __device__ __forceinline__ void object_features_impl(const ObjJob& J, int obj, i
             }
 #pragma unroll
             for (int u = 0; u < 4; u++)
-                if (at[u] >= 0) {
-                    smask[at[u]] = lab[u] == l;
-                    shem[at[u]] = (uint8_t)hv[u];
-                }
+                if (at[u] >= 0) spx[at[u]] = (uint16_t)(hv[u] | (lab[u] == l ? 0x100 : 0));
         }
     }
     __syncwarp();
-    auto IN = [&](int y, int x) -> bool {
-        return staged ? smask[(y - ry0) * rw + (x - rx0)] != 0 : J.labels[(size_t)y * W + x] == l;
-    };
-    auto HV = [&](int y, int x) -> int {
-        return staged ? (int)shem[(y - ry0) * rw + (x - rx0)] : (int)J.hem8[(size_t)y * W + x];
-    };
-    auto SOBEL = [&](int y, int x) -> int {
-        const int ym = max(y - 1, 0), yp = min(y + 1, H - 1), xm = max(x - 1, 0), xp = min(x + 1, W - 1);
-        const int a = HV(ym, xm), b = HV(ym, x), c = HV(ym, xp), d = HV(y, xm), f = HV(y, xp);
-        const int g = HV(yp, xm), h = HV(yp, x), i = HV(yp, xp);
-        const int gx = (c + 2 * f + i) - (a + 2 * d + g);
-        const int gy = (g + 2 * h + i) - (a + 2 * b + c);
-        return gx * gx + gy * gy;
+    // pixel (y, x) of the region as hem8 | (in object) << 8: the 3x3
+    // neighbourhood of a pixel serves its Sobel sums, its perimeter test and
+    // its co-occurrence partners
+    auto PX = [&](int y, int x) -> uint32_t {
+        if (staged) return spx[(y - ry0) * rw + (x - rx0)];
+        const size_t o = (size_t)y * W + x;
+        return (uint32_t)J.hem8[o] | (J.labels[o] == l ? 0x100u : 0u);
     };
     int cnt = 0, per = 0, mn = 255, mx = 0, gmn = 0x7fffffff, gmx = 0;
     long long S = 0, Q = 0;
     float wm = 0.f, wq = 0.f;  // this lane's running mean and sum of squared deviations of |Sobel|
-    const int odx[4] = {1, 0, 1, 1}, ody[4] = {0, 1, 1, -1};
     // lane walks the box row-major with stride 32, advancing (y, x) without divisions
     int y = box.y + lane / bw, x = box.x + lane % bw;
     for (long long idx = lane; idx < npx; idx += 32) {
         const int cy = y, cx = x;
         x += 32;
         while (x > box.z) { x -= bw; y++; }
-        if (!IN(cy, cx)) continue;
-        const int v = HV(cy, cx);
+        const uint32_t pc = PX(cy, cx);
+        if (!(pc >> 8)) continue;
+        const int v = (int)(pc & 0xffu);
         cnt++;
         S += v;
         Q += v * v;
         mn = min(mn, v);
         mx = max(mx, v);
-        per += (cy == 0 || !IN(cy - 1, cx));
-        per += (cy == H - 1 || !IN(cy + 1, cx));
-        per += (cx == 0 || !IN(cy, cx - 1));
-        per += (cx == W - 1 || !IN(cy, cx + 1));
-        const int m2 = SOBEL(cy, cx);
+        // the 8 neighbours, clamped to the image (the replicated border of the Sobel sums)
+        const int ym = max(cy - 1, 0), yp = min(cy + 1, H - 1), xm = max(cx - 1, 0), xp = min(cx + 1, W - 1);
+        const uint32_t a = PX(ym, xm), b = PX(ym, cx), c = PX(ym, xp), d = PX(cy, xm), f = PX(cy, xp);
+        const uint32_t g = PX(yp, xm), h = PX(yp, cx), i = PX(yp, xp);
+        per += (cy == 0 || !(b >> 8));
+        per += (cy == H - 1 || !(h >> 8));
+        per += (cx == 0 || !(d >> 8));
+        per += (cx == W - 1 || !(f >> 8));
+        const int gx = (int)((c & 0xffu) + 2 * (f & 0xffu) + (i & 0xffu)) - (int)((a & 0xffu) + 2 * (d & 0xffu) + (g & 0xffu));
+        const int gy = (int)((g & 0xffu) + 2 * (h & 0xffu) + (i & 0xffu)) - (int)((a & 0xffu) + 2 * (b & 0xffu) + (c & 0xffu));
+        const int m2 = gx * gx + gy * gy;
         {  // Welford's update
-            const float gv = sqrtf((float)m2), d = __fsub_rn(gv, wm);
-            wm = __fadd_rn(wm, __fdiv_rn(d, (float)cnt));
-            wq = __fmaf_rn(d, __fsub_rn(gv, wm), wq);
+            const float gv = sqrtf((float)m2), dv = __fsub_rn(gv, wm);
+            wm = __fadd_rn(wm, __fdiv_rn(dv, (float)cnt));
+            wq = __fmaf_rn(dv, __fsub_rn(gv, wm), wq);
         }
         gmn = min(gmn, m2);
         gmx = max(gmx, m2);
-#pragma unroll
-        for (int o = 0; o < 4; o++) {
-            const int yy = cy + ody[o], xx = cx + odx[o];
-            if (yy < 0 || yy >= H || xx >= W) continue;
-            if (!IN(yy, xx)) continue;
-            atomicAdd(&glcm[o * 64 + (v >> 5) * 8 + (HV(yy, xx) >> 5)], 1);
-        }
+        // co-occurrence partners (x + 1, y), (x, y + 1), (x + 1, y + 1), (x + 1, y - 1) inside the image
+        const int vb = (v >> 5) * 8;
+        if (cx + 1 < W && (f >> 8)) atomicAdd(&glcm[0 * 64 + vb + ((f & 0xffu) >> 5)], 1);
+        if (cy + 1 < H && (h >> 8)) atomicAdd(&glcm[1 * 64 + vb + ((h & 0xffu) >> 5)], 1);
+        if (cy + 1 < H && cx + 1 < W && (i >> 8)) atomicAdd(&glcm[2 * 64 + vb + ((i & 0xffu) >> 5)], 1);
+        if (cy > 0 && cx + 1 < W && (c >> 8)) atomicAdd(&glcm[3 * 64 + vb + ((c & 0xffu) >> 5)], 1);
     }
     const long long N = warp_sum<long long>(cnt);
     const long long Ssum = warp_sum<long long>(S), Qsum = warp_sum<long long>(Q);
@@ -274,16 +269,15 @@ __device__ __forceinline__ void object_features_impl(const ObjJob& J, int obj, i
 // boxes larger than the stage read global memory; that rare path is kept out
 // of line so the common one stays small in the instruction cache
 __device__ __noinline__ void object_features_global(const ObjJob& J, int obj, int* glcm) {
-    object_features_impl<false>(J, obj, glcm, nullptr, nullptr);
+    object_features_impl<false>(J, obj, glcm, nullptr);
 }
 
-__device__ __forceinline__ void object_features(const ObjJob& J, int obj, int* glcm, uint8_t* smask,
-                                                uint8_t* shem) {
+__device__ __forceinline__ void object_features(const ObjJob& J, int obj, int* glcm, uint16_t* spx) {
     const int4 box = J.bbox[obj];
     const int rx0 = max(box.x - 1, 0), ry0 = max(box.y - 1, 0);
     const long long rw = (long long)min(box.z + 1, J.W - 1) - rx0 + 1, rh = (long long)min(box.w + 1, J.H - 1) - ry0 + 1;
     if (rw > 0 && rh > 0 && rw * rh <= STAGE_PX)
-        object_features_impl<true>(J, obj, glcm, smask, shem);
+        object_features_impl<true>(J, obj, glcm, spx);
     else
         object_features_global(J, obj, glcm);
 }
@@ -293,8 +287,7 @@ constexpr int FW = 4;  // object warps per CTA
 // Plain form: objects [0, K) of one tile, one warp each.
 struct ObjSmem {
     int glcm[4 * 64];
-    uint8_t mask[STAGE_PX];
-    uint8_t hem[STAGE_PX];
+    uint16_t px[STAGE_PX];  // hem8 | (in object) << 8
 };
 
 __global__ void __launch_bounds__(FW * 32) k_fobj_plain(ObjJob J, int K) {
@@ -302,7 +295,7 @@ __global__ void __launch_bounds__(FW * 32) k_fobj_plain(ObjJob J, int K) {
     const int warp = threadIdx.x >> 5;
     ObjSmem& S = sm[warp];
     for (int obj = blockIdx.x * FW + warp; obj < K; obj += gridDim.x * FW)
-        object_features(J, obj, S.glcm, S.mask, S.hem);
+        object_features(J, obj, S.glcm, S.px);
 }
 
 __global__ void k_obj_prefix(Launch L) {
@@ -338,7 +331,7 @@ __global__ void __launch_bounds__(FW * 32) k_fobj_batched(Launch L) {
         const int t = find_tile(L.tiles, L.ntiles, item, &TileDev::obj_base);
         const TileDev& T = L.tiles[t];
         ObjJob J{T.hem8, T.labels, T.W, T.H, T.bbox, T.feats};
-        object_features(J, item - T.obj_base, S.glcm, S.mask, S.hem);
+        object_features(J, item - T.obj_base, S.glcm, S.px);
     }
 }
 
