@@ -136,10 +136,16 @@ __device__ __forceinline__ bool ws_nb_in(const B& b, int q) {
 
 template <class B>
 __device__ __forceinline__ int ws_find(const B& b, int x) {
+    // path halving: a non-root is pointed at its grandparent (an ancestor,
+    // whatever concurrent unions do, so the forest stays valid); without it
+    // the walks over a plateau of a thousand pixels grow with its size
+    constexpr typename B::Wt IDX = ((typename B::Wt)1 << B::SH) - 1;
     for (;;) {
-        const int p = (int)(b.w[x] & (((typename B::Wt)1 << B::SH) - 1));
+        const int p = (int)(b.w[x] & IDX);
         if (p == x) return x;
-        x = p;
+        const int gp = (int)(b.w[p] & IDX);
+        if (gp != p) b.w[x] = (typename B::Wt)gp;
+        x = gp;
     }
 }
 
