@@ -79,8 +79,8 @@ constexpr int STAGE_PX = 5120;  // staged region (box + 1-px margin) capacity pe
 // Features of object `obj` by one warp; glcm: this warp's 4x64 counters;
 // spx: this warp's staging buffer.  When the object's box plus a
 // 1-pixel margin (clipped to the image) fits, it is staged once with
-// coalesced row loads as an in-object byte mask and hem8, and every
-// neighbourhood read comes from shared memory; larger boxes read global
+// coalesced row loads as one 16-bit word per pixel (hem8 and an in-object
+// bit), and every neighbourhood read comes from shared memory; larger boxes read global
 // memory directly.  Sobel neighbours (clamped to the image), 4-neighbours and
 // co-occurrence partners of box pixels all lie inside that region.
 template <bool STAGED>
