@@ -575,45 +575,69 @@ __device__ __forceinline__ bool border_can_raise(WarpTile& S, int lane) {
 __device__ __forceinline__ int border_r(WarpTile& S, int s, int p) {
     return s == 0 ? rpx(S, 0, p) : s == 1 ? rpx(S, RT - 1, p) : s == 2 ? rpx(S, p, 0) : rpx(S, p, RT - 1);
 }
-__device__ __forceinline__ void side_coord(int s, int h, int& hy, int& hx) {
-    hy = s == 0 ? -1 : s == 1 ? RT : h;
-    hx = s == 2 ? -1 : s == 3 ? RT : h;
-}
 __device__ __forceinline__ void side_requests(WarpTile& S, int lane) {
-#pragma unroll 1
-    for (int s = 0; s < 4; s++) {
-        auto cv = [&](int p) -> int {  // border value at p if it changed since the last requests, else 0
-            if (p < 0 || p >= RT) return 0;
-            const int v = border_r(S, s, p);
-            return v != S.B0[s][p] ? v : 0;
-        };
-        auto raises = [&](int m, int h) -> bool {
-            int hy, hx;
-            side_coord(s, h, hy, hx);
-            return min(m, halo_m(S, hy, hx)) > halo_r(S, hy, hx);
-        };
-        bool line = false;
+    // lane l holds border pixels 2l and 2l + 1 of every side: one block word
+    // of R (top: block (0, l) bytes 0, 1; bottom: block (NB-1, l) bytes 2, 3;
+    // left: block (l, 0) bytes 0, 2; right: block (l, NB-1) bytes 1, 3); the
+    // changed values of the pixels beyond its pair come from the next lanes
+    const uint32_t wt = S.B[lane].x, wb = S.B[(NB - 1) * BS + lane].x;
+    const uint32_t wl = S.B[lane * BS].x, wr = S.B[lane * BS + NB - 1].x;
+    const int p0 = 2 * lane, p1 = 2 * lane + 1;
 #pragma unroll
-        for (int u = 0; u < RT / 32; u++) {
-            const int h = lane * (RT / 32) + u;
-            line |= raises(max(max(cv(h - 1), cv(h)), cv(h + 1)), h);
+    for (int s = 0; s < 4; s++) {
+        const uint32_t w = s == 0 ? wt : s == 1 ? wb : s == 2 ? wl : wr;
+        const int sh0 = s == 0 ? 0 : s == 1 ? 16 : s == 2 ? 0 : 8;
+        const int sh1 = s == 0 ? 8 : s == 1 ? 24 : s == 2 ? 16 : 24;
+        const int v0 = (int)((w >> sh0) & 0xffu), v1 = (int)((w >> sh1) & 0xffu);
+        // border values changed since the last requests (else 0)
+        const int c0 = v0 != (int)S.B0[s][p0] ? v0 : 0, c1 = v1 != (int)S.B0[s][p1] ? v1 : 0;
+        int cl = __shfl_up_sync(FULL, c1, 1), cr = __shfl_down_sync(FULL, c0, 1);
+        if (lane == 0) cl = 0;
+        if (lane == 31) cr = 0;
+        const int m0 = max(max(cl, c0), c1), m1 = max(max(c0, c1), cr);
+        // the halo pixels facing p0, p1: R and M
+        int hr0, hr1, hm0, hm1;
+        if (s == 0) {
+            hr0 = (int)(S.HRow[0][p0 + 1] & 0xffu); hr1 = (int)(S.HRow[0][p1 + 1] & 0xffu);
+            hm0 = S.HMr[0][p0 + 1]; hm1 = S.HMr[0][p1 + 1];
+        } else if (s == 1) {
+            hr0 = (int)(S.HRow[1][p0 + 1] >> 16); hr1 = (int)(S.HRow[1][p1 + 1] >> 16);
+            hm0 = S.HMr[1][p0 + 1]; hm1 = S.HMr[1][p1 + 1];
+        } else if (s == 2) {
+            hr0 = (int)(S.HC[0][p0 + 1] & 0xffu); hr1 = (int)(S.HC[0][p1 + 1] & 0xffu);
+            hm0 = S.HMc[0][p0 + 1]; hm1 = S.HMc[0][p1 + 1];
+        } else {
+            hr0 = (int)(S.HC[1][p0 + 1] >> 16); hr1 = (int)(S.HC[1][p1 + 1] >> 16);
+            hm0 = S.HMc[1][p0 + 1]; hm1 = S.HMc[1][p1 + 1];
         }
-        const bool lo = lane == 0 && raises(cv(0), -1);
-        const bool hi = lane == 31 && raises(cv(RT - 1), RT);
+        const bool line = min(m0, hm0) > hr0 || min(m1, hm1) > hr1;
+        // the corners (-1 and RT along the side) belong to the diagonal
+        // neighbours; corner pixels are read from the halo rows
+        const int kl = s == 1 ? 1 : 0, kh = s == 0 ? 0 : 1;        // halo row of the low / high corner
+        const int il = s == 3 ? RT + 1 : 0, ih = s == 2 ? 0 : RT + 1;  // its index in that row
+        bool lo = false, hi = false;
+        if (lane == 0) {
+            const int r = kl ? (int)(S.HRow[1][il] >> 16) : (int)(S.HRow[0][il] & 0xffu);
+            lo = min(c0, (int)S.HMr[kl][il]) > r;
+        }
+        if (lane == 31) {
+            const int r = kh ? (int)(S.HRow[1][ih] >> 16) : (int)(S.HRow[0][ih] & 0xffu);
+            hi = min(c1, (int)S.HMr[kh][ih]) > r;
+        }
         const bool anyl = __any_sync(FULL, line), anylo = __any_sync(FULL, lo), anyhi = __any_sync(FULL, hi);
         if (lane == 0) {
             // corners: top -> UL, UR; bottom -> DL, DR; left -> UL, DL; right -> UR, DR
-            const int cl = s == 0 ? 4 : s == 1 ? 6 : s == 2 ? 4 : 5;
-            const int ch = s == 0 ? 5 : s == 1 ? 7 : s == 2 ? 6 : 7;
+            const int fl = s == 0 ? 4 : s == 1 ? 6 : s == 2 ? 4 : 5;
+            const int fh = s == 0 ? 5 : s == 1 ? 7 : s == 2 ? 6 : 7;
             if (anyl) S.flags[s] = 1;
-            if (anylo) S.flags[cl] = 1;
-            if (anyhi) S.flags[ch] = 1;
+            if (anylo) S.flags[fl] = 1;
+            if (anyhi) S.flags[fh] = 1;
         }
+        // the side's border becomes the reference for the next requests
+        S.B0[s][p0] = (uint8_t)v0;
+        S.B0[s][p1] = (uint8_t)v1;
     }
     __syncwarp();
-#pragma unroll 1
-    for (int s = 0; s < 4; s++)
-        for (int p = lane; p < RT; p += 32) S.B0[s][p] = (uint8_t)border_r(S, s, p);
 }
 
 __global__ void __launch_bounds__(32, RECON_MIN_BLOCKS) k_recon(Launch L) {
