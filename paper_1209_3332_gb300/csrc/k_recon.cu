@@ -548,19 +548,36 @@ __device__ __forceinline__ bool can_raise(const WarpTile& S, int lane) {
 // tile's interior was at a fixed point before the halo grew, only border
 // pixels can have become raisable, so this is the exact test in that case.
 __device__ __forceinline__ bool border_can_raise(WarpTile& S, int lane) {
+    // lane l: border pixels 2l and 2l + 1 of each side from one block word of
+    // R and one of M, and the four halo pixels around them (the halo lines
+    // hold the corners too, with the same values as the halo rows)
+    const uint2 bt = S.B[lane], bb = S.B[(NB - 1) * BS + lane];
+    const uint2 bl = S.B[lane * BS], br = S.B[lane * BS + NB - 1];
+    const int i = 2 * lane;
+    auto raisable = [](int h0, int h1, int h2, uint32_t r, uint32_t m, int sh) -> bool {
+        const int mh = max(max(h0, h1), h2);
+        return min(mh, (int)((m >> sh) & 0xffu)) > (int)((r >> sh) & 0xffu);
+    };
     bool v = false;
-#pragma unroll
-    for (int k = 0; k < 2; k++) {
-        const int p = 2 * lane + k;
-#pragma unroll
-        for (int s = 0; s < 2; s++) {
-            const int hy = s ? RT : -1, by = s ? RT - 1 : 0;
-            const int mh = __vimax3_s32(halo_r(S, hy, p - 1), halo_r(S, hy, p), halo_r(S, hy, p + 1));
-            v |= min(mh, (int)mpx(S, by, p)) > (int)rpx(S, by, p);
-            const int hx = s ? RT : -1, bx = s ? RT - 1 : 0;
-            const int mv = __vimax3_s32(halo_r(S, p - 1, hx), halo_r(S, p, hx), halo_r(S, p + 1, hx));
-            v |= min(mv, (int)mpx(S, p, bx)) > (int)rpx(S, p, bx);
-        }
+    {
+        const int a = S.HRow[0][i] & 0xff, b = S.HRow[0][i + 1] & 0xff, c = S.HRow[0][i + 2] & 0xff,
+                  d = S.HRow[0][i + 3] & 0xff;
+        v |= raisable(a, b, c, bt.x, bt.y, 0) | raisable(b, c, d, bt.x, bt.y, 8);  // top row
+    }
+    {
+        const int a = S.HRow[1][i] >> 16, b = S.HRow[1][i + 1] >> 16, c = S.HRow[1][i + 2] >> 16,
+                  d = S.HRow[1][i + 3] >> 16;
+        v |= raisable(a, b, c, bb.x, bb.y, 16) | raisable(b, c, d, bb.x, bb.y, 24);  // bottom row
+    }
+    {
+        const int a = S.HC[0][i] & 0xff, b = S.HC[0][i + 1] & 0xff, c = S.HC[0][i + 2] & 0xff,
+                  d = S.HC[0][i + 3] & 0xff;
+        v |= raisable(a, b, c, bl.x, bl.y, 0) | raisable(b, c, d, bl.x, bl.y, 16);  // left column
+    }
+    {
+        const int a = S.HC[1][i] >> 16, b = S.HC[1][i + 1] >> 16, c = S.HC[1][i + 2] >> 16,
+                  d = S.HC[1][i + 3] >> 16;
+        v |= raisable(a, b, c, br.x, br.y, 8) | raisable(b, c, d, br.x, br.y, 24);  // right column
     }
     return __any_sync(FULL, v);
 }
@@ -572,9 +589,6 @@ __device__ __forceinline__ bool border_can_raise(WarpTile& S, int lane) {
 // to h can raise it.  h = -1 and h = RT are the halo corners, which belong
 // to the diagonal neighbours.  The side's border then becomes the reference
 // for the next requests.
-__device__ __forceinline__ int border_r(WarpTile& S, int s, int p) {
-    return s == 0 ? rpx(S, 0, p) : s == 1 ? rpx(S, RT - 1, p) : s == 2 ? rpx(S, p, 0) : rpx(S, p, RT - 1);
-}
 __device__ __forceinline__ void side_requests(WarpTile& S, int lane) {
     // lane l holds border pixels 2l and 2l + 1 of every side: one block word
     // of R (top: block (0, l) bytes 0, 1; bottom: block (NB-1, l) bytes 2, 3;
@@ -672,10 +686,20 @@ __global__ void __launch_bounds__(32, RECON_MIN_BLOCKS) k_recon(Launch L) {
         __syncwarp();
         load_tile(S, Rg, Mg, W, H, x0, y0, lane);
         __syncwarp();
-        // the border as loaded is the reference for the first requests
-#pragma unroll 1
-        for (int s = 0; s < 4; s++)
-            for (int p = lane; p < RT; p += 32) S.B0[s][p] = (uint8_t)border_r(S, s, p);
+        // the border as loaded is the reference for the first requests (lane l:
+        // border pixels 2l, 2l + 1 of each side, from one block word per side)
+        {
+            const uint32_t wt = S.B[lane].x, wb = S.B[(NB - 1) * BS + lane].x;
+            const uint32_t wl = S.B[lane * BS].x, wr = S.B[lane * BS + NB - 1].x;
+            S.B0[0][2 * lane] = (uint8_t)wt;
+            S.B0[0][2 * lane + 1] = (uint8_t)(wt >> 8);
+            S.B0[1][2 * lane] = (uint8_t)(wb >> 16);
+            S.B0[1][2 * lane + 1] = (uint8_t)(wb >> 24);
+            S.B0[2][2 * lane] = (uint8_t)wl;
+            S.B0[2][2 * lane + 1] = (uint8_t)(wl >> 16);
+            S.B0[3][2 * lane] = (uint8_t)(wr >> 8);
+            S.B0[3][2 * lane + 1] = (uint8_t)(wr >> 24);
+        }
         __syncwarp();
         for (;;) {
             int nr = 0;
