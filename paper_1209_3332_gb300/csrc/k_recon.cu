@@ -432,7 +432,7 @@ __device__ __forceinline__ void row_sweeps(WarpTile& S, int lane) {
         S.B[ju * BS + lane].x = __byte_perm(u0, u1, PACK_ROWS);
     };
     uint2 bd = S.B[lane], bu = S.B[(NB - 1) * BS + lane];
-#pragma unroll 1
+#pragma unroll 3
     for (int k = 0; k < NB / 2 - 1; k++) {  // first half: disjoint rows, next blocks loaded one step ahead
         const uint2 nd = S.B[(k + 1) * BS + lane], nu = S.B[(NB - 2 - k) * BS + lane];
         step(bd, bu, k);
@@ -443,7 +443,7 @@ __device__ __forceinline__ void row_sweeps(WarpTile& S, int lane) {
     // the middle: each chain's next block row is the one the other chain just stored
     bd = S.B[(NB / 2) * BS + lane];
     bu = S.B[(NB / 2 - 1) * BS + lane];
-#pragma unroll 1
+#pragma unroll 3
     for (int k = NB / 2; k < NB - 1; k++) {
         const uint2 nd = S.B[(k + 1) * BS + lane], nu = S.B[(NB - 2 - k) * BS + lane];
         step(bd, bu, k);
@@ -470,7 +470,7 @@ __device__ __forceinline__ void col_sweeps(WarpTile& S, int lane) {
         S.B[lane * BS + il].x = __byte_perm(l0, l1, PACK_COLS);
     };
     uint2 br = S.B[lane * BS], bl = S.B[lane * BS + NB - 1];
-#pragma unroll 1
+#pragma unroll 3
     for (int k = 0; k < NB / 2 - 1; k++) {
         const uint2 nr = S.B[lane * BS + k + 1], nl = S.B[lane * BS + NB - 2 - k];
         step(br, bl, k);
@@ -480,7 +480,7 @@ __device__ __forceinline__ void col_sweeps(WarpTile& S, int lane) {
     step(br, bl, NB / 2 - 1);
     br = S.B[lane * BS + NB / 2];
     bl = S.B[lane * BS + NB / 2 - 1];
-#pragma unroll 1
+#pragma unroll 3
     for (int k = NB / 2; k < NB - 1; k++) {
         const uint2 nr = S.B[lane * BS + k + 1], nl = S.B[lane * BS + NB - 2 - k];
         step(br, bl, k);
